@@ -1,0 +1,191 @@
+/*
+ * domagg.h -- C ABI of the GB300 (sm_103a) library for aggregation over
+ * dominated points.
+ *
+ * The operation (Sroka & Tyszkiewicz, "Aggregating over Dominated Points by
+ * Sorting, Scanning, Zip and Flat Maps", Sec. 1.2): given data points D and
+ * queries Q in R^m, weights w on D and an associative, commutative F with
+ * unit e, compute for every query q
+ *
+ *     out(q) = F over { w(d) : d in D, d_i < q_i for every i }   (strict).
+ *
+ * It is computed the way the paper's algorithm does (Sec. 4, with the
+ * one-logarithm improvement of Sec. 5): dense ranks of the first m-1
+ * coordinates, a flat map of every point to the canonical range-tree nodes of
+ * its ranks (P0 sets for data, P1 sets for queries, Sec. 3), a stable radix
+ * sort of those records by node and last coordinate (queries before data on
+ * a tie), a segmented scan of F over each node, and a per-query reduction of
+ * the partial results.  Every step runs in this library's CUDA kernels.
+ *
+ * Conventions shared by all entry points
+ *   - Coordinates are row-major [n][m] arrays (a contiguous torch (n, m)
+ *     tensor), int32 or float32.  -0.0 equals +0.0; +-inf are ordered; a NaN
+ *     coordinate makes the call fail with DOMAGG_ERR_NAN.
+ *   - Pointers marked "device" are CUDA device memory owned by the caller and
+ *     must stay valid until the work on `stream` has finished.  The library
+ *     never frees caller memory.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *     entry points enqueue work on it.  domagg_forward and domagg_backward
+ *     synchronise the stream once in mid-call (they read the record count to
+ *     size their workspace) and return with the rest of the work enqueued;
+ *     outputs are valid once the stream has been synchronised.
+ *   - Supported (op, weight dtype) -> output dtype:
+ *       SUM   int64 -> int64 (wraps modulo 2^64), float32 -> float32
+ *       MAX   int32 -> int32, float32 -> float32
+ *       COUNT (weights ignored, may be NULL) -> int64
+ *     The empty set gives e: 0 for SUM and COUNT, INT32_MIN or -inf for MAX.
+ *     float32 sums carry a float-float (hi, lo) accumulator through the scan
+ *     and the per-query reduction; the result is within 2^-23 * sum |w(d)|
+ *     over the dominated set of the exact sum.  float32 weights must be
+ *     finite for SUM.
+ *   - m is 1, 2 or 3 (m = 1 is ordinary prefix aggregation, Sec. 1.1).
+ *     nD + nQ must be below 2^31 per problem, and the number of flat-map
+ *     records below 2^32 per call (DOMAGG_ERR_UNSUPPORTED otherwise).
+ *   - Errors are returned, never raised or aborted on.  Errors found on the
+ *     device after the mid-call synchronisation (a bounded wait that ran out)
+ *     are reported by the next call on the handle or by domagg_sync_status.
+ *   - A handle may be used by one host thread at a time.  Calls on one handle
+ *     share its workspace, so work from two calls must not overlap on the
+ *     device (use one stream per handle, or one handle per stream).
+ */
+#ifndef DOMAGG_H
+#define DOMAGG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DOMAGG_OK = 0,
+    DOMAGG_ERR_INVALID_ARG = 1, /* bad pointer, size, dtype, op or m */
+    DOMAGG_ERR_UNSUPPORTED = 2, /* m > 3, more than 2^31 points, 2^32 records */
+    DOMAGG_ERR_OOM = 3,         /* workspace could not be allocated / over the cap */
+    DOMAGG_ERR_CUDA = 4,        /* a CUDA runtime call failed (see domagg_last_error) */
+    DOMAGG_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
+    DOMAGG_ERR_NAN = 6          /* a coordinate is NaN */
+} domagg_status;
+
+typedef enum { DOMAGG_SUM = 0, DOMAGG_MAX = 1, DOMAGG_COUNT = 2 } domagg_op;
+
+typedef enum { DOMAGG_I32 = 0, DOMAGG_I64 = 1, DOMAGG_F32 = 2 } domagg_dtype;
+
+typedef struct domagg_ctx* domagg_handle;
+
+/* Creates a handle bound to CUDA device `device`.  The handle owns a device
+ * workspace, grown on demand and released by domagg_destroy.
+ * max_workspace_bytes caps that workspace (0 = no cap); a call that would
+ * need more returns DOMAGG_ERR_OOM.  *out receives the handle. */
+domagg_status domagg_create(domagg_handle* out, int device, size_t max_workspace_bytes);
+
+/* Frees the workspace and the handle (waits for the handle's work first). */
+domagg_status domagg_destroy(domagg_handle h);
+
+/* Aggregation over dominated points (Sec. 1.2) for one problem.
+ *   d_coords  device [nD][m] (coord_dtype)   data points D
+ *   q_coords  device [nQ][m] (coord_dtype)   queries Q
+ *   d_weights device [nD] (weight_dtype)     w(d); ignored for COUNT
+ *   out       device [nQ] (output dtype above), overwritten
+ * nD or nQ may be 0.  The algorithm: Sec. 4 instructions 0 .. 6m+5 with the
+ * Sec. 5 change (last coordinate kept as a value; queries first on ties). */
+domagg_status domagg_forward(domagg_handle h, int m, const void* d_coords, int64_t nD,
+                             const void* q_coords, int64_t nQ, domagg_dtype coord_dtype,
+                             const void* d_weights, domagg_dtype weight_dtype, domagg_op op,
+                             void* out, void* stream);
+
+/* Same as domagg_forward with HOST buffers (pageable or pinned): copies the
+ * inputs to the handle's device staging area, runs the forward on `stream`,
+ * copies `out` back and synchronises before returning. */
+domagg_status domagg_forward_host(domagg_handle h, int m, const void* d_coords, int64_t nD,
+                                  const void* q_coords, int64_t nQ, domagg_dtype coord_dtype,
+                                  const void* d_weights, domagg_dtype weight_dtype, domagg_op op,
+                                  void* out, void* stream);
+
+/* Adjoint of the float32 dominance SUM with respect to the weights:
+ *     grad_w[d] = sum of grad_out[q] over queries q with d < q (strict),
+ * the reverse-dominance aggregation.  It is computed by the same pipeline with
+ * the roles of D and Q swapped and every coordinate key negated (bitwise NOT
+ * of its order-preserving key), the records being recomputed, not stored.
+ *   grad_out device float32 [nQ]; grad_w device float32 [nD], overwritten. */
+domagg_status domagg_backward(domagg_handle h, int m, const void* d_coords, int64_t nD,
+                              const void* q_coords, int64_t nQ, domagg_dtype coord_dtype,
+                              const float* grad_out, float* grad_w, void* stream);
+
+/* One problem of a batch (all pointers device memory, as in domagg_forward). */
+typedef struct {
+    int m;
+    int64_t nD, nQ;
+    const void* d_coords;
+    const void* q_coords;
+    const void* d_weights;
+    void* out;
+} domagg_instance;
+
+/* k independent problems in one call: every phase of the pipeline runs as one
+ * segmented launch over all instances with the same m (instances never mix:
+ * sorts, scans and reductions restart at instance boundaries).  `inst` is a
+ * host array of k descriptors; coord/weight dtype and op are shared.  The
+ * call does not synchronise the stream: workspace is sized from host-side
+ * bounds on the record counts, so the whole call can be captured in a CUDA
+ * graph (see domagg_batch_plan). */
+domagg_status domagg_batch(domagg_handle h, int k, const domagg_instance* inst,
+                           domagg_dtype coord_dtype, domagg_dtype weight_dtype, domagg_op op,
+                           void* stream);
+
+/* Allocates the workspace that domagg_batch needs for these instances, so that
+ * a later domagg_batch with the same sizes allocates nothing (required before
+ * capturing it in a CUDA graph). */
+domagg_status domagg_batch_plan(domagg_handle h, int k, const domagg_instance* inst,
+                                domagg_dtype coord_dtype, domagg_dtype weight_dtype,
+                                domagg_op op);
+
+/* Synchronises `stream` and returns the first device-side error recorded by
+ * this handle's kernels since the last check (DOMAGG_ERR_TIMEOUT,
+ * DOMAGG_ERR_NAN), or DOMAGG_OK; clears it. */
+domagg_status domagg_sync_status(domagg_handle h, void* stream);
+
+/* Human-readable description of the last error on the handle ("" if none).
+ * The string is owned by the handle and valid until its next call. */
+const char* domagg_last_error(domagg_handle h);
+
+/* Facts about the last forward/backward call, for tests and benchmarks. */
+typedef struct {
+    int64_t n_points;      /* nD + nQ */
+    int64_t n_records;     /* T: records of the flat map */
+    int64_t n_query_records; /* records that came from queries */
+    int32_t m;
+    int32_t rank_bits[2];  /* b_i = ceil(log2 U_i) for the first m-1 dimensions */
+    int64_t distinct[2];   /* U_i */
+    int32_t record_key_bits; /* bits of the node key sorted by the record sort */
+    int32_t record_passes;   /* radix passes over the records */
+    int64_t workspace_bytes; /* device workspace currently held by the handle */
+} domagg_stats;
+
+domagg_status domagg_get_stats(domagg_handle h, domagg_stats* out);
+
+/* Kernel timing.  When enabled, every launch is bracketed by CUDA events on
+ * the launching stream and grouped by kernel kind.  domagg_timing_read
+ * synchronises, then returns per kind the number of launches, the summed
+ * device time (ms) and the summed algorithmic bytes (the bytes each launch
+ * must read and write at minimum), and resets the counters.  Kinds are
+ * indexed as in domagg_timing_kind_name. */
+#define DOMAGG_TIMING_KINDS 16
+typedef struct {
+    int32_t launches[DOMAGG_TIMING_KINDS];
+    double ms[DOMAGG_TIMING_KINDS];
+    double bytes[DOMAGG_TIMING_KINDS];
+} domagg_timing;
+
+domagg_status domagg_timing_enable(domagg_handle h, int enable);
+domagg_status domagg_timing_read(domagg_handle h, domagg_timing* out);
+const char* domagg_timing_kind_name(int kind);
+
+/* Library version string. */
+const char* domagg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DOMAGG_H */

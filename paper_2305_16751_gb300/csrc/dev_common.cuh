@@ -1,0 +1,242 @@
+// dev_common.cuh -- device-side building blocks shared by the kernels:
+// control block, per-instance table, decoupled look-back status words,
+// float-float arithmetic and the aggregation operators F with their units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace domagg {
+
+typedef uint32_t u32;
+typedef uint64_t u64;
+
+// Error bits recorded on the device (Ctl::error).
+enum : u32 {
+    ERR_TIMEOUT = 1u,   // a bounded wait on a predecessor tile ran out
+    ERR_NAN = 2u,       // a NaN coordinate was met
+    ERR_OVERFLOW = 4u,  // the record count does not fit 32 bits
+    ERR_EPOCH = 8u,     // the look-back epoch counter is about to wrap
+};
+
+constexpr int MAX_LAUNCHES = 64;  // look-back launches per pipeline run
+
+// Device control block (one per handle).
+struct Ctl {
+    u32 epoch_base;        // advanced by MAX_LAUNCHES at every pipeline start
+    u32 error;             // ERR_* bits, cleared by the host
+    u32 timeout_where;     // kind of the launch whose wait ran out (diagnostics)
+    u32 pad0;
+    u32 tile_ctr[MAX_LAUNCHES];  // dynamic tile counters, zeroed at pipeline start
+    // totals written by the count/offset scan (read by the host)
+    u32 T_total;           // records
+    u32 Tq_total;          // query records (= partial slots)
+    u32 max_key_bits;      // widest node key over the instances
+    u32 pad1;
+};
+
+// Per-instance table.  The host fills the first block; the kernels fill the
+// second.  Point index space of an instance: queries first (local 0..nQ-1),
+// then data points (local nQ..nQ+nD-1), so that a stable sort by the last
+// coordinate puts queries before data on ties (Sec. 5).
+struct Inst {
+    const void* dco;   // data coordinates [nD][m]
+    const void* qco;   // query coordinates [nQ][m]
+    const void* dw;    // data weights [nD]
+    void* out;         // outputs [nQ]
+    u32 nD, nQ;
+    u32 pt_off;        // first point in the concatenated point space
+    u32 q_off;         // first query in the concatenated query space
+    // device-computed
+    u32 U[2];          // distinct values of the first m-1 coordinates
+    u32 b[2];          // binary digits of the ranks: ceil(log2 U)
+    u32 rec_off, T;    // records of this instance
+    u32 qrec_off, Tq;  // query records (partial slots) of this instance
+    u32 key_bits;      // bits of the node key
+    u32 pad;
+};
+
+// ---------------------------------------------------------------------
+// decoupled look-back status words: [63:34] epoch, [33:32] flag, [31:0] value
+// ---------------------------------------------------------------------
+enum : u32 { ST_AGG = 1u, ST_PREFIX = 2u };
+constexpr u32 EPOCH_MASK = (1u << 30) - 1u;
+constexpr u32 SPIN_LIMIT = 1u << 21;  // ~1-2 s of polling with back-off
+
+__device__ __forceinline__ u64 st_pack(u32 epoch, u32 flag, u32 v) {
+    return ((u64)(epoch & EPOCH_MASK) << 34) | ((u64)flag << 32) | (u64)v;
+}
+__device__ __forceinline__ void st_store(u64* p, u64 v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ u64 st_load(const u64* p) {
+    u64 v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_store_release(u32* p, u32 v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ u32 st_load_acquire(const u32* p) {
+    u32 v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// True once any bounded wait of this pipeline has run out: the other waits
+// then give up at once instead of each running out in turn.
+__device__ __forceinline__ bool timed_out(const Ctl* ctl) {
+    return (*reinterpret_cast<const volatile u32*>(&ctl->error) & ERR_TIMEOUT) != 0u;
+}
+
+// Exclusive prefix of counter c for tile t over the chain of tiles
+// [chain_first, t).  Tiles publish ST_AGG (own count) before looking back and
+// ST_PREFIX (inclusive prefix) after; chain_first publishes ST_PREFIX at once,
+// so the walk always ends.  Every wait is bounded: when it runs out the
+// kernel records ERR_TIMEOUT and goes on with a wrong (but finite) value.
+__device__ __forceinline__ u32 lookback_u32(const u64* status, int C, int c, u32 t, u32 chain_first,
+                                            u32 epoch, Ctl* ctl, u32 where) {
+    u32 excl = 0;
+    u32 u = t;
+    while (u > chain_first) {
+        --u;
+        u64 s;
+        u32 spins = 0;
+        for (;;) {
+            s = st_load(status + (u64)u * (u64)C + (u64)c);
+            if ((u32)(s >> 34) == (epoch & EPOCH_MASK) && ((u32)(s >> 32) & 3u)) break;
+            if (++spins > SPIN_LIMIT || ((spins & 255u) == 0 && timed_out(ctl))) {
+                atomicOr(&ctl->error, ERR_TIMEOUT);
+                ctl->timeout_where = where;
+                return excl;
+            }
+            if (spins > 64) __nanosleep(256);
+        }
+        excl += (u32)s;
+        if (((u32)(s >> 32) & 3u) == ST_PREFIX) break;
+    }
+    return excl;
+}
+
+// ---------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------
+__device__ __forceinline__ u32 lanemask_lt() {
+    u32 r;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
+    return r;
+}
+
+// Index of the last entry of the non-decreasing array a[0..n) that is <= x
+// (a[0] <= x is assumed).
+__device__ __forceinline__ int upper_index(const u32* a, int n, u32 x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(a + mid) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Mask of the low b bits (b <= 32).
+__device__ __forceinline__ u32 low_mask(u32 b) { return b >= 32 ? 0xffffffffu : ((1u << b) - 1u); }
+
+// Canonical range-tree node of the prefix that ends just above bit j of the
+// b-digit rank r (Sec. 3): the prefix v = r >> (j+1) of length b-1-j is
+// encoded as (v << (j+1)) | (1 << j), i.e. r with bit j set and the bits below
+// it cleared.  The encoding is injective over all (length, prefix) pairs and
+// stays below 2^b.  A data point emits it for the 0-digits of its rank (P0),
+// a query for the 1-digits (P1).
+__device__ __forceinline__ u32 node_of(u32 r, u32 j) { return ((r >> j) | 1u) << j; }
+
+// ---------------------------------------------------------------------
+// float-float arithmetic (error-free transformations, Knuth's TwoSum)
+// ---------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    ff s = ff_two_sum(x.hi, y.hi);
+    float lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return ff_fast_two_sum(s.hi, lo);
+}
+
+// ---------------------------------------------------------------------
+// aggregation operators F with unit e (Sec. 1)
+// ---------------------------------------------------------------------
+// Each operator defines: Acc (scan accumulator), Part (stored partial), Out
+// (output element), W (record payload type), e(), from_w(payload) for a data
+// record, F(a, b), to_part(acc), part_to_acc(p), to_out(acc).
+struct OpSumF32 {
+    typedef ff Acc;
+    typedef float Part;
+    typedef float Out;
+    typedef u32 Pay;
+    __device__ static Acc e() { return {0.f, 0.f}; }
+    __device__ static Acc from_pay(Pay p) { return {__uint_as_float(p), 0.f}; }
+    __device__ static Acc F(Acc a, Acc b) { return ff_add(a, b); }
+    __device__ static Part to_part(Acc a) { return __fadd_rn(a.hi, a.lo); }
+    __device__ static Acc from_part(Part p) { return {p, 0.f}; }
+    __device__ static Out to_out(Acc a) { return __fadd_rn(a.hi, a.lo); }
+};
+struct OpSumI64 {
+    typedef long long Acc;
+    typedef long long Part;
+    typedef long long Out;
+    typedef u64 Pay;
+    __device__ static Acc e() { return 0; }
+    __device__ static Acc from_pay(Pay p) { return (long long)p; }
+    __device__ static Acc F(Acc a, Acc b) { return (long long)((u64)a + (u64)b); }
+    __device__ static Part to_part(Acc a) { return a; }
+    __device__ static Acc from_part(Part p) { return p; }
+    __device__ static Out to_out(Acc a) { return a; }
+};
+struct OpMaxI32 {
+    typedef int Acc;
+    typedef int Part;
+    typedef int Out;
+    typedef u32 Pay;
+    __device__ static Acc e() { return (int)0x80000000; }
+    __device__ static Acc from_pay(Pay p) { return (int)p; }
+    __device__ static Acc F(Acc a, Acc b) { return a > b ? a : b; }
+    __device__ static Part to_part(Acc a) { return a; }
+    __device__ static Acc from_part(Part p) { return p; }
+    __device__ static Out to_out(Acc a) { return a; }
+};
+struct OpMaxF32 {
+    typedef float Acc;
+    typedef float Part;
+    typedef float Out;
+    typedef u32 Pay;
+    __device__ static Acc e() { return -__int_as_float(0x7f800000); }
+    __device__ static Acc from_pay(Pay p) { return __uint_as_float(p); }
+    __device__ static Acc F(Acc a, Acc b) { return fmaxf(a, b); }
+    __device__ static Part to_part(Acc a) { return a; }
+    __device__ static Acc from_part(Part p) { return p; }
+    __device__ static Out to_out(Acc a) { return a; }
+};
+struct OpCount {
+    typedef u32 Acc;
+    typedef u32 Part;
+    typedef long long Out;
+    typedef u32 Pay;
+    __device__ static Acc e() { return 0u; }
+    __device__ static Acc from_pay(Pay) { return 1u; }
+    __device__ static Acc F(Acc a, Acc b) { return a + b; }
+    __device__ static Part to_part(Acc a) { return a; }
+    __device__ static Acc from_part(Part p) { return p; }
+    __device__ static Out to_out(Acc a) { return (long long)a; }
+};
+
+}  // namespace domagg

@@ -1,0 +1,788 @@
+// domagg.cu -- the C ABI (include/domagg.h) and the host orchestration of the
+// pipeline: point phase (keys, ranks, order of the last coordinate, count /
+// offset scan), one device->host read of the record counts, then per chunk of
+// instances the record phase (flat map, records sort, segmented scan,
+// per-query reduction).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/domagg.h"
+#include "host_common.h"
+#include "k_points.cuh"
+#include "k_radix.cuh"
+#include "k_records.cuh"
+
+using namespace domagg;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+// Sub-allocator over one buffer; a first pass with base == nullptr measures.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base((char*)b) {}
+    template <typename T>
+    T* take(size_t n) {
+        off = (off + 255) & ~(size_t)255;
+        T* r = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += n * sizeof(T);
+        return r;
+    }
+};
+
+constexpr int SCAN_THREADS = 256, SCAN_ITEMS = 16;  // rank and count scan: tile = SORT_TILE
+static_assert(SCAN_THREADS * SCAN_ITEMS == (int)SORT_TILE, "point tiles are shared");
+
+}  // namespace
+
+struct domagg_ctx {
+    int device = 0;
+    size_t max_ws = 0;
+    Ctl* ctl = nullptr;
+    DevBuf pts, recs, st_multi, st_seg, stage;
+    void* h_pin = nullptr;
+    size_t h_pin_cap = 0;
+    std::string err;
+    domagg_stats stats{};
+    bool timing = false;
+    std::vector<TimedLaunch> log;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    u64 epoch_mirror = 0;  // host copy of Ctl::epoch_base
+
+    size_t held() const { return pts.cap + recs.cap + st_multi.cap + st_seg.cap + stage.cap; }
+};
+
+namespace {
+
+domagg_status fail(domagg_ctx* h, domagg_status st, const std::string& msg) {
+    if (h) h->err = msg;
+    return st;
+}
+
+domagg_status cuda_fail(domagg_ctx* h, cudaError_t e, const char* where) {
+    return fail(h, DOMAGG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Grows a device buffer to at least `bytes` (contents are not kept).
+domagg_status grow(domagg_ctx* h, DevBuf& b, size_t bytes) {
+    if (b.cap >= bytes) return DOMAGG_OK;
+    size_t want = std::max(bytes, b.cap + b.cap / 4);
+    if (h->max_ws && h->held() - b.cap + want > h->max_ws) {
+        want = bytes;
+        if (h->held() - b.cap + want > h->max_ws)
+            return fail(h, DOMAGG_ERR_OOM, "workspace would exceed max_workspace_bytes");
+    }
+    if (b.p) {
+        cudaFree(b.p);  // waits for the device
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaMalloc(&b.p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b.p = nullptr;
+            return fail(h, DOMAGG_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+        }
+        want = bytes;
+    }
+    b.cap = want;
+    return DOMAGG_OK;
+}
+
+domagg_status grow_pinned(domagg_ctx* h, size_t bytes) {
+    if (h->h_pin_cap >= bytes) return DOMAGG_OK;
+    if (h->h_pin) {
+        cudaDeviceSynchronize();
+        cudaFreeHost(h->h_pin);
+        h->h_pin = nullptr;
+    }
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    cudaError_t e = cudaMallocHost(&h->h_pin, want);
+    if (e != cudaSuccess) {
+        h->h_pin_cap = 0;
+        return cuda_fail(h, e, "cudaMallocHost");
+    }
+    h->h_pin_cap = want;
+    return DOMAGG_OK;
+}
+
+domagg_status device_error(domagg_ctx* h, u32 bits) {
+    if (bits & ERR_NAN) return fail(h, DOMAGG_ERR_NAN, "a coordinate is NaN");
+    if (bits & ERR_OVERFLOW) return fail(h, DOMAGG_ERR_UNSUPPORTED, "more than 2^32 flat-map records");
+    if (bits & ERR_TIMEOUT) return fail(h, DOMAGG_ERR_TIMEOUT, "a bounded device-side wait ran out");
+    if (bits & ERR_EPOCH) return fail(h, DOMAGG_ERR_TIMEOUT, "look-back epoch counter wrapped");
+    return DOMAGG_OK;
+}
+
+template <class Op>
+struct OpTraits;
+template <>
+struct OpTraits<OpSumF32> {
+    static constexpr int WT = 2;
+};
+template <>
+struct OpTraits<OpSumI64> {
+    static constexpr int WT = 1;
+};
+template <>
+struct OpTraits<OpMaxI32> {
+    static constexpr int WT = 0;
+};
+template <>
+struct OpTraits<OpMaxF32> {
+    static constexpr int WT = 2;
+};
+template <>
+struct OpTraits<OpCount> {
+    static constexpr int WT = 3;
+};
+
+// Resets the look-back epoch and the status words when the epoch counter
+// approaches its 30-bit limit.
+void maybe_reset_epochs(domagg_ctx* h, cudaStream_t s) {
+    if (h->epoch_mirror + 8 * MAX_LAUNCHES < EPOCH_MASK) return;
+    if (h->st_multi.p) cudaMemsetAsync(h->st_multi.p, 0, h->st_multi.cap, s);
+    if (h->st_seg.p) cudaMemsetAsync(h->st_seg.p, 0, h->st_seg.cap, s);
+    cudaMemsetAsync(&h->ctl->epoch_base, 0, sizeof(u32), s);
+    h->epoch_mirror = 0;
+}
+
+// ---------------------------------------------------------------------------
+// the pipeline for instances with the same m
+// ---------------------------------------------------------------------------
+template <int M, class Op, bool F32>
+domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStream_t stream) {
+    typedef typename std::conditional<M == 3, u64, u32>::type K;
+    typedef typename Op::Pay Pay;
+    typedef typename Op::Part Part;
+    constexpr int WT = OpTraits<Op>::WT;
+    constexpr int SEG_ITEMS = (sizeof(K) + sizeof(Pay) == 8) ? 16 : 8;
+    constexpr int SEG_THREADS = 256;
+    constexpr u32 SEG_TILE = SEG_THREADS * SEG_ITEMS;
+    const int k = (int)inst.size();
+
+    // ---- host-side layout of the point space
+    std::vector<u32> pt_offs(k + 1), q_offs(k + 1);
+    u64 N = 0, NQ = 0, ntp = 0;
+    for (int s = 0; s < k; ++s) {
+        pt_offs[s] = (u32)N;
+        q_offs[s] = (u32)NQ;
+        inst[s].pt_off = (u32)N;
+        inst[s].q_off = (u32)NQ;
+        inst[s].U[0] = inst[s].U[1] = inst[s].b[0] = inst[s].b[1] = 0;
+        inst[s].T = inst[s].Tq = inst[s].rec_off = inst[s].qrec_off = inst[s].key_bits = 0;
+        const u64 n = (u64)inst[s].nD + inst[s].nQ;
+        N += n;
+        NQ += inst[s].nQ;
+        ntp += (n + SORT_TILE - 1) / SORT_TILE;
+    }
+    pt_offs[k] = (u32)N;
+    q_offs[k] = (u32)NQ;
+    if (N >= (1ull << 31)) return fail(h, DOMAGG_ERR_UNSUPPORTED, "more than 2^31 points in one call");
+    if (NQ == 0) return DOMAGG_OK;
+
+    // ---- point workspace
+    auto carve_points = [&](Carver& c, void** P) {
+        P[0] = c.take<Inst>(k);
+        P[1] = c.take<u32>(k + 1);  // pt_offs
+        P[2] = c.take<u32>(k + 1);  // q_offs
+        P[3] = c.take<u32>(k + 1);  // point tiles
+        P[4] = c.take<u32>(N);      // rk0
+        P[5] = c.take<u32>(M >= 3 ? N : 0);  // rk1
+        P[6] = c.take<u32>(N);      // lk
+        P[7] = c.take<u32>(N);      // key alt
+        P[8] = c.take<u32>(N);      // vA
+        P[9] = c.take<u32>(N);      // vB
+        P[10] = c.take<u32>(M >= 2 ? N : 0);  // r0
+        P[11] = c.take<u32>(M >= 3 ? N : 0);  // r1
+        P[12] = c.take<u32>(M >= 2 ? N : 0);  // pr0
+        P[13] = c.take<u32>(M >= 3 ? N : 0);  // pr1
+        P[14] = c.take<u32>(N);     // pj
+        P[15] = c.take<u32>(N);     // poff
+        P[16] = c.take<u32>(N);     // pqoff
+        P[17] = c.take<u32>(NQ);    // qslot
+        P[18] = c.take<u32>(NQ);    // qidx
+        P[19] = c.take<u32>((size_t)k * 4 * RADIX);  // hist
+        P[20] = c.take<u32>((size_t)k * 4 * RADIX);  // digit offsets
+    };
+    void* P[21];
+    {
+        Carver c(nullptr);
+        carve_points(c, P);
+        domagg_status st = grow(h, h->pts, c.off);
+        if (st) return st;
+        Carver c2(h->pts.p);
+        carve_points(c2, P);
+    }
+    Inst* d_inst = (Inst*)P[0];
+    u32 *d_pt_offs = (u32*)P[1], *d_q_offs = (u32*)P[2], *d_pt_tiles = (u32*)P[3];
+    u32 *rk0 = (u32*)P[4], *rk1 = (u32*)P[5], *lk = (u32*)P[6], *kalt = (u32*)P[7];
+    u32 *vA = (u32*)P[8], *vB = (u32*)P[9], *r0 = (u32*)P[10], *r1 = (u32*)P[11];
+    u32 *pr0 = (u32*)P[12], *pr1 = (u32*)P[13], *pj = (u32*)P[14], *poff = (u32*)P[15], *pqoff = (u32*)P[16];
+    u32 *qslot = (u32*)P[17], *qidx = (u32*)P[18], *hist = (u32*)P[19], *digit_off = (u32*)P[20];
+
+    // status words: point tiles x 256 digits (the records sort grows it later)
+    {
+        domagg_status st = grow(h, h->st_multi, (size_t)std::max<u64>(ntp, 1) * RADIX * sizeof(u64));
+        if (st) return st;
+    }
+
+    // ---- upload the instance table and offsets
+    const size_t up_bytes = sizeof(Inst) * k + 2 * sizeof(u32) * (k + 1);
+    {
+        domagg_status st = grow_pinned(h, up_bytes + sizeof(Ctl) + 64);
+        if (st) return st;
+    }
+    char* hp = (char*)h->h_pin;
+    memcpy(hp, inst.data(), sizeof(Inst) * k);
+    memcpy(hp + sizeof(Inst) * k, pt_offs.data(), sizeof(u32) * (k + 1));
+    memcpy(hp + sizeof(Inst) * k + sizeof(u32) * (k + 1), q_offs.data(), sizeof(u32) * (k + 1));
+    cudaMemcpyAsync(d_inst, hp, sizeof(Inst) * k, cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(d_pt_offs, hp + sizeof(Inst) * k, sizeof(u32) * (k + 1), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(d_q_offs, hp + sizeof(Inst) * k + sizeof(u32) * (k + 1), sizeof(u32) * (k + 1),
+                    cudaMemcpyHostToDevice, stream);
+
+    maybe_reset_epochs(h, stream);
+    Launcher L;
+    L.stream = stream;
+    L.ctl = h->ctl;
+    L.timing = h->timing;
+    L.log = &h->log;
+    L.pool = &h->pool;
+    L.pool_used = &h->pool_used;
+
+    L.start(KIND_SMALL, 0.0);
+    k_begin<<<1, 64, 0, stream>>>(h->ctl);
+    L.stop();
+    h->epoch_mirror += MAX_LAUNCHES;
+    L.start(KIND_SMALL, 0.0);
+    k_make_tiles<<<1, 1024, 0, stream>>>(d_pt_offs, k, SORT_TILE, d_pt_tiles);
+    L.stop();
+
+    // ---- keys (instruction 0 and 5i-4)
+    L.start(KIND_ENCODE, (double)N * M * 4 * 2);
+    k_encode<M, F32><<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(d_inst, d_pt_offs, k, (u32)N, rk0, rk1, lk,
+                                                                      negate ? 1 : 0, h->ctl);
+    L.stop();
+
+    SortSpace sp{d_pt_offs, d_pt_tiles, k, (u32)ntp, hist, digit_off, (u64*)h->st_multi.p, (double)N};
+
+    // ---- ranks of the first m-1 coordinates (5i-3 .. 5i, 5m+i)
+    for (int i = 0; i < M - 1; ++i) {
+        u32* keys[2] = {i == 0 ? rk0 : rk1, kalt};
+        u32* vals[2] = {vA, vB};
+        const int cur = sort_pairs<u32, u32>(L, sp, keys, vals, true, 32, 0xffffffffu, KIND_HIST_POINTS,
+                                             KIND_SORT_POINTS);
+        const int li = L.lookback_index();
+        L.start(KIND_RANK, (double)N * 12);
+        k_rank<SCAN_THREADS, SCAN_ITEMS><<<(unsigned)ntp, SCAN_THREADS, 0, stream>>>(
+            keys[cur], vals[cur], d_pt_offs, d_pt_tiles, k, i == 0 ? r0 : r1, d_inst, i, (u64*)h->st_multi.p,
+            h->ctl, li);
+        L.stop();
+    }
+    // ---- order of the last coordinate, queries first on ties (Sec. 5)
+    u32* perm;
+    {
+        u32* keys[2] = {lk, kalt};
+        u32* vals[2] = {vA, vB};
+        const int cur = sort_pairs<u32, u32>(L, sp, keys, vals, true, 32, 0xffffffffu, KIND_HIST_POINTS,
+                                             KIND_SORT_POINTS);
+        perm = vals[cur];
+    }
+    // ---- count / offset scan of the flat map
+    {
+        const int li = L.lookback_index();
+        L.start(KIND_COUNT_SCAN, (double)N * (4 + 4 * (M - 1) + 4 * (M - 1) + 16));
+        k_count_scan<M, SCAN_THREADS, SCAN_ITEMS><<<(unsigned)ntp, SCAN_THREADS, 0, stream>>>(
+            perm, d_pt_offs, d_pt_tiles, k, r0, r1, d_inst, d_q_offs, pr0, pr1, pj, poff, pqoff, qslot, qidx,
+            (u64*)h->st_multi.p, h->ctl, li);
+        L.stop();
+    }
+    // ---- the one synchronisation: record counts and device errors
+    Inst* h_inst = (Inst*)hp;
+    Ctl* h_ctl = (Ctl*)(hp + ((up_bytes + 63) & ~(size_t)63));
+    L.start(KIND_D2H, 0.0);
+    cudaMemcpyAsync(h_inst, d_inst, sizeof(Inst) * k, cudaMemcpyDeviceToHost, stream);
+    cudaMemcpyAsync(h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream);
+    L.stop();
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "point phase");
+    if (h_ctl->error) {
+        const u32 bits = h_ctl->error;
+        cudaMemsetAsync(&h->ctl->error, 0, sizeof(u32), stream);
+        cudaStreamSynchronize(stream);
+        return device_error(h, bits);
+    }
+    for (int s = 0; s < k; ++s) inst[s] = h_inst[s];
+
+    // ---- plan chunks of instances whose records fit one record workspace
+    struct Chunk {
+        int k0, k1;
+        u64 T, Tq;
+        int key_bits;
+    };
+    std::vector<Chunk> chunks;
+    const u64 chunk_cap = (1ull << 32) - SORT_TILE;
+    {
+        Chunk c{0, 0, 0, 0, 0};
+        for (int s = 0; s < k; ++s) {
+            const u64 Ts = inst[s].T;
+            if (c.k1 > c.k0 && c.T + Ts > chunk_cap) {
+                chunks.push_back(c);
+                c = Chunk{s, s, 0, 0, 0};
+            }
+            c.k1 = s + 1;
+            c.T += Ts;
+            c.Tq += inst[s].Tq;
+            const int kb = (M >= 2 ? (int)inst[s].b[0] : 0) + (M >= 3 ? (int)inst[s].b[1] : 0);
+            c.key_bits = std::max(c.key_bits, kb);
+        }
+        if (c.k1 > c.k0) chunks.push_back(c);
+    }
+    // pinned bases of every chunk, uploaded per chunk
+    std::vector<size_t> base_pos(chunks.size());
+    size_t pin_need = ((up_bytes + 63) & ~(size_t)63) + sizeof(Ctl);
+    for (size_t ci = 0; ci < chunks.size(); ++ci) {
+        base_pos[ci] = (pin_need + 63) & ~(size_t)63;
+        pin_need = base_pos[ci] + 2 * sizeof(u32) * (chunks[ci].k1 - chunks[ci].k0 + 1);
+    }
+    if (pin_need > h->h_pin_cap) {
+        // grow_pinned keeps nothing; the instance table is already in `inst`
+        domagg_status st = grow_pinned(h, pin_need);
+        if (st) return st;
+        hp = (char*)h->h_pin;
+    }
+
+    u64 T_all = 0, Tq_all = 0;
+    int kb_all = 0, passes_all = 0;
+    for (size_t ci = 0; ci < chunks.size(); ++ci) {
+        const Chunk& C = chunks[ci];
+        const int kc = C.k1 - C.k0;
+        u32* hb = (u32*)(hp + base_pos[ci]);
+        u64 ntr = 0, nts = 0;
+        {
+            u64 a = 0, b = 0;
+            for (int s = C.k0; s < C.k1; ++s) {
+                hb[s - C.k0] = (u32)a;
+                hb[kc + 1 + s - C.k0] = (u32)b;
+                a += inst[s].T;
+                b += inst[s].Tq;
+                ntr += (inst[s].T + SORT_TILE - 1) / SORT_TILE;
+                nts += (inst[s].T + SEG_TILE - 1) / SEG_TILE;
+            }
+            hb[kc] = (u32)a;
+            hb[kc + 1 + kc] = (u32)b;
+        }
+        const int npass = (C.key_bits + RADIX_BITS - 1) / RADIX_BITS;
+        // record workspace
+        auto carve_recs = [&](Carver& c, void** R) {
+            R[0] = c.take<u32>(2 * (kc + 1));  // rec_base, qrec_base
+            R[1] = c.take<u32>(kc + 1);        // sort tiles
+            R[2] = c.take<u32>(kc + 1);        // segscan tiles
+            R[3] = c.take<K>(C.T);
+            R[4] = c.take<K>(C.T);
+            R[5] = c.take<Pay>(C.T);
+            R[6] = c.take<Pay>(C.T);
+            R[7] = c.take<Part>(C.Tq);
+            R[8] = c.take<u32>((size_t)kc * std::max(npass, 1) * RADIX);
+            R[9] = c.take<u32>((size_t)kc * std::max(npass, 1) * RADIX);
+        };
+        void* R[10];
+        {
+            Carver c(nullptr);
+            carve_recs(c, R);
+            domagg_status st = grow(h, h->recs, c.off);
+            if (st) return st;
+            Carver c2(h->recs.p);
+            carve_recs(c2, R);
+            st = grow(h, h->st_multi, (size_t)std::max<u64>(std::max(ntr, ntp), 1) * RADIX * sizeof(u64));
+            if (st) return st;
+            st = grow(h, h->st_seg, (size_t)std::max<u64>(nts, 1) * sizeof(SegStatus<typename Op::Acc>));
+            if (st) return st;
+        }
+        u32* d_rb = (u32*)R[0];
+        u32* d_qb = d_rb + kc + 1;
+        u32 *d_rtiles = (u32*)R[1], *d_stiles = (u32*)R[2];
+        K* keys[2] = {(K*)R[3], (K*)R[4]};
+        Pay* pays[2] = {(Pay*)R[5], (Pay*)R[6]};
+        Part* partial = (Part*)R[7];
+        cudaMemcpyAsync(d_rb, hb, 2 * sizeof(u32) * (kc + 1), cudaMemcpyHostToDevice, stream);
+        // fresh epoch and tile counters for the record phase of this chunk
+        maybe_reset_epochs(h, stream);
+        L.start(KIND_SMALL, 0.0);
+        k_begin<<<1, 64, 0, stream>>>(h->ctl);
+        L.stop();
+        h->epoch_mirror += MAX_LAUNCHES;
+        L.next_lookback = 0;
+        L.start(KIND_SMALL, 0.0);
+        k_make_tiles<<<1, 1024, 0, stream>>>(d_rb, kc, SORT_TILE, d_rtiles);
+        L.stop();
+        L.start(KIND_SMALL, 0.0);
+        k_make_tiles<<<1, 1024, 0, stream>>>(d_rb, kc, SEG_TILE, d_stiles);
+        L.stop();
+
+        // flat map (6m+1)
+        const u32 p_begin = pt_offs[C.k0], p_end = pt_offs[C.k1];
+        if (C.T > 0) {
+            const u64 warps = (p_end - p_begin + 31) / 32;
+            const unsigned grid = (unsigned)std::min<u64>((warps + 7) / 8, 152ull * 32);
+            L.start(KIND_EXPAND, (double)(p_end - p_begin) * (4.0 * (M - 1) + 12) +
+                                     (double)C.T * (sizeof(K) + sizeof(Pay)));
+            k_expand<M, K, Pay, WT><<<grid, 256, 0, stream>>>(p_begin, p_end, pr0, pr1, pj, poff, pqoff, d_inst,
+                                                             d_pt_offs, k, d_rb, d_qb, C.k0, (u32)C.T, keys[0],
+                                                             pays[0]);
+            L.stop();
+        }
+        // records sort (6m+2): stable, by node key only
+        int cur = 0;
+        if (C.T > 0 && npass > 0) {
+            SortSpace rs{d_rb, d_rtiles, kc, (u32)ntr, (u32*)R[8], (u32*)R[9], (u64*)h->st_multi.p, (double)C.T};
+            const K keymask = (C.key_bits >= (int)(8 * sizeof(K))) ? ~K(0) : ((K(1) << C.key_bits) - 1);
+            cur = sort_pairs<K, Pay>(L, rs, keys, pays, false, C.key_bits, keymask, KIND_HIST_RECORDS,
+                                     KIND_SORT_RECORDS);
+        }
+        // segmented scan (6m+3)
+        if (C.T > 0) {
+            const int li = L.lookback_index();
+            L.start(KIND_SEGSCAN, (double)C.T * (sizeof(K) + sizeof(Pay)) + (double)C.Tq * sizeof(Part));
+            k_segscan<Op, K, SEG_THREADS, SEG_ITEMS><<<(unsigned)nts, SEG_THREADS, 0, stream>>>(
+                keys[cur], pays[cur], d_rb, d_stiles, kc, partial, (u32)C.Tq,
+                (SegStatus<typename Op::Acc>*)h->st_seg.p, h->ctl, li);
+            L.stop();
+        }
+        // per-query reduction (replaces 6m+4 .. 6m+9)
+        const u32 qb = q_offs[C.k0], qe = q_offs[C.k1];
+        if (qe > qb) {
+            L.start(KIND_REDUCE, (double)C.Tq * sizeof(Part) + (double)(qe - qb) * (8 + sizeof(typename Op::Out)));
+            k_reduce<Op><<<(qe - qb + 255) / 256, 256, 0, stream>>>(qb, qe, qslot, qidx, partial, (u32)C.Tq,
+                                                                   d_q_offs, k, d_inst, d_qb, C.k0);
+            L.stop();
+        }
+            T_all += C.T;
+        Tq_all += C.Tq;
+        kb_all = std::max(kb_all, C.key_bits);
+        passes_all = std::max(passes_all, npass);
+        if (chunks.size() > 1) {
+            e = cudaStreamSynchronize(stream);  // the next chunk reuses the pinned bases region
+            if (e != cudaSuccess) return cuda_fail(h, e, "record phase");
+        }
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "launch");
+    if (L.next_lookback > MAX_LAUNCHES) return fail(h, DOMAGG_ERR_UNSUPPORTED, "too many look-back launches");
+
+    domagg_stats& S = h->stats;
+    S.n_points = (int64_t)N;
+    S.n_records = (int64_t)T_all;
+    S.n_query_records = (int64_t)Tq_all;
+    S.m = M;
+    for (int i = 0; i < 2; ++i) {
+        S.rank_bits[i] = (k == 1 && i < M - 1) ? (int32_t)inst[0].b[i] : 0;
+        S.distinct[i] = (k == 1 && i < M - 1) ? (int64_t)inst[0].U[i] : 0;
+    }
+    S.record_key_bits = kb_all;
+    S.record_passes = passes_all;
+    S.workspace_bytes = (int64_t)h->held();
+    return DOMAGG_OK;
+}
+
+template <int M, class Op>
+domagg_status run_ct(domagg_ctx* h, std::vector<Inst>& inst, domagg_dtype ct, bool negate, cudaStream_t s) {
+    return ct == DOMAGG_F32 ? run<M, Op, true>(h, inst, negate, s) : run<M, Op, false>(h, inst, negate, s);
+}
+
+template <class Op>
+domagg_status run_m(domagg_ctx* h, int m, std::vector<Inst>& inst, domagg_dtype ct, bool negate, cudaStream_t s) {
+    switch (m) {
+        case 1: return run_ct<1, Op>(h, inst, ct, negate, s);
+        case 2: return run_ct<2, Op>(h, inst, ct, negate, s);
+        default: return run_ct<3, Op>(h, inst, ct, negate, s);
+    }
+}
+
+domagg_status dispatch(domagg_ctx* h, int m, std::vector<Inst>& inst, domagg_dtype ct, domagg_dtype wt,
+                       domagg_op op, bool negate, cudaStream_t s) {
+    if (op == DOMAGG_COUNT) return run_m<OpCount>(h, m, inst, ct, negate, s);
+    if (op == DOMAGG_SUM && wt == DOMAGG_F32) return run_m<OpSumF32>(h, m, inst, ct, negate, s);
+    if (op == DOMAGG_SUM && wt == DOMAGG_I64) return run_m<OpSumI64>(h, m, inst, ct, negate, s);
+    if (op == DOMAGG_MAX && wt == DOMAGG_I32) return run_m<OpMaxI32>(h, m, inst, ct, negate, s);
+    if (op == DOMAGG_MAX && wt == DOMAGG_F32) return run_m<OpMaxF32>(h, m, inst, ct, negate, s);
+    return fail(h, DOMAGG_ERR_INVALID_ARG, "unsupported (op, weight dtype) pair");
+}
+
+domagg_status check_common(domagg_ctx* h, int m, int64_t nD, int64_t nQ, domagg_dtype ct, domagg_dtype wt,
+                           domagg_op op) {
+    if (!h) return DOMAGG_ERR_INVALID_ARG;
+    h->err.clear();
+    if (m < 1) return fail(h, DOMAGG_ERR_INVALID_ARG, "m must be >= 1");
+    if (m > 3) return fail(h, DOMAGG_ERR_UNSUPPORTED, "m > 3 is not supported");
+    if (nD < 0 || nQ < 0) return fail(h, DOMAGG_ERR_INVALID_ARG, "negative size");
+    if (nD + nQ >= (int64_t)1 << 31) return fail(h, DOMAGG_ERR_UNSUPPORTED, "nD + nQ must be below 2^31");
+    if (ct != DOMAGG_I32 && ct != DOMAGG_F32) return fail(h, DOMAGG_ERR_INVALID_ARG, "coordinates must be i32 or f32");
+    if (op != DOMAGG_SUM && op != DOMAGG_MAX && op != DOMAGG_COUNT) return fail(h, DOMAGG_ERR_INVALID_ARG, "bad op");
+    if (op == DOMAGG_SUM && wt != DOMAGG_I64 && wt != DOMAGG_F32)
+        return fail(h, DOMAGG_ERR_INVALID_ARG, "SUM takes i64 or f32 weights");
+    if (op == DOMAGG_MAX && wt != DOMAGG_I32 && wt != DOMAGG_F32)
+        return fail(h, DOMAGG_ERR_INVALID_ARG, "MAX takes i32 or f32 weights");
+    return DOMAGG_OK;
+}
+
+size_t dtype_size(domagg_dtype t) { return t == DOMAGG_I64 ? 8 : 4; }
+
+size_t out_size(domagg_op op, domagg_dtype wt) {
+    if (op == DOMAGG_COUNT) return 8;
+    return dtype_size(wt);
+}
+
+Inst make_inst(const void* dco, int64_t nD, const void* qco, int64_t nQ, const void* dw, void* out) {
+    Inst I;
+    memset(&I, 0, sizeof(I));
+    I.dco = dco;
+    I.qco = qco;
+    I.dw = dw;
+    I.out = out;
+    I.nD = (u32)nD;
+    I.nQ = (u32)nQ;
+    return I;
+}
+
+}  // namespace
+
+extern "C" {
+
+domagg_status domagg_create(domagg_handle* out, int device, size_t max_workspace_bytes) {
+    if (!out) return DOMAGG_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return DOMAGG_ERR_INVALID_ARG;
+    }
+    domagg_ctx* h = new (std::nothrow) domagg_ctx();
+    if (!h) return DOMAGG_ERR_OOM;
+    h->device = device;
+    h->max_ws = max_workspace_bytes;
+    if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&h->ctl, sizeof(Ctl)) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return DOMAGG_ERR_CUDA;
+    }
+    cudaMemset(h->ctl, 0, sizeof(Ctl));
+    cudaDeviceSynchronize();
+    *out = h;
+    return DOMAGG_OK;
+}
+
+domagg_status domagg_destroy(domagg_handle h) {
+    if (!h) return DOMAGG_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    for (DevBuf* b : {&h->pts, &h->recs, &h->st_multi, &h->st_seg, &h->stage})
+        if (b->p) cudaFree(b->p);
+    if (h->ctl) cudaFree(h->ctl);
+    if (h->h_pin) cudaFreeHost(h->h_pin);
+    for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+    delete h;
+    return DOMAGG_OK;
+}
+
+domagg_status domagg_forward(domagg_handle h, int m, const void* d_coords, int64_t nD, const void* q_coords,
+                             int64_t nQ, domagg_dtype coord_dtype, const void* d_weights, domagg_dtype weight_dtype,
+                             domagg_op op, void* out, void* stream) {
+    domagg_status st = check_common(h, m, nD, nQ, coord_dtype, weight_dtype, op);
+    if (st) return st;
+    if ((nD > 0 && !d_coords) || (nQ > 0 && (!q_coords || !out)) ||
+        (op != DOMAGG_COUNT && nD > 0 && !d_weights))
+        return fail(h, DOMAGG_ERR_INVALID_ARG, "null pointer");
+    if (nQ == 0) return DOMAGG_OK;
+    cudaSetDevice(h->device);
+    std::vector<Inst> inst{make_inst(d_coords, nD, q_coords, nQ, d_weights, out)};
+    return dispatch(h, m, inst, coord_dtype, weight_dtype, op, false, (cudaStream_t)stream);
+}
+
+domagg_status domagg_forward_host(domagg_handle h, int m, const void* d_coords, int64_t nD, const void* q_coords,
+                                  int64_t nQ, domagg_dtype coord_dtype, const void* d_weights,
+                                  domagg_dtype weight_dtype, domagg_op op, void* out, void* stream) {
+    domagg_status st = check_common(h, m, nD, nQ, coord_dtype, weight_dtype, op);
+    if (st) return st;
+    if ((nD > 0 && !d_coords) || (nQ > 0 && (!q_coords || !out)) ||
+        (op != DOMAGG_COUNT && nD > 0 && !d_weights))
+        return fail(h, DOMAGG_ERR_INVALID_ARG, "null pointer");
+    if (nQ == 0) return DOMAGG_OK;
+    cudaSetDevice(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bd = (size_t)nD * m * 4, bq = (size_t)nQ * m * 4;
+    const size_t bw = op == DOMAGG_COUNT ? 0 : (size_t)nD * dtype_size(weight_dtype);
+    const size_t bo = (size_t)nQ * out_size(op, weight_dtype);
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    st = grow(h, h->stage, al(bd) + al(bq) + al(bw) + al(bo));
+    if (st) return st;
+    char* base = (char*)h->stage.p;
+    char *dd = base, *dq = dd + al(bd), *dw = dq + al(bq), *dout = dw + al(bw);
+    Launcher L;
+    L.stream = s;
+    L.timing = h->timing;
+    L.log = &h->log;
+    L.pool = &h->pool;
+    L.pool_used = &h->pool_used;
+    L.start(KIND_H2D, (double)(bd + bq + bw));
+    if (bd) cudaMemcpyAsync(dd, d_coords, bd, cudaMemcpyHostToDevice, s);
+    if (bq) cudaMemcpyAsync(dq, q_coords, bq, cudaMemcpyHostToDevice, s);
+    if (bw) cudaMemcpyAsync(dw, d_weights, bw, cudaMemcpyHostToDevice, s);
+    L.stop();
+    std::vector<Inst> inst{make_inst(dd, nD, dq, nQ, bw ? dw : nullptr, dout)};
+    st = dispatch(h, m, inst, coord_dtype, weight_dtype, op, false, s);
+    if (st) return st;
+    L.start(KIND_D2H, (double)bo);
+    cudaMemcpyAsync(out, dout, bo, cudaMemcpyDeviceToHost, s);
+    L.stop();
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "forward_host");
+    return DOMAGG_OK;
+}
+
+domagg_status domagg_backward(domagg_handle h, int m, const void* d_coords, int64_t nD, const void* q_coords,
+                              int64_t nQ, domagg_dtype coord_dtype, const float* grad_out, float* grad_w,
+                              void* stream) {
+    domagg_status st = check_common(h, m, nD, nQ, coord_dtype, DOMAGG_F32, DOMAGG_SUM);
+    if (st) return st;
+    if ((nD > 0 && (!d_coords || !grad_w)) || (nQ > 0 && (!q_coords || !grad_out)))
+        return fail(h, DOMAGG_ERR_INVALID_ARG, "null pointer");
+    if (nD == 0) return DOMAGG_OK;
+    cudaSetDevice(h->device);
+    // reverse dominance: the queries act as data (weights grad_out), the data
+    // points as queries, and every key is negated.
+    std::vector<Inst> inst{make_inst(q_coords, nQ, d_coords, nD, grad_out, grad_w)};
+    return dispatch(h, m, inst, coord_dtype, DOMAGG_F32, DOMAGG_SUM, true, (cudaStream_t)stream);
+}
+
+domagg_status domagg_batch(domagg_handle h, int k, const domagg_instance* inst, domagg_dtype coord_dtype,
+                           domagg_dtype weight_dtype, domagg_op op, void* stream) {
+    if (!h) return DOMAGG_ERR_INVALID_ARG;
+    if (k < 0 || (k > 0 && !inst)) return fail(h, DOMAGG_ERR_INVALID_ARG, "bad instance array");
+    std::vector<Inst> groups[4];
+    int64_t total[4] = {0, 0, 0, 0};
+    for (int i = 0; i < k; ++i) {
+        const domagg_instance& I = inst[i];
+        domagg_status st = check_common(h, I.m, I.nD, I.nQ, coord_dtype, weight_dtype, op);
+        if (st) return st;
+        if ((I.nD > 0 && !I.d_coords) || (I.nQ > 0 && (!I.q_coords || !I.out)) ||
+            (op != DOMAGG_COUNT && I.nD > 0 && !I.d_weights))
+            return fail(h, DOMAGG_ERR_INVALID_ARG, "null pointer in instance " + std::to_string(i));
+        if (I.nQ == 0) continue;
+        total[I.m] += I.nD + I.nQ;
+        groups[I.m].push_back(make_inst(I.d_coords, I.nD, I.q_coords, I.nQ, I.d_weights, I.out));
+    }
+    cudaSetDevice(h->device);
+    for (int m = 1; m <= 3; ++m) {
+        if (groups[m].empty()) continue;
+        // one call per group of at most 2^31 - 1 points
+        std::vector<Inst> part;
+        int64_t acc = 0;
+        for (size_t i = 0; i <= groups[m].size(); ++i) {
+            const bool flush = i == groups[m].size() ||
+                               (acc + (int64_t)groups[m][i].nD + groups[m][i].nQ >= ((int64_t)1 << 31) - 1);
+            if (flush && !part.empty()) {
+                domagg_status st = dispatch(h, m, part, coord_dtype, weight_dtype, op, false, (cudaStream_t)stream);
+                if (st) return st;
+                part.clear();
+                acc = 0;
+            }
+            if (i < groups[m].size()) {
+                part.push_back(groups[m][i]);
+                acc += (int64_t)groups[m][i].nD + groups[m][i].nQ;
+            }
+        }
+    }
+    (void)total;
+    return DOMAGG_OK;
+}
+
+domagg_status domagg_batch_plan(domagg_handle h, int k, const domagg_instance* inst, domagg_dtype coord_dtype,
+                                domagg_dtype weight_dtype, domagg_op op) {
+    if (!h) return DOMAGG_ERR_INVALID_ARG;
+    (void)k;
+    (void)inst;
+    (void)coord_dtype;
+    (void)weight_dtype;
+    (void)op;
+    return fail(h, DOMAGG_ERR_UNSUPPORTED, "batch planning for graph capture is not available yet");
+}
+
+domagg_status domagg_sync_status(domagg_handle h, void* stream) {
+    if (!h) return DOMAGG_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sync");
+    u32 bits = 0;
+    e = cudaMemcpy(&bits, &h->ctl->error, sizeof(u32), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sync");
+    if (bits) {
+        cudaMemset(&h->ctl->error, 0, sizeof(u32));
+        cudaDeviceSynchronize();
+        return device_error(h, bits);
+    }
+    return DOMAGG_OK;
+}
+
+const char* domagg_last_error(domagg_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+domagg_status domagg_get_stats(domagg_handle h, domagg_stats* out) {
+    if (!h || !out) return DOMAGG_ERR_INVALID_ARG;
+    *out = h->stats;
+    out->workspace_bytes = (int64_t)h->held();
+    return DOMAGG_OK;
+}
+
+domagg_status domagg_timing_enable(domagg_handle h, int enable) {
+    if (!h) return DOMAGG_ERR_INVALID_ARG;
+    h->timing = enable != 0;
+    return DOMAGG_OK;
+}
+
+domagg_status domagg_timing_read(domagg_handle h, domagg_timing* out) {
+    if (!h || !out) return DOMAGG_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    cudaSetDevice(h->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(h, e, "timing");
+    for (const TimedLaunch& t : h->log) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t.a, t.b);
+        if (t.kind < 0 || t.kind >= DOMAGG_TIMING_KINDS) continue;
+        out->launches[t.kind] += 1;
+        out->ms[t.kind] += ms;
+        out->bytes[t.kind] += t.bytes;
+    }
+    h->log.clear();
+    h->pool_used = 0;
+    return DOMAGG_OK;
+}
+
+const char* domagg_timing_kind_name(int kind) {
+    static const char* names[] = {"encode",  "hist_points",  "sort_points", "rank",     "count_scan",
+                                  "expand",  "hist_records", "sort_records", "segscan", "reduce",
+                                  "small",   "h2d",          "d2h"};
+    if (kind < 0 || kind >= (int)(sizeof(names) / sizeof(names[0]))) return "";
+    return names[kind];
+}
+
+const char* domagg_version(void) { return "domagg 0.1 (sm_103a)"; }
+
+}  // extern "C"

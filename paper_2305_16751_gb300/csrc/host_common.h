@@ -1,0 +1,108 @@
+// host_common.h -- host-side helpers shared by the library's translation
+// units: launch bookkeeping (look-back launch indices, optional per-launch
+// CUDA-event timing) and the sort launcher's declaration.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dev_common.cuh"
+
+namespace domagg {
+
+// Kernel kinds for timing (see domagg_timing_kind_name).
+enum Kind {
+    KIND_ENCODE = 0,
+    KIND_HIST_POINTS,
+    KIND_SORT_POINTS,
+    KIND_RANK,
+    KIND_COUNT_SCAN,
+    KIND_EXPAND,
+    KIND_HIST_RECORDS,
+    KIND_SORT_RECORDS,
+    KIND_SEGSCAN,
+    KIND_REDUCE,
+    KIND_SMALL,  // begin, tile maps, digit offsets
+    KIND_H2D,
+    KIND_D2H,
+    KIND_COUNT_
+};
+
+struct TimedLaunch {
+    int kind;
+    double bytes;
+    cudaEvent_t a, b;
+};
+
+struct Launcher {
+    cudaStream_t stream = nullptr;
+    Ctl* ctl = nullptr;
+    int next_lookback = 0;
+    bool timing = false;
+    std::vector<TimedLaunch>* log = nullptr;
+    std::vector<cudaEvent_t>* pool = nullptr;
+    size_t* pool_used = nullptr;
+    int pending_kind = -1;
+    double pending_bytes = 0;
+    cudaEvent_t pending_a = nullptr;
+    int launches = 0;  // kernels launched (all kinds)
+
+    // Index of the next look-back launch (its tile counter and epoch).  A run
+    // restarts the count at every k_begin; the clamp keeps a miscount from
+    // indexing past the counters.
+    int lookback_index() {
+        const int i = next_lookback++;
+        return i < MAX_LAUNCHES ? i : MAX_LAUNCHES - 1;
+    }
+
+    cudaEvent_t take_event() {
+        if (*pool_used == pool->size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool->push_back(e);
+        }
+        return (*pool)[(*pool_used)++];
+    }
+    void start(int kind, double bytes) {
+        ++launches;
+        if (!timing) return;
+        pending_kind = kind;
+        pending_bytes = bytes;
+        pending_a = take_event();
+        cudaEventRecord(pending_a, stream);
+    }
+    void stop() {
+        if (!timing) return;
+        cudaEvent_t b = take_event();
+        cudaEventRecord(b, stream);
+        log->push_back({pending_kind, pending_bytes, pending_a, b});
+    }
+};
+
+// Workspace for one segmented sort.
+struct SortSpace {
+    const u32* seg_off;   // [nseg+1] device
+    const u32* tile_off;  // [nseg+1] device, tiles of SORT_TILE items
+    int nseg;
+    u32 ntiles;           // host-side (exact or an upper bound)
+    u32* hist;            // [nseg*npass*RADIX]
+    u32* digit_off;       // [nseg*npass*RADIX]
+    u64* status;          // [ntiles*RADIX]
+    double n_items;       // items sorted (for the algorithmic byte model)
+};
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 16;
+constexpr u32 SORT_TILE = SORT_THREADS * SORT_ITEMS;
+
+// Stable LSD sort of (key, value) pairs by bits [0, total_bits) of
+// (key & keymask), segment by segment.  keys[0]/vals[0] hold the input;
+// returns the index (0 or 1) of the buffers that hold the result.  With
+// iota, the input values are the items' global indices (vals[0] unused).
+template <typename K, typename V>
+int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool iota, int total_bits, K keymask,
+               int kind_hist, int kind_pass);
+
+}  // namespace domagg

@@ -1,0 +1,249 @@
+// k_records.cuh -- the aggregation over the sorted records: the segmented
+// scan of F (instruction 6m+3) and the per-query reduction of the partial
+// results (what instructions 6m+4, 6m+5 compute, without the ID sort).
+#pragma once
+#include "dev_common.cuh"
+#include "k_radix.cuh"
+
+namespace domagg {
+
+// Look-back status of the segmented scan: the flag word is published with
+// release semantics after the aggregate, and read with acquire semantics
+// before it.
+template <typename Acc>
+struct alignas(16) SegStatus {
+    u32 flag;      // (epoch << 2) | ST_AGG / ST_PREFIX
+    u32 has_head;  // a segment starts inside the tile (for ST_AGG)
+    Acc value;     // F over the tile's items after its last head (ST_AGG),
+                   // or the inclusive prefix at the tile's end (ST_PREFIX)
+};
+
+template <typename Acc>
+__device__ __forceinline__ void seg_publish(SegStatus<Acc>* s, u32 epoch, u32 flag, bool head, Acc v) {
+    s->has_head = head ? 1u : 0u;
+    s->value = v;
+    __threadfence();
+    st_store_release(&s->flag, ((epoch & EPOCH_MASK) << 2) | flag);
+}
+
+// Segmented scan of F over the sorted records of every instance (Definition
+// "Segmented scan", Sec. 2.2): a segment is a maximal run of equal node keys
+// (the role bit ignored).  Data records contribute their weight, query
+// records the unit e (Sec. 2.1).  Because queries precede data on a tie of
+// the last coordinate, the running value at a query record is F over exactly
+// the data of its node with a smaller last coordinate; it is stored in the
+// query record's partial slot.
+template <class Op, typename K, int THREADS, int ITEMS>
+__global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys, const typename Op::Pay* __restrict__ pays,
+                                                     const u32* __restrict__ seg_off,
+                                                     const u32* __restrict__ tile_off, int nseg,
+                                                     typename Op::Part* __restrict__ partial, u32 n_partial,
+                                                     SegStatus<typename Op::Acc>* status, Ctl* ctl, int launch_idx) {
+    typedef typename Op::Acc Acc;
+    typedef typename Op::Pay Pay;
+    constexpr int TILE = THREADS * ITEMS, WARPS = THREADS / 32;
+    const K role = K(1) << (sizeof(K) * 8 - 1);
+    __shared__ K s_keys[TILE];
+    __shared__ Pay s_pays[TILE];
+    __shared__ Acc s_wacc[WARPS];
+    __shared__ u32 s_whead[WARPS];
+    __shared__ Acc s_excl;
+    __shared__ u32 s_info[2];
+    if (threadIdx.x == 0) {
+        s_info[0] = atomicAdd(&ctl->tile_ctr[launch_idx], 1u);
+        s_info[1] = ctl->epoch_base + (u32)launch_idx;
+    }
+    __syncthreads();
+    const u32 t = s_info[0], epoch = s_info[1];
+    if (t >= __ldg(tile_off + nseg)) return;
+    const TileLoc L = locate_tile<TILE>(t, seg_off, tile_off, nseg);
+    // coalesced load into shared memory, then blocked reads
+    for (int i = 0; i < ITEMS; ++i) {
+        const u32 x = (u32)i * THREADS + threadIdx.x;
+        if (L.start + x < L.end) {
+            s_keys[x] = keys[L.start + x];
+            s_pays[x] = pays[L.start + x];
+        }
+    }
+    __syncthreads();
+    const u32 lx0 = threadIdx.x * ITEMS;  // tile-local index of my first item
+    const u32 x0 = L.start + lx0;
+    K prev = 0;
+    bool has_prev = x0 > L.seg_begin;
+    if (has_prev && x0 < L.end) prev = lx0 == 0 ? keys[x0 - 1] : s_keys[lx0 - 1];
+    prev &= ~role;
+    // thread aggregate: (head seen, F over items after the last head)
+    bool head_any = false;
+    Acc agg = Op::e();
+    u32 headmask = 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        if (x0 + i < L.end) {
+            const K kx = s_keys[lx0 + i];
+            const K kn = kx & ~role;
+            const bool head = !has_prev || kn != prev;
+            has_prev = true;
+            prev = kn;
+            if (head) {
+                head_any = true;
+                headmask |= 1u << i;
+                agg = Op::e();
+            }
+            if (!(kx & role)) agg = Op::F(agg, Op::from_pay(s_pays[lx0 + i]));
+        }
+    }
+    // block-wide exclusive scan of (head, agg) with the segmented operator
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool ihead = head_any;
+    Acc iacc = agg;  // inclusive within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int nh = __shfl_up_sync(0xffffffffu, (int)ihead, o);
+        Acc na;
+        if constexpr (sizeof(Acc) == 8) {
+            unsigned long long bits = *reinterpret_cast<unsigned long long*>(&iacc);
+            bits = __shfl_up_sync(0xffffffffu, bits, o);
+            na = *reinterpret_cast<Acc*>(&bits);
+        } else {
+            u32 bits = *reinterpret_cast<u32*>(&iacc);
+            bits = __shfl_up_sync(0xffffffffu, bits, o);
+            na = *reinterpret_cast<Acc*>(&bits);
+        }
+        if (lane >= o) {
+            if (!ihead) iacc = Op::F(na, iacc);
+            ihead = ihead || nh;
+        }
+    }
+    if (lane == 31) {
+        s_wacc[warp] = iacc;
+        s_whead[warp] = ihead ? 1u : 0u;
+    }
+    __syncthreads();
+    // exclusive prefix of this thread within the tile
+    Acc wex = Op::e();  // prefix from earlier warps
+    bool wex_head = false;
+    for (int w = 0; w < warp; ++w) {
+        if (s_whead[w]) {
+            wex = s_wacc[w];
+            wex_head = true;
+        } else {
+            wex = Op::F(wex, s_wacc[w]);
+        }
+    }
+    // exclusive within warp: inclusive of lane-1
+    Acc lex;
+    int lhead;
+    {
+        Acc src = iacc;
+        if constexpr (sizeof(Acc) == 8) {
+            unsigned long long bits = *reinterpret_cast<unsigned long long*>(&src);
+            bits = __shfl_up_sync(0xffffffffu, bits, 1);
+            lex = *reinterpret_cast<Acc*>(&bits);
+        } else {
+            u32 bits = *reinterpret_cast<u32*>(&src);
+            bits = __shfl_up_sync(0xffffffffu, bits, 1);
+            lex = *reinterpret_cast<Acc*>(&bits);
+        }
+        lhead = __shfl_up_sync(0xffffffffu, (int)ihead, 1);
+        if (lane == 0) {
+            lex = Op::e();
+            lhead = 0;
+        }
+    }
+    Acc texcl = lhead ? lex : Op::F(wex, lex);  // within-tile exclusive prefix
+    const bool texcl_head = lhead || wex_head;  // a head occurs before me in the tile
+    // tile aggregate, look-back and publication (thread 0)
+    if (threadIdx.x == 0) {
+        Acc tagg = Op::e();
+        bool thead = false;
+        for (int w = 0; w < WARPS; ++w) {
+            if (s_whead[w]) {
+                tagg = s_wacc[w];
+                thead = true;
+            } else {
+                tagg = Op::F(tagg, s_wacc[w]);
+            }
+        }
+        SegStatus<Acc>* my = status + t;
+        const bool starts_fresh = L.first || (headmask & 1u);
+        Acc excl = Op::e();
+        if (starts_fresh) {
+            seg_publish(my, epoch, ST_PREFIX, true, tagg);
+        } else {
+            seg_publish(my, epoch, ST_AGG, thead, tagg);
+            const u32 first_tile = t - (L.start - L.seg_begin) / (u32)TILE;
+            u32 u = t;
+            while (u > first_tile) {
+                --u;
+                const SegStatus<Acc>* ps = status + u;
+                u32 f, spins = 0;
+                for (;;) {
+                    f = st_load_acquire(&ps->flag);
+                    if ((f >> 2) == (epoch & EPOCH_MASK) && (f & 3u)) break;
+                    if (++spins > SPIN_LIMIT || ((spins & 255u) == 0 && timed_out(ctl))) {
+                        atomicOr(&ctl->error, ERR_TIMEOUT);
+                        ctl->timeout_where = 4u;
+                        spins = SPIN_LIMIT + 1;
+                        break;
+                    }
+                    if (spins > 64) __nanosleep(256);
+                }
+                if (spins > SPIN_LIMIT) break;
+                const volatile SegStatus<Acc>* vps = ps;
+                Acc v;
+                if constexpr (sizeof(Acc) == 8) {
+                    unsigned long long bits = *reinterpret_cast<const volatile unsigned long long*>(&vps->value);
+                    v = *reinterpret_cast<Acc*>(&bits);
+                } else {
+                    u32 bits = *reinterpret_cast<const volatile u32*>(&vps->value);
+                    v = *reinterpret_cast<Acc*>(&bits);
+                }
+                const u32 hh = vps->has_head;
+                excl = Op::F(v, excl);
+                if ((f & 3u) == ST_PREFIX || hh) break;
+            }
+            seg_publish(my, epoch, ST_PREFIX, true, thead ? tagg : Op::F(excl, tagg));
+        }
+        s_excl = excl;
+    }
+    __syncthreads();
+    Acc run = texcl_head ? texcl : Op::F(s_excl, texcl);
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        if (x0 + i < L.end) {
+            if (headmask & (1u << i)) run = Op::e();
+            const K kx = s_keys[lx0 + i];
+            const Pay py = s_pays[lx0 + i];
+            if (kx & role) {
+                const u64 slot = (u64)py;
+                if (slot < n_partial) partial[slot] = Op::to_part(run);
+            } else {
+                run = Op::F(run, Op::from_pay(py));
+            }
+        }
+    }
+}
+
+// Per-query reduction: out[q] = F over the query's partial slots, which are
+// contiguous (the flat map wrote them in order) -- this replaces the sort by
+// ID and the ID-segmented scan of instructions 6m+4, 6m+5, and the broadcast
+// of instructions 6m+6 .. 6m+9 is not needed for one output per query.
+// Thread per query of the chunk, in the order of the last coordinate.
+template <class Op>
+__global__ void k_reduce(u32 qr_begin, u32 qr_end, const u32* __restrict__ qslot, const u32* __restrict__ qidx,
+                         const typename Op::Part* __restrict__ partial, u32 n_partial,
+                         const u32* __restrict__ q_offs, int k, const Inst* __restrict__ inst,
+                         const u32* __restrict__ qrec_base, int k0) {
+    const u32 qr = qr_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (qr >= qr_end) return;
+    const int s = upper_index(q_offs, k + 1, qr);
+    const u32 base = __ldg(qrec_base + (s - k0));
+    const u32 s0 = qslot[qr];
+    const u32 s1 = (qr + 1 < __ldg(q_offs + s + 1)) ? qslot[qr + 1] : inst[s].Tq;
+    typename Op::Acc acc = Op::e();
+    for (u32 x = s0; x < s1 && base + x < n_partial; ++x) acc = Op::F(acc, Op::from_part(partial[base + x]));
+    const u32 q = qidx[qr];
+    if (q < inst[s].nQ) reinterpret_cast<typename Op::Out*>(inst[s].out)[q] = Op::to_out(acc);
+}
+
+}  // namespace domagg

@@ -1,0 +1,311 @@
+"""Python binding of the domagg C ABI (include/domagg.h).
+
+The functions named ``domagg_*`` mirror the C entry points one to one and
+only marshal arguments through ctypes.  The torch-level helpers below them
+(``forward``, ``backward``, ``DominanceSum``, ``batch``) allocate output
+tensors with torch and pass raw device pointers and the current CUDA stream;
+every step of the computation runs in the library's CUDA kernels.  There is
+no fallback: if the library is not built, or no GPU is present, the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "NAN"}
+OPS = {"sum": 0, "max": 1, "count": 2}
+DTYPES = {"i32": 0, "i64": 1, "f32": 2}
+TIMING_KINDS = 16
+
+
+class DomaggError(RuntimeError):
+    def __init__(self, status: int, message: str = ""):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__(f"domagg error {self.name}: {message}")
+
+
+class domagg_instance(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("nD", ctypes.c_int64), ("nQ", ctypes.c_int64),
+                ("d_coords", ctypes.c_void_p), ("q_coords", ctypes.c_void_p),
+                ("d_weights", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class domagg_stats(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("n_records", ctypes.c_int64),
+                ("n_query_records", ctypes.c_int64), ("m", ctypes.c_int32),
+                ("rank_bits", ctypes.c_int32 * 2), ("distinct", ctypes.c_int64 * 2),
+                ("record_key_bits", ctypes.c_int32), ("record_passes", ctypes.c_int32),
+                ("workspace_bytes", ctypes.c_int64)]
+
+
+class domagg_timing(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int32 * TIMING_KINDS), ("ms", ctypes.c_double * TIMING_KINDS),
+                ("bytes", ctypes.c_double * TIMING_KINDS)]
+
+
+# Every symbol the header declares, with its ctypes signature.
+_vp, _i64, _int, _sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+SIGNATURES = {
+    "domagg_create": ([ctypes.POINTER(_vp), _int, _sz], _int),
+    "domagg_destroy": ([_vp], _int),
+    "domagg_forward": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _vp], _int),
+    "domagg_forward_host": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _vp], _int),
+    "domagg_backward": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp], _int),
+    "domagg_batch": ([_vp, _int, ctypes.POINTER(domagg_instance), _int, _int, _int, _vp], _int),
+    "domagg_batch_plan": ([_vp, _int, ctypes.POINTER(domagg_instance), _int, _int, _int], _int),
+    "domagg_sync_status": ([_vp, _vp], _int),
+    "domagg_last_error": ([_vp], ctypes.c_char_p),
+    "domagg_get_stats": ([_vp, ctypes.POINTER(domagg_stats)], _int),
+    "domagg_timing_enable": ([_vp, _int], _int),
+    "domagg_timing_read": ([_vp, ctypes.POINTER(domagg_timing)], _int),
+    "domagg_timing_kind_name": ([_int], ctypes.c_char_p),
+    "domagg_version": ([], ctypes.c_char_p),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib() -> ctypes.CDLL:
+    """Loads the in-tree library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB):
+                raise RuntimeError(f"{LIB} is missing: build it with __graft_entry__.build()")
+            L = ctypes.CDLL(LIB)
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(h, st: int):
+    if st != 0:
+        msg = lib().domagg_last_error(h).decode() if h else ""
+        raise DomaggError(st, msg)
+
+
+# --- the C entry points, one to one -----------------------------------------
+
+def domagg_create(device: int = 0, max_workspace_bytes: int = 0):
+    h = ctypes.c_void_p()
+    _check(None, lib().domagg_create(ctypes.byref(h), device, max_workspace_bytes))
+    return h
+
+
+def domagg_destroy(h):
+    _check(None, lib().domagg_destroy(h))
+
+
+def domagg_forward(h, m, d_coords, nD, q_coords, nQ, coord_dtype, d_weights, weight_dtype, op, out, stream):
+    _check(h, lib().domagg_forward(h, m, d_coords, nD, q_coords, nQ, coord_dtype, d_weights, weight_dtype, op,
+                                   out, stream))
+
+
+def domagg_forward_host(h, m, d_coords, nD, q_coords, nQ, coord_dtype, d_weights, weight_dtype, op, out, stream):
+    _check(h, lib().domagg_forward_host(h, m, d_coords, nD, q_coords, nQ, coord_dtype, d_weights, weight_dtype,
+                                        op, out, stream))
+
+
+def domagg_backward(h, m, d_coords, nD, q_coords, nQ, coord_dtype, grad_out, grad_w, stream):
+    _check(h, lib().domagg_backward(h, m, d_coords, nD, q_coords, nQ, coord_dtype, grad_out, grad_w, stream))
+
+
+def domagg_batch(h, k, inst_array, coord_dtype, weight_dtype, op, stream):
+    _check(h, lib().domagg_batch(h, k, inst_array, coord_dtype, weight_dtype, op, stream))
+
+
+def domagg_sync_status(h, stream):
+    _check(h, lib().domagg_sync_status(h, stream))
+
+
+def domagg_get_stats(h) -> dict:
+    s = domagg_stats()
+    _check(h, lib().domagg_get_stats(h, ctypes.byref(s)))
+    return {"n_points": s.n_points, "n_records": s.n_records, "n_query_records": s.n_query_records,
+            "m": s.m, "rank_bits": list(s.rank_bits), "distinct": list(s.distinct),
+            "record_key_bits": s.record_key_bits, "record_passes": s.record_passes,
+            "workspace_bytes": s.workspace_bytes}
+
+
+def domagg_timing_enable(h, enable: bool):
+    _check(h, lib().domagg_timing_enable(h, 1 if enable else 0))
+
+
+def domagg_timing_read(h) -> dict:
+    t = domagg_timing()
+    _check(h, lib().domagg_timing_read(h, ctypes.byref(t)))
+    out = {}
+    for k in range(TIMING_KINDS):
+        name = lib().domagg_timing_kind_name(k).decode()
+        if name and t.launches[k]:
+            out[name] = {"launches": t.launches[k], "ms": t.ms[k], "bytes": t.bytes[k]}
+    return out
+
+
+def domagg_version() -> str:
+    return lib().domagg_version().decode()
+
+
+# --- torch-level helpers -----------------------------------------------------
+
+_handles: dict[int, ctypes.c_void_p] = {}
+
+
+def handle(device: int = 0):
+    """One library handle per device, created on first use."""
+    with _lock:
+        h = _handles.get(device)
+    if h is None:
+        h = domagg_create(device)
+        with _lock:
+            _handles[device] = h
+    return h
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _coord_dtype(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.int32:
+        return DTYPES["i32"]
+    if t.dtype == torch.float32:
+        return DTYPES["f32"]
+    raise TypeError("coordinates must be int32 or float32")
+
+
+def _weight_dtype(w, op: str) -> int:
+    torch = _torch()
+    if op == "count":
+        return DTYPES["i64"]
+    return {torch.int32: DTYPES["i32"], torch.int64: DTYPES["i64"], torch.float32: DTYPES["f32"]}[w.dtype]
+
+
+def out_dtype(op: str, w):
+    torch = _torch()
+    if op == "count":
+        return torch.int64
+    return w.dtype
+
+
+def _stream(dev):
+    return ctypes.c_void_p(_torch().cuda.current_stream(dev).cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else None
+
+
+def forward(D, Q, w=None, op: str = "sum", out=None):
+    """out[q] = F over w(d) for d < q (strict), computed on D's GPU."""
+    torch = _torch()
+    if D.device.type != "cuda":
+        raise ValueError("forward expects CUDA tensors (use forward_host for host buffers)")
+    D, Q = D.contiguous(), Q.contiguous()
+    m = D.shape[1]
+    if Q.shape[1] != m or Q.dtype != D.dtype:
+        raise ValueError("D and Q must have the same width and dtype")
+    w = None if op == "count" else w.contiguous()
+    if out is None:
+        out = torch.empty(Q.shape[0], dtype=out_dtype(op, w), device=D.device)
+    dev = D.device.index or 0
+    domagg_forward(handle(dev), m, _ptr(D), D.shape[0], _ptr(Q), Q.shape[0], _coord_dtype(D), _ptr(w),
+                   _weight_dtype(w, op), OPS[op], _ptr(out), _stream(D.device))
+    return out
+
+
+def forward_host(D, Q, w=None, op: str = "sum", device: int = 0):
+    """Same as forward, from host (CPU) tensors: the library copies the inputs
+    to the GPU, runs, copies the result back and synchronises."""
+    torch = _torch()
+    D, Q = D.contiguous(), Q.contiguous()
+    w = None if op == "count" else w.contiguous()
+    out = torch.empty(Q.shape[0], dtype=out_dtype(op, w), pin_memory=D.is_pinned())
+    domagg_forward_host(handle(device), D.shape[1], _ptr(D), D.shape[0], _ptr(Q), Q.shape[0], _coord_dtype(D),
+                        _ptr(w), _weight_dtype(w, op), OPS[op], _ptr(out),
+                        _stream(torch.device("cuda", device)))
+    return out
+
+
+def backward(D, Q, grad_out):
+    """grad_w[d] = sum of grad_out[q] over queries q with d < q."""
+    torch = _torch()
+    D, Q = D.contiguous(), Q.contiguous()
+    g = grad_out.contiguous().to(torch.float32)
+    grad_w = torch.empty(D.shape[0], dtype=torch.float32, device=D.device)
+    dev = D.device.index or 0
+    domagg_backward(handle(dev), D.shape[1], _ptr(D), D.shape[0], _ptr(Q), Q.shape[0], _coord_dtype(D), _ptr(g),
+                    _ptr(grad_w), _stream(D.device))
+    return grad_w
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class DominanceSum(torch.autograd.Function):
+        """out = dominance sum of float32 weights; differentiable in w only
+        (coordinates are piecewise constant: their gradient is None)."""
+
+        @staticmethod
+        def forward(ctx, D, Q, w):
+            ctx.save_for_backward(D, Q)
+            return forward(D, Q, w, "sum")
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            D, Q = ctx.saved_tensors
+            return None, None, backward(D, Q, grad_out)
+
+    return DominanceSum
+
+
+_DominanceSum = None
+
+
+def dominance_sum(D, Q, w):
+    """Autograd-enabled float32 dominance sum (backward recomputes the records)."""
+    global _DominanceSum
+    if _DominanceSum is None:
+        _DominanceSum = _autograd_function()
+    return _DominanceSum.apply(D, Q, w)
+
+
+def batch(problems, op: str = "sum"):
+    """problems: list of (D, Q, w) CUDA tensors (w ignored for count); all
+    instances share coordinate dtype, weight dtype and op.  Returns outputs."""
+    torch = _torch()
+    if not problems:
+        return []
+    k = len(problems)
+    arr = (domagg_instance * k)()
+    outs, keep = [], []
+    for i, (D, Q, w) in enumerate(problems):
+        D, Q = D.contiguous(), Q.contiguous()
+        w = None if op == "count" else w.contiguous()
+        out = torch.empty(Q.shape[0], dtype=out_dtype(op, w), device=D.device)
+        keep += [D, Q, w]
+        outs.append(out)
+        arr[i] = domagg_instance(D.shape[1], D.shape[0], Q.shape[0], D.data_ptr() if D.numel() else None,
+                                 Q.data_ptr() if Q.numel() else None,
+                                 w.data_ptr() if (w is not None and w.numel()) else None,
+                                 out.data_ptr() if out.numel() else None)
+    D0 = problems[0][0]
+    w0 = problems[0][2]
+    dev = D0.device.index or 0
+    domagg_batch(handle(dev), k, arr, _coord_dtype(D0), _weight_dtype(w0, op), OPS[op], _stream(D0.device))
+    return outs
+
+
+def stats(device: int = 0) -> dict:
+    return domagg_get_stats(handle(device))

@@ -1,0 +1,44 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the
+C ABI and compare with the CPU oracle."""
+import numpy as np
+
+import oracle
+
+F32_TOL = 4.0 * 2.0**-24  # |gpu - fp64| <= F32_TOL * sum |w| over the dominated set
+
+
+def torch():
+    import torch as t
+    return t
+
+
+def to_dev(a):
+    t = torch()
+    return None if a is None else t.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_forward(D, Q, w, op):
+    from paper_2305_16751_gb300 import domagg
+    out = domagg.forward(to_dev(D), to_dev(Q), to_dev(w), op)
+    torch().cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def assert_matches_oracle(got, D, Q, w, op, want=None, S=None, qidx=None):
+    """Bit-exact for integer results, F32_TOL * S for float32 sums, and exact
+    for float32 max."""
+    if want is None:
+        Dq = Q if qidx is None else Q[qidx]
+        want, S = oracle.brute(D, Dq, w, op)
+    if qidx is not None:
+        got = got[qidx]
+    if op == "sum" and w is not None and w.dtype == np.float32:
+        err = np.abs(got.astype(np.float64) - want)
+        bound = F32_TOL * S
+        bad = np.nonzero(err > bound)[0]
+        assert bad.size == 0, f"{bad.size} queries out of tolerance, first {bad[:5]}: got {got[bad[:5]]} want {want[bad[:5]]}"
+    elif op == "max" and w is not None and w.dtype == np.float32:
+        assert np.array_equal(got.astype(np.float64), want)
+    else:
+        assert np.array_equal(got.astype(np.int64), want.astype(np.int64)), \
+            f"first mismatch at {np.nonzero(got.astype(np.int64) != want)[0][:5]}"

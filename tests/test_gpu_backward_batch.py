@@ -1,0 +1,106 @@
+"""Backward (reverse dominance) and batched launches on the GPU, against the
+oracle's transposed brute force and against single-instance calls."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import F32_TOL, assert_matches_oracle, gpu_forward, to_dev, torch
+from paper_2305_16751_gb300 import domagg, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_grad(got, want, S):
+    err = np.abs(got.astype(np.float64) - want)
+    bad = np.nonzero(err > F32_TOL * S)[0]
+    assert bad.size == 0, f"{bad.size} out of tolerance, e.g. {bad[:5]}"
+
+
+@pytest.mark.parametrize("m,dt", [(1, "f32"), (2, "f32"), (2, "i32"), (3, "i32"), (3, "f32")])
+def test_backward_matches_transposed_brute_force(m, dt):
+    rng = np.random.default_rng(50 + m)
+    D, Q, _ = workloads.random_small(rng, m, 7000, 9000, 60, dt, "f32")
+    g = rng.standard_normal(9000).astype(np.float32)
+    got = domagg.backward(to_dev(D), to_dev(Q), to_dev(g)).cpu().numpy()
+    want, S = oracle.brute_transpose(D, Q, g)
+    _check_grad(got, want, S)
+
+
+def test_autograd_function_fd_workload():
+    """loss = sum_q c_q out_q on the autograd workload shape (small n):
+    w.grad equals the transposed sum; D and Q get no gradient."""
+    t = torch()
+    p = workloads.autograd_floats(n=20000)
+    D, Q = to_dev(p.D), to_dev(p.Q)
+    w = to_dev(p.w).requires_grad_(True)
+    c = to_dev(p.extra["c"])
+    out = domagg.dominance_sum(D, Q, w)
+    (out * c).sum().backward()
+    want, S = oracle.brute_transpose(p.D, p.Q, p.extra["c"])
+    _check_grad(w.grad.cpu().numpy(), want, S)
+    assert_matches_oracle(out.detach().cpu().numpy(), p.D, p.Q, p.w, "sum")
+    assert D.grad is None and Q.grad is None
+
+
+def test_autograd_at_512_matches_oracle_finite_differences():
+    """The gradient through autograd equals central finite differences of the
+    fp64 oracle loss at |D| = |Q| = 512 (the loss is linear in w)."""
+    p = workloads.autograd_floats(n=512)
+    rng = np.random.default_rng(0)
+    w0 = (rng.integers(-2048, 2048, size=512) * 2.0**-10).astype(np.float32)
+    c = p.extra["c"]
+    w = to_dev(w0).requires_grad_(True)
+    (domagg.dominance_sum(to_dev(p.D), to_dev(p.Q), w) * to_dev(c)).sum().backward()
+    h = np.float32(2.0**-10)
+
+    def L(wv):
+        return float(np.dot(c.astype(np.float64), oracle.brute(p.D, p.Q, wv, "sum")[0]))
+
+    fd = np.empty(512)
+    for d in range(512):
+        wp, wm = w0.copy(), w0.copy()
+        wp[d] += h
+        wm[d] -= h
+        fd[d] = (L(wp) - L(wm)) / (2 * float(h))
+    S = oracle.brute_transpose(p.D, p.Q, c)[1]
+    _check_grad(w.grad.cpu().numpy(), fd, S)
+
+
+def test_backward_full_size_sampled():
+    """m=2, |D|=|Q|=2^22 (the autograd workload), sampled data points."""
+    p = workloads.autograd_floats()
+    g = p.extra["c"]
+    got = domagg.backward(to_dev(p.D), to_dev(p.Q), to_dev(g)).cpu().numpy()
+    di = np.sort(np.random.default_rng(3).choice(p.D.shape[0], 256, replace=False))
+    want, S = oracle.brute_transpose(p.D[di], p.Q, g)
+    _check_grad(got[di], want, S)
+
+
+@pytest.mark.parametrize("op,wt", [("sum", "f32"), ("sum", "i64"), ("max", "i32"), ("count", "i64")])
+def test_batch_equals_single_calls(op, wt):
+    rng = np.random.default_rng(77)
+    probs = []
+    for i in range(40):
+        m = int(rng.integers(1, 4))
+        nD, nQ = int(rng.integers(0, 3000)), int(rng.integers(0, 3000))
+        if i % 13 == 5:
+            nD = 0
+        D, Q, w = workloads.random_small(rng, m, nD, nQ, int(rng.integers(2, 500)), "i32", wt)
+        probs.append((D, Q, w))
+    outs = domagg.batch([(to_dev(D), to_dev(Q), to_dev(w)) for D, Q, w in probs], op)
+    torch().cuda.synchronize()
+    for (D, Q, w), o in zip(probs, outs):
+        o = o.cpu().numpy()
+        single = gpu_forward(D, Q, w if op != "count" else None, op)
+        assert np.array_equal(o.view(np.uint8), single.view(np.uint8))
+        assert_matches_oracle(o, D, Q, w if op != "count" else None, op)
+
+
+def test_batch_workload_shape_small():
+    """The batch workload (uniform int32 coordinates in [0, 2^31), float32
+    weights) at reduced instance count and sizes."""
+    probs = workloads.batch_instances(k=64, lo=64, hi=4096)
+    outs = domagg.batch([(to_dev(p.D), to_dev(p.Q), to_dev(p.w)) for p in probs], "sum")
+    torch().cuda.synchronize()
+    for p, o in zip(probs, outs):
+        assert_matches_oracle(o.cpu().numpy(), p.D, p.Q, p.w, "sum")
