@@ -76,8 +76,11 @@ domagg_status cuda_fail(domagg_ctx* h, cudaError_t e, const char* where) {
     return fail(h, DOMAGG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-// Grows a device buffer to at least `bytes` (contents are not kept).
-domagg_status grow(domagg_ctx* h, DevBuf& b, size_t bytes) {
+// Grows a device buffer to at least `bytes` (contents are not kept).  Status
+// buffers are zeroed when (re)allocated: fresh memory may hold old data of
+// this process, and a stale word must never look like a status of the
+// current epoch.
+domagg_status grow(domagg_ctx* h, DevBuf& b, size_t bytes, bool zero = false) {
     if (b.cap >= bytes) return DOMAGG_OK;
     size_t want = std::max(bytes, b.cap + b.cap / 4);
     if (h->max_ws && h->held() - b.cap + want > h->max_ws) {
@@ -102,6 +105,11 @@ domagg_status grow(domagg_ctx* h, DevBuf& b, size_t bytes) {
         want = bytes;
     }
     b.cap = want;
+    if (zero) {
+        e = cudaMemset(b.p, 0, want);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();  // ordered before any stream's next kernel
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemset of status words");
+    }
     return DOMAGG_OK;
 }
 
@@ -239,7 +247,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
 
     // status words: point tiles x 256 digits (the records sort grows it later)
     {
-        domagg_status st = grow(h, h->st_multi, (size_t)std::max<u64>(ntp, 1) * RADIX * sizeof(u64));
+        domagg_status st = grow(h, h->st_multi, (size_t)std::max<u64>(ntp, 1) * RADIX * sizeof(u64), true);
         if (st) return st;
     }
 
@@ -411,9 +419,9 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             if (st) return st;
             Carver c2(h->recs.p);
             carve_recs(c2, R);
-            st = grow(h, h->st_multi, (size_t)std::max<u64>(std::max(ntr, ntp), 1) * RADIX * sizeof(u64));
+            st = grow(h, h->st_multi, (size_t)std::max<u64>(std::max(ntr, ntp), 1) * RADIX * sizeof(u64), true);
             if (st) return st;
-            st = grow(h, h->st_seg, (size_t)std::max<u64>(nts, 1) * sizeof(SegStatus<typename Op::Acc>));
+            st = grow(h, h->st_seg, (size_t)std::max<u64>(nts, 1) * sizeof(SegStatus<typename Op::Acc>), true);
             if (st) return st;
         }
         u32* d_rb = (u32*)R[0];

@@ -7,23 +7,42 @@
 
 namespace domagg {
 
-// Look-back status of the segmented scan: the flag word is published with
-// release semantics after the aggregate, and read with acquire semantics
-// before it.
+// Look-back status of the segmented scan.  The aggregate and the inclusive
+// prefix live in separate fields, each written once before the flag that
+// announces it (release), and read after that flag (acquire): a reader that
+// saw ST_AGG never meets a half-written prefix.
 template <typename Acc>
-struct alignas(16) SegStatus {
+struct alignas(32) SegStatus {
     u32 flag;      // (epoch << 2) | ST_AGG / ST_PREFIX
-    u32 has_head;  // a segment starts inside the tile (for ST_AGG)
-    Acc value;     // F over the tile's items after its last head (ST_AGG),
-                   // or the inclusive prefix at the tile's end (ST_PREFIX)
+    u32 has_head;  // a segment starts inside the tile (with ST_AGG)
+    Acc agg;       // F over the tile's items after its last head (ST_AGG)
+    Acc incl;      // inclusive prefix at the tile's end (ST_PREFIX)
 };
 
 template <typename Acc>
-__device__ __forceinline__ void seg_publish(SegStatus<Acc>* s, u32 epoch, u32 flag, bool head, Acc v) {
+__device__ __forceinline__ void seg_publish_agg(SegStatus<Acc>* s, u32 epoch, bool head, Acc v) {
     s->has_head = head ? 1u : 0u;
-    s->value = v;
+    s->agg = v;
     __threadfence();
-    st_store_release(&s->flag, ((epoch & EPOCH_MASK) << 2) | flag);
+    st_store_release(&s->flag, ((epoch & EPOCH_MASK) << 2) | ST_AGG);
+}
+template <typename Acc>
+__device__ __forceinline__ void seg_publish_prefix(SegStatus<Acc>* s, u32 epoch, Acc v) {
+    s->incl = v;
+    __threadfence();
+    st_store_release(&s->flag, ((epoch & EPOCH_MASK) << 2) | ST_PREFIX);
+}
+template <typename Acc>
+__device__ __forceinline__ Acc volatile_read(const Acc* p) {
+    Acc v;
+    if constexpr (sizeof(Acc) == 8) {
+        unsigned long long bits = *reinterpret_cast<const volatile unsigned long long*>(p);
+        v = *reinterpret_cast<Acc*>(&bits);
+    } else {
+        u32 bits = *reinterpret_cast<const volatile u32*>(p);
+        v = *reinterpret_cast<Acc*>(&bits);
+    }
+    return v;
 }
 
 // Segmented scan of F over the sorted records of every instance (Definition
@@ -168,9 +187,9 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys,
         const bool starts_fresh = L.first || (headmask & 1u);
         Acc excl = Op::e();
         if (starts_fresh) {
-            seg_publish(my, epoch, ST_PREFIX, true, tagg);
+            seg_publish_prefix(my, epoch, tagg);
         } else {
-            seg_publish(my, epoch, ST_AGG, thead, tagg);
+            seg_publish_agg(my, epoch, thead, tagg);
             const u32 first_tile = t - (L.start - L.seg_begin) / (u32)TILE;
             u32 u = t;
             while (u > first_tile) {
@@ -189,20 +208,15 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys,
                     if (spins > 64) __nanosleep(256);
                 }
                 if (spins > SPIN_LIMIT) break;
-                const volatile SegStatus<Acc>* vps = ps;
-                Acc v;
-                if constexpr (sizeof(Acc) == 8) {
-                    unsigned long long bits = *reinterpret_cast<const volatile unsigned long long*>(&vps->value);
-                    v = *reinterpret_cast<Acc*>(&bits);
-                } else {
-                    u32 bits = *reinterpret_cast<const volatile u32*>(&vps->value);
-                    v = *reinterpret_cast<Acc*>(&bits);
+                if ((f & 3u) == ST_PREFIX) {
+                    excl = Op::F(volatile_read(&ps->incl), excl);
+                    break;
                 }
-                const u32 hh = vps->has_head;
-                excl = Op::F(v, excl);
-                if ((f & 3u) == ST_PREFIX || hh) break;
+                const u32 hh = *reinterpret_cast<const volatile u32*>(&ps->has_head);
+                excl = Op::F(volatile_read(&ps->agg), excl);
+                if (hh) break;
             }
-            seg_publish(my, epoch, ST_PREFIX, true, thead ? tagg : Op::F(excl, tagg));
+            seg_publish_prefix(my, epoch, thead ? tagg : Op::F(excl, tagg));
         }
         s_excl = excl;
     }
