@@ -91,19 +91,40 @@ __device__ __forceinline__ bool timed_out(const Ctl* ctl) {
 // Exclusive prefix of counter c for tile t over the chain of tiles
 // [chain_first, t).  Tiles publish ST_AGG (own count) before looking back and
 // ST_PREFIX (inclusive prefix) after; chain_first publishes ST_PREFIX at once,
-// so the walk always ends.  Every wait is bounded: when it runs out the
-// kernel records ERR_TIMEOUT and goes on with a wrong (but finite) value.
+// so the walk always ends.  The walk reads LOOKBACK_BATCH predecessors per
+// round (independent loads in flight) and consumes them in order, stopping at
+// the first that is not yet published; long chains of aggregates therefore
+// cost one L2 round trip per batch, not per tile.  Every wait is bounded:
+// when it runs out the kernel records ERR_TIMEOUT and goes on with a wrong
+// (but finite) value.
+constexpr int LOOKBACK_BATCH = 16;
+__device__ __forceinline__ bool st_ready(u64 s, u32 epoch) {
+    return (u32)(s >> 34) == (epoch & EPOCH_MASK) && ((u32)(s >> 32) & 3u);
+}
 __device__ __forceinline__ u32 lookback_u32(const u64* status, int C, int c, u32 t, u32 chain_first,
                                             u32 epoch, Ctl* ctl, u32 where) {
     u32 excl = 0;
-    u32 u = t;
+    u32 u = t;  // tiles [u, t) are consumed
+    u32 spins = 0;
     while (u > chain_first) {
-        --u;
-        u64 s;
-        u32 spins = 0;
-        for (;;) {
-            s = st_load(status + (u64)u * (u64)C + (u64)c);
-            if ((u32)(s >> 34) == (epoch & EPOCH_MASK) && ((u32)(s >> 32) & 3u)) break;
+        u64 s[LOOKBACK_BATCH];
+        const u32 avail = u - chain_first;
+#pragma unroll
+        for (int j = 0; j < LOOKBACK_BATCH; ++j)
+            s[j] = (u32)j < avail ? st_load(status + (u64)(u - 1 - j) * (u64)C + (u64)c) : 0ull;
+        u32 used = 0;
+        bool done = false;
+#pragma unroll
+        for (int j = 0; j < LOOKBACK_BATCH; ++j) {
+            if (done || (u32)j >= avail || used != (u32)j) continue;
+            if (!st_ready(s[j], epoch)) continue;
+            excl += (u32)s[j];
+            used = j + 1;
+            if (((u32)(s[j] >> 32) & 3u) == ST_PREFIX) done = true;
+        }
+        if (done) break;
+        u -= used;
+        if (used == 0) {
             if (++spins > SPIN_LIMIT || ((spins & 255u) == 0 && timed_out(ctl))) {
                 atomicOr(&ctl->error, ERR_TIMEOUT);
                 ctl->timeout_where = where;
@@ -111,8 +132,6 @@ __device__ __forceinline__ u32 lookback_u32(const u64* status, int C, int c, u32
             }
             if (spins > 64) __nanosleep(256);
         }
-        excl += (u32)s;
-        if (((u32)(s >> 32) & 3u) == ST_PREFIX) break;
     }
     return excl;
 }
@@ -124,6 +143,32 @@ __device__ __forceinline__ u32 lanemask_lt() {
     u32 r;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(r));
     return r;
+}
+
+// Lanes of the warp whose 8-bit digit equals this lane's, among the lanes in
+// `valid` (all lanes call it).  Built from one ballot per digit bit: the
+// hardware match instruction has a far lower throughput than ballots.
+__device__ __forceinline__ u32 match_digit8(u32 d, u32 valid) {
+    u32 m = valid;
+#pragma unroll
+    for (int bit = 0; bit < 8; ++bit) {
+        const u32 set = (d >> bit) & 1u;
+        const u32 bal = __ballot_sync(0xffffffffu, set);
+        m &= set ? bal : ~bal;
+    }
+    return m;
+}
+
+// Adds one count for digit d (if valid) to a per-warp histogram h.  Lanes that
+// share lane 0's digit are added together (one atomic), which removes the
+// contention of skewed digit distributions where one digit dominates; the
+// other lanes add one each.
+__device__ __forceinline__ void warp_hist_add(u32* h, u32 d, bool valid, u32 lane) {
+    const u32 d0 = __shfl_sync(0xffffffffu, d, 0);
+    const bool same = valid && d == d0;
+    const u32 grp = __ballot_sync(0xffffffffu, same);
+    if (valid && !same) atomicAdd(&h[d], 1u);
+    else if (same && lane == (u32)(__ffs(grp) - 1)) atomicAdd(&h[d0], (u32)__popc(grp));
 }
 
 // Index of the last entry of the non-decreasing array a[0..n) that is <= x
@@ -148,6 +193,48 @@ __device__ __forceinline__ u32 low_mask(u32 b) { return b >= 32 ? 0xffffffffu : 
 // stays below 2^b.  A data point emits it for the 0-digits of its rank (P0),
 // a query for the 1-digits (P1).
 __device__ __forceinline__ u32 node_of(u32 r, u32 j) { return ((r >> j) | 1u) << j; }
+
+// ---------------------------------------------------------------------
+// TMA bulk copies into shared memory, completed on an mbarrier
+// ---------------------------------------------------------------------
+__device__ __forceinline__ u32 smem_addr(const void* p) { return (u32)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(u64* bar, u32 count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// Orders this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (TMA) accesses to the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(u64* bar, u32 bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// Global -> shared bulk copy; both addresses 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, u32 bytes, u64* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(u64* bar, u32 parity) {
+    u32 ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for phase `parity` of an mbarrier.  Returns false (and records
+// ERR_TIMEOUT) if it did not complete within the limit.
+constexpr u32 MBAR_SPIN_LIMIT = 1u << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(u64* bar, u32 parity, Ctl* ctl, u32 where) {
+    for (u32 i = 0; i < MBAR_SPIN_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicOr(&ctl->error, ERR_TIMEOUT);
+    ctl->timeout_where = where;
+    return false;
+}
 
 // ---------------------------------------------------------------------
 // float-float arithmetic (error-free transformations, Knuth's TwoSum)

@@ -37,13 +37,13 @@ struct Carver {
     T* take(size_t n) {
         off = (off + 255) & ~(size_t)255;
         T* r = base ? reinterpret_cast<T*>(base + off) : nullptr;
-        off += n * sizeof(T);
+        off += n * sizeof(T) + 64;  // slack: 16-byte-aligned bulk reads may run past the end
         return r;
     }
 };
 
-constexpr int SCAN_THREADS = 256, SCAN_ITEMS = 16;  // rank and count scan: tile = SORT_TILE
-static_assert(SCAN_THREADS * SCAN_ITEMS == (int)SORT_TILE, "point tiles are shared");
+constexpr int SCAN_THREADS = 256, SCAN_ITEMS = 16;  // rank and count scan
+static_assert(SCAN_THREADS * SCAN_ITEMS == (int)POINT_TILE, "point scan tiles");
 
 }  // namespace
 
@@ -187,6 +187,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
 
     // ---- host-side layout of the point space
     std::vector<u32> pt_offs(k + 1), q_offs(k + 1);
+    std::vector<u64> pt_sizes(k);
     u64 N = 0, NQ = 0, ntp = 0;
     for (int s = 0; s < k; ++s) {
         pt_offs[s] = (u32)N;
@@ -196,9 +197,10 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         inst[s].U[0] = inst[s].U[1] = inst[s].b[0] = inst[s].b[1] = 0;
         inst[s].T = inst[s].Tq = inst[s].rec_off = inst[s].qrec_off = inst[s].key_bits = 0;
         const u64 n = (u64)inst[s].nD + inst[s].nQ;
+        pt_sizes[s] = n;
         N += n;
         NQ += inst[s].nQ;
-        ntp += (n + SORT_TILE - 1) / SORT_TILE;
+        ntp += (n + POINT_TILE - 1) / POINT_TILE;
     }
     pt_offs[k] = (u32)N;
     q_offs[k] = (u32)NQ;
@@ -228,8 +230,9 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         P[18] = c.take<u32>(NQ);    // qidx
         P[19] = c.take<u32>((size_t)k * 4 * RADIX);  // hist
         P[20] = c.take<u32>((size_t)k * 4 * RADIX);  // digit offsets
+        P[21] = c.take<u32>(k + 1);                  // the sorts' tile map
     };
-    void* P[21];
+    void* P[22];
     {
         Carver c(nullptr);
         carve_points(c, P);
@@ -244,10 +247,12 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     u32 *vA = (u32*)P[8], *vB = (u32*)P[9], *r0 = (u32*)P[10], *r1 = (u32*)P[11];
     u32 *pr0 = (u32*)P[12], *pr1 = (u32*)P[13], *pj = (u32*)P[14], *poff = (u32*)P[15], *pqoff = (u32*)P[16];
     u32 *qslot = (u32*)P[17], *qidx = (u32*)P[18], *hist = (u32*)P[19], *digit_off = (u32*)P[20];
+    u32* d_sort_tiles = (u32*)P[21];
 
     // status words: point tiles x 256 digits (the records sort grows it later)
     {
-        domagg_status st = grow(h, h->st_multi, (size_t)std::max<u64>(ntp, 1) * RADIX * sizeof(u64), true);
+        const u64 nst = std::max<u64>(tiles_of(pt_sizes, SORT_MIN_TILE), ntp);
+        domagg_status st = grow(h, h->st_multi, (size_t)std::max<u64>(nst, 1) * RADIX * sizeof(u64), true);
         if (st) return st;
     }
 
@@ -280,7 +285,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     L.stop();
     h->epoch_mirror += MAX_LAUNCHES;
     L.start(KIND_SMALL, 0.0);
-    k_make_tiles<<<1, 1024, 0, stream>>>(d_pt_offs, k, SORT_TILE, d_pt_tiles);
+    k_make_tiles<<<1, 1024, 0, stream>>>(d_pt_offs, k, POINT_TILE, d_pt_tiles);
     L.stop();
 
     // ---- keys (instruction 0 and 5i-4)
@@ -289,7 +294,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                                                                       negate ? 1 : 0, h->ctl);
     L.stop();
 
-    SortSpace sp{d_pt_offs, d_pt_tiles, k, (u32)ntp, hist, digit_off, (u64*)h->st_multi.p, (double)N};
+    SortSpace sp{d_pt_offs, k, &pt_sizes, d_sort_tiles, hist, digit_off, (u64*)h->st_multi.p, (double)N};
 
     // ---- ranks of the first m-1 coordinates (5i-3 .. 5i, 5m+i)
     for (int i = 0; i < M - 1; ++i) {
@@ -346,7 +351,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         int key_bits;
     };
     std::vector<Chunk> chunks;
-    const u64 chunk_cap = (1ull << 32) - SORT_TILE;
+    const u64 chunk_cap = (1ull << 32) - 65536;
     {
         Chunk c{0, 0, 0, 0, 0};
         for (int s = 0; s < k; ++s) {
@@ -384,6 +389,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         const int kc = C.k1 - C.k0;
         u32* hb = (u32*)(hp + base_pos[ci]);
         u64 ntr = 0, nts = 0;
+        std::vector<u64> rec_sizes(kc);
         {
             u64 a = 0, b = 0;
             for (int s = C.k0; s < C.k1; ++s) {
@@ -391,7 +397,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                 hb[kc + 1 + s - C.k0] = (u32)b;
                 a += inst[s].T;
                 b += inst[s].Tq;
-                ntr += (inst[s].T + SORT_TILE - 1) / SORT_TILE;
+                rec_sizes[s - C.k0] = inst[s].T;
+                ntr += (inst[s].T + SORT_MIN_TILE - 1) / SORT_MIN_TILE;
                 nts += (inst[s].T + SEG_TILE - 1) / SEG_TILE;
             }
             hb[kc] = (u32)a;
@@ -439,9 +446,6 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         h->epoch_mirror += MAX_LAUNCHES;
         L.next_lookback = 0;
         L.start(KIND_SMALL, 0.0);
-        k_make_tiles<<<1, 1024, 0, stream>>>(d_rb, kc, SORT_TILE, d_rtiles);
-        L.stop();
-        L.start(KIND_SMALL, 0.0);
         k_make_tiles<<<1, 1024, 0, stream>>>(d_rb, kc, SEG_TILE, d_stiles);
         L.stop();
 
@@ -460,7 +464,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         // records sort (6m+2): stable, by node key only
         int cur = 0;
         if (C.T > 0 && npass > 0) {
-            SortSpace rs{d_rb, d_rtiles, kc, (u32)ntr, (u32*)R[8], (u32*)R[9], (u64*)h->st_multi.p, (double)C.T};
+            SortSpace rs{d_rb, kc, &rec_sizes, d_rtiles, (u32*)R[8], (u32*)R[9], (u64*)h->st_multi.p, (double)C.T};
             const K keymask = (C.key_bits >= (int)(8 * sizeof(K))) ? ~K(0) : ((K(1) << C.key_bits) - 1);
             cur = sort_pairs<K, Pay>(L, rs, keys, pays, false, C.key_bits, keymask, KIND_HIST_RECORDS,
                                      KIND_SORT_RECORDS);

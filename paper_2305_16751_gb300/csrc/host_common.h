@@ -83,19 +83,26 @@ struct Launcher {
 
 // Workspace for one segmented sort.
 struct SortSpace {
-    const u32* seg_off;   // [nseg+1] device
-    const u32* tile_off;  // [nseg+1] device, tiles of SORT_TILE items
+    const u32* seg_off;         // [nseg+1] device
     int nseg;
-    u32 ntiles;           // host-side (exact or an upper bound)
-    u32* hist;            // [nseg*npass*RADIX]
-    u32* digit_off;       // [nseg*npass*RADIX]
-    u64* status;          // [ntiles*RADIX]
-    double n_items;       // items sorted (for the algorithmic byte model)
+    const std::vector<u64>* seg_sizes;  // host copy of the segment sizes
+    u32* tile_off;              // [nseg+1] device scratch (the sort's tile map)
+    u32* hist;                  // [nseg*npass*RADIX]
+    u32* digit_off;             // [nseg*npass*RADIX]
+    u64* status;                // [tiles*RADIX], tiles of at least SORT_MIN_TILE items
+    double n_items;             // items sorted (for the algorithmic byte model)
 };
 
-constexpr int SORT_THREADS = 256;
-constexpr int SORT_ITEMS = 16;
-constexpr u32 SORT_TILE = SORT_THREADS * SORT_ITEMS;
+// Smallest tile any sort instantiation uses (status words are sized by it).
+constexpr u32 SORT_MIN_TILE = 2048;
+inline u64 tiles_of(const std::vector<u64>& sizes, u64 tile) {
+    u64 t = 0;
+    for (u64 n : sizes) t += (n + tile - 1) / tile;
+    return t;
+}
+
+// Point-phase scans (ranks, count scan) tile the points in 4096s.
+constexpr u32 POINT_TILE = 4096;
 
 // Stable LSD sort of (key, value) pairs by bits [0, total_bits) of
 // (key & keymask), segment by segment.  keys[0]/vals[0] hold the input;

@@ -41,33 +41,57 @@ __device__ __forceinline__ TileLoc locate_tile(u32 t, const u32* seg_off, const 
     return L;
 }
 
+// Locates range r of `range_items` items: its segment and [start, end).
+__device__ __forceinline__ TileLoc locate_range(u32 r, const u32* seg_off, const u32* range_off, int nseg,
+                                                u32 range_items) {
+    TileLoc L;
+    L.seg = upper_index(range_off, nseg + 1, r);
+    L.seg_begin = __ldg(seg_off + L.seg);
+    L.seg_end = __ldg(seg_off + L.seg + 1);
+    const u32 first = __ldg(range_off + L.seg);
+    L.start = L.seg_begin + (r - first) * range_items;
+    L.end = min(L.start + range_items, L.seg_end);
+    L.first = (r == first);
+    return L;
+}
+
 // Digit histograms of all passes, per segment: hist[(seg*npass + p)*RADIX + d].
-template <typename K, int THREADS, int ITEMS>
-__global__ __launch_bounds__(THREADS) void k_radix_hist(const K* __restrict__ keys, const u32* __restrict__ seg_off,
-                                                        const u32* __restrict__ tile_off, int nseg, int npass,
-                                                        int shift0, K keymask, u32* __restrict__ hist) {
-    constexpr int TILE = THREADS * ITEMS;
-    extern __shared__ u32 sh_hist[];  // [npass][RADIX]
-    const u32 t = blockIdx.x;
-    if (t >= __ldg(tile_off + nseg)) return;
-    for (int x = threadIdx.x; x < npass * RADIX; x += THREADS) sh_hist[x] = 0;
+// One block per range of `range_items` items (ranges never straddle a
+// segment); counts are aggregated per warp with match_any before the
+// shared-memory atomics, so skewed digits do not serialise.
+template <typename K>
+__global__ __launch_bounds__(256) void k_radix_hist(const K* __restrict__ keys, const u32* __restrict__ seg_off,
+                                                    const u32* __restrict__ range_off, int nseg, u32 range_items,
+                                                    int npass, int shift0, K keymask, u32* __restrict__ hist) {
+    extern __shared__ u32 sh_hist[];  // [8 warps][npass][RADIX]
+    const u32 r = blockIdx.x;
+    if (r >= __ldg(range_off + nseg)) return;
+    const u32 lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int x = threadIdx.x; x < 8 * npass * RADIX; x += 256) sh_hist[x] = 0;
     __syncthreads();
-    TileLoc L = locate_tile<TILE>(t, seg_off, tile_off, nseg);
-    const u32 lt = lanemask_lt();
-    for (u32 base = L.start; base < L.end; base += THREADS) {
-        const u32 i = base + threadIdx.x;
-        const bool valid = i < L.end;
-        K k = valid ? keys[i] : K(0);
-        for (int p = 0; p < npass; ++p) {
-            u32 d = valid ? digit_of(k, keymask, shift0 + p * RADIX_BITS) : 0xffffu;
-            u32 peers = __match_any_sync(0xffffffffu, d);
-            if (valid && (peers & lt) == 0) atomicAdd(&sh_hist[p * RADIX + d], (u32)__popc(peers));
+    const TileLoc L = locate_range(r, seg_off, range_off, nseg, range_items);
+    u32* wh = sh_hist + warp * npass * RADIX;
+    for (u32 base = L.start; base < L.end; base += 256u * 8u) {
+        K kk[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const u32 x = base + (u32)j * 256u + threadIdx.x;
+            kk[j] = x < L.end ? keys[x] : K(0);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool valid = base + (u32)j * 256u + threadIdx.x < L.end;
+            for (int p = 0; p < npass; ++p)
+                warp_hist_add(wh + p * RADIX, digit_of(kk[j], keymask, shift0 + p * RADIX_BITS), valid, lane);
         }
     }
     __syncthreads();
     u32* gh = hist + (u64)L.seg * npass * RADIX;
-    for (int x = threadIdx.x; x < npass * RADIX; x += THREADS)
-        if (sh_hist[x]) atomicAdd(gh + x, sh_hist[x]);
+    for (int x = threadIdx.x; x < npass * RADIX; x += 256) {
+        u32 c = 0;
+        for (int w = 0; w < 8; ++w) c += sh_hist[w * npass * RADIX + x];
+        if (c) atomicAdd(gh + x, c);
+    }
 }
 
 // Exclusive scan of every (segment, pass) histogram plus the segment start:
@@ -91,145 +115,287 @@ static __global__ __launch_bounds__(RADIX) void k_radix_offsets(const u32* __res
     digit_off[(u64)sp * RADIX + threadIdx.x] = __ldg(seg_off + seg) + add + inc - v;
 }
 
-// Shared-memory footprint of one onesweep tile.
-template <typename K, typename V, int THREADS, int ITEMS>
-constexpr size_t onesweep_smem() {
-    return (size_t)THREADS * ITEMS * (sizeof(K) + sizeof(V)) + (size_t)(THREADS / 32) * (RADIX + 1) * 4 +
-           2 * RADIX * 4;
+// Items per thread of a onesweep tile: about 32 KB of (key, value) pairs.
+template <typename K, typename V>
+__host__ __device__ constexpr int onesweep_items() {
+    return 128 / (int)(sizeof(K) + sizeof(V));
+}
+constexpr int ONESWEEP_THREADS = 256;
+
+// Shared-memory layout of the persistent onesweep kernel: two tile buffers
+// (keys, then values, each with 16 bytes of alignment slack at both ends),
+// the warp histograms and the per-digit bases.
+template <typename K, typename V, int TILE>
+struct OnesweepSmem {
+    static constexpr int WARPS = ONESWEEP_THREADS / 32;
+    static constexpr size_t KBYTES = ((size_t)(TILE + 2 * 16 / sizeof(K)) * sizeof(K) + 15) & ~(size_t)15;
+    static constexpr size_t VBYTES = ((size_t)(TILE + 2 * 16 / sizeof(V)) * sizeof(V) + 15) & ~(size_t)15;
+    static constexpr size_t BUF = KBYTES + VBYTES;
+    static constexpr size_t WHIST = (size_t)WARPS * (RADIX + 1) * 4;
+    static constexpr size_t TOTAL = 2 * BUF + WHIST + 2 * RADIX * 4 + 64;
+};
+
+template <typename K, typename V>
+__host__ __device__ constexpr size_t onesweep_smem() {
+    return OnesweepSmem<K, V, ONESWEEP_THREADS * onesweep_items<K, V>()>::TOTAL;
 }
 
 // One LSD pass: stable scatter of every segment by digit `pass`.
+//
+// Persistent CTAs claim ranges of consecutive tiles from a global counter,
+// in increasing order.  For a range the CTA
+//   1. counts its digits (one read of the keys),
+//   2. publishes the count and runs one decoupled look-back over the earlier
+//      ranges of the segment (bounded waits), which gives the global position
+//      of the range's first item of every digit,
+//   3. streams the range tile by tile: the next tile's keys and values are
+//      fetched into the other shared-memory buffer by TMA bulk copies
+//      (cp.async.bulk, completion on an mbarrier) while the current tile is
+//      ranked (warp-level stable match_any ranking), sorted locally in shared
+//      memory and written out with coalesced stores at running per-digit
+//      positions.
+// There is no inter-CTA wait inside a range; the look-back runs once per
+// range (hundreds of thousands of items), not once per tile.
+//
 // IOTA: the values are the items' own global indices (first pass of a sort
 // that returns a permutation); `vin` is not read.
-template <typename K, typename V, int THREADS, int ITEMS, bool IOTA>
-__global__ __launch_bounds__(THREADS) void k_onesweep(const K* __restrict__ kin, const V* __restrict__ vin,
-                                                      K* __restrict__ kout, V* __restrict__ vout,
-                                                      const u32* __restrict__ seg_off,
-                                                      const u32* __restrict__ tile_off, int nseg,
-                                                      const u32* __restrict__ digit_off, int npass, int pass,
-                                                      int shift, K keymask, u64* status, Ctl* ctl,
-                                                      int launch_idx) {
-    constexpr int WARPS = THREADS / 32, TILE = THREADS * ITEMS;
-    extern __shared__ __align__(16) unsigned char smem[];
-    K* s_keys = reinterpret_cast<K*>(smem);
-    V* s_vals = reinterpret_cast<V*>(s_keys + TILE);
-    u32* s_whist = reinterpret_cast<u32*>(s_vals + TILE);  // [WARPS][RADIX+1]
-    u32* s_dstart = s_whist + WARPS * (RADIX + 1);         // tile-local digit starts
-    u32* s_gbase = s_dstart + RADIX;                       // counts, then global bases
-    __shared__ u32 s_info[2];
+template <typename K, typename V, bool IOTA>
+__global__ __launch_bounds__(ONESWEEP_THREADS, 3) void k_onesweep(
+    const K* __restrict__ kin, const V* __restrict__ vin, K* __restrict__ kout, V* __restrict__ vout,
+    const u32* __restrict__ seg_off, const u32* __restrict__ range_off, int nseg, u32 range_items,
+    const u32* __restrict__ digit_off, int npass, int pass, int shift, K keymask, u64* status, Ctl* ctl,
+    int launch_idx) {
+    constexpr int THREADS = ONESWEEP_THREADS, ITEMS = onesweep_items<K, V>();
+    constexpr int TILE = THREADS * ITEMS, WARPS = THREADS / 32;
+    typedef OnesweepSmem<K, V, TILE> SM;
+    constexpr u32 KAL = 16 / sizeof(K), VAL = 16 / sizeof(V);  // items per 16 bytes
+    extern __shared__ __align__(128) unsigned char smem[];
+    u32* s_whist = reinterpret_cast<u32*>(smem + 2 * SM::BUF);  // [WARPS][RADIX+1]
+    u32* s_dstart = s_whist + WARPS * (RADIX + 1);              // tile-local digit starts
+    u32* s_run = s_dstart + RADIX;                              // next global position per digit
+    u64* s_bar = reinterpret_cast<u64*>(s_run + RADIX);         // [2]
+    u32* s_info = reinterpret_cast<u32*>(s_bar + 2);            // range, koff[2], voff[2], epoch, abort
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        s_info[0] = atomicAdd(&ctl->tile_ctr[launch_idx], 1u);
-        s_info[1] = ctl->epoch_base + (u32)launch_idx;
-    }
-    for (int x = tid; x < WARPS * (RADIX + 1); x += THREADS) s_whist[x] = 0;
-    __syncthreads();
-    const u32 t = s_info[0], epoch = s_info[1];
-    if (t >= __ldg(tile_off + nseg)) return;
-    const TileLoc L = locate_tile<TILE>(t, seg_off, tile_off, nseg);
-
-    // load: warp w owns items [start + w*32*ITEMS, ...), item i of lane l at
-    // offset i*32 + l (coalesced), which is also the order of ranking.
-    K key[ITEMS];
-    V val[ITEMS];
-    u32 dig[ITEMS], rnk[ITEMS];
-    const u32 wbase = L.start + (u32)warp * 32u * ITEMS;
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        const u32 idx = wbase + (u32)i * 32u + (u32)lane;
-        if (idx < L.end) {
-            key[i] = kin[idx];
-            val[i] = IOTA ? (V)idx : vin[idx];
-            dig[i] = digit_of(key[i], keymask, shift);
-        } else {
-            key[i] = K(0);
-            val[i] = V(0);
-            dig[i] = RADIX;  // padding: counted apart, never written
-        }
-    }
-    // warp-level stable ranking
-    u32* wh = s_whist + warp * (RADIX + 1);
+    const u32 nranges = __ldg(range_off + nseg);
     const u32 lt = lanemask_lt();
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        const u32 d = dig[i];
-        const u32 peers = __match_any_sync(0xffffffffu, d);
-        const u32 before = wh[d];
-        __syncwarp();
-        rnk[i] = before + __popc(peers & lt);
-        if ((peers & lt) == 0) wh[d] = before + __popc(peers);
-        __syncwarp();
+    // TMA loads of items [a, e) into buffer b (one thread)
+    auto issue = [&](int b, u32 a, u32 e) {
+        const u32 ka = a / KAL * KAL, kb = (e + KAL - 1) / KAL * KAL;
+        const u32 kbytes = (kb - ka) * (u32)sizeof(K);
+        u32 vbytes = 0, va = 0;
+        if (!IOTA) {
+            va = a / VAL * VAL;
+            const u32 vb = (e + VAL - 1) / VAL * VAL;
+            vbytes = (vb - va) * (u32)sizeof(V);
+        }
+        s_info[1 + b] = a - ka;
+        s_info[3 + b] = a - va;
+        unsigned char* buf = smem + b * SM::BUF;
+        mbar_arrive_expect_tx(&s_bar[b], kbytes + vbytes);
+        bulk_g2s(buf, kin + ka, kbytes, &s_bar[b]);
+        if (!IOTA) bulk_g2s(buf + SM::KBYTES, vin + va, vbytes, &s_bar[b]);
+    };
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        fence_mbar_init();
+        s_info[5] = ctl->epoch_base + (u32)launch_idx;
+        s_info[6] = 0;
     }
     __syncthreads();
-    // per digit: exclusive offsets of the warps, and the tile's count
-    for (int d = tid; d < RADIX; d += THREADS) {
-        u32 sum = 0;
-        for (int w = 0; w < WARPS; ++w) {
-            const u32 c = s_whist[w * (RADIX + 1) + d];
-            s_whist[w * (RADIX + 1) + d] = sum;
-            sum += c;
+    const u32 epoch = s_info[5];
+    u32 phase[2] = {0u, 0u};
+    bool pending[2] = {false, false};  // thread 0's view of copies in flight
+    int b = 0;
+    for (;;) {
+        if (tid == 0) s_info[0] = atomicAdd(&ctl->tile_ctr[launch_idx], 1u);
+        for (int x = tid; x < WARPS * (RADIX + 1); x += THREADS) s_whist[x] = 0;
+        __syncthreads();
+        const u32 r = s_info[0];
+        if (r >= nranges) break;
+        const TileLoc L = locate_range(r, seg_off, range_off, nseg, range_items);
+        const u32 ntile = (L.end - L.start + TILE - 1) / TILE;
+        if (tid == 0) {  // the first tile's load overlaps the range histogram
+            fence_proxy_async_smem();
+            issue(b, L.start, min(L.start + (u32)TILE, L.end));
+            pending[b] = true;
         }
-        s_gbase[d] = sum;
-    }
-    __syncthreads();
-    if (warp == 0) {  // exclusive scan of the tile counts over the digits
-        constexpr int PER = RADIX / 32;
-        u32 v[PER], s = 0;
+        // 1. digit counts of the range (per-warp histograms, then summed)
+        {
+            u32* wh = s_whist + warp * (RADIX + 1);
+            for (u32 base = L.start; base < L.end; base += (u32)THREADS * 8u) {
+                K kk[8];
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            v[j] = s_gbase[lane * PER + j];
-            s += v[j];
-        }
-        u32 inc = s;
+                for (int j = 0; j < 8; ++j) {
+                    const u32 x = base + (u32)j * THREADS + (u32)tid;
+                    kk[j] = x < L.end ? kin[x] : K(0);
+                }
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const u32 n = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += n;
+                for (int j = 0; j < 8; ++j)
+                    warp_hist_add(wh, digit_of(kk[j], keymask, shift), base + (u32)j * THREADS + (u32)tid < L.end,
+                                  (u32)lane);
+            }
+            __syncthreads();
+            for (int d = tid; d < RADIX; d += THREADS) {
+                u32 c = 0;
+                for (int w = 0; w < WARPS; ++w) c += s_whist[w * (RADIX + 1) + d];
+                s_dstart[d] = c;
+            }
+            __syncthreads();
         }
-        u32 ex = inc - s;
+        // 2. publish the range's counts and look back over the earlier ranges
+        {
+            const u32 first_range = r - (L.start - L.seg_begin) / range_items;
+            for (int d = tid; d < RADIX; d += THREADS) {
+                const u32 cnt = s_dstart[d];
+                u64* st = status + (u64)r * RADIX + d;
+                u32 excl = 0;
+                if (L.first) {
+                    st_store(st, st_pack(epoch, ST_PREFIX, cnt));
+                } else {
+                    st_store(st, st_pack(epoch, ST_AGG, cnt));
+                    excl = lookback_u32(status, RADIX, d, r, first_range, epoch, ctl, 1u);
+                    st_store(st, st_pack(epoch, ST_PREFIX, excl + cnt));
+                }
+                s_run[d] = __ldg(digit_off + ((u64)L.seg * npass + pass) * RADIX + d) + excl;
+            }
+        }
+        // 3. the tiles of the range, in order
+        for (u32 j = 0; j < ntile; ++j) {
+            const u32 a = L.start + j * (u32)TILE;
+            const u32 n = min(a + (u32)TILE, L.end) - a;
+            for (int x = tid; x < WARPS * (RADIX + 1); x += THREADS) s_whist[x] = 0;
+            fence_proxy_async_smem();
+            __syncthreads();  // counters cleared; the other buffer is free
+            if (tid == 0 && j + 1 < ntile) {
+                const u32 a2 = a + (u32)TILE;
+                issue(b ^ 1, a2, min(a2 + (u32)TILE, L.end));
+                pending[b ^ 1] = true;
+            }
+            // every thread observes the completion of the copy it reads
+            if (mbar_wait_bounded(&s_bar[b], phase[b], ctl, 5u)) {
+                phase[b] ^= 1u;
+                if (tid == 0) pending[b] = false;
+            } else {
+                s_info[6] = 1u;
+            }
+            __syncthreads();
+            if (s_info[6]) break;
+            const K* bk = reinterpret_cast<const K*>(smem + b * SM::BUF) + s_info[1 + b];
+            const V* bv = reinterpret_cast<const V*>(smem + b * SM::BUF + SM::KBYTES) + s_info[3 + b];
+            // warp w ranks items [w*32*ITEMS, ...); item i of lane l at i*32 + l
+            K key[ITEMS];
+            u32 pos[ITEMS];
+            const u32 wbase = (u32)warp * 32u * ITEMS;
+            u32* wh = s_whist + warp * (RADIX + 1);
+            // digit matches of all items first (independent ballots pipeline) ...
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            s_dstart[lane * PER + j] = ex;
-            ex += v[j];
-        }
-    }
-    __syncthreads();
-    // publish, look back, and turn counts into global bases
-    const u32 first_tile = t - (L.start - L.seg_begin) / (u32)TILE;
-    for (int d = tid; d < RADIX; d += THREADS) {
-        const u32 cnt = s_gbase[d];
-        u64* st = status + (u64)t * RADIX + d;
-        u32 excl = 0;
-        if (L.first) {
-            st_store(st, st_pack(epoch, ST_PREFIX, cnt));
-        } else {
-            st_store(st, st_pack(epoch, ST_AGG, cnt));
-            excl = lookback_u32(status, RADIX, d, t, first_tile, epoch, ctl, 1u);
-            st_store(st, st_pack(epoch, ST_PREFIX, excl + cnt));
-        }
-        s_gbase[d] = __ldg(digit_off + ((u64)L.seg * npass + pass) * RADIX + d) + excl - s_dstart[d];
-    }
-    __syncthreads();
-    // local scatter: items grouped by digit, stable
+            for (int i = 0; i < ITEMS; ++i) {
+                const u32 x = wbase + (u32)i * 32u + (u32)lane;
+                const bool valid = x < n;
+                key[i] = valid ? bk[x] : K(0);
+                pos[i] = match_digit8(digit_of(key[i], keymask, shift), __ballot_sync(0xffffffffu, valid));
+            }
+            // ... then, item by item, the group's leader advances the warp's
+            // count of the digit (shared-memory atomics of one warp are
+            // performed in program order) and shares the old count
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        if (dig[i] < RADIX) {
-            const u32 pos = s_dstart[dig[i]] + s_whist[warp * (RADIX + 1) + dig[i]] + rnk[i];
-            s_keys[pos] = key[i];
-            s_vals[pos] = val[i];
+            for (int i = 0; i < ITEMS; ++i) {
+                const u32 x = wbase + (u32)i * 32u + (u32)lane;
+                const u32 peers = pos[i];
+                const bool valid = x < n;
+                const int leader = valid ? __ffs(peers) - 1 : lane;
+                u32 old = 0;
+                if (valid && lane == leader) old = atomicAdd(&wh[digit_of(key[i], keymask, shift)], (u32)__popc(peers));
+                pos[i] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
+            }
+            __syncthreads();
+            for (int d = tid; d < RADIX; d += THREADS) {  // exclusive over warps; tile count
+                u32 sum = 0;
+                for (int w = 0; w < WARPS; ++w) {
+                    const u32 c = s_whist[w * (RADIX + 1) + d];
+                    s_whist[w * (RADIX + 1) + d] = sum;
+                    sum += c;
+                }
+                s_dstart[d] = sum;
+            }
+            __syncthreads();
+            if (warp == 0) {  // exclusive scan of the tile counts over the digits (in place)
+                constexpr int PER = RADIX / 32;
+                u32 v[PER], sacc = 0;
+#pragma unroll
+                for (int q = 0; q < PER; ++q) {
+                    v[q] = s_dstart[lane * PER + q];
+                    sacc += v[q];
+                }
+                u32 inc = sacc;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const u32 nn = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += nn;
+                }
+                u32 ex = inc - sacc;
+#pragma unroll
+                for (int q = 0; q < PER; ++q) {
+                    s_dstart[lane * PER + q] = ex;
+                    ex += v[q];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const u32 x = wbase + (u32)i * 32u + (u32)lane;
+                if (x < n) {
+                    const u32 d = digit_of(key[i], keymask, shift);
+                    pos[i] += s_dstart[d] + s_whist[warp * (RADIX + 1) + d];
+                }
+            }
+            K* sk = reinterpret_cast<K*>(smem + b * SM::BUF);
+            V* sv = reinterpret_cast<V*>(smem + b * SM::BUF + SM::KBYTES);
+            __syncthreads();  // all keys are in registers: stage over the key buffer
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const u32 x = wbase + (u32)i * 32u + (u32)lane;
+                if (x < n) sk[pos[i]] = key[i];
+            }
+            V val[ITEMS];
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const u32 x = wbase + (u32)i * 32u + (u32)lane;
+                val[i] = IOTA ? (V)(a + x) : (x < n ? bv[x] : V(0));
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const u32 x = wbase + (u32)i * 32u + (u32)lane;
+                if (x < n) sv[pos[i]] = val[i];
+            }
+            __syncthreads();
+            for (u32 x = tid; x < n; x += THREADS) {
+                const K k = sk[x];
+                const u32 d = digit_of(k, keymask, shift);
+                const u32 dst = s_run[d] + (x - s_dstart[d]);
+                if (dst >= L.seg_begin && dst < L.seg_end) {  // only fails after a timed-out wait
+                    kout[dst] = k;
+                    vout[dst] = sv[x];
+                }
+            }
+            __syncthreads();
+            if (tid < RADIX) {  // advance the running positions by this tile's counts
+                const u32 d = tid;
+                const u32 next = d + 1 < RADIX ? s_dstart[d + 1] : n;
+                s_run[d] += next - s_dstart[d];
+            }
+            b ^= 1;
         }
+        __syncthreads();
+        if (s_info[6]) break;
     }
-    __syncthreads();
-    // global scatter: consecutive threads write consecutive positions of a digit
-    const u32 n = L.end - L.start;
-    for (u32 x = tid; x < n; x += THREADS) {
-        const K k = s_keys[x];
-        const u32 dst = s_gbase[digit_of(k, keymask, shift)] + x;
-        if (dst >= L.seg_begin && dst < L.seg_end) {  // only fails after a timed-out wait
-            kout[dst] = k;
-            vout[dst] = s_vals[x];
-        }
+    // a copy may still be in flight if a wait ran out: wait for it (bounded)
+    if (tid == 0) {
+        for (int bb = 0; bb < 2; ++bb)
+            if (pending[bb]) mbar_wait_bounded(&s_bar[bb], phase[bb], ctl, 6u);
     }
 }
 
