@@ -183,6 +183,15 @@ __device__ __forceinline__ int upper_index(const u32* a, int n, u32 x) {
     return lo;
 }
 
+// Padded shared-memory index: one spare element per 32, so that reading a
+// tile in blocked order (thread t takes elements t*ITEMS ..) and in striped
+// order are both free of bank conflicts.
+__device__ __forceinline__ u32 pidx(u32 x) { return x + (x >> 5); }
+template <int N>
+struct Padded {
+    static constexpr int value = N + N / 32 + 1;
+};
+
 // Mask of the low b bits (b <= 32).
 __device__ __forceinline__ u32 low_mask(u32 b) { return b >= 32 ? 0xffffffffu : ((1u << b) - 1u); }
 

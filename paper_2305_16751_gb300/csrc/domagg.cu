@@ -453,10 +453,12 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         const u32 p_begin = pt_offs[C.k0], p_end = pt_offs[C.k1];
         if (C.T > 0) {
             const u64 warps = (p_end - p_begin + 31) / 32;
-            const unsigned grid = (unsigned)std::min<u64>((warps + 7) / 8, 152ull * 32);
+            const unsigned grid = (unsigned)std::min<u64>((warps + 7) / 8, 152ull * 16);
+            const int esmem = (EXPAND_THREADS / 32) * EXPAND_STAGE_BYTES;
+            cudaFuncSetAttribute(k_expand<M, K, Pay, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, esmem);
             L.start(KIND_EXPAND, (double)(p_end - p_begin) * (4.0 * (M - 1) + 12) +
                                      (double)C.T * (sizeof(K) + sizeof(Pay)));
-            k_expand<M, K, Pay, WT><<<grid, 256, 0, stream>>>(p_begin, p_end, pr0, pr1, pj, poff, pqoff, d_inst,
+            k_expand<M, K, Pay, WT><<<grid, EXPAND_THREADS, esmem, stream>>>(p_begin, p_end, pr0, pr1, pj, poff, pqoff, d_inst,
                                                              d_pt_offs, k, d_rb, d_qb, C.k0, (u32)C.T, keys[0],
                                                              pays[0]);
             L.stop();

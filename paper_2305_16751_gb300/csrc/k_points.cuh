@@ -97,11 +97,11 @@ __device__ __forceinline__ void load_blocked_u32(const u32* __restrict__ src, u3
                                                  u32 (&out)[ITEMS], u32 fill) {
     for (int i = 0; i < ITEMS; ++i) {
         const u32 x = (u32)i * THREADS + threadIdx.x;
-        sbuf[x] = (start + x < end) ? src[start + x] : fill;
+        sbuf[pidx(x)] = (start + x < end) ? src[start + x] : fill;
     }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) out[i] = sbuf[threadIdx.x * ITEMS + i];
+    for (int i = 0; i < ITEMS; ++i) out[i] = sbuf[pidx(threadIdx.x * ITEMS + i)];
     __syncthreads();
 }
 
@@ -147,7 +147,7 @@ __global__ __launch_bounds__(THREADS) void k_rank(const u32* __restrict__ skeys,
                                                   int nseg, u32* __restrict__ rank_out, Inst* inst, int dim,
                                                   u64* status, Ctl* ctl, int launch_idx) {
     constexpr int TILE = THREADS * ITEMS;
-    __shared__ u32 sbuf[TILE];
+    __shared__ u32 sbuf[Padded<TILE>::value];
     __shared__ u32 scratch[THREADS / 32];
     __shared__ u32 s_info[3];
     if (threadIdx.x == 0) {
@@ -233,7 +233,7 @@ __global__ __launch_bounds__(THREADS) void k_count_scan(
     u32* __restrict__ pqoff, u32* __restrict__ qslot, u32* __restrict__ qidx, u64* status, Ctl* ctl,
     int launch_idx) {
     constexpr int TILE = THREADS * ITEMS;
-    __shared__ u32 sbuf[TILE];
+    __shared__ u32 sbuf[Padded<TILE>::value];
     __shared__ u32 scratch[3 * (THREADS / 32)];
     __shared__ u32 s_info[2];
     __shared__ u32 s_excl[3];
@@ -326,22 +326,30 @@ __global__ __launch_bounds__(THREADS) void k_count_scan(
 // first m-1 ranks (node_of): for m = 3, node0 << b1 | node1.  The role bit
 // (top bit of the key) marks query records; it is not part of the sort key.
 // Payload: data -> the weight's bits (Op::Pay), query -> its partial slot.
-// One warp handles 32 consecutive points and writes their records together:
-// lane l writes record (base + l + 32i), whose owner it finds by a binary
-// search over the lanes' record offsets.
+//
+// One warp handles 32 consecutive points.  Each lane enumerates its own
+// point's records (lowest set bit first: one find-first-set per record) into
+// a per-warp staging buffer in shared memory, EXPAND_STAGE_BYTES at a time;
+// the warp then copies the staged run to global memory with coalesced stores.
+constexpr int EXPAND_THREADS = 256;
+constexpr int EXPAND_STAGE_BYTES = 8192;  // per warp
 template <int M, typename K, typename Pay, int WT>
-__global__ void k_expand(u32 p_begin, u32 p_end, const u32* __restrict__ pr0, const u32* __restrict__ pr1,
-                         const u32* __restrict__ pj, const u32* __restrict__ poff, const u32* __restrict__ pqoff,
-                         const Inst* __restrict__ inst, const u32* __restrict__ pt_offs, int k,
-                         const u32* __restrict__ rec_base, const u32* __restrict__ qrec_base, int k0,
-                         u32 n_rec, K* __restrict__ kout, Pay* __restrict__ pout) {
-    const int lane = threadIdx.x & 31;
+__global__ __launch_bounds__(EXPAND_THREADS) void k_expand(
+    u32 p_begin, u32 p_end, const u32* __restrict__ pr0, const u32* __restrict__ pr1,
+    const u32* __restrict__ pj, const u32* __restrict__ poff, const u32* __restrict__ pqoff,
+    const Inst* __restrict__ inst, const u32* __restrict__ pt_offs, int k, const u32* __restrict__ rec_base,
+    const u32* __restrict__ qrec_base, int k0, u32 n_rec, K* __restrict__ kout, Pay* __restrict__ pout) {
+    constexpr u32 CH = EXPAND_STAGE_BYTES / (sizeof(K) + sizeof(Pay));  // records staged per warp
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    K* sk = reinterpret_cast<K*>(smem + warp * EXPAND_STAGE_BYTES);
+    Pay* sp = reinterpret_cast<Pay*>(sk + CH);
     const u32 warps = (gridDim.x * blockDim.x) >> 5;
     const K role = K(1) << (sizeof(K) * 8 - 1);
     for (u32 wb = p_begin + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; wb < p_end; wb += warps * 32u) {
         const u32 p = wb + lane;
         const bool valid = p < p_end;
-        u32 r0 = 0, r1 = 0, bits0 = 0, bits1 = 0, c1 = 1, b1 = 0, cnt = 0, off_rel = 0xffffffffu, gbase = 0;
+        u32 r0 = 0, r1 = 0, bits0 = 0, bits1 = 0, b1 = 0, cnt = 0, gbase = 0;
         bool q = false;
         Pay pay = 0;
         if (valid) {
@@ -359,7 +367,6 @@ __global__ void k_expand(u32 p_begin, u32 p_end, const u32* __restrict__ pr0, co
                 r1 = pr1[p];
                 b1 = inst[s].b[1];
                 bits1 = (q ? r1 : ~r1) & low_mask(b1);
-                c1 = (u32)__popc(bits1);
             }
             cnt = record_count<M>(bits0, bits1);
             gbase = __ldg(rec_base + (s - k0)) + poff[p];
@@ -371,54 +378,46 @@ __global__ void k_expand(u32 p_begin, u32 p_end, const u32* __restrict__ pr0, co
                 pay = (Pay)reinterpret_cast<const u32*>(inst[s].dw)[local - nQ];
             }
         }
-        // records of this warp: [gbase(lane 0), gbase(lane 0) + R)
+        // records of this warp: [wstart, wstart + R)
         const u32 wstart = __shfl_sync(0xffffffffu, gbase, 0);
-        if (valid) off_rel = gbase - wstart;
+        const u32 off_rel = valid ? gbase - wstart : 0u;
         u32 R = valid ? off_rel + cnt : 0u;
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) R = max(R, __shfl_xor_sync(0xffffffffu, R, o));
-        for (u32 xb = 0; xb < R; xb += 32u) {
-            const u32 x = xb + lane;
-            int owner = 0;
-#pragma unroll
-            for (int st = 16; st >= 1; st >>= 1) {
-                const u32 v = __shfl_sync(0xffffffffu, off_rel, owner + st);
-                if (v <= x) owner += st;
-            }
-            const u32 o_rel = __shfl_sync(0xffffffffu, off_rel, owner);
-            const u32 o_r0 = __shfl_sync(0xffffffffu, r0, owner);
-            const u32 o_bits0 = __shfl_sync(0xffffffffu, bits0, owner);
-            const u32 o_r1 = __shfl_sync(0xffffffffu, r1, owner);
-            const u32 o_bits1 = __shfl_sync(0xffffffffu, bits1, owner);
-            const u32 o_c1 = __shfl_sync(0xffffffffu, c1, owner);
-            const u32 o_b1 = __shfl_sync(0xffffffffu, b1, owner);
-            const int o_q = __shfl_sync(0xffffffffu, (int)q, owner);
-            Pay o_pay;
-            if (sizeof(Pay) == 8) {
-                const u32 lo = __shfl_sync(0xffffffffu, (u32)(u64)pay, owner);
-                const u32 hi = __shfl_sync(0xffffffffu, (u32)((u64)pay >> 32), owner);
-                o_pay = (Pay)(((u64)hi << 32) | lo);
-            } else {
-                o_pay = (Pay)__shfl_sync(0xffffffffu, (u32)pay, owner);
-            }
-            if (x < R && wstart + x < n_rec) {
-                const u32 kk = x - o_rel;
+        // enumeration state: the current node of dimension 0 (lowest pending
+        // bit of rem0) and the pending bits of dimension 1
+        u32 rem0 = bits0, rem1 = bits1, kk = 0;
+        for (u32 c0 = 0; c0 < R; c0 += CH) {
+            const u32 c1 = min(c0 + CH, R);
+            for (u32 idx = off_rel + kk; kk < cnt && idx < c1; ++kk, ++idx) {
                 K key;
                 if (M == 1) {
                     key = K(0);
                 } else if (M == 2) {
-                    const u32 j0 = __fns(o_bits0, 0, (int)kk + 1);
-                    key = (K)node_of(o_r0, j0);
+                    const u32 j0 = __ffs(rem0) - 1;
+                    rem0 &= rem0 - 1;
+                    key = (K)node_of(r0, j0);
                 } else {
-                    const u32 k0i = kk / o_c1, k1i = kk - k0i * o_c1;
-                    const u32 j0 = __fns(o_bits0, 0, (int)k0i + 1);
-                    const u32 j1 = __fns(o_bits1, 0, (int)k1i + 1);
-                    key = ((K)node_of(o_r0, j0) << o_b1) | (K)node_of(o_r1, j1);
+                    const u32 j0 = __ffs(rem0) - 1, j1 = __ffs(rem1) - 1;
+                    key = ((K)node_of(r0, j0) << b1) | (K)node_of(r1, j1);
+                    rem1 &= rem1 - 1;
+                    if (rem1 == 0) {  // next node of dimension 0
+                        rem0 &= rem0 - 1;
+                        rem1 = bits1;
+                    }
                 }
-                if (o_q) key |= role;
-                kout[wstart + x] = key;
-                pout[wstart + x] = o_q ? (Pay)(o_pay + kk) : o_pay;
+                if (q) key |= role;
+                sk[idx - c0] = key;
+                sp[idx - c0] = q ? (Pay)(pay + kk) : pay;
             }
+            __syncwarp();
+            for (u32 x = c0 + lane; x < c1; x += 32u) {
+                if (wstart + x < n_rec) {
+                    kout[wstart + x] = sk[x - c0];
+                    pout[wstart + x] = sp[x - c0];
+                }
+            }
+            __syncwarp();
         }
     }
 }

@@ -115,12 +115,19 @@ static __global__ __launch_bounds__(RADIX) void k_radix_offsets(const u32* __res
     digit_off[(u64)sp * RADIX + threadIdx.x] = __ldg(seg_off + seg) + add + inc - v;
 }
 
-// Items per thread of a onesweep tile: about 32 KB of (key, value) pairs.
+// Items per thread of a onesweep tile: ONESWEEP_TILE_BYTES of (key, value)
+// pairs per tile.
+#ifndef ONESWEEP_TILE_BYTES
+#define ONESWEEP_TILE_BYTES 32768
+#endif
 template <typename K, typename V>
 __host__ __device__ constexpr int onesweep_items() {
-    return 128 / (int)(sizeof(K) + sizeof(V));
+    return ONESWEEP_TILE_BYTES / 256 / (int)(sizeof(K) + sizeof(V));
 }
 constexpr int ONESWEEP_THREADS = 256;
+#ifndef ONESWEEP_MIN_CTAS
+#define ONESWEEP_MIN_CTAS 3
+#endif
 
 // Shared-memory layout of the persistent onesweep kernel: two tile buffers
 // (keys, then values, each with 16 bytes of alignment slack at both ends),
@@ -160,7 +167,7 @@ __host__ __device__ constexpr size_t onesweep_smem() {
 // IOTA: the values are the items' own global indices (first pass of a sort
 // that returns a permutation); `vin` is not read.
 template <typename K, typename V, bool IOTA>
-__global__ __launch_bounds__(ONESWEEP_THREADS, 3) void k_onesweep(
+__global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_onesweep(
     const K* __restrict__ kin, const V* __restrict__ vin, K* __restrict__ kout, V* __restrict__ vout,
     const u32* __restrict__ seg_off, const u32* __restrict__ range_off, int nseg, u32 range_items,
     const u32* __restrict__ digit_off, int npass, int pass, int shift, K keymask, u64* status, Ctl* ctl,

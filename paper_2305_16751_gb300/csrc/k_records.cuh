@@ -33,6 +33,18 @@ __device__ __forceinline__ void seg_publish_prefix(SegStatus<Acc>* s, u32 epoch,
     st_store_release(&s->flag, ((epoch & EPOCH_MASK) << 2) | ST_PREFIX);
 }
 template <typename Acc>
+__device__ __forceinline__ Acc shfl_xor_acc(Acc v, int o) {
+    if constexpr (sizeof(Acc) == 8) {
+        unsigned long long bits = *reinterpret_cast<unsigned long long*>(&v);
+        bits = __shfl_xor_sync(0xffffffffu, bits, o);
+        return *reinterpret_cast<Acc*>(&bits);
+    } else {
+        u32 bits = *reinterpret_cast<u32*>(&v);
+        bits = __shfl_xor_sync(0xffffffffu, bits, o);
+        return *reinterpret_cast<Acc*>(&bits);
+    }
+}
+template <typename Acc>
 __device__ __forceinline__ Acc volatile_read(const Acc* p) {
     Acc v;
     if constexpr (sizeof(Acc) == 8) {
@@ -62,8 +74,8 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys,
     typedef typename Op::Pay Pay;
     constexpr int TILE = THREADS * ITEMS, WARPS = THREADS / 32;
     const K role = K(1) << (sizeof(K) * 8 - 1);
-    __shared__ K s_keys[TILE];
-    __shared__ Pay s_pays[TILE];
+    __shared__ K s_keys[Padded<TILE>::value];
+    __shared__ Pay s_pays[Padded<TILE>::value];
     __shared__ Acc s_wacc[WARPS];
     __shared__ u32 s_whead[WARPS];
     __shared__ Acc s_excl;
@@ -80,8 +92,8 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys,
     for (int i = 0; i < ITEMS; ++i) {
         const u32 x = (u32)i * THREADS + threadIdx.x;
         if (L.start + x < L.end) {
-            s_keys[x] = keys[L.start + x];
-            s_pays[x] = pays[L.start + x];
+            s_keys[pidx(x)] = keys[L.start + x];
+            s_pays[pidx(x)] = pays[L.start + x];
         }
     }
     __syncthreads();
@@ -89,7 +101,7 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys,
     const u32 x0 = L.start + lx0;
     K prev = 0;
     bool has_prev = x0 > L.seg_begin;
-    if (has_prev && x0 < L.end) prev = lx0 == 0 ? keys[x0 - 1] : s_keys[lx0 - 1];
+    if (has_prev && x0 < L.end) prev = lx0 == 0 ? keys[x0 - 1] : s_keys[pidx(lx0 - 1)];
     prev &= ~role;
     // thread aggregate: (head seen, F over items after the last head)
     bool head_any = false;
@@ -98,7 +110,7 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys,
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         if (x0 + i < L.end) {
-            const K kx = s_keys[lx0 + i];
+            const K kx = s_keys[pidx(lx0 + i)];
             const K kn = kx & ~role;
             const bool head = !has_prev || kn != prev;
             has_prev = true;
@@ -108,7 +120,7 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys,
                 headmask |= 1u << i;
                 agg = Op::e();
             }
-            if (!(kx & role)) agg = Op::F(agg, Op::from_pay(s_pays[lx0 + i]));
+            if (!(kx & role)) agg = Op::F(agg, Op::from_pay(s_pays[pidx(lx0 + i)]));
         }
     }
     // block-wide exclusive scan of (head, agg) with the segmented operator
@@ -171,8 +183,12 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys,
     }
     Acc texcl = lhead ? lex : Op::F(wex, lex);  // within-tile exclusive prefix
     const bool texcl_head = lhead || wex_head;  // a head occurs before me in the tile
-    // tile aggregate, look-back and publication (thread 0)
-    if (threadIdx.x == 0) {
+    // tile aggregate, look-back and publication (warp 0).  The look-back is
+    // warp-cooperative: lane l examines tile u-1-l, so one round trip to L2
+    // covers 32 predecessors; the aggregates up to the first tile that ends
+    // the chain (a published prefix, or a segment head inside the tile) are
+    // combined with a masked warp reduction.
+    if (warp == 0) {
         Acc tagg = Op::e();
         bool thead = false;
         for (int w = 0; w < WARPS; ++w) {
@@ -184,41 +200,65 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys,
             }
         }
         SegStatus<Acc>* my = status + t;
-        const bool starts_fresh = L.first || (headmask & 1u);
+        const bool starts_fresh = L.first || (__shfl_sync(0xffffffffu, headmask, 0) & 1u);
         Acc excl = Op::e();
         if (starts_fresh) {
-            seg_publish_prefix(my, epoch, tagg);
+            if (lane == 0) seg_publish_prefix(my, epoch, tagg);
         } else {
-            seg_publish_agg(my, epoch, thead, tagg);
+            if (lane == 0) seg_publish_agg(my, epoch, thead, tagg);
             const u32 first_tile = t - (L.start - L.seg_begin) / (u32)TILE;
-            u32 u = t;
+            u32 u = t;  // tiles [u, t) have been combined into excl
+            u32 spins = 0;
             while (u > first_tile) {
-                --u;
-                const SegStatus<Acc>* ps = status + u;
-                u32 f, spins = 0;
-                for (;;) {
+                const bool exists = u - 1 - (u32)lane >= first_tile && (u32)lane < u - first_tile;
+                u32 f = 0, hh = 0;
+                Acc v = Op::e();
+                bool ready = true, term = false;
+                if (exists) {
+                    const SegStatus<Acc>* ps = status + (u - 1 - lane);
                     f = st_load_acquire(&ps->flag);
-                    if ((f >> 2) == (epoch & EPOCH_MASK) && (f & 3u)) break;
+                    ready = (f >> 2) == (epoch & EPOCH_MASK) && (f & 3u);
+                    if (ready) {
+                        if ((f & 3u) == ST_PREFIX) {
+                            v = volatile_read(&ps->incl);
+                            term = true;
+                        } else {
+                            hh = *reinterpret_cast<const volatile u32*>(&ps->has_head);
+                            v = volatile_read(&ps->agg);
+                            term = hh != 0;
+                        }
+                    }
+                } else {
+                    ready = false;  // beyond the chain start: never consumed
+                }
+                const u32 nr = __ballot_sync(0xffffffffu, !ready);
+                const u32 tm = __ballot_sync(0xffffffffu, term);
+                const int k_nr = nr ? __ffs(nr) - 1 : 32;
+                const int k_tm = tm ? __ffs(tm) - 1 : 32;
+                const bool finish = k_tm < k_nr;
+                const int take = finish ? k_tm + 1 : k_nr;  // lanes [0, take) are combined
+                if (take > 0) {
+                    Acc r = lane < take ? v : Op::e();
+#pragma unroll
+                    for (int o = 16; o >= 1; o >>= 1) r = Op::F(r, shfl_xor_acc(r, o));
+                    excl = Op::F(r, excl);
+                    u -= (u32)take;
+                }
+                if (finish) break;
+                if (take == 0) {
                     if (++spins > SPIN_LIMIT || ((spins & 255u) == 0 && timed_out(ctl))) {
-                        atomicOr(&ctl->error, ERR_TIMEOUT);
-                        ctl->timeout_where = 4u;
-                        spins = SPIN_LIMIT + 1;
+                        if (lane == 0) {
+                            atomicOr(&ctl->error, ERR_TIMEOUT);
+                            ctl->timeout_where = 4u;
+                        }
                         break;
                     }
                     if (spins > 64) __nanosleep(256);
                 }
-                if (spins > SPIN_LIMIT) break;
-                if ((f & 3u) == ST_PREFIX) {
-                    excl = Op::F(volatile_read(&ps->incl), excl);
-                    break;
-                }
-                const u32 hh = *reinterpret_cast<const volatile u32*>(&ps->has_head);
-                excl = Op::F(volatile_read(&ps->agg), excl);
-                if (hh) break;
             }
-            seg_publish_prefix(my, epoch, thead ? tagg : Op::F(excl, tagg));
+            if (lane == 0) seg_publish_prefix(my, epoch, thead ? tagg : Op::F(excl, tagg));
         }
-        s_excl = excl;
+        if (lane == 0) s_excl = excl;
     }
     __syncthreads();
     Acc run = texcl_head ? texcl : Op::F(s_excl, texcl);
@@ -226,8 +266,8 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys,
     for (int i = 0; i < ITEMS; ++i) {
         if (x0 + i < L.end) {
             if (headmask & (1u << i)) run = Op::e();
-            const K kx = s_keys[lx0 + i];
-            const Pay py = s_pays[lx0 + i];
+            const K kx = s_keys[pidx(lx0 + i)];
+            const Pay py = s_pays[pidx(lx0 + i)];
             if (kx & role) {
                 const u64 slot = (u64)py;
                 if (slot < n_partial) partial[slot] = Op::to_part(run);
