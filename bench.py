@@ -113,6 +113,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def profiled_traffic(records: int):
+    """DRAM bytes of one records radix pass, from the committed ncu summary
+    (bytes per record, scaled to this workload's record count); None if the
+    kernel source changed since that capture."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2305_16751_gb300", "csrc", "k_radix.cuh")
+    prof = os.path.join(ROOT, "profiles", "k_onesweep_records_m2_n2e22.md")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        fields = dict(ln.split(":", 1) for ln in open(prof) if ln.startswith(("kernel_source", "traffic_bytes")))
+    except (OSError, ValueError):
+        return None
+    if fields.get("kernel_source_sha256_16", "").strip() != digest:
+        return None
+    return float(fields["traffic_bytes_per_record"]) * records
+
+
 def cpu_baseline(p, seconds: float):
     """The oracle as it stands (brute force by the definition, OpenMP over
     queries) on a bounded sample of the workload's queries against all data."""
@@ -239,7 +256,8 @@ def main():
                        "records": st["n_records"], "record_passes": st["record_passes"],
                        "l2": "inputs (320 MB) and workspace (>6 GB) exceed the 129 MB L2; no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                         "frac": achieved / peak, "traffic": profiled_traffic(st["n_records"]),
+                         "peak_source": peak_src,
                          "kernel": "k_onesweep (records radix pass)",
                          "launch_ms": dom["ms"] / max(dom["launches"], 1),
                          "bytes_per_launch": dom["bytes"] / max(dom["launches"], 1)},
