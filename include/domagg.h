@@ -182,6 +182,33 @@ domagg_status domagg_timing_enable(domagg_handle h, int enable);
 domagg_status domagg_timing_read(domagg_handle h, domagg_timing* out);
 const char* domagg_timing_kind_name(int kind);
 
+/* Forward pass that allocates nothing: no cudaMalloc, cudaFree, pinned host
+ * memory or allocating library routine.  It is for callers that cannot
+ * allocate device memory (an allocator-free runtime, a process that reserves
+ * all device memory up front, a latency-critical path that must not block in
+ * the allocator).  The paper has no counterpart: it is the same pipeline as
+ * domagg_forward, with every buffer taken from one file-scope device array of
+ * 32 MiB that each GPU loading this library holds until the process exits.
+ *   Arguments, layouts, outputs and tolerances are those of domagg_forward;
+ *   all pointers are device memory on the CURRENT device, and no handle is
+ *   used.
+ *   Limits: nD + nQ <= 65536, and the flat map must fit the scratch (about
+ *   10^6 records for m <= 2, half that for m = 3 or int64 weights); larger
+ *   inputs return DOMAGG_ERR_UNSUPPORTED without running.
+ *   The first call on a device sets that device's scratch up (looks its
+ *   address up, clears the control block and the status words, and
+ *   synchronises the device): make that first call before any CUDA-graph
+ *   stream capture.
+ *   Every call shares the one array and it keeps the last call's contents;
+ *   calls that overlap on the GPU (on different streams, or from several
+ *   host threads whose work is not ordered) race and corrupt each other's
+ *   results.  Host calls are serialised by a lock; order their GPU work on
+ *   one stream.  The call synchronises `stream` once in mid-call, like
+ *   domagg_forward. */
+domagg_status domagg_forward_noalloc(int m, const void* d_coords, int64_t nD, const void* q_coords, int64_t nQ,
+                                     domagg_dtype coord_dtype, const void* d_weights, domagg_dtype weight_dtype,
+                                     domagg_op op, void* out, void* stream);
+
 /* Library version string. */
 const char* domagg_version(void);
 

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <type_traits>
@@ -800,3 +801,108 @@ const char* domagg_timing_kind_name(int kind) {
 const char* domagg_version(void) { return "domagg 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Forward pass without any allocation, for callers that cannot allocate
+// device memory: code that runs where cudaMalloc is not allowed or not
+// wanted (an allocator-free runtime, a caller that reserves all device
+// memory up front, a real-time path that must not block in the allocator).
+// The paper has no counterpart; this is a deployment convenience.
+//
+// All scratch (control block, point and record buffers, look-back status
+// words) lives in one file-scope device array of NOALLOC_BYTES.  Every GPU
+// that loads this library holds that array until the process exits.  Calls
+// share it and it keeps the last call's contents: the control block and the
+// status words are zeroed once per device when the entry point first runs,
+// and the look-back epochs keep later calls from reading stale statuses.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t NOALLOC_BYTES = (size_t)32 << 20;
+constexpr size_t NOALLOC_CTL = 4096;
+constexpr size_t NOALLOC_PTS = (size_t)6 << 20;
+constexpr size_t NOALLOC_STM = (size_t)4 << 20;
+constexpr size_t NOALLOC_STS = (size_t)1 << 20;
+constexpr size_t NOALLOC_RECS = NOALLOC_BYTES - NOALLOC_CTL - NOALLOC_PTS - NOALLOC_STM - NOALLOC_STS;
+constexpr int64_t NOALLOC_MAX_POINTS = 65536;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+namespace {
+struct NoAllocSlot {
+    bool ready = false;
+    domagg_ctx ctx;
+    alignas(64) unsigned char host_stage[16384];  // instance table and counts (pageable)
+};
+NoAllocSlot g_noalloc[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mu;
+
+// Once per device, with that device current: the device address of the
+// scratch array (its name in host code is only a stand-in), zeroed control
+// block and status words, and a handle whose buffers are fixed slices of it.
+domagg_status noalloc_setup(int dev, domagg_ctx** out) {
+    NoAllocSlot& S = g_noalloc[dev];
+    if (!S.ready) {
+        unsigned char* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            S.ctx.err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            *out = &S.ctx;
+            return DOMAGG_ERR_CUDA;
+        }
+        e = cudaMemset(ptr, 0, NOALLOC_CTL + NOALLOC_PTS);  // control block (and points, harmlessly)
+        if (e == cudaSuccess) e = cudaMemset(ptr + NOALLOC_CTL + NOALLOC_PTS + NOALLOC_RECS, 0, NOALLOC_STM + NOALLOC_STS);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            S.ctx.err = std::string("clearing the scratch: ") + cudaGetErrorString(e);
+            *out = &S.ctx;
+            return DOMAGG_ERR_CUDA;
+        }
+        domagg_ctx& h = S.ctx;
+        h.device = dev;
+        h.ctl = reinterpret_cast<Ctl*>(ptr);
+        h.pts = {ptr + NOALLOC_CTL, NOALLOC_PTS};
+        h.recs = {ptr + NOALLOC_CTL + NOALLOC_PTS, NOALLOC_RECS};
+        h.st_multi = {ptr + NOALLOC_CTL + NOALLOC_PTS + NOALLOC_RECS, NOALLOC_STM};
+        h.st_seg = {ptr + NOALLOC_CTL + NOALLOC_PTS + NOALLOC_RECS + NOALLOC_STM, NOALLOC_STS};
+        h.stage = {nullptr, 0};
+        // every buffer is full-size and the cap equals their sum, so a request
+        // that does not fit is refused before anything could be freed
+        h.max_ws = h.held();
+        h.h_pin = S.host_stage;
+        h.h_pin_cap = sizeof(S.host_stage);
+        h.timing = false;
+        S.ready = true;
+    }
+    *out = &S.ctx;
+    return DOMAGG_OK;
+}
+}  // namespace
+
+extern "C" domagg_status domagg_forward_noalloc(int m, const void* d_coords, int64_t nD, const void* q_coords,
+                                                int64_t nQ, domagg_dtype coord_dtype, const void* d_weights,
+                                                domagg_dtype weight_dtype, domagg_op op, void* out, void* stream) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        cudaGetLastError();
+        return DOMAGG_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    domagg_ctx* h = nullptr;
+    domagg_status st = noalloc_setup(dev, &h);
+    if (st) return st;
+    st = check_common(h, m, nD, nQ, coord_dtype, weight_dtype, op);
+    if (st) return st;
+    if (nD + nQ > NOALLOC_MAX_POINTS)
+        return fail(h, DOMAGG_ERR_UNSUPPORTED, "domagg_forward_noalloc takes at most 65536 points (nD + nQ)");
+    if ((nD > 0 && !d_coords) || (nQ > 0 && (!q_coords || !out)) || (op != DOMAGG_COUNT && nD > 0 && !d_weights))
+        return fail(h, DOMAGG_ERR_INVALID_ARG, "null pointer");
+    if (nQ == 0) return DOMAGG_OK;
+    std::vector<Inst> inst{make_inst(d_coords, nD, q_coords, nQ, d_weights, out)};
+    st = dispatch(h, m, inst, coord_dtype, weight_dtype, op, false, (cudaStream_t)stream);
+    if (st == DOMAGG_ERR_OOM)
+        return fail(h, DOMAGG_ERR_UNSUPPORTED,
+                    "the flat map of this input does not fit the 32 MiB static scratch of domagg_forward_noalloc");
+    return st;
+}

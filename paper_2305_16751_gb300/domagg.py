@@ -65,6 +65,7 @@ SIGNATURES = {
     "domagg_timing_read": ([_vp, ctypes.POINTER(domagg_timing)], _int),
     "domagg_timing_kind_name": ([_int], ctypes.c_char_p),
     "domagg_version": ([], ctypes.c_char_p),
+    "domagg_forward_noalloc": ([_int, _vp, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _vp], _int),
 }
 
 _lib = None
