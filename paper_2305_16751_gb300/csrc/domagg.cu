@@ -187,12 +187,13 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     const int k = (int)inst.size();
 
     // ---- host-side layout of the point space
-    std::vector<u32> pt_offs(k + 1), q_offs(k + 1);
+    std::vector<u32> pt_offs(k + 1), q_offs(k + 1), chunk_off(k + 1);
     std::vector<u64> pt_sizes(k);
-    u64 N = 0, NQ = 0, ntp = 0;
+    u64 N = 0, NQ = 0, ntp = 0, NC = 0;
     for (int s = 0; s < k; ++s) {
         pt_offs[s] = (u32)N;
         q_offs[s] = (u32)NQ;
+        chunk_off[s] = (u32)NC;
         inst[s].pt_off = (u32)N;
         inst[s].q_off = (u32)NQ;
         inst[s].U[0] = inst[s].U[1] = inst[s].b[0] = inst[s].b[1] = 0;
@@ -201,10 +202,12 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         pt_sizes[s] = n;
         N += n;
         NQ += inst[s].nQ;
+        NC += (n + 31) / 32;
         ntp += (n + POINT_TILE - 1) / POINT_TILE;
     }
     pt_offs[k] = (u32)N;
     q_offs[k] = (u32)NQ;
+    chunk_off[k] = (u32)NC;
     if (N >= (1ull << 31)) return fail(h, DOMAGG_ERR_UNSUPPORTED, "more than 2^31 points in one call");
     if (NQ == 0) return DOMAGG_OK;
 
@@ -225,15 +228,17 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         P[12] = c.take<u32>(M >= 2 ? N : 0);  // pr0
         P[13] = c.take<u32>(M >= 3 ? N : 0);  // pr1
         P[14] = c.take<u32>(N);     // pj
-        P[15] = c.take<u32>(N);     // poff
-        P[16] = c.take<u32>(N);     // pqoff
-        P[17] = c.take<u32>(NQ);    // qslot
-        P[18] = c.take<u32>(NQ);    // qidx
+        P[15] = c.take<u32>(k + 1);  // chunk offsets
+        P[16] = c.take<u32>((size_t)NC * LMAX);  // query chunk bases per level
+        P[17] = c.take<u32>((size_t)k * LMAX);   // query records per (instance, level)
+        P[18] = nullptr;
         P[19] = c.take<u32>((size_t)k * 4 * RADIX);  // hist
         P[20] = c.take<u32>((size_t)k * 4 * RADIX);  // digit offsets
         P[21] = c.take<u32>(k + 1);                  // the sorts' tile map
+        P[22] = c.take<u32>((size_t)NC * LMAX);      // chunk bases per level
+        P[23] = c.take<u32>((size_t)k * LMAX);       // records per (instance, level)
     };
-    void* P[22];
+    void* P[24];
     {
         Carver c(nullptr);
         carve_points(c, P);
@@ -246,9 +251,11 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     u32 *d_pt_offs = (u32*)P[1], *d_q_offs = (u32*)P[2], *d_pt_tiles = (u32*)P[3];
     u32 *rk0 = (u32*)P[4], *rk1 = (u32*)P[5], *lk = (u32*)P[6], *kalt = (u32*)P[7];
     u32 *vA = (u32*)P[8], *vB = (u32*)P[9], *r0 = (u32*)P[10], *r1 = (u32*)P[11];
-    u32 *pr0 = (u32*)P[12], *pr1 = (u32*)P[13], *pj = (u32*)P[14], *poff = (u32*)P[15], *pqoff = (u32*)P[16];
-    u32 *qslot = (u32*)P[17], *qidx = (u32*)P[18], *hist = (u32*)P[19], *digit_off = (u32*)P[20];
+    u32 *pr0 = (u32*)P[12], *pr1 = (u32*)P[13], *pj = (u32*)P[14], *d_chunk_off = (u32*)P[15];
+    u32 *qchunk_base = (u32*)P[16], *qlvl_tot = (u32*)P[17];
+    u32 *hist = (u32*)P[19], *digit_off = (u32*)P[20];
     u32* d_sort_tiles = (u32*)P[21];
+    u32 *chunk_base = (u32*)P[22], *lvl_tot = (u32*)P[23];
 
     // status words: point tiles x 256 digits (the records sort grows it later)
     {
@@ -258,18 +265,23 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     }
 
     // ---- upload the instance table and offsets
-    const size_t up_bytes = sizeof(Inst) * k + 2 * sizeof(u32) * (k + 1);
+    const size_t up_bytes = sizeof(Inst) * k + 3 * sizeof(u32) * (k + 1);
+    const size_t lvl_pos = (up_bytes + 63) & ~(size_t)63;                          // level totals (read back)
+    const size_t ctl_pos = (lvl_pos + 2 * sizeof(u32) * k * LMAX + 63) & ~(size_t)63;  // control block (read back)
     {
-        domagg_status st = grow_pinned(h, up_bytes + sizeof(Ctl) + 64);
+        domagg_status st = grow_pinned(h, ctl_pos + sizeof(Ctl) + 64);
         if (st) return st;
     }
     char* hp = (char*)h->h_pin;
     memcpy(hp, inst.data(), sizeof(Inst) * k);
     memcpy(hp + sizeof(Inst) * k, pt_offs.data(), sizeof(u32) * (k + 1));
     memcpy(hp + sizeof(Inst) * k + sizeof(u32) * (k + 1), q_offs.data(), sizeof(u32) * (k + 1));
+    memcpy(hp + sizeof(Inst) * k + 2 * sizeof(u32) * (k + 1), chunk_off.data(), sizeof(u32) * (k + 1));
     cudaMemcpyAsync(d_inst, hp, sizeof(Inst) * k, cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(d_pt_offs, hp + sizeof(Inst) * k, sizeof(u32) * (k + 1), cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(d_q_offs, hp + sizeof(Inst) * k + sizeof(u32) * (k + 1), sizeof(u32) * (k + 1),
+                    cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(d_chunk_off, hp + sizeof(Inst) * k + 2 * sizeof(u32) * (k + 1), sizeof(u32) * (k + 1),
                     cudaMemcpyHostToDevice, stream);
 
     maybe_reset_epochs(h, stream);
@@ -319,20 +331,23 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                                              KIND_SORT_POINTS);
         perm = vals[cur];
     }
-    // ---- count / offset scan of the flat map
+    // ---- count / offset scan of the flat map, per level
     {
         const int li = L.lookback_index();
-        L.start(KIND_COUNT_SCAN, (double)N * (4 + 4 * (M - 1) + 4 * (M - 1) + 16));
-        k_count_scan<M, SCAN_THREADS, SCAN_ITEMS><<<(unsigned)ntp, SCAN_THREADS, 0, stream>>>(
-            perm, d_pt_offs, d_pt_tiles, k, r0, r1, d_inst, d_q_offs, pr0, pr1, pj, poff, pqoff, qslot, qidx,
-            (u64*)h->st_multi.p, h->ctl, li);
+        L.start(KIND_COUNT_SCAN, (double)N * (4 + 4 * (M - 1) + 4 * (M - 1) + 4) + (double)NC * 8 * LMAX);
+        k_count_scan<M><<<(unsigned)ntp, 256, 0, stream>>>(perm, d_pt_offs, d_pt_tiles, k, d_chunk_off, r0, r1, d_inst,
+                                                           pr0, pr1, pj, chunk_base, qchunk_base, lvl_tot, qlvl_tot,
+                                                           (u64*)h->st_multi.p, h->ctl, li);
         L.stop();
     }
     // ---- the one synchronisation: record counts and device errors
     Inst* h_inst = (Inst*)hp;
-    Ctl* h_ctl = (Ctl*)(hp + ((up_bytes + 63) & ~(size_t)63));
+    u32* h_lvl = (u32*)(hp + lvl_pos);
+    Ctl* h_ctl = (Ctl*)(hp + ctl_pos);
     L.start(KIND_D2H, 0.0);
     cudaMemcpyAsync(h_inst, d_inst, sizeof(Inst) * k, cudaMemcpyDeviceToHost, stream);
+    cudaMemcpyAsync(h_lvl, lvl_tot, sizeof(u32) * k * LMAX, cudaMemcpyDeviceToHost, stream);
+    cudaMemcpyAsync(h_lvl + (size_t)k * LMAX, qlvl_tot, sizeof(u32) * k * LMAX, cudaMemcpyDeviceToHost, stream);
     cudaMemcpyAsync(h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream);
     L.stop();
     cudaError_t e = cudaStreamSynchronize(stream);
@@ -343,38 +358,61 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         cudaStreamSynchronize(stream);
         return device_error(h, bits);
     }
-    for (int s = 0; s < k; ++s) inst[s] = h_inst[s];
+    // per instance: its levels, their record counts and sort-key bits
+    std::vector<u32> nlev(k), lvl(h_lvl, h_lvl + (size_t)k * LMAX), qlvl(h_lvl + (size_t)k * LMAX, h_lvl + (size_t)2 * k * LMAX);
+    for (int s = 0; s < k; ++s) {
+        inst[s] = h_inst[s];
+        nlev[s] = inst[s].nQ + inst[s].nD == 0 ? 0u : (M == 1 ? 1u : inst[s].b[0]);
+        u64 T = 0, Tq = 0;
+        for (u32 lv = 0; lv < nlev[s]; ++lv) {
+            T += lvl[(size_t)s * LMAX + lv];
+            Tq += qlvl[(size_t)s * LMAX + lv];
+        }
+        if (T >= (1ull << 32)) return fail(h, DOMAGG_ERR_UNSUPPORTED, "more than 2^32 flat-map records");
+        inst[s].T = (u32)T;
+        inst[s].Tq = (u32)Tq;
+    }
+    auto level_bits = [&](int s, u32 lv) -> u32 {
+        if (M == 1) return 0u;
+        const u32 b = inst[s].b[0] - 1u - lv;  // prefix length of level lv
+        return M == 2 ? b : b + inst[s].b[1];
+    };
 
     // ---- plan chunks of instances whose records fit one record workspace
     struct Chunk {
         int k0, k1;
-        u64 T, Tq;
+        u64 T, Tq, nseg;
         int key_bits;
     };
     std::vector<Chunk> chunks;
     const u64 chunk_cap = (1ull << 32) - 65536;
     {
-        Chunk c{0, 0, 0, 0, 0};
+        Chunk c{0, 0, 0, 0, 0, 0};
         for (int s = 0; s < k; ++s) {
             const u64 Ts = inst[s].T;
             if (c.k1 > c.k0 && c.T + Ts > chunk_cap) {
                 chunks.push_back(c);
-                c = Chunk{s, s, 0, 0, 0};
+                c = Chunk{s, s, 0, 0, 0, 0};
             }
             c.k1 = s + 1;
             c.T += Ts;
             c.Tq += inst[s].Tq;
-            const int kb = (M >= 2 ? (int)inst[s].b[0] : 0) + (M >= 3 ? (int)inst[s].b[1] : 0);
-            c.key_bits = std::max(c.key_bits, kb);
+            c.nseg += nlev[s];
+            for (u32 lv = 0; lv < nlev[s]; ++lv) c.key_bits = std::max(c.key_bits, (int)level_bits(s, lv));
         }
         if (c.k1 > c.k0) chunks.push_back(c);
     }
-    // pinned bases of every chunk, uploaded per chunk
+    // pinned upload area of every chunk: per instance record and slot bases,
+    // per segment offsets and key bits, per (instance, level) segment bases
+    auto chunk_upload_words = [&](const Chunk& c) -> size_t {
+        const size_t kc = (size_t)(c.k1 - c.k0);
+        return 2 * (kc + 1) + (c.nseg + 1) + c.nseg + 2 * kc * LMAX;
+    };
     std::vector<size_t> base_pos(chunks.size());
-    size_t pin_need = ((up_bytes + 63) & ~(size_t)63) + sizeof(Ctl);
+    size_t pin_need = ctl_pos + sizeof(Ctl);
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
         base_pos[ci] = (pin_need + 63) & ~(size_t)63;
-        pin_need = base_pos[ci] + 2 * sizeof(u32) * (chunks[ci].k1 - chunks[ci].k0 + 1);
+        pin_need = base_pos[ci] + sizeof(u32) * chunk_upload_words(chunks[ci]);
     }
     if (pin_need > h->h_pin_cap) {
         // grow_pinned keeps nothing; the instance table is already in `inst`
@@ -388,36 +426,56 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
         const Chunk& C = chunks[ci];
         const int kc = C.k1 - C.k0;
+        const u64 nseg = C.nseg;
         u32* hb = (u32*)(hp + base_pos[ci]);
-        u64 ntr = 0, nts = 0;
-        std::vector<u64> rec_sizes(kc);
+        u32* h_rb = hb;                      // [kc+1] record base per instance
+        u32* h_qb = hb + kc + 1;             // [kc+1] query-slot base per instance
+        u32* h_so = h_qb + kc + 1;           // [nseg+1] segment offsets
+        u32* h_sbits = h_so + nseg + 1;      // [nseg] segment key bits
+        u32* h_sbase = h_sbits + nseg;       // [kc][LMAX] segment base per (instance, level)
+        u32* h_qsbase = h_sbase + (size_t)kc * LMAX;  // [kc][LMAX] query-slot base per (instance, level)
+        std::vector<u64> seg_sizes(nseg);
+        u64 nts = 0;
         {
-            u64 a = 0, b = 0;
+            u64 a = 0, b = 0, sg = 0;
             for (int s = C.k0; s < C.k1; ++s) {
-                hb[s - C.k0] = (u32)a;
-                hb[kc + 1 + s - C.k0] = (u32)b;
-                a += inst[s].T;
-                b += inst[s].Tq;
-                rec_sizes[s - C.k0] = inst[s].T;
-                ntr += (inst[s].T + SORT_MIN_TILE - 1) / SORT_MIN_TILE;
-                nts += (inst[s].T + SEG_TILE - 1) / SEG_TILE;
+                h_rb[s - C.k0] = (u32)a;
+                h_qb[s - C.k0] = (u32)b;
+                for (u32 lv = 0; lv < LMAX; ++lv) {
+                    h_sbase[(size_t)(s - C.k0) * LMAX + lv] = 0;
+                    h_qsbase[(size_t)(s - C.k0) * LMAX + lv] = 0;
+                }
+                for (u32 lv = 0; lv < nlev[s]; ++lv) {
+                    const u64 sz = lvl[(size_t)s * LMAX + lv];
+                    h_so[sg] = (u32)a;
+                    h_sbits[sg] = level_bits(s, lv);
+                    h_sbase[(size_t)(s - C.k0) * LMAX + lv] = (u32)a;
+                    h_qsbase[(size_t)(s - C.k0) * LMAX + lv] = (u32)b;
+                    seg_sizes[sg] = sz;
+                    nts += (sz + SEG_TILE - 1) / SEG_TILE;
+                    a += sz;
+                    b += qlvl[(size_t)s * LMAX + lv];
+                    ++sg;
+                }
             }
-            hb[kc] = (u32)a;
-            hb[kc + 1 + kc] = (u32)b;
+            h_rb[kc] = (u32)a;
+            h_qb[kc] = (u32)b;
+            h_so[nseg] = (u32)a;
         }
         const int npass = (C.key_bits + RADIX_BITS - 1) / RADIX_BITS;
+        const u64 ntr = tiles_of(seg_sizes, SORT_MIN_TILE);
         // record workspace
         auto carve_recs = [&](Carver& c, void** R) {
-            R[0] = c.take<u32>(2 * (kc + 1));  // rec_base, qrec_base
-            R[1] = c.take<u32>(kc + 1);        // sort tiles
-            R[2] = c.take<u32>(kc + 1);        // segscan tiles
+            R[0] = c.take<u32>(chunk_upload_words(C));  // the uploaded bases and segment tables
+            R[1] = c.take<u32>(nseg + 1);                // sort ranges
+            R[2] = c.take<u32>(nseg + 1);                // segscan tiles
             R[3] = c.take<K>(C.T);
             R[4] = c.take<K>(C.T);
             R[5] = c.take<Pay>(C.T);
             R[6] = c.take<Pay>(C.T);
             R[7] = c.take<Part>(C.Tq);
-            R[8] = c.take<u32>((size_t)kc * std::max(npass, 1) * RADIX);
-            R[9] = c.take<u32>((size_t)kc * std::max(npass, 1) * RADIX);
+            R[8] = c.take<u32>((size_t)nseg * std::max(npass, 1) * RADIX);
+            R[9] = c.take<u32>((size_t)nseg * std::max(npass, 1) * RADIX);
         };
         void* R[10];
         {
@@ -432,13 +490,17 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             st = grow(h, h->st_seg, (size_t)std::max<u64>(nts, 1) * sizeof(SegStatus<typename Op::Acc>), true);
             if (st) return st;
         }
-        u32* d_rb = (u32*)R[0];
-        u32* d_qb = d_rb + kc + 1;
+        u32* d_up = (u32*)R[0];
+        u32* d_qb = d_up + kc + 1;
+        u32* d_so = d_qb + kc + 1;
+        u32* d_sbits = d_so + nseg + 1;
+        u32* d_sbase = d_sbits + nseg;
+        u32* d_qsbase = d_sbase + (size_t)kc * LMAX;
         u32 *d_rtiles = (u32*)R[1], *d_stiles = (u32*)R[2];
         K* keys[2] = {(K*)R[3], (K*)R[4]};
         Pay* pays[2] = {(Pay*)R[5], (Pay*)R[6]};
         Part* partial = (Part*)R[7];
-        cudaMemcpyAsync(d_rb, hb, 2 * sizeof(u32) * (kc + 1), cudaMemcpyHostToDevice, stream);
+        cudaMemcpyAsync(d_up, hb, sizeof(u32) * chunk_upload_words(C), cudaMemcpyHostToDevice, stream);
         // fresh epoch and tile counters for the record phase of this chunk
         maybe_reset_epochs(h, stream);
         L.start(KIND_SMALL, 0.0);
@@ -447,54 +509,52 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         h->epoch_mirror += MAX_LAUNCHES;
         L.next_lookback = 0;
         L.start(KIND_SMALL, 0.0);
-        k_make_tiles<<<1, 1024, 0, stream>>>(d_rb, kc, SEG_TILE, d_stiles);
+        k_make_tiles<<<1, 1024, 0, stream>>>(d_so, (int)nseg, SEG_TILE, d_stiles);
         L.stop();
 
-        // flat map (6m+1)
-        const u32 p_begin = pt_offs[C.k0], p_end = pt_offs[C.k1];
+        // flat map (6m+1), level by level
+        const u64 nchunk = chunk_off[C.k1] - chunk_off[C.k0];
         if (C.T > 0) {
-            const u64 warps = (p_end - p_begin + 31) / 32;
-            const unsigned grid = (unsigned)std::min<u64>((warps + 7) / 8, 152ull * 16);
-            const int esmem = (EXPAND_THREADS / 32) * EXPAND_STAGE_BYTES;
-            cudaFuncSetAttribute(k_expand<M, K, Pay, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, esmem);
-            L.start(KIND_EXPAND, (double)(p_end - p_begin) * (4.0 * (M - 1) + 12) +
+            const unsigned grid = (unsigned)std::min<u64>((nchunk + 7) / 8, 152ull * 16);
+            L.start(KIND_EXPAND, (double)(pt_offs[C.k1] - pt_offs[C.k0]) * (4.0 * (M - 1) + 12) +
                                      (double)C.T * (sizeof(K) + sizeof(Pay)));
-            k_expand<M, K, Pay, WT><<<grid, EXPAND_THREADS, esmem, stream>>>(p_begin, p_end, pr0, pr1, pj, poff, pqoff, d_inst,
-                                                             d_pt_offs, k, d_rb, d_qb, C.k0, (u32)C.T, keys[0],
-                                                             pays[0]);
+            k_expand<M, K, Pay, WT><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pj,
+                                                             chunk_base, qchunk_base, d_inst, d_sbase, d_qsbase,
+                                                             (u32)C.T, keys[0], pays[0]);
             L.stop();
         }
-        // records sort (6m+2): stable, by node key only
-        int cur = 0;
+        // records sort (6m+2): stable, each level by the bits of its prefix
         if (C.T > 0 && npass > 0) {
-            SortSpace rs{d_rb, kc, &rec_sizes, d_rtiles, (u32*)R[8], (u32*)R[9], (u64*)h->st_multi.p, (double)C.T};
-            const K keymask = (C.key_bits >= (int)(8 * sizeof(K))) ? ~K(0) : ((K(1) << C.key_bits) - 1);
-            cur = sort_pairs<K, Pay>(L, rs, keys, pays, false, C.key_bits, keymask, KIND_HIST_RECORDS,
-                                     KIND_SORT_RECORDS);
+            SortSpace rs{d_so, (int)nseg, &seg_sizes, d_rtiles, (u32*)R[8], (u32*)R[9], (u64*)h->st_multi.p,
+                         (double)C.T};
+            const K keymask = ~(K(1) << (sizeof(K) * 8 - 1));  // all but the role bit
+            sort_pairs<K, Pay>(L, rs, keys, pays, false, C.key_bits, keymask, KIND_HIST_RECORDS, KIND_SORT_RECORDS,
+                               d_sbits);
         }
         // segmented scan (6m+3)
         if (C.T > 0) {
             const int li = L.lookback_index();
             L.start(KIND_SEGSCAN, (double)C.T * (sizeof(K) + sizeof(Pay)) + (double)C.Tq * sizeof(Part));
             k_segscan<Op, K, SEG_THREADS, SEG_ITEMS><<<(unsigned)nts, SEG_THREADS, 0, stream>>>(
-                keys[cur], pays[cur], d_rb, d_stiles, kc, partial, (u32)C.Tq,
+                keys[0], keys[1], pays[0], pays[1], d_so, d_stiles, (int)nseg, d_sbits, partial, (u32)C.Tq,
                 (SegStatus<typename Op::Acc>*)h->st_seg.p, h->ctl, li);
             L.stop();
         }
         // per-query reduction (replaces 6m+4 .. 6m+9)
         const u32 qb = q_offs[C.k0], qe = q_offs[C.k1];
         if (qe > qb) {
+            const unsigned grid = (unsigned)std::min<u64>((nchunk + 7) / 8, 152ull * 16);
             L.start(KIND_REDUCE, (double)C.Tq * sizeof(Part) + (double)(qe - qb) * (8 + sizeof(typename Op::Out)));
-            k_reduce<Op><<<(qe - qb + 255) / 256, 256, 0, stream>>>(qb, qe, qslot, qidx, partial, (u32)C.Tq,
-                                                                   d_q_offs, k, d_inst, d_qb, C.k0);
+            k_reduce<Op, M><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pj,
+                                                      qchunk_base, d_qsbase, d_inst, partial, (u32)C.Tq);
             L.stop();
         }
-            T_all += C.T;
+        T_all += C.T;
         Tq_all += C.Tq;
         kb_all = std::max(kb_all, C.key_bits);
         passes_all = std::max(passes_all, npass);
         if (chunks.size() > 1) {
-            e = cudaStreamSynchronize(stream);  // the next chunk reuses the pinned bases region
+            e = cudaStreamSynchronize(stream);  // the next chunk reuses the record workspace's tables
             if (e != cudaSuccess) return cuda_fail(h, e, "record phase");
         }
     }

@@ -108,8 +108,11 @@ constexpr u32 POINT_TILE = 4096;
 // (key & keymask), segment by segment.  keys[0]/vals[0] hold the input;
 // returns the index (0 or 1) of the buffers that hold the result.  With
 // iota, the input values are the items' global indices (vals[0] unused).
+// With seg_bits (device, one entry per segment), segment s is sorted by its
+// first seg_bits[s] bits only and its result is in buffer
+// ceil(seg_bits[s] / 8) % 2; the return value is then meaningless.
 template <typename K, typename V>
 int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool iota, int total_bits, K keymask,
-               int kind_hist, int kind_pass);
+               int kind_hist, int kind_pass, const u32* seg_bits = nullptr);
 
 }  // namespace domagg

@@ -219,24 +219,43 @@ __device__ __forceinline__ u32 record_count(u32 bits0, u32 bits1) {
     return (u32)__popc(bits0) * (u32)__popc(bits1);
 }
 
+// Levels of the flat map (Sec. 5 records, grouped by the level of their
+// first node).  A record of the first rank dimension at bit position j
+// (prefix length b0-1-j) belongs to level j.  Records are laid out level
+// by level (per instance); inside a level they keep the order of the last
+// coordinate, and the sort then only needs the bits of the prefix.  m = 1
+// has a single level holding every point.
+constexpr int LMAX = 32;
+
+template <int M>
+__device__ __forceinline__ u32 levels_of(const Inst& I) {
+    return M == 1 ? 1u : I.b[0];
+}
+
 // Count and offset scan of the flat map, in the order of the last
-// coordinate (points were sorted by it, queries first on ties).  Per
-// instance (segmented chains) it scans three counters: records, query
-// records (= partial slots) and query points.  Writes the point's ranks,
-// index and offsets in this order, and per query (in this order) its slot
-// base and its index in Q.  The instance's last tile stores T and Tq.
-template <int M, int THREADS, int ITEMS>
-__global__ __launch_bounds__(THREADS) void k_count_scan(
+// coordinate (points were sorted by it, queries first on ties).  Tiles of
+// 4096 points never straddle an instance; every warp walks 16 chunks of 32
+// consecutive points.  Per instance (segmented look-back chains) it scans
+// 2 x LMAX counters: the records of every level, and the query records
+// (= partial slots) of every level.  Writes, in this order, the point's
+// ranks and index; per chunk of 32 points the exclusive count of both kinds
+// at the chunk's first point, for every level; per instance both totals of
+// every level.  The partial slots of a level are thereby a dense range in
+// which each query's records keep the order of the last coordinate.
+constexpr int CS_ROUNDS = 16;
+template <int M>
+__global__ __launch_bounds__(256) void k_count_scan(
     const u32* __restrict__ perm, const u32* __restrict__ seg_off, const u32* __restrict__ tile_off, int nseg,
-    const u32* __restrict__ r0, const u32* __restrict__ r1, Inst* inst, const u32* __restrict__ q_offs,
-    u32* __restrict__ pr0, u32* __restrict__ pr1, u32* __restrict__ pj, u32* __restrict__ poff,
-    u32* __restrict__ pqoff, u32* __restrict__ qslot, u32* __restrict__ qidx, u64* status, Ctl* ctl,
+    const u32* __restrict__ chunk_off, const u32* __restrict__ r0, const u32* __restrict__ r1, Inst* inst,
+    u32* __restrict__ pr0, u32* __restrict__ pr1, u32* __restrict__ pj, u32* __restrict__ chunk_base,
+    u32* __restrict__ qchunk_base, u32* __restrict__ lvl_tot, u32* __restrict__ qlvl_tot, u64* status, Ctl* ctl,
     int launch_idx) {
-    constexpr int TILE = THREADS * ITEMS;
-    __shared__ u32 sbuf[Padded<TILE>::value];
-    __shared__ u32 scratch[3 * (THREADS / 32)];
+    constexpr int WARPS = 8, C = 2 * LMAX, TILE = WARPS * CS_ROUNDS * 32;
+    static_assert(TILE == 4096, "point tiles");
+    __shared__ u32 s_w[WARPS][C];
+    __shared__ u32 s_excl[C];
     __shared__ u32 s_info[2];
-    __shared__ u32 s_excl[3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         s_info[0] = atomicAdd(&ctl->tile_ctr[launch_idx], 1u);
         s_info[1] = ctl->epoch_base + (u32)launch_idx;
@@ -245,179 +264,206 @@ __global__ __launch_bounds__(THREADS) void k_count_scan(
     const u32 t = s_info[0], epoch = s_info[1];
     if (t >= __ldg(tile_off + nseg)) return;
     const TileLoc L = locate_tile<TILE>(t, seg_off, tile_off, nseg);
-    const u32 nQ = inst[L.seg].nQ;
-    const u32 b0 = M >= 2 ? inst[L.seg].b[0] : 0u, b1 = M >= 3 ? inst[L.seg].b[1] : 0u;
+    const Inst& I = inst[L.seg];
+    const u32 nQ = I.nQ;
+    const u32 nlev = levels_of<M>(I);
+    const u32 b0 = M >= 2 ? I.b[0] : 0u, b1 = M >= 3 ? I.b[1] : 0u;
     const u32 m0 = low_mask(b0), m1 = low_mask(b1);
-    u32 j[ITEMS];
-    load_blocked_u32<THREADS, ITEMS>(perm, L.start, L.end, sbuf, j, 0u);
-    const u32 x0 = L.start + threadIdx.x * ITEMS;
     const u32 n_total = __ldg(seg_off + nseg);
+    const u32 wstart = L.start + (u32)warp * CS_ROUNDS * 32u;
+    // per lane (= level): the counts of every chunk of the warp
+    u32 rc[CS_ROUNDS], qc[CS_ROUNDS];
+    u32 run_all = 0, run_q = 0;
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i)  // a permutation entry outside the point space is never followed
-        if (j[i] >= n_total) j[i] = L.seg_begin + nQ;
-    u32 c[3] = {0, 0, 0};
-    u32 rr0[ITEMS], rr1[ITEMS], cnt[ITEMS];
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        rr0[i] = rr1[i] = cnt[i] = 0;
-        if (x0 + i < L.end) {
-            const bool q = (j[i] - L.seg_begin) < nQ;
-            if (M >= 2) rr0[i] = r0[j[i]];
-            if (M >= 3) rr1[i] = r1[j[i]];
-            const u32 bits0 = (q ? rr0[i] : ~rr0[i]) & m0;
-            const u32 bits1 = (q ? rr1[i] : ~rr1[i]) & m1;
-            cnt[i] = record_count<M>(bits0, bits1);
-            c[0] += cnt[i];
-            if (q) {
-                c[1] += cnt[i];
-                c[2] += 1;
+    for (int i = 0; i < CS_ROUNDS; ++i) {
+        const u32 x = wstart + (u32)i * 32u + (u32)lane;
+        const bool valid = x < L.end;
+        u32 j = valid ? perm[x] : L.seg_begin;
+        if (j >= n_total) j = L.seg_begin;  // never taken for a valid permutation
+        const bool q = valid && (j - L.seg_begin) < nQ;
+        u32 a = 0, c = 0, bits0 = 0, c1 = 1;
+        if (M >= 2 && valid) a = r0[j];
+        if (M >= 3 && valid) c = r1[j];
+        if (M >= 2) bits0 = (q ? a : ~a) & m0;
+        if (M >= 3) c1 = (u32)__popc((q ? c : ~c) & m1);
+        if (M == 1) bits0 = 1u;
+        if (!valid) bits0 = 0;
+        if (valid) {
+            if (M >= 2) pr0[x] = a;
+            if (M >= 3) pr1[x] = c;
+            pj[x] = j;
+        }
+        u32 mine = 0, mine_q = 0;
+        for (u32 lv = 0; lv < nlev; ++lv) {
+            const u32 w = ((bits0 >> lv) & 1u) ? c1 : 0u;
+            const u32 sa = __reduce_add_sync(0xffffffffu, w);
+            const u32 sq = __reduce_add_sync(0xffffffffu, q ? w : 0u);
+            if ((u32)lane == lv) {
+                mine = sa;
+                mine_q = sq;
             }
         }
+        rc[i] = mine;
+        qc[i] = mine_q;
+        run_all += mine;
+        run_q += mine_q;
     }
-    u32 tot[3];
-    block_exscan<THREADS, 3>(c, tot, scratch);
-    if (threadIdx.x < 3) {
-        const int cc = threadIdx.x;
-        u64* st = status + (u64)t * 3 + cc;
+    s_w[warp][lane] = run_all;
+    s_w[warp][LMAX + lane] = run_q;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        const int c = threadIdx.x;
+        u32 sum = 0;
+        for (int w = 0; w < WARPS; ++w) {
+            const u32 v = s_w[w][c];
+            s_w[w][c] = sum;
+            sum += v;
+        }
+        u64* st = status + (u64)t * C + c;
         u32 excl = 0;
         const u32 first_tile = t - (L.start - L.seg_begin) / (u32)TILE;
         if (L.first) {
-            st_store(st, st_pack(epoch, ST_PREFIX, tot[cc]));
+            st_store(st, st_pack(epoch, ST_PREFIX, sum));
         } else {
-            st_store(st, st_pack(epoch, ST_AGG, tot[cc]));
-            excl = lookback_u32(status, 3, cc, t, first_tile, epoch, ctl, 3u);
-            st_store(st, st_pack(epoch, ST_PREFIX, excl + tot[cc]));
+            st_store(st, st_pack(epoch, ST_AGG, sum));
+            excl = lookback_u32(status, C, c, t, first_tile, epoch, ctl, 3u);
+            st_store(st, st_pack(epoch, ST_PREFIX, excl + sum));
         }
-        if (excl + tot[cc] < excl) atomicOr(&ctl->error, ERR_OVERFLOW);
-        s_excl[cc] = excl;
-        if (L.end == L.seg_end) {  // last tile of the instance
-            if (cc == 0) inst[L.seg].T = excl + tot[0];
-            if (cc == 1) inst[L.seg].Tq = excl + tot[1];
+        if (excl + sum < excl) atomicOr(&ctl->error, ERR_OVERFLOW);
+        s_excl[c] = excl;
+        if (L.end == L.seg_end) {  // last tile of the instance: totals
+            if (c < LMAX) lvl_tot[(u64)L.seg * LMAX + c] = excl + sum;
+            else qlvl_tot[(u64)L.seg * LMAX + (c - LMAX)] = excl + sum;
         }
     }
     __syncthreads();
-    u32 off = s_excl[0] + c[0], qoff = s_excl[1] + c[1], qr = s_excl[2] + c[2];
-    const u32 qbase = __ldg(q_offs + L.seg);
+    const u32 base_all = s_excl[lane] + s_w[warp][lane];
+    const u32 base_q = s_excl[LMAX + lane] + s_w[warp][LMAX + lane];
+    const u32 cbase = __ldg(chunk_off + L.seg) + (wstart - L.seg_begin) / 32u;
+    u32 ra = 0, rq = 0;
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        const u32 x = x0 + i;
-        if (x < L.end) {
-            const u32 local = j[i] - L.seg_begin;
-            const bool q = local < nQ;
-            if (M >= 2) pr0[x] = rr0[i];
-            if (M >= 3) pr1[x] = rr1[i];
-            pj[x] = j[i];
-            poff[x] = off;
-            pqoff[x] = qoff;
-            if (q && qr < nQ) {
-                qslot[qbase + qr] = qoff;
-                qidx[qbase + qr] = local;
-                qoff += cnt[i];
-                qr += 1;
-            }
-            off += cnt[i];
+    for (int i = 0; i < CS_ROUNDS; ++i) {
+        if (wstart + (u32)i * 32u < L.end && (u32)lane < nlev) {
+            chunk_base[(u64)(cbase + i) * LMAX + lane] = base_all + ra;
+            qchunk_base[(u64)(cbase + i) * LMAX + lane] = base_q + rq;
         }
+        ra += rc[i];
+        rq += qc[i];
     }
 }
 
-// Flat map (instruction 6m+1, Sec. 5): every point writes its records,
-// (node key | role bit, payload), at its offset in the record array of its
-// chunk.  The node key concatenates the canonical node of every one of the
-// first m-1 ranks (node_of): for m = 3, node0 << b1 | node1.  The role bit
-// (top bit of the key) marks query records; it is not part of the sort key.
-// Payload: data -> the weight's bits (Op::Pay), query -> its partial slot.
-//
-// One warp handles 32 consecutive points.  Each lane enumerates its own
-// point's records (lowest set bit first: one find-first-set per record) into
-// a per-warp staging buffer in shared memory, EXPAND_STAGE_BYTES at a time;
-// the warp then copies the staged run to global memory with coalesced stores.
-constexpr int EXPAND_THREADS = 256;
-constexpr int EXPAND_STAGE_BYTES = 8192;  // per warp
+// Flat map (instruction 6m+1, Sec. 5), level by level.  Every point writes
+// its records (sort key | role bit, payload) into the segment of their
+// level; a warp handles one chunk of 32 consecutive points of an instance and
+// writes each level's records contiguously (the chunk's base from the count
+// scan plus the exclusive count of the lanes before), so stores coalesce.
+// Sort key: the prefix of the first rank at that level, v0 = r0 >> (j+1);
+// for m = 3 followed by the canonical node of the second rank (node_of),
+// v0 << b1 | node1.  The role bit (top bit of the key) marks query records.
+// Payload: data -> the weight's bits (Op::Pay), query -> its partial slot,
+// a dense per-level position (query slot base of the level + the chunk's
+// query count of the level + the lanes before).
 template <int M, typename K, typename Pay, int WT>
-__global__ __launch_bounds__(EXPAND_THREADS) void k_expand(
-    u32 p_begin, u32 p_end, const u32* __restrict__ pr0, const u32* __restrict__ pr1,
-    const u32* __restrict__ pj, const u32* __restrict__ poff, const u32* __restrict__ pqoff,
-    const Inst* __restrict__ inst, const u32* __restrict__ pt_offs, int k, const u32* __restrict__ rec_base,
-    const u32* __restrict__ qrec_base, int k0, u32 n_rec, K* __restrict__ kout, Pay* __restrict__ pout) {
-    constexpr u32 CH = EXPAND_STAGE_BYTES / (sizeof(K) + sizeof(Pay));  // records staged per warp
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    K* sk = reinterpret_cast<K*>(smem + warp * EXPAND_STAGE_BYTES);
-    Pay* sp = reinterpret_cast<Pay*>(sk + CH);
+__global__ __launch_bounds__(256) void k_expand(
+    const u32* __restrict__ chunk_off, int k, int k0, int k1, const u32* __restrict__ pt_offs,
+    const u32* __restrict__ pr0, const u32* __restrict__ pr1, const u32* __restrict__ pj,
+    const u32* __restrict__ chunk_base, const u32* __restrict__ qchunk_base, const Inst* __restrict__ inst,
+    const u32* __restrict__ seg_base /*[k1-k0][LMAX]*/, const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/,
+    u32 n_rec, K* __restrict__ kout, Pay* __restrict__ pout) {
+    const int lane = threadIdx.x & 31;
+    const u32 lt = lanemask_lt();
+    const u32 c_begin = __ldg(chunk_off + k0), c_end = __ldg(chunk_off + k1);
     const u32 warps = (gridDim.x * blockDim.x) >> 5;
     const K role = K(1) << (sizeof(K) * 8 - 1);
-    for (u32 wb = p_begin + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32u; wb < p_end; wb += warps * 32u) {
-        const u32 p = wb + lane;
-        const bool valid = p < p_end;
-        u32 r0 = 0, r1 = 0, bits0 = 0, bits1 = 0, b1 = 0, cnt = 0, gbase = 0;
+    for (u32 c = c_begin + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); c < c_end; c += warps) {
+        const int s = upper_index(chunk_off, k + 1, c);
+        const Inst& I = inst[s];
+        const u32 ps = __ldg(pt_offs + s), pe = __ldg(pt_offs + s + 1);
+        const u32 p = ps + (c - __ldg(chunk_off + s)) * 32u + (u32)lane;
+        const bool valid = p < pe;
+        const u32 nQ = I.nQ;
+        const u32 nlev = levels_of<M>(I);
+        const u32 b1 = M >= 3 ? I.b[1] : 0u;
+        // lane lv holds the bases of level lv (read once, shuffled below)
+        const u32 my_all = (u32)lane < nlev ? __ldg(seg_base + (u64)(s - k0) * LMAX + lane) +
+                                                  __ldg(chunk_base + (u64)c * LMAX + lane)
+                                            : 0u;
+        const u32 my_q = (u32)lane < nlev ? __ldg(qseg_base + (u64)(s - k0) * LMAX + lane) +
+                                                __ldg(qchunk_base + (u64)c * LMAX + lane)
+                                          : 0u;
+        u32 a = 0, cc = 0, bits0 = 0, bits1 = 0, c1 = 1;
         bool q = false;
-        Pay pay = 0;
+        Pay w = 0;
         if (valid) {
-            const int s = upper_index(pt_offs, k + 1, p);
             u32 j = pj[p];
-            const u32 nQ = inst[s].nQ, nD = inst[s].nD;
-            if (j - __ldg(pt_offs + s) >= nQ + nD) j = __ldg(pt_offs + s);  // never taken for a valid permutation
-            const u32 local = j - __ldg(pt_offs + s);
+            if (j - ps >= pe - ps) j = ps;  // never taken for a valid permutation
+            const u32 local = j - ps;
             q = local < nQ;
             if (M >= 2) {
-                r0 = pr0[p];
-                bits0 = (q ? r0 : ~r0) & low_mask(inst[s].b[0]);
+                a = pr0[p];
+                bits0 = (q ? a : ~a) & low_mask(I.b[0]);
             }
             if (M >= 3) {
-                r1 = pr1[p];
-                b1 = inst[s].b[1];
-                bits1 = (q ? r1 : ~r1) & low_mask(b1);
+                cc = pr1[p];
+                bits1 = (q ? cc : ~cc) & low_mask(b1);
+                c1 = (u32)__popc(bits1);
             }
-            cnt = record_count<M>(bits0, bits1);
-            gbase = __ldg(rec_base + (s - k0)) + poff[p];
-            if (q) {
-                pay = (Pay)(__ldg(qrec_base + (s - k0)) + pqoff[p]);
-            } else if (WT == 1) {  // int64 weights
-                pay = (Pay)reinterpret_cast<const long long*>(inst[s].dw)[local - nQ];
-            } else if (WT == 0 || WT == 2) {  // 32-bit weights
-                pay = (Pay)reinterpret_cast<const u32*>(inst[s].dw)[local - nQ];
+            if (M == 1) bits0 = 1u;
+            if (!q) {
+                if (WT == 1) w = (Pay)reinterpret_cast<const long long*>(I.dw)[local - nQ];
+                else if (WT == 0 || WT == 2) w = (Pay)reinterpret_cast<const u32*>(I.dw)[local - nQ];
             }
         }
-        // records of this warp: [wstart, wstart + R)
-        const u32 wstart = __shfl_sync(0xffffffffu, gbase, 0);
-        const u32 off_rel = valid ? gbase - wstart : 0u;
-        u32 R = valid ? off_rel + cnt : 0u;
+        if (M >= 3 && c1 == 0) bits0 = 0;  // no records at all
+        const u32 live = __ballot_sync(0xffffffffu, bits0 != 0u);
+        if (live == 0u) continue;
+        for (u32 lv = 0; lv < nlev; ++lv) {
+            const bool has = (bits0 >> lv) & 1u;
+            const u32 hb = __ballot_sync(0xffffffffu, has);
+            if (hb == 0u) continue;
+            const u32 qb = __ballot_sync(0xffffffffu, has && q);
+            const u32 base_all = __shfl_sync(0xffffffffu, my_all, lv);
+            const u32 base_q = __shfl_sync(0xffffffffu, my_q, lv);
+            u32 ex, exq;
+            if (M <= 2) {
+                ex = (u32)__popc(hb & lt);
+                exq = (u32)__popc(qb & lt);
+            } else {
+                const u32 wv = has ? c1 : 0u, wq = (has && q) ? c1 : 0u;
+                u32 inc = wv, incq = wq;
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) R = max(R, __shfl_xor_sync(0xffffffffu, R, o));
-        // enumeration state: the current node of dimension 0 (lowest pending
-        // bit of rem0) and the pending bits of dimension 1
-        u32 rem0 = bits0, rem1 = bits1, kk = 0;
-        for (u32 c0 = 0; c0 < R; c0 += CH) {
-            const u32 c1 = min(c0 + CH, R);
-            for (u32 idx = off_rel + kk; kk < cnt && idx < c1; ++kk, ++idx) {
-                K key;
-                if (M == 1) {
-                    key = K(0);
-                } else if (M == 2) {
-                    const u32 j0 = __ffs(rem0) - 1;
-                    rem0 &= rem0 - 1;
-                    key = (K)node_of(r0, j0);
-                } else {
-                    const u32 j0 = __ffs(rem0) - 1, j1 = __ffs(rem1) - 1;
-                    key = ((K)node_of(r0, j0) << b1) | (K)node_of(r1, j1);
-                    rem1 &= rem1 - 1;
-                    if (rem1 == 0) {  // next node of dimension 0
-                        rem0 &= rem0 - 1;
-                        rem1 = bits1;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const u32 n1 = __shfl_up_sync(0xffffffffu, inc, o);
+                    const u32 n2 = __shfl_up_sync(0xffffffffu, incq, o);
+                    if (lane >= o) {
+                        inc += n1;
+                        incq += n2;
                     }
                 }
-                if (q) key |= role;
-                sk[idx - c0] = key;
-                sp[idx - c0] = q ? (Pay)(pay + kk) : pay;
+                ex = inc - wv;
+                exq = incq - wq;
             }
-            __syncwarp();
-            for (u32 x = c0 + lane; x < c1; x += 32u) {
-                if (wstart + x < n_rec) {
-                    kout[wstart + x] = sk[x - c0];
-                    pout[wstart + x] = sp[x - c0];
+            if (!has) continue;
+            const u32 pos = base_all + ex;
+            const Pay pay = q ? (Pay)(base_q + exq) : w;
+            const K kv = M == 1 ? K(0) : (K)(a >> (lv + 1));
+            if (M <= 2) {
+                if (pos < n_rec) {
+                    kout[pos] = q ? (kv | role) : kv;
+                    pout[pos] = pay;
+                }
+            } else {
+                u32 rem = bits1;
+                for (u32 kk = 0; rem; ++kk) {
+                    const u32 j1 = __ffs(rem) - 1;
+                    rem &= rem - 1;
+                    const K key = (kv << b1) | (K)node_of(cc, j1);
+                    if (pos + kk < n_rec) {
+                        kout[pos + kk] = q ? (key | role) : key;
+                        pout[pos + kk] = q ? (Pay)(pay + kk) : pay;
+                    }
                 }
             }
-            __syncwarp();
         }
     }
 }

@@ -170,8 +170,8 @@ template <typename K, typename V, bool IOTA>
 __global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_onesweep(
     const K* __restrict__ kin, const V* __restrict__ vin, K* __restrict__ kout, V* __restrict__ vout,
     const u32* __restrict__ seg_off, const u32* __restrict__ range_off, int nseg, u32 range_items,
-    const u32* __restrict__ digit_off, int npass, int pass, int shift, K keymask, u64* status, Ctl* ctl,
-    int launch_idx) {
+    const u32* __restrict__ seg_bits, const u32* __restrict__ digit_off, int npass, int pass, int shift,
+    K keymask, u64* status, Ctl* ctl, int launch_idx) {
     constexpr int THREADS = ONESWEEP_THREADS, ITEMS = onesweep_items<K, V>();
     constexpr int TILE = THREADS * ITEMS, WARPS = THREADS / 32;
     typedef OnesweepSmem<K, V, TILE> SM;
@@ -222,6 +222,13 @@ __global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_oneswee
         const u32 r = s_info[0];
         if (r >= nranges) break;
         const TileLoc L = locate_range(r, seg_off, range_off, nseg, range_items);
+        // a segment whose keys have fewer digits is already in place (the
+        // barrier keeps thread 0's next claim from overwriting s_info[0]
+        // before every thread has read it)
+        if (seg_bits && (u32)pass * RADIX_BITS >= __ldg(seg_bits + L.seg)) {
+            __syncthreads();
+            continue;
+        }
         const u32 ntile = (L.end - L.start + TILE - 1) / TILE;
         if (tid == 0) {  // the first tile's load overlaps the range histogram
             fence_proxy_async_smem();

@@ -65,9 +65,12 @@ __device__ __forceinline__ Acc volatile_read(const Acc* p) {
 // the data of its node with a smaller last coordinate; it is stored in the
 // query record's partial slot.
 template <class Op, typename K, int THREADS, int ITEMS>
-__global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys, const typename Op::Pay* __restrict__ pays,
+__global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys0, const K* __restrict__ keys1,
+                                                     const typename Op::Pay* __restrict__ pays0,
+                                                     const typename Op::Pay* __restrict__ pays1,
                                                      const u32* __restrict__ seg_off,
                                                      const u32* __restrict__ tile_off, int nseg,
+                                                     const u32* __restrict__ seg_bits,
                                                      typename Op::Part* __restrict__ partial, u32 n_partial,
                                                      SegStatus<typename Op::Acc>* status, Ctl* ctl, int launch_idx) {
     typedef typename Op::Acc Acc;
@@ -88,6 +91,10 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys,
     const u32 t = s_info[0], epoch = s_info[1];
     if (t >= __ldg(tile_off + nseg)) return;
     const TileLoc L = locate_tile<TILE>(t, seg_off, tile_off, nseg);
+    // the sort left this segment in the buffer of its pass count's parity
+    const bool odd = ((__ldg(seg_bits + L.seg) + RADIX_BITS - 1) / RADIX_BITS) & 1u;
+    const K* __restrict__ keys = odd ? keys1 : keys0;
+    const typename Op::Pay* __restrict__ pays = odd ? pays1 : pays0;
     // coalesced load into shared memory, then blocked reads
     for (int i = 0; i < ITEMS; ++i) {
         const u32 x = (u32)i * THREADS + threadIdx.x;
@@ -103,12 +110,15 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys,
     bool has_prev = x0 > L.seg_begin;
     if (has_prev && x0 < L.end) prev = lx0 == 0 ? keys[x0 - 1] : s_keys[pidx(lx0 - 1)];
     prev &= ~role;
-    // thread aggregate: (head seen, F over items after the last head)
+    // thread aggregate: (head seen, F over items after the last head); the
+    // running value at every query record is kept for the output pass
     bool head_any = false;
     Acc agg = Op::e();
-    u32 headmask = 0;
+    u32 headmask = 0, qmask = 0;
+    Acc loc[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
+        loc[i] = Op::e();
         if (x0 + i < L.end) {
             const K kx = s_keys[pidx(lx0 + i)];
             const K kn = kx & ~role;
@@ -120,7 +130,12 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys,
                 headmask |= 1u << i;
                 agg = Op::e();
             }
-            if (!(kx & role)) agg = Op::F(agg, Op::from_pay(s_pays[pidx(lx0 + i)]));
+            if (kx & role) {
+                qmask |= 1u << i;
+                loc[i] = agg;
+            } else {
+                agg = Op::F(agg, Op::from_pay(s_pays[pidx(lx0 + i)]));
+            }
         }
     }
     // block-wide exclusive scan of (head, agg) with the segmented operator
@@ -261,43 +276,92 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys,
         if (lane == 0) s_excl = excl;
     }
     __syncthreads();
-    Acc run = texcl_head ? texcl : Op::F(s_excl, texcl);
+    // output: a query record before the thread's first head continues the
+    // segment coming from the left (prefix); after it, its own run suffices
+    const Acc prefix = texcl_head ? texcl : Op::F(s_excl, texcl);
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        if (x0 + i < L.end) {
-            if (headmask & (1u << i)) run = Op::e();
-            const K kx = s_keys[pidx(lx0 + i)];
-            const Pay py = s_pays[pidx(lx0 + i)];
-            if (kx & role) {
-                const u64 slot = (u64)py;
-                if (slot < n_partial) partial[slot] = Op::to_part(run);
-            } else {
-                run = Op::F(run, Op::from_pay(py));
-            }
+        if (qmask & (1u << i)) {
+            const u64 slot = (u64)s_pays[pidx(lx0 + i)];
+            const bool own = (headmask & ((2u << i) - 1u)) != 0;
+            if (slot < n_partial) partial[slot] = Op::to_part(own ? loc[i] : Op::F(prefix, loc[i]));
         }
     }
 }
 
-// Per-query reduction: out[q] = F over the query's partial slots, which are
-// contiguous (the flat map wrote them in order) -- this replaces the sort by
-// ID and the ID-segmented scan of instructions 6m+4, 6m+5, and the broadcast
-// of instructions 6m+6 .. 6m+9 is not needed for one output per query.
-// Thread per query of the chunk, in the order of the last coordinate.
-template <class Op>
-__global__ void k_reduce(u32 qr_begin, u32 qr_end, const u32* __restrict__ qslot, const u32* __restrict__ qidx,
-                         const typename Op::Part* __restrict__ partial, u32 n_partial,
-                         const u32* __restrict__ q_offs, int k, const Inst* __restrict__ inst,
-                         const u32* __restrict__ qrec_base, int k0) {
-    const u32 qr = qr_begin + blockIdx.x * blockDim.x + threadIdx.x;
-    if (qr >= qr_end) return;
-    const int s = upper_index(q_offs, k + 1, qr);
-    const u32 base = __ldg(qrec_base + (s - k0));
-    const u32 s0 = qslot[qr];
-    const u32 s1 = (qr + 1 < __ldg(q_offs + s + 1)) ? qslot[qr + 1] : inst[s].Tq;
-    typename Op::Acc acc = Op::e();
-    for (u32 x = s0; x < s1 && base + x < n_partial; ++x) acc = Op::F(acc, Op::from_part(partial[base + x]));
-    const u32 q = qidx[qr];
-    if (q < inst[s].nQ) reinterpret_cast<typename Op::Out*>(inst[s].out)[q] = Op::to_out(acc);
+// Per-query reduction: out[q] = F over the query's partial results.  This
+// replaces the sort by ID and the ID-segmented scan of instructions 6m+4,
+// 6m+5 (the broadcast of 6m+6 .. 6m+9 is not needed for one output per
+// query).  The partials of level lv are a dense range in which queries keep
+// the order of the last coordinate, so a warp walking one chunk of 32
+// consecutive points reads every level's partials as one contiguous run:
+// the chunk's query base of the level plus the query lanes before it.
+template <class Op, int M>
+__global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_off, int k, int k0, int k1,
+                                                const u32* __restrict__ pt_offs, const u32* __restrict__ pr0,
+                                                const u32* __restrict__ pr1, const u32* __restrict__ pj,
+                                                const u32* __restrict__ qchunk_base,
+                                                const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/,
+                                                const Inst* __restrict__ inst,
+                                                const typename Op::Part* __restrict__ partial, u32 n_partial) {
+    const int lane = threadIdx.x & 31;
+    const u32 lt = lanemask_lt();
+    const u32 c_begin = __ldg(chunk_off + k0), c_end = __ldg(chunk_off + k1);
+    const u32 warps = (gridDim.x * blockDim.x) >> 5;
+    for (u32 c = c_begin + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); c < c_end; c += warps) {
+        const int s = upper_index(chunk_off, k + 1, c);
+        const Inst& I = inst[s];
+        const u32 ps = __ldg(pt_offs + s), pe = __ldg(pt_offs + s + 1);
+        const u32 p = ps + (c - __ldg(chunk_off + s)) * 32u + (u32)lane;
+        const bool valid = p < pe;
+        const u32 nQ = I.nQ;
+        const u32 nlev = levels_of<M>(I);
+        const u32 my_q = (u32)lane < nlev ? __ldg(qseg_base + (u64)(s - k0) * LMAX + lane) +
+                                                __ldg(qchunk_base + (u64)c * LMAX + lane)
+                                          : 0u;
+        u32 local = 0, bits0 = 0, c1 = 1;
+        bool q = false;
+        if (valid) {
+            u32 j = pj[p];
+            if (j - ps >= pe - ps) j = ps;  // never taken for a valid permutation
+            local = j - ps;
+            q = local < nQ;
+            if (q) {
+                if (M >= 2) bits0 = pr0[p] & low_mask(I.b[0]);
+                if (M >= 3) c1 = (u32)__popc(pr1[p] & low_mask(I.b[1]));
+                if (M == 1) bits0 = 1u;
+                if (M >= 3 && c1 == 0) bits0 = 0;
+            }
+        }
+        if (__ballot_sync(0xffffffffu, q) == 0u) continue;
+        typename Op::Acc acc = Op::e();
+        for (u32 lv = 0; lv < nlev; ++lv) {
+            const bool has = (bits0 >> lv) & 1u;
+            const u32 hb = __ballot_sync(0xffffffffu, has);
+            if (hb == 0u) continue;
+            const u32 base_q = __shfl_sync(0xffffffffu, my_q, lv);
+            u32 exq;
+            if (M <= 2) {
+                exq = (u32)__popc(hb & lt);
+            } else {
+                const u32 wq = has ? c1 : 0u;
+                u32 inc = wq;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const u32 nn = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += nn;
+                }
+                exq = inc - wq;
+            }
+            if (has) {
+                const u32 base = base_q + exq;
+                const u32 cnt = M <= 2 ? 1u : c1;
+                for (u32 kk = 0; kk < cnt && base + kk < n_partial; ++kk)
+                    acc = Op::F(acc, Op::from_part(partial[base + kk]));
+            }
+        }
+        if (q) reinterpret_cast<typename Op::Out*>(I.out)[local] = Op::to_out(acc);
+    }
 }
 
 }  // namespace domagg

@@ -20,7 +20,7 @@ static u64 resident_ctas(size_t smem) {
 
 template <typename K, typename V>
 int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool iota, int total_bits, K keymask,
-               int kind_hist, int kind_pass) {
+               int kind_hist, int kind_pass, const u32* seg_bits) {
     constexpr u32 TILE = ONESWEEP_THREADS * onesweep_items<K, V>();
     static_assert(TILE >= SORT_MIN_TILE, "status words are sized for SORT_MIN_TILE");
     const int npass = (total_bits + RADIX_BITS - 1) / RADIX_BITS;
@@ -58,20 +58,24 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
         if (iota && p == 0)
             k_onesweep<K, V, true><<<grid, ONESWEEP_THREADS, smem, L.stream>>>(
                 keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], sp.seg_off, sp.tile_off, sp.nseg, range_items,
-                sp.digit_off, npass, p, p * RADIX_BITS, keymask, sp.status, L.ctl, li);
+                seg_bits, sp.digit_off, npass, p, p * RADIX_BITS, keymask, sp.status, L.ctl, li);
         else
             k_onesweep<K, V, false><<<grid, ONESWEEP_THREADS, smem, L.stream>>>(
                 keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], sp.seg_off, sp.tile_off, sp.nseg, range_items,
-                sp.digit_off, npass, p, p * RADIX_BITS, keymask, sp.status, L.ctl, li);
+                seg_bits, sp.digit_off, npass, p, p * RADIX_BITS, keymask, sp.status, L.ctl, li);
         L.stop();
         cur ^= 1;
     }
     return cur;
 }
 
-template int sort_pairs<u32, u32>(Launcher&, const SortSpace&, u32**, u32**, bool, int, u32, int, int);
-template int sort_pairs<u64, u32>(Launcher&, const SortSpace&, u64**, u32**, bool, int, u64, int, int);
-template int sort_pairs<u32, u64>(Launcher&, const SortSpace&, u32**, u64**, bool, int, u32, int, int);
-template int sort_pairs<u64, u64>(Launcher&, const SortSpace&, u64**, u64**, bool, int, u64, int, int);
+template int sort_pairs<u32, u32>(Launcher&, const SortSpace&, u32**, u32**, bool, int, u32, int, int,
+                                     const u32*);
+template int sort_pairs<u64, u32>(Launcher&, const SortSpace&, u64**, u32**, bool, int, u64, int, int,
+                                     const u32*);
+template int sort_pairs<u32, u64>(Launcher&, const SortSpace&, u32**, u64**, bool, int, u32, int, int,
+                                     const u32*);
+template int sort_pairs<u64, u64>(Launcher&, const SortSpace&, u64**, u64**, bool, int, u64, int, int,
+                                     const u32*);
 
 }  // namespace domagg
