@@ -237,8 +237,9 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         P[21] = c.take<u32>(k + 1);                  // the sorts' tile map
         P[22] = c.take<u32>((size_t)NC * LMAX);      // chunk bases per level
         P[23] = c.take<u32>((size_t)k * LMAX);       // records per (instance, level)
+        P[24] = c.take<u32>((size_t)sort_range_bound(pt_sizes) * RADIX);  // first-pass range bases
     };
-    void* P[24];
+    void* P[25];
     {
         Carver c(nullptr);
         carve_points(c, P);
@@ -307,14 +308,16 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                                                                       negate ? 1 : 0, h->ctl);
     L.stop();
 
-    SortSpace sp{d_pt_offs, k, &pt_sizes, d_sort_tiles, hist, digit_off, (u64*)h->st_multi.p, (double)N};
+    SortSpace sp{d_pt_offs, k, &pt_sizes, d_sort_tiles, hist, digit_off, (u64*)h->st_multi.p, (double)N,
+                 (u32*)P[24], sort_range_bound(pt_sizes)};
 
     // ---- ranks of the first m-1 coordinates (5i-3 .. 5i, 5m+i)
     for (int i = 0; i < M - 1; ++i) {
         u32* keys[2] = {i == 0 ? rk0 : rk1, kalt};
         u32* vals[2] = {vA, vB};
+        // only the sorted key sequence matters for dense ranks: any order of equal digits
         const int cur = sort_pairs<u32, u32>(L, sp, keys, vals, true, 32, 0xffffffffu, KIND_HIST_POINTS,
-                                             KIND_SORT_POINTS);
+                                             KIND_SORT_POINTS, nullptr, false);
         const int li = L.lookback_index();
         L.start(KIND_RANK, (double)N * 12);
         k_rank<SCAN_THREADS, SCAN_ITEMS><<<(unsigned)ntp, SCAN_THREADS, 0, stream>>>(
@@ -476,8 +479,9 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             R[7] = c.take<Part>(C.Tq);
             R[8] = c.take<u32>((size_t)nseg * std::max(npass, 1) * RADIX);
             R[9] = c.take<u32>((size_t)nseg * std::max(npass, 1) * RADIX);
+            R[10] = c.take<u32>((size_t)sort_range_bound(seg_sizes) * RADIX);  // first-pass range bases
         };
-        void* R[10];
+        void* R[11];
         {
             Carver c(nullptr);
             carve_recs(c, R);
@@ -526,7 +530,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         // records sort (6m+2): stable, each level by the bits of its prefix
         if (C.T > 0 && npass > 0) {
             SortSpace rs{d_so, (int)nseg, &seg_sizes, d_rtiles, (u32*)R[8], (u32*)R[9], (u64*)h->st_multi.p,
-                         (double)C.T};
+                         (double)C.T, (u32*)R[10], sort_range_bound(seg_sizes)};
             const K keymask = ~(K(1) << (sizeof(K) * 8 - 1));  // all but the role bit
             sort_pairs<K, Pay>(L, rs, keys, pays, false, C.key_bits, keymask, KIND_HIST_RECORDS, KIND_SORT_RECORDS,
                                d_sbits);

@@ -91,7 +91,11 @@ struct SortSpace {
     u32* digit_off;             // [nseg*npass*RADIX]
     u64* status;                // [tiles*RADIX], tiles of at least SORT_MIN_TILE items
     double n_items;             // items sorted (for the algorithmic byte model)
+    u32* range_scratch = nullptr;  // [range_scratch_ranges*RADIX]: first-pass bases per range
+    u64 range_scratch_ranges = 0;
 };
+
+
 
 // Smallest tile any sort instantiation uses (status words are sized by it).
 constexpr u32 SORT_MIN_TILE = 2048;
@@ -99,6 +103,14 @@ inline u64 tiles_of(const std::vector<u64>& sizes, u64 tile) {
     u64 t = 0;
     for (u64 n : sizes) t += (n + tile - 1) / tile;
     return t;
+}
+
+// Ranges the onesweep uses at most for these segment sizes (upper bound).
+inline u64 sort_range_bound(const std::vector<u64>& sizes) {
+    u64 t = 0;
+    for (u64 n : sizes) t += (n + SORT_MIN_TILE - 1) / SORT_MIN_TILE;
+    const u64 cap = 4096 + sizes.size();  // about four ranges per resident CTA, at least one per segment
+    return t < cap ? t : cap;
 }
 
 // Point-phase scans (ranks, count scan) tile the points in 4096s.
@@ -111,8 +123,10 @@ constexpr u32 POINT_TILE = 4096;
 // With seg_bits (device, one entry per segment), segment s is sorted by its
 // first seg_bits[s] bits only and its result is in buffer
 // ceil(seg_bits[s] / 8) % 2; the return value is then meaningless.
+// stable = false allows any order among equal digits (for sorts whose result
+// is only the sorted key sequence).
 template <typename K, typename V>
 int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool iota, int total_bits, K keymask,
-               int kind_hist, int kind_pass, const u32* seg_bits = nullptr);
+               int kind_hist, int kind_pass, const u32* seg_bits = nullptr, bool stable = true);
 
 }  // namespace domagg

@@ -62,7 +62,8 @@ __device__ __forceinline__ TileLoc locate_range(u32 r, const u32* seg_off, const
 template <typename K>
 __global__ __launch_bounds__(256) void k_radix_hist(const K* __restrict__ keys, const u32* __restrict__ seg_off,
                                                     const u32* __restrict__ range_off, int nseg, u32 range_items,
-                                                    int npass, int shift0, K keymask, u32* __restrict__ hist) {
+                                                    int npass, int shift0, K keymask, u32* __restrict__ hist,
+                                                    u32* __restrict__ range_cnt0) {
     extern __shared__ u32 sh_hist[];  // [8 warps][npass][RADIX]
     const u32 r = blockIdx.x;
     if (r >= __ldg(range_off + nseg)) return;
@@ -91,6 +92,28 @@ __global__ __launch_bounds__(256) void k_radix_hist(const K* __restrict__ keys, 
         u32 c = 0;
         for (int w = 0; w < 8; ++w) c += sh_hist[w * npass * RADIX + x];
         if (c) atomicAdd(gh + x, c);
+        if (range_cnt0 && x < RADIX) range_cnt0[(u64)r * RADIX + x] = c;  // this range's first-pass counts
+    }
+}
+
+// First-pass global position of every (range, digit): the digit's start in
+// the segment plus the counts of the segment's earlier ranges.  In place over
+// the per-range counts; one block per segment, one thread per digit.
+static __global__ __launch_bounds__(RADIX) void k_range_bases(const u32* __restrict__ range_off,
+                                                             const u32* __restrict__ digit_off, int npass,
+                                                             u32* __restrict__ range_cnt0) {
+    const int seg = blockIdx.x, d = threadIdx.x;
+    u32 run = __ldg(digit_off + (u64)seg * npass * RADIX + d);  // pass 0
+    const u32 r0 = __ldg(range_off + seg), r1 = __ldg(range_off + seg + 1);
+    for (u32 r = r0; r < r1; r += 16) {  // 16 loads in flight, then the running sum
+        u32 c[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) c[i] = r + i < r1 ? range_cnt0[(u64)(r + i) * RADIX + d] : 0u;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if (r + i < r1) range_cnt0[(u64)(r + i) * RADIX + d] = run;
+            run += c[i];
+        }
     }
 }
 
@@ -166,12 +189,16 @@ __host__ __device__ constexpr size_t onesweep_smem() {
 //
 // IOTA: the values are the items' own global indices (first pass of a sort
 // that returns a permutation); `vin` is not read.
-template <typename K, typename V, bool IOTA>
+// STABLE = false (the dense-rank sorts, where only the sorted key sequence
+// matters) ranks with one shared-memory atomic per item instead of the digit
+// match.  range_base (first pass only, may be null) holds every range's
+// global position per digit, which replaces the range's count and look-back.
+template <typename K, typename V, bool IOTA, bool STABLE>
 __global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_onesweep(
     const K* __restrict__ kin, const V* __restrict__ vin, K* __restrict__ kout, V* __restrict__ vout,
     const u32* __restrict__ seg_off, const u32* __restrict__ range_off, int nseg, u32 range_items,
-    const u32* __restrict__ seg_bits, const u32* __restrict__ digit_off, int npass, int pass, int shift,
-    K keymask, u64* status, Ctl* ctl, int launch_idx) {
+    const u32* __restrict__ seg_bits, const u32* __restrict__ range_base, const u32* __restrict__ digit_off,
+    int npass, int pass, int shift, K keymask, u64* status, Ctl* ctl, int launch_idx) {
     constexpr int THREADS = ONESWEEP_THREADS, ITEMS = onesweep_items<K, V>();
     constexpr int TILE = THREADS * ITEMS, WARPS = THREADS / 32;
     typedef OnesweepSmem<K, V, TILE> SM;
@@ -236,7 +263,9 @@ __global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_oneswee
             pending[b] = true;
         }
         // 1. digit counts of the range (per-warp histograms, then summed)
-        {
+        if (range_base) {
+            for (int d = tid; d < RADIX; d += THREADS) s_run[d] = __ldg(range_base + (u64)r * RADIX + d);
+        } else {
             u32* wh = s_whist + warp * (RADIX + 1);
             for (u32 base = L.start; base < L.end; base += (u32)THREADS * 8u) {
                 K kk[8];
@@ -257,7 +286,6 @@ __global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_oneswee
                 s_dstart[d] = c;
             }
             __syncthreads();
-        }
         // 2. publish the range's counts and look back over the earlier ranges
         {
             const u32 first_range = r - (L.start - L.seg_begin) / range_items;
@@ -274,6 +302,7 @@ __global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_oneswee
                 }
                 s_run[d] = __ldg(digit_off + ((u64)L.seg * npass + pass) * RADIX + d) + excl;
             }
+        }
         }
         // 3. the tiles of the range, in order
         for (u32 j = 0; j < ntile; ++j) {
@@ -303,6 +332,15 @@ __global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_oneswee
             u32 pos[ITEMS];
             const u32 wbase = (u32)warp * 32u * ITEMS;
             u32* wh = s_whist + warp * (RADIX + 1);
+            if (!STABLE) {
+                // any order inside a digit will do: one atomic per item
+#pragma unroll
+                for (int i = 0; i < ITEMS; ++i) {
+                    const u32 x = wbase + (u32)i * 32u + (u32)lane;
+                    key[i] = x < n ? bk[x] : K(0);
+                    pos[i] = x < n ? atomicAdd(&wh[digit_of(key[i], keymask, shift)], 1u) : 0u;
+                }
+            } else {
             // digit matches of all items first (independent ballots pipeline) ...
 #pragma unroll
             for (int i = 0; i < ITEMS; ++i) {
@@ -323,6 +361,7 @@ __global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_oneswee
                 u32 old = 0;
                 if (valid && lane == leader) old = atomicAdd(&wh[digit_of(key[i], keymask, shift)], (u32)__popc(peers));
                 pos[i] = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
+            }
             }
             __syncthreads();
             for (int d = tid; d < RADIX; d += THREADS) {  // exclusive over warps; tile count

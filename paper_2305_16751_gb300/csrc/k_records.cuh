@@ -304,7 +304,10 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
                                                 const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/,
                                                 const Inst* __restrict__ inst,
                                                 const typename Op::Part* __restrict__ partial, u32 n_partial) {
-    const int lane = threadIdx.x & 31;
+    typedef typename Op::Part Part;
+    __shared__ u32 s_mask[8][LMAX];  // per warp: query lanes holding a record of level lv
+    __shared__ u32 s_base[8][LMAX];  // per warp: first partial slot of level lv in this chunk
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const u32 lt = lanemask_lt();
     const u32 c_begin = __ldg(chunk_off + k0), c_end = __ldg(chunk_off + k1);
     const u32 warps = (gridDim.x * blockDim.x) >> 5;
@@ -316,10 +319,7 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
         const bool valid = p < pe;
         const u32 nQ = I.nQ;
         const u32 nlev = levels_of<M>(I);
-        const u32 my_q = (u32)lane < nlev ? __ldg(qseg_base + (u64)(s - k0) * LMAX + lane) +
-                                                __ldg(qchunk_base + (u64)c * LMAX + lane)
-                                          : 0u;
-        u32 local = 0, bits0 = 0, c1 = 1;
+        u32 local = 0, bits0 = 0, bits1 = 0, c1 = 1;
         bool q = false;
         if (valid) {
             u32 j = pj[p];
@@ -328,22 +328,43 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
             q = local < nQ;
             if (q) {
                 if (M >= 2) bits0 = pr0[p] & low_mask(I.b[0]);
-                if (M >= 3) c1 = (u32)__popc(pr1[p] & low_mask(I.b[1]));
+                if (M >= 3) {
+                    bits1 = pr1[p] & low_mask(I.b[1]);
+                    c1 = (u32)__popc(bits1);
+                }
                 if (M == 1) bits0 = 1u;
                 if (M >= 3 && c1 == 0) bits0 = 0;
             }
         }
         if (__ballot_sync(0xffffffffu, q) == 0u) continue;
-        typename Op::Acc acc = Op::e();
+        // per level: which lanes have a record there, and the level's base
+        if ((u32)lane < nlev)
+            s_base[warp][lane] = __ldg(qseg_base + (u64)(s - k0) * LMAX + lane) +
+                                 __ldg(qchunk_base + (u64)c * LMAX + lane);
         for (u32 lv = 0; lv < nlev; ++lv) {
-            const bool has = (bits0 >> lv) & 1u;
-            const u32 hb = __ballot_sync(0xffffffffu, has);
-            if (hb == 0u) continue;
-            const u32 base_q = __shfl_sync(0xffffffffu, my_q, lv);
-            u32 exq;
-            if (M <= 2) {
-                exq = (u32)__popc(hb & lt);
-            } else {
+            const u32 hb = __ballot_sync(0xffffffffu, (bits0 >> lv) & 1u);
+            if ((u32)lane == lv) s_mask[warp][lv] = hb;
+        }
+        __syncwarp();
+        typename Op::Acc acc = Op::e();
+        if (M <= 2) {
+            // one partial per query and level, at the level's base plus the
+            // query lanes of that level before this one; each lane walks only
+            // its own levels (unrolled so the loads run ahead of the adds)
+            u32 rem = bits0;
+#pragma unroll 4
+            while (rem) {
+                const u32 lv = __ffs(rem) - 1;
+                rem &= rem - 1;
+                const u32 slot = s_base[warp][lv] + (u32)__popc(s_mask[warp][lv] & lt);
+                if (slot < n_partial) acc = Op::F(acc, Op::from_part(partial[slot]));
+            }
+        }
+        if (M >= 3) {
+            // m = 3: exclusive sums of c1 over the lanes of each level (warp-uniform loop)
+            for (u32 lv = 0; lv < nlev; ++lv) {
+                const bool has = (bits0 >> lv) & 1u;
+                if (s_mask[warp][lv] == 0u) continue;
                 const u32 wq = has ? c1 : 0u;
                 u32 inc = wq;
 #pragma unroll
@@ -351,16 +372,15 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
                     const u32 nn = __shfl_up_sync(0xffffffffu, inc, o);
                     if (lane >= o) inc += nn;
                 }
-                exq = inc - wq;
-            }
-            if (has) {
-                const u32 base = base_q + exq;
-                const u32 cnt = M <= 2 ? 1u : c1;
-                for (u32 kk = 0; kk < cnt && base + kk < n_partial; ++kk)
-                    acc = Op::F(acc, Op::from_part(partial[base + kk]));
+                if (has) {
+                    const u32 base = s_base[warp][lv] + inc - wq;
+                    for (u32 kk = 0; kk < c1 && base + kk < n_partial; ++kk)
+                        acc = Op::F(acc, Op::from_part(partial[base + kk]));
+                }
             }
         }
         if (q) reinterpret_cast<typename Op::Out*>(I.out)[local] = Op::to_out(acc);
+        __syncwarp();
     }
 }
 

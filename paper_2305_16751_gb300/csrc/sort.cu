@@ -9,32 +9,45 @@ namespace domagg {
 
 // Persistent grid: as many CTAs as fit on the GPU at once (from the
 // occupancy calculator).
-template <typename K, typename V, bool IOTA>
+template <typename K, typename V>
 static u64 resident_ctas(size_t smem) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K, V, IOTA>, ONESWEEP_THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K, V, false, true>, ONESWEEP_THREADS, smem);
     return (u64)std::max(sms, 1) * (u64)std::max(per_sm, 1);
+}
+
+template <typename K, typename V, bool IOTA, bool STABLE>
+static void launch_pass(Launcher& L, unsigned grid, size_t smem, K* kin, V* vin, K* kout, V* vout,
+                        const SortSpace& sp, u32 range_items, const u32* seg_bits, const u32* range_base, int npass,
+                        int p, K keymask, int li) {
+    k_onesweep<K, V, IOTA, STABLE><<<grid, ONESWEEP_THREADS, smem, L.stream>>>(
+        kin, vin, kout, vout, sp.seg_off, sp.tile_off, sp.nseg, range_items, seg_bits, range_base, sp.digit_off,
+        npass, p, p * RADIX_BITS, keymask, sp.status, L.ctl, li);
 }
 
 template <typename K, typename V>
 int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool iota, int total_bits, K keymask,
-               int kind_hist, int kind_pass, const u32* seg_bits) {
+               int kind_hist, int kind_pass, const u32* seg_bits, bool stable) {
     constexpr u32 TILE = ONESWEEP_THREADS * onesweep_items<K, V>();
     static_assert(TILE >= SORT_MIN_TILE, "status words are sized for SORT_MIN_TILE");
     const int npass = (total_bits + RADIX_BITS - 1) / RADIX_BITS;
     const u64 ntiles = tiles_of(*sp.seg_sizes, TILE);
     if (npass == 0 || ntiles == 0) return 0;
     constexpr size_t smem = onesweep_smem<K, V>();
-    cudaFuncSetAttribute(k_onesweep<K, V, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_onesweep<K, V, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_onesweep<K, V, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_onesweep<K, V, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_onesweep<K, V, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_onesweep<K, V, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     // ranges: about four per resident CTA, whole tiles, never across segments
-    const u64 G = resident_ctas<K, V, false>(smem);
+    const u64 G = resident_ctas<K, V>(smem);
     const u64 rt = std::max<u64>(1, (ntiles + 4 * G - 1) / (4 * G));
     const u32 range_items = (u32)std::min<u64>(rt * TILE, 1ull << 30);
     const u64 nranges = tiles_of(*sp.seg_sizes, range_items);
     const unsigned grid = (unsigned)std::min<u64>(G, nranges);
+    // the first pass takes its range bases from the histogram (no count, no look-back)
+    u32* range_base = (sp.range_scratch && nranges <= sp.range_scratch_ranges) ? sp.range_scratch : nullptr;
     L.start(KIND_SMALL, 0.0);
     k_make_tiles<<<1, 1024, 0, L.stream>>>(sp.seg_off, sp.nseg, range_items, sp.tile_off);
     L.stop();
@@ -44,25 +57,32 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
     cudaMemsetAsync(sp.hist, 0, hist_bytes, L.stream);
     L.start(kind_hist, sp.n_items * sizeof(K));
     k_radix_hist<K><<<(unsigned)nranges, 256, hist_smem, L.stream>>>(
-        keys[0], sp.seg_off, sp.tile_off, sp.nseg, range_items, npass, 0, keymask, sp.hist);
+        keys[0], sp.seg_off, sp.tile_off, sp.nseg, range_items, npass, 0, keymask, sp.hist, range_base);
     L.stop();
     L.start(KIND_SMALL, 0.0);
     k_radix_offsets<<<sp.nseg * npass, RADIX, 0, L.stream>>>(sp.hist, sp.seg_off, npass, sp.digit_off);
     L.stop();
+    if (range_base) {
+        L.start(KIND_SMALL, 0.0);
+        k_range_bases<<<sp.nseg, RADIX, 0, L.stream>>>(sp.tile_off, sp.digit_off, npass, range_base);
+        L.stop();
+    }
     int cur = 0;
     for (int p = 0; p < npass; ++p) {
         const int li = L.lookback_index();
         // each pass reads and writes every (key, value) pair once
         const double vbytes = (iota && p == 0) ? sizeof(V) : 2.0 * sizeof(V);
         L.start(kind_pass, sp.n_items * (2.0 * sizeof(K) + vbytes));
-        if (iota && p == 0)
-            k_onesweep<K, V, true><<<grid, ONESWEEP_THREADS, smem, L.stream>>>(
-                keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], sp.seg_off, sp.tile_off, sp.nseg, range_items,
-                seg_bits, sp.digit_off, npass, p, p * RADIX_BITS, keymask, sp.status, L.ctl, li);
-        else
-            k_onesweep<K, V, false><<<grid, ONESWEEP_THREADS, smem, L.stream>>>(
-                keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], sp.seg_off, sp.tile_off, sp.nseg, range_items,
-                seg_bits, sp.digit_off, npass, p, p * RADIX_BITS, keymask, sp.status, L.ctl, li);
+        const u32* rb = p == 0 ? range_base : nullptr;
+        K *ki = keys[cur], *ko = keys[cur ^ 1];
+        V *vi = vals[cur], *vo = vals[cur ^ 1];
+        if (iota && p == 0) {
+            if (stable) launch_pass<K, V, true, true>(L, grid, smem, ki, vi, ko, vo, sp, range_items, seg_bits, rb, npass, p, keymask, li);
+            else launch_pass<K, V, true, false>(L, grid, smem, ki, vi, ko, vo, sp, range_items, seg_bits, rb, npass, p, keymask, li);
+        } else {
+            if (stable) launch_pass<K, V, false, true>(L, grid, smem, ki, vi, ko, vo, sp, range_items, seg_bits, rb, npass, p, keymask, li);
+            else launch_pass<K, V, false, false>(L, grid, smem, ki, vi, ko, vo, sp, range_items, seg_bits, rb, npass, p, keymask, li);
+        }
         L.stop();
         cur ^= 1;
     }
@@ -70,12 +90,12 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
 }
 
 template int sort_pairs<u32, u32>(Launcher&, const SortSpace&, u32**, u32**, bool, int, u32, int, int,
-                                     const u32*);
+                                     const u32*, bool);
 template int sort_pairs<u64, u32>(Launcher&, const SortSpace&, u64**, u32**, bool, int, u64, int, int,
-                                     const u32*);
+                                     const u32*, bool);
 template int sort_pairs<u32, u64>(Launcher&, const SortSpace&, u32**, u64**, bool, int, u32, int, int,
-                                     const u32*);
+                                     const u32*, bool);
 template int sort_pairs<u64, u64>(Launcher&, const SortSpace&, u64**, u64**, bool, int, u64, int, int,
-                                     const u32*);
+                                     const u32*, bool);
 
 }  // namespace domagg

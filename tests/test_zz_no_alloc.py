@@ -33,7 +33,7 @@ def _cases():
     rng = np.random.default_rng(31)
     p = workloads.tied_floats(n=12000)
     yield "m2 f32 sum", p.D, p.Q, p.w, "sum"
-    D, Q, w = workloads.random_small(rng, 3, 9000, 8000, 3000, "i32", "i64")
+    D, Q, w = workloads.random_small(rng, 3, 6000, 5000, 3000, "i32", "i64")
     yield "m3 i64 sum", D, Q, w, "sum"
     D, Q, w = workloads.random_small(rng, 2, 20000, 15000, 40000, "f32", "i32")
     yield "m2 i32 max", D, Q, w, "max"
