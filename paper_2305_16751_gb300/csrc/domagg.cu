@@ -529,8 +529,9 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         }
         // records sort (6m+2): stable, each level by the bits of its prefix
         if (C.T > 0 && npass > 0) {
+            std::vector<u32> sbits_host(h_sbits, h_sbits + nseg);
             SortSpace rs{d_so, (int)nseg, &seg_sizes, d_rtiles, (u32*)R[8], (u32*)R[9], (u64*)h->st_multi.p,
-                         (double)C.T, (u32*)R[10], sort_range_bound(seg_sizes)};
+                         (double)C.T, (u32*)R[10], sort_range_bound(seg_sizes), &sbits_host};
             const K keymask = ~(K(1) << (sizeof(K) * 8 - 1));  // all but the role bit
             sort_pairs<K, Pay>(L, rs, keys, pays, false, C.key_bits, keymask, KIND_HIST_RECORDS, KIND_SORT_RECORDS,
                                d_sbits);

@@ -93,6 +93,7 @@ struct SortSpace {
     double n_items;             // items sorted (for the algorithmic byte model)
     u32* range_scratch = nullptr;  // [range_scratch_ranges*RADIX]: first-pass bases per range
     u64 range_scratch_ranges = 0;
+    const std::vector<u32>* seg_bits_host = nullptr;  // host copy of seg_bits (byte model)
 };
 
 

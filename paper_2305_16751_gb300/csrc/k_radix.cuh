@@ -396,13 +396,26 @@ __global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_oneswee
                 }
             }
             __syncthreads();
+            // per (warp, digit): the warp's first local position; per digit:
+            // the global position of local index 0
+            // (then s_dstart is reused for the latter and the running
+            // positions advance by the tile's counts)
+            static_assert(THREADS == RADIX, "one thread per digit");
+            {
+                const int d = tid;
+                const u32 ds = s_dstart[d];
+                const u32 dn = d + 1 < RADIX ? s_dstart[d + 1] : n;
+                for (int w = 0; w < WARPS; ++w) s_whist[w * (RADIX + 1) + d] += ds;
+                const u32 gdst = s_run[d] - ds;
+                s_run[d] += dn - ds;
+                __syncthreads();
+                s_dstart[d] = gdst;
+            }
+            __syncthreads();
 #pragma unroll
             for (int i = 0; i < ITEMS; ++i) {
                 const u32 x = wbase + (u32)i * 32u + (u32)lane;
-                if (x < n) {
-                    const u32 d = digit_of(key[i], keymask, shift);
-                    pos[i] += s_dstart[d] + s_whist[warp * (RADIX + 1) + d];
-                }
+                if (x < n) pos[i] += wh[digit_of(key[i], keymask, shift)];
             }
             K* sk = reinterpret_cast<K*>(smem + b * SM::BUF);
             V* sv = reinterpret_cast<V*>(smem + b * SM::BUF + SM::KBYTES);
@@ -425,20 +438,14 @@ __global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_oneswee
                 if (x < n) sv[pos[i]] = val[i];
             }
             __syncthreads();
+            const u32 seg_len = L.seg_end - L.seg_begin;
             for (u32 x = tid; x < n; x += THREADS) {
                 const K k = sk[x];
-                const u32 d = digit_of(k, keymask, shift);
-                const u32 dst = s_run[d] + (x - s_dstart[d]);
-                if (dst >= L.seg_begin && dst < L.seg_end) {  // only fails after a timed-out wait
+                const u32 dst = s_dstart[digit_of(k, keymask, shift)] + x;  // (global position of index 0)
+                if (dst - L.seg_begin < seg_len) {  // only fails after a timed-out wait
                     kout[dst] = k;
                     vout[dst] = sv[x];
                 }
-            }
-            __syncthreads();
-            if (tid < RADIX) {  // advance the running positions by this tile's counts
-                const u32 d = tid;
-                const u32 next = d + 1 < RADIX ? s_dstart[d + 1] : n;
-                s_run[d] += next - s_dstart[d];
             }
             b ^= 1;
         }

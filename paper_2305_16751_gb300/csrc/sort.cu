@@ -70,9 +70,16 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
     int cur = 0;
     for (int p = 0; p < npass; ++p) {
         const int li = L.lookback_index();
-        // each pass reads and writes every (key, value) pair once
+        // each pass reads and writes every (key, value) pair it moves once;
+        // segments whose keys have fewer digits are not moved
+        double moved = sp.n_items;
+        if (seg_bits && sp.seg_bits_host) {
+            moved = 0;
+            for (size_t sgi = 0; sgi < sp.seg_sizes->size(); ++sgi)
+                if ((u32)p * RADIX_BITS < (*sp.seg_bits_host)[sgi]) moved += (double)(*sp.seg_sizes)[sgi];
+        }
         const double vbytes = (iota && p == 0) ? sizeof(V) : 2.0 * sizeof(V);
-        L.start(kind_pass, sp.n_items * (2.0 * sizeof(K) + vbytes));
+        L.start(kind_pass, moved * (2.0 * sizeof(K) + vbytes));
         const u32* rb = p == 0 ? range_base : nullptr;
         K *ki = keys[cur], *ko = keys[cur ^ 1];
         V *vi = vals[cur], *vo = vals[cur ^ 1];
