@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--n", type=int, default=2**24, help="|D| = |Q| of the m=2 workload")
     ap.add_argument("--n3", type=int, default=2**21, help="|D| = |Q| of the m=3 workload")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the baseline sample")
-    ap.add_argument("--no-extras", action="store_true", help="skip fwd_bwd, m3, e2e and the CPU baseline")
+    ap.add_argument("--no-extras", action="store_true", help="skip fwd_bwd, m3, batch, e2e and the CPU baseline")
+    ap.add_argument("--batch-k", type=int, default=512, help="instances of the batch workload")
     return ap.parse_args()
 
 
@@ -176,6 +177,31 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def bench_batch(args, dev, stream, torch, domagg, workloads):
+    """k instances of the batch workload (m in {2, 3}, |D| = |Q| log-uniform
+    in [256, 2^18], int32 coordinates uniform in [0, 2^31), float32 weights,
+    F = sum) in one domagg_batch call, against a loop of domagg_forward calls
+    over the same instances."""
+    probs = workloads.batch_instances(k=args.batch_k)
+    inst = [(torch.from_numpy(p.D).to(dev), torch.from_numpy(p.Q).to(dev), torch.from_numpy(p.w).to(dev))
+            for p in probs]
+    nq = sum(p.Q.shape[0] for p in probs)
+    npts = sum(p.Q.shape[0] + p.D.shape[0] for p in probs)
+    tb = timed_steps(lambda: domagg.batch(inst, "sum"), 2, 1, stream, torch)
+    b_ms = statistics.mean(tb)
+
+    def loop():
+        for D, Q, w in inst:
+            domagg.forward(D, Q, w, "sum")
+
+    tl = timed_steps(loop, 1, 1, stream, torch)
+    l_ms = statistics.mean(tl)
+    return {"value": nq / (b_ms / 1e3), "unit": "queries/s", "ms_per_step": b_ms, "instances": len(probs),
+            "points": npts, "queries": nq, "per_instance_loop": {"value": nq / (l_ms / 1e3), "ms_per_step": l_ms},
+            "workload": f"{len(probs)} instances, m in {{2,3}} 50/50, |D|=|Q| log-uniform [256, 2^18], "
+                        "int32 coords U[0,2^31), f32 w, sum"}
+
+
 def timed_steps(fn, steps, warmup, stream, torch):
     for _ in range(warmup):
         fn()
@@ -290,6 +316,7 @@ def main():
         line["m3"] = {"value": p3.Q.shape[0] / (m3_ms / 1e3), "unit": "queries/s", "ms_per_step": m3_ms,
                       "workload": "m3_nD2^21_nQ2^21_gmm_i32coords_i64w_sum", "records": st3["n_records"]}
         del D3, Q3, w3, o3
+        line["batch"] = bench_batch(args, dev, stream, torch, domagg, workloads)
         # end to end through the host-buffer entry point
         Dh = torch.from_numpy(p.D).pin_memory()
         Qh = torch.from_numpy(p.Q).pin_memory()

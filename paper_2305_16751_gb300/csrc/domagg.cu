@@ -388,7 +388,19 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         int key_bits;
     };
     std::vector<Chunk> chunks;
-    const u64 chunk_cap = (1ull << 32) - 65536;
+    // a chunk's records must fit 32-bit positions and the device: at most
+    // ~60% of the free memory (plus the record workspace already held)
+    u64 chunk_cap = (1ull << 32) - 65536;
+    {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+            const double per_rec = 2.0 * sizeof(K) + 2.0 * sizeof(Pay) + sizeof(Part) + 8.0;
+            const double budget = std::max(0.6 * (double)free_b + (double)h->recs.cap, 2.0e9);
+            chunk_cap = std::min<u64>(chunk_cap, (u64)(budget / per_rec));
+        } else {
+            cudaGetLastError();
+        }
+    }
     {
         Chunk c{0, 0, 0, 0, 0, 0};
         for (int s = 0; s < k; ++s) {
