@@ -395,8 +395,10 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         size_t free_b = 0, total_b = 0;
         if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
             const double per_rec = 2.0 * sizeof(K) + 2.0 * sizeof(Pay) + sizeof(Part) + 8.0;
-            const double budget = std::max(0.6 * (double)free_b + (double)h->recs.cap, 2.0e9);
-            chunk_cap = std::min<u64>(chunk_cap, (u64)(budget / per_rec));
+            double budget = std::max(0.6 * (double)free_b + (double)h->recs.cap, 2.0e9);
+            // a capped handle also caps the records of one chunk
+            if (h->max_ws) budget = std::min(budget, 0.5 * (double)(h->max_ws - std::min(h->max_ws, h->held() - h->recs.cap)));
+            chunk_cap = std::max<u64>(1, std::min<u64>(chunk_cap, (u64)(budget / per_rec)));
         } else {
             cudaGetLastError();
         }

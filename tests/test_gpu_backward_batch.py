@@ -104,3 +104,35 @@ def test_batch_workload_shape_small():
     torch().cuda.synchronize()
     for p, o in zip(probs, outs):
         assert_matches_oracle(o.cpu().numpy(), p.D, p.Q, p.w, "sum")
+
+
+def test_batch_split_into_record_chunks():
+    """A handle whose workspace cap is small processes a batch in several
+    record chunks (a synchronisation between them); results equal the
+    single calls."""
+    import ctypes
+    t = torch()
+    rng = np.random.default_rng(5)
+    probs = []
+    for i in range(12):
+        m = 2 + (i % 2)
+        D, Q, w = workloads.random_small(rng, m, 3000 + 100 * i, 2500, 2000, "i32", "i64")
+        probs.append((D, Q, w))
+    h = domagg.domagg_create(0, 64 << 20)
+    try:
+        arr = (domagg.domagg_instance * len(probs))()
+        keep, outs = [], []
+        for i, (D, Q, w) in enumerate(probs):
+            Dd, Qd, wd = to_dev(D), to_dev(Q), to_dev(w)
+            o = t.empty(Q.shape[0], dtype=t.int64, device="cuda")
+            keep += [Dd, Qd, wd]
+            outs.append(o)
+            arr[i] = domagg.domagg_instance(D.shape[1], D.shape[0], Q.shape[0], Dd.data_ptr(), Qd.data_ptr(),
+                                            wd.data_ptr(), o.data_ptr())
+        domagg.domagg_batch(h, len(probs), arr, domagg.DTYPES["i32"], domagg.DTYPES["i64"], domagg.OPS["sum"],
+                            ctypes.c_void_p(t.cuda.current_stream().cuda_stream))
+        t.cuda.synchronize()
+        for (D, Q, w), o in zip(probs, outs):
+            assert np.array_equal(o.cpu().numpy(), gpu_forward(D, Q, w, "sum"))
+    finally:
+        domagg.domagg_destroy(h)
