@@ -202,6 +202,18 @@ def bench_batch(args, dev, stream, torch, domagg, workloads):
                         "int32 coords U[0,2^31), f32 w, sum"}
 
 
+def job_throughput(local_ms: float, units_per_rank: int, world: int, device=None):
+    """Whole-job throughput: every rank's units over the slowest rank's time
+    (max over ranks of the timed region).  Returns (units/s, max ms)."""
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return world * units_per_rank / (ms / 1e3), ms
+
+
 def timed_steps(fn, steps, warmup, stream, torch):
     for _ in range(warmup):
         fn()
@@ -259,13 +271,8 @@ def main():
         times = timed_steps(step, args.steps, args.warmup, stream, torch)
     kinds = domagg.domagg_timing_read(h)
     domagg.domagg_timing_enable(h, False)
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    value, total_ms = job_throughput(sum(times), p.Q.shape[0] * args.steps, world, dev)
     ms = total_ms / args.steps
-    value = world * p.Q.shape[0] / (ms / 1e3)
     st = domagg.stats(local)
     # kinds were logged over warmup + steps calls
     calls = args.warmup + args.steps

@@ -1,0 +1,52 @@
+"""The multi-process path of bench.py (one process per GPU, independent
+replicas) on CPU: two gloo ranks agree on the slowest rank's time and on
+the whole-job throughput (all ranks' queries over that time)."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        local_ms = [40.0, 100.0][rank]  # rank 1 is the slowest
+        value, ms = bench.job_throughput(local_ms, 1000, world)
+        q.put((rank, value, ms))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_job_throughput_is_max_over_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, value, ms in res:
+        assert ms == pytest.approx(100.0)
+        assert value == pytest.approx(2 * 1000 / 0.1)
+
+
+def test_single_process_throughput():
+    import bench
+    value, ms = bench.job_throughput(50.0, 500, 1)
+    assert ms == 50.0 and value == pytest.approx(500 / 0.05)
