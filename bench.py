@@ -114,21 +114,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def profiled_traffic(records: int):
-    """DRAM bytes of one records radix pass, from the committed ncu summary
-    (bytes per record, scaled to this workload's record count); None if the
-    kernel source changed since that capture."""
+def profiled_traffic(bytes_per_launch: float):
+    """DRAM bytes of one records radix pass: the committed ncu summary's
+    measured DRAM bytes per algorithmic byte (read + write of every key and
+    value a pass moves), times this run's algorithmic bytes per launch; None
+    if the kernel source changed since that capture."""
     import hashlib
     src = os.path.join(ROOT, "paper_2305_16751_gb300", "csrc", "k_radix.cuh")
     prof = os.path.join(ROOT, "profiles", "k_onesweep_records_m2_n2e22.md")
     try:
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        fields = dict(ln.split(":", 1) for ln in open(prof) if ln.startswith(("kernel_source", "traffic_bytes")))
+        fields = dict(ln.split(":", 1) for ln in open(prof) if ln.startswith(("kernel_source", "traffic_per")))
     except (OSError, ValueError):
         return None
     if fields.get("kernel_source_sha256_16", "").strip() != digest:
         return None
-    return float(fields["traffic_bytes_per_record"]) * records
+    return float(fields["traffic_per_algorithmic_byte"]) * bytes_per_launch
 
 
 def cpu_baseline(p, seconds: float):
@@ -287,9 +288,10 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": args.n, "m": 2, "op": "sum", "weights": "f32",
                        "records": st["n_records"], "record_passes": st["record_passes"],
-                       "l2": "inputs (320 MB) and workspace (>6 GB) exceed the 129 MB L2; no flush"},
+                       "l2": f"inputs ({(p.D.nbytes + p.Q.nbytes + p.w.nbytes) >> 20} MB) and the records workspace "
+                             f"({st['n_records'] * 16 >> 20} MB) exceed the 129 MB L2; no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(st["n_records"]),
+                         "frac": achieved / peak, "traffic": profiled_traffic(dom["bytes"] / max(dom["launches"], 1)),
                          "peak_source": peak_src,
                          "kernel": "k_onesweep (records radix pass)",
                          "launch_ms": dom["ms"] / max(dom["launches"], 1),

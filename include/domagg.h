@@ -126,17 +126,17 @@ typedef struct {
 /* k independent problems in one call: every phase of the pipeline runs as one
  * segmented launch over all instances with the same m (instances never mix:
  * sorts, scans and reductions restart at instance boundaries).  `inst` is a
- * host array of k descriptors; coord/weight dtype and op are shared.  The
- * call does not synchronise the stream: workspace is sized from host-side
- * bounds on the record counts, so the whole call can be captured in a CUDA
- * graph (see domagg_batch_plan). */
+ * host array of k descriptors; coord/weight dtype and op are shared.  Like
+ * domagg_forward, the call synchronises `stream` once per group of
+ * instances with the same m (to read their record counts) and once more per
+ * record chunk when the records of a group do not fit the workspace at once
+ * (a chunk holds whole instances); the remaining work is left enqueued. */
 domagg_status domagg_batch(domagg_handle h, int k, const domagg_instance* inst,
                            domagg_dtype coord_dtype, domagg_dtype weight_dtype, domagg_op op,
                            void* stream);
 
-/* Allocates the workspace that domagg_batch needs for these instances, so that
- * a later domagg_batch with the same sizes allocates nothing (required before
- * capturing it in a CUDA graph). */
+/* Reserved for planning a batch for CUDA-graph capture.  Not implemented:
+ * returns DOMAGG_ERR_UNSUPPORTED (domagg_batch synchronises, see above). */
 domagg_status domagg_batch_plan(domagg_handle h, int k, const domagg_instance* inst,
                                 domagg_dtype coord_dtype, domagg_dtype weight_dtype,
                                 domagg_op op);
