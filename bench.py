@@ -182,7 +182,8 @@ def bench_batch(args, dev, stream, torch, domagg, workloads):
     """k instances of the batch workload (m in {2, 3}, |D| = |Q| log-uniform
     in [256, 2^18], int32 coordinates uniform in [0, 2^31), float32 weights,
     F = sum) in one domagg_batch call, against a loop of domagg_forward calls
-    over the same instances."""
+    over the same instances, and as a planned batch replayed from a CUDA
+    graph."""
     probs = workloads.batch_instances(k=args.batch_k)
     inst = [(torch.from_numpy(p.D).to(dev), torch.from_numpy(p.Q).to(dev), torch.from_numpy(p.w).to(dev))
             for p in probs]
@@ -197,8 +198,22 @@ def bench_batch(args, dev, stream, torch, domagg, workloads):
 
     tl = timed_steps(loop, 1, 1, stream, torch)
     l_ms = statistics.mean(tl)
+    # the planned batch captured once in a CUDA graph, then replayed
+    plan = domagg.BatchPlan(inst, "sum", headroom=0.05)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            plan.run()
+    tg = timed_steps(graph.replay, 3, 1, stream, torch)
+    plan.status()
+    g_ms = statistics.mean(tg)
+    plan_gb = plan.workspace_bytes() / 1e9
+    plan.close()
     return {"value": nq / (b_ms / 1e3), "unit": "queries/s", "ms_per_step": b_ms, "instances": len(probs),
             "points": npts, "queries": nq, "per_instance_loop": {"value": nq / (l_ms / 1e3), "ms_per_step": l_ms},
+            "graph_replay": {"value": nq / (g_ms / 1e3), "ms_per_step": g_ms, "plan_workspace_gb": plan_gb},
             "workload": f"{len(probs)} instances, m in {{2,3}} 50/50, |D|=|Q| log-uniform [256, 2^18], "
                         "int32 coords U[0,2^31), f32 w, sum"}
 

@@ -135,11 +135,45 @@ domagg_status domagg_batch(domagg_handle h, int k, const domagg_instance* inst,
                            domagg_dtype coord_dtype, domagg_dtype weight_dtype, domagg_op op,
                            void* stream);
 
-/* Reserved for planning a batch for CUDA-graph capture.  Not implemented:
- * returns DOMAGG_ERR_UNSUPPORTED (domagg_batch synchronises, see above). */
-domagg_status domagg_batch_plan(domagg_handle h, int k, const domagg_instance* inst,
-                                domagg_dtype coord_dtype, domagg_dtype weight_dtype,
-                                domagg_op op);
+/* A planned batch: the same k problems (same descriptors: pointers and sizes)
+ * run again and again -- for instance replayed from a CUDA graph -- with the
+ * contents of their buffers free to change between runs.  The paper has no
+ * counterpart (it is the pipeline of domagg_batch, Sec. 4 with Sec. 5, with
+ * its host-side layout step moved to the device).
+ *
+ * domagg_batch_plan runs the batch on `stream` twice (writing the outputs
+ * each time) and returns when both runs have finished: the first run
+ * measures every instance's record counts; the plan then reserves, in a
+ * private workspace on `device`, room for (1 + headroom) times those counts
+ * (plus 1024) per record chunk, and the second, planned run allocates that
+ * workspace for good.  headroom >= 0.  The descriptors in `inst` are copied;
+ * the buffers they point to must outlive the plan.
+ *
+ * domagg_plan_run enqueues one planned run on `stream`: kernel launches only
+ * -- no synchronisation, no allocation, no host<->device copy -- so it can be
+ * captured into a CUDA graph and replayed.  The record layout is computed on
+ * the device from the current record counts.  If a run meets more records
+ * (or query records) in a chunk than the plan reserved, the kernels of that
+ * chunk write nothing outside the workspace, its outputs are undefined, and
+ * DOMAGG_ERR_OOM is recorded for domagg_plan_status.  Device errors of a run
+ * (NaN coordinates, a bounded wait that ran out, capacity) are only reported
+ * by domagg_plan_status.  Runs of one plan must not overlap on the device
+ * (one stream, or graph launches ordered on one stream).
+ *
+ * domagg_plan_status synchronises `stream` and returns (and clears) the first
+ * device-side error recorded by the plan's runs, or DOMAGG_OK.
+ * domagg_plan_workspace_bytes returns the device bytes the plan holds.
+ * domagg_plan_destroy waits for the device and frees the plan. */
+typedef struct domagg_plan_s* domagg_plan;
+
+domagg_status domagg_batch_plan(domagg_plan* out, int device, int k, const domagg_instance* inst,
+                                domagg_dtype coord_dtype, domagg_dtype weight_dtype, domagg_op op,
+                                double headroom, void* stream);
+domagg_status domagg_plan_run(domagg_plan p, void* stream);
+domagg_status domagg_plan_status(domagg_plan p, void* stream);
+const char* domagg_plan_last_error(domagg_plan p);
+int64_t domagg_plan_workspace_bytes(domagg_plan p);
+domagg_status domagg_plan_destroy(domagg_plan p);
 
 /* Synchronises `stream` and returns the first device-side error recorded by
  * this handle's kernels since the last check (DOMAGG_ERR_TIMEOUT,

@@ -16,6 +16,7 @@ enum : u32 {
     ERR_NAN = 2u,       // a NaN coordinate was met
     ERR_OVERFLOW = 4u,  // the record count does not fit 32 bits
     ERR_EPOCH = 8u,     // the look-back epoch counter is about to wrap
+    ERR_CAPACITY = 16u, // a planned run met more records than its plan reserved
 };
 
 constexpr int MAX_LAUNCHES = 64;  // look-back launches per pipeline run

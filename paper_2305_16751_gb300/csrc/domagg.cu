@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -62,6 +63,7 @@ struct domagg_ctx {
     std::vector<cudaEvent_t> pool;
     size_t pool_used = 0;
     u64 epoch_mirror = 0;  // host copy of Ctl::epoch_base
+    bool frozen = false;   // owned by a plan: its workspace must not grow any more
 
     size_t held() const { return pts.cap + recs.cap + st_multi.cap + st_seg.cap + stage.cap; }
 };
@@ -83,6 +85,7 @@ domagg_status cuda_fail(domagg_ctx* h, cudaError_t e, const char* where) {
 // current epoch.
 domagg_status grow(domagg_ctx* h, DevBuf& b, size_t bytes, bool zero = false) {
     if (b.cap >= bytes) return DOMAGG_OK;
+    if (h->frozen) return fail(h, DOMAGG_ERR_OOM, "a planned run needs more workspace than its plan reserved");
     size_t want = std::max(bytes, b.cap + b.cap / 4);
     if (h->max_ws && h->held() - b.cap + want > h->max_ws) {
         want = bytes;
@@ -116,6 +119,7 @@ domagg_status grow(domagg_ctx* h, DevBuf& b, size_t bytes, bool zero = false) {
 
 domagg_status grow_pinned(domagg_ctx* h, size_t bytes) {
     if (h->h_pin_cap >= bytes) return DOMAGG_OK;
+    if (h->frozen) return fail(h, DOMAGG_ERR_OOM, "a planned run needs more pinned memory than its plan reserved");
     if (h->h_pin) {
         cudaDeviceSynchronize();
         cudaFreeHost(h->h_pin);
@@ -136,6 +140,7 @@ domagg_status device_error(domagg_ctx* h, u32 bits) {
     if (bits & ERR_OVERFLOW) return fail(h, DOMAGG_ERR_UNSUPPORTED, "more than 2^32 flat-map records");
     if (bits & ERR_TIMEOUT) return fail(h, DOMAGG_ERR_TIMEOUT, "a bounded device-side wait ran out");
     if (bits & ERR_EPOCH) return fail(h, DOMAGG_ERR_TIMEOUT, "look-back epoch counter wrapped");
+    if (bits & ERR_CAPACITY) return fail(h, DOMAGG_ERR_OOM, "more records than the plan reserved (outputs undefined)");
     return DOMAGG_OK;
 }
 
@@ -172,11 +177,27 @@ void maybe_reset_epochs(domagg_ctx* h, cudaStream_t s) {
     h->epoch_mirror = 0;
 }
 
+// A record chunk of a planned batch: whole instances [k0, k1) whose records
+// get a fixed capacity, laid out on the device (k_layout) instead of on the
+// host, so a planned run never reads a count back.
+struct PlannedChunk {
+    int k0, k1;
+    u64 T_cap, Tq_cap;   // reserved records and query records (>= 1)
+    int nslot;           // segment slots: every instance's largest possible level count
+    int key_bits;        // bound on the node-key bits of any level
+    u32* d_slot_map;     // device [nslot]: (instance - k0) << 5 | level
+};
+
 // ---------------------------------------------------------------------------
 // the pipeline for instances with the same m
 // ---------------------------------------------------------------------------
+// With `planned`, the run takes its record chunks and capacities from a plan
+// and neither synchronises, allocates, copies from the host nor changes a
+// kernel attribute (it may be captured in a CUDA graph); the point tables were
+// uploaded by the plan's earlier runs and are still in place.
 template <int M, class Op, bool F32>
-domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStream_t stream) {
+domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStream_t stream,
+                  const std::vector<PlannedChunk>* planned = nullptr) {
     typedef typename std::conditional<M == 3, u64, u32>::type K;
     typedef typename Op::Pay Pay;
     typedef typename Op::Part Part;
@@ -231,7 +252,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         P[15] = c.take<u32>(k + 1);  // chunk offsets
         P[16] = c.take<u32>((size_t)NC * LMAX);  // query chunk bases per level
         P[17] = c.take<u32>((size_t)k * LMAX);   // query records per (instance, level)
-        P[18] = nullptr;
+        P[18] = c.take<Pay>(WT == 3 ? 0 : N);  // weights in the order of the last coordinate
         P[19] = c.take<u32>((size_t)k * 4 * RADIX);  // hist
         P[20] = c.take<u32>((size_t)k * 4 * RADIX);  // digit offsets
         P[21] = c.take<u32>(k + 1);                  // the sorts' tile map
@@ -269,11 +290,13 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     const size_t up_bytes = sizeof(Inst) * k + 3 * sizeof(u32) * (k + 1);
     const size_t lvl_pos = (up_bytes + 63) & ~(size_t)63;                          // level totals (read back)
     const size_t ctl_pos = (lvl_pos + 2 * sizeof(u32) * k * LMAX + 63) & ~(size_t)63;  // control block (read back)
+    char* hp = nullptr;
+    if (!planned) {
     {
         domagg_status st = grow_pinned(h, ctl_pos + sizeof(Ctl) + 64);
         if (st) return st;
     }
-    char* hp = (char*)h->h_pin;
+    hp = (char*)h->h_pin;
     memcpy(hp, inst.data(), sizeof(Inst) * k);
     memcpy(hp + sizeof(Inst) * k, pt_offs.data(), sizeof(u32) * (k + 1));
     memcpy(hp + sizeof(Inst) * k + sizeof(u32) * (k + 1), q_offs.data(), sizeof(u32) * (k + 1));
@@ -284,12 +307,14 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                     cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(d_chunk_off, hp + sizeof(Inst) * k + 2 * sizeof(u32) * (k + 1), sizeof(u32) * (k + 1),
                     cudaMemcpyHostToDevice, stream);
-
     maybe_reset_epochs(h, stream);
+    }
+
     Launcher L;
+    L.frozen = planned != nullptr;
     L.stream = stream;
     L.ctl = h->ctl;
-    L.timing = h->timing;
+    L.timing = h->timing && !planned;
     L.log = &h->log;
     L.pool = &h->pool;
     L.pool_used = &h->pool_used;
@@ -337,13 +362,42 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     // ---- count / offset scan of the flat map, per level
     {
         const int li = L.lookback_index();
-        L.start(KIND_COUNT_SCAN, (double)N * (4 + 4 * (M - 1) + 4 * (M - 1) + 4) + (double)NC * 8 * LMAX);
-        k_count_scan<M><<<(unsigned)ntp, 256, 0, stream>>>(perm, d_pt_offs, d_pt_tiles, k, d_chunk_off, r0, r1, d_inst,
-                                                           pr0, pr1, pj, chunk_base, qchunk_base, lvl_tot, qlvl_tot,
+        // perm, gathered ranks, ranks / index / weight written in order, weight gathered
+        L.start(KIND_COUNT_SCAN, (double)N * (4 + 8.0 * (M - 1) + 4 + (WT == 3 ? 0 : 2.0 * sizeof(Pay))) +
+                                     (double)NC * 8 * LMAX);
+        k_count_scan<M, Pay, WT><<<(unsigned)ntp, 256, 0, stream>>>(
+            perm, d_pt_offs, d_pt_tiles, k, d_chunk_off, r0, r1, d_inst, pr0, pr1, pj, (Pay*)P[18], chunk_base,
+            qchunk_base, lvl_tot, qlvl_tot,
                                                            (u64*)h->st_multi.p, h->ctl, li);
         L.stop();
     }
-    // ---- the one synchronisation: record counts and device errors
+    // ---- record chunks: from the counts (one synchronisation) or from the plan
+    struct Chunk {
+        int k0, k1;
+        u64 T, Tq, nseg;
+        int key_bits;
+        const u32* slot_map;  // planned: the chunk's segment slots (device)
+    };
+    std::vector<Chunk> chunks;
+    std::vector<u32> nlev(k), lvl, qlvl;
+    auto level_bits = [&](int s, u32 lv) -> u32 {
+        if (M == 1) return 0u;
+        const u32 b = inst[s].b[0] - 1u - lv;  // prefix length of level lv
+        return M == 2 ? b : b + inst[s].b[1];
+    };
+    // pinned upload area of every chunk: per instance record and slot bases,
+    // per segment offsets and key bits, per (instance, level) segment bases
+    auto chunk_upload_words = [&](const Chunk& c) -> size_t {
+        const size_t kc = (size_t)(c.k1 - c.k0);
+        return 2 * (kc + 1) + (c.nseg + 1) + c.nseg + 2 * kc * LMAX;
+    };
+    std::vector<size_t> base_pos;
+    cudaError_t e = cudaSuccess;
+    if (planned) {
+        for (const PlannedChunk& pc : *planned)
+            chunks.push_back(Chunk{pc.k0, pc.k1, pc.T_cap, pc.Tq_cap, (u64)pc.nslot, pc.key_bits, pc.d_slot_map});
+    } else {
+    // the one synchronisation: record counts and device errors
     Inst* h_inst = (Inst*)hp;
     u32* h_lvl = (u32*)(hp + lvl_pos);
     Ctl* h_ctl = (Ctl*)(hp + ctl_pos);
@@ -353,7 +407,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     cudaMemcpyAsync(h_lvl + (size_t)k * LMAX, qlvl_tot, sizeof(u32) * k * LMAX, cudaMemcpyDeviceToHost, stream);
     cudaMemcpyAsync(h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream);
     L.stop();
-    cudaError_t e = cudaStreamSynchronize(stream);
+    e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "point phase");
     if (h_ctl->error) {
         const u32 bits = h_ctl->error;
@@ -362,7 +416,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         return device_error(h, bits);
     }
     // per instance: its levels, their record counts and sort-key bits
-    std::vector<u32> nlev(k), lvl(h_lvl, h_lvl + (size_t)k * LMAX), qlvl(h_lvl + (size_t)k * LMAX, h_lvl + (size_t)2 * k * LMAX);
+    lvl.assign(h_lvl, h_lvl + (size_t)k * LMAX);
+    qlvl.assign(h_lvl + (size_t)k * LMAX, h_lvl + (size_t)2 * k * LMAX);
     for (int s = 0; s < k; ++s) {
         inst[s] = h_inst[s];
         nlev[s] = inst[s].nQ + inst[s].nD == 0 ? 0u : (M == 1 ? 1u : inst[s].b[0]);
@@ -375,21 +430,10 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         inst[s].T = (u32)T;
         inst[s].Tq = (u32)Tq;
     }
-    auto level_bits = [&](int s, u32 lv) -> u32 {
-        if (M == 1) return 0u;
-        const u32 b = inst[s].b[0] - 1u - lv;  // prefix length of level lv
-        return M == 2 ? b : b + inst[s].b[1];
-    };
 
-    // ---- plan chunks of instances whose records fit one record workspace
-    struct Chunk {
-        int k0, k1;
-        u64 T, Tq, nseg;
-        int key_bits;
-    };
-    std::vector<Chunk> chunks;
-    // a chunk's records must fit 32-bit positions and the device: at most
-    // ~60% of the free memory (plus the record workspace already held)
+    // chunks of instances whose records fit one record workspace: below
+    // 2^32 records and ~60% of the free memory (plus the record workspace
+    // already held)
     u64 chunk_cap = (1ull << 32) - 65536;
     {
         size_t free_b = 0, total_b = 0;
@@ -404,12 +448,12 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         }
     }
     {
-        Chunk c{0, 0, 0, 0, 0, 0};
+        Chunk c{0, 0, 0, 0, 0, 0, nullptr};
         for (int s = 0; s < k; ++s) {
             const u64 Ts = inst[s].T;
             if (c.k1 > c.k0 && c.T + Ts > chunk_cap) {
                 chunks.push_back(c);
-                c = Chunk{s, s, 0, 0, 0, 0};
+                c = Chunk{s, s, 0, 0, 0, 0, nullptr};
             }
             c.k1 = s + 1;
             c.T += Ts;
@@ -419,13 +463,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         }
         if (c.k1 > c.k0) chunks.push_back(c);
     }
-    // pinned upload area of every chunk: per instance record and slot bases,
-    // per segment offsets and key bits, per (instance, level) segment bases
-    auto chunk_upload_words = [&](const Chunk& c) -> size_t {
-        const size_t kc = (size_t)(c.k1 - c.k0);
-        return 2 * (kc + 1) + (c.nseg + 1) + c.nseg + 2 * kc * LMAX;
-    };
-    std::vector<size_t> base_pos(chunks.size());
+    base_pos.resize(chunks.size());
     size_t pin_need = ctl_pos + sizeof(Ctl);
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
         base_pos[ci] = (pin_need + 63) & ~(size_t)63;
@@ -437,6 +475,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         if (st) return st;
         hp = (char*)h->h_pin;
     }
+    }
 
     u64 T_all = 0, Tq_all = 0;
     int kb_all = 0, passes_all = 0;
@@ -444,16 +483,22 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         const Chunk& C = chunks[ci];
         const int kc = C.k1 - C.k0;
         const u64 nseg = C.nseg;
-        u32* hb = (u32*)(hp + base_pos[ci]);
-        u32* h_rb = hb;                      // [kc+1] record base per instance
-        u32* h_qb = hb + kc + 1;             // [kc+1] query-slot base per instance
-        u32* h_so = h_qb + kc + 1;           // [nseg+1] segment offsets
-        u32* h_sbits = h_so + nseg + 1;      // [nseg] segment key bits
-        u32* h_sbase = h_sbits + nseg;       // [kc][LMAX] segment base per (instance, level)
-        u32* h_qsbase = h_sbase + (size_t)kc * LMAX;  // [kc][LMAX] query-slot base per (instance, level)
-        std::vector<u64> seg_sizes(nseg);
+        u32 *hb = nullptr, *h_rb = nullptr, *h_qb = nullptr, *h_so = nullptr, *h_sbits = nullptr, *h_sbase = nullptr,
+            *h_qsbase = nullptr;
+        if (!planned) {
+            hb = (u32*)(hp + base_pos[ci]);
+            h_rb = hb;                            // [kc+1] record base per instance
+            h_qb = hb + kc + 1;                   // [kc+1] query-slot base per instance
+            h_so = h_qb + kc + 1;                 // [nseg+1] segment offsets
+            h_sbits = h_so + nseg + 1;            // [nseg] segment key bits
+            h_sbase = h_sbits + nseg;             // [kc][LMAX] segment base per (instance, level)
+            h_qsbase = h_sbase + (size_t)kc * LMAX;  // [kc][LMAX] query-slot base per (instance, level)
+        }
+        std::vector<u64> seg_sizes(planned ? 0 : nseg);
         u64 nts = 0;
-        {
+        if (planned) {
+            nts = C.T / SEG_TILE + nseg;  // bound: sum ceil(n_s / tile) <= T / tile + nseg
+        } else {
             u64 a = 0, b = 0, sg = 0;
             for (int s = C.k0; s < C.k1; ++s) {
                 h_rb[s - C.k0] = (u32)a;
@@ -480,7 +525,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             h_so[nseg] = (u32)a;
         }
         const int npass = (C.key_bits + RADIX_BITS - 1) / RADIX_BITS;
-        const u64 ntr = tiles_of(seg_sizes, SORT_MIN_TILE);
+        const u64 ntr = planned ? C.T / SORT_MIN_TILE + nseg : tiles_of(seg_sizes, SORT_MIN_TILE);
+        const u64 nrange_bound = planned ? sort_range_bound_n(C.T, nseg) : sort_range_bound(seg_sizes);
         // record workspace
         auto carve_recs = [&](Carver& c, void** R) {
             R[0] = c.take<u32>(chunk_upload_words(C));  // the uploaded bases and segment tables
@@ -493,7 +539,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             R[7] = c.take<Part>(C.Tq);
             R[8] = c.take<u32>((size_t)nseg * std::max(npass, 1) * RADIX);
             R[9] = c.take<u32>((size_t)nseg * std::max(npass, 1) * RADIX);
-            R[10] = c.take<u32>((size_t)sort_range_bound(seg_sizes) * RADIX);  // first-pass range bases
+            R[10] = c.take<u32>((size_t)nrange_bound * RADIX);  // first-pass range bases
         };
         void* R[11];
         {
@@ -518,14 +564,22 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         K* keys[2] = {(K*)R[3], (K*)R[4]};
         Pay* pays[2] = {(Pay*)R[5], (Pay*)R[6]};
         Part* partial = (Part*)R[7];
-        cudaMemcpyAsync(d_up, hb, sizeof(u32) * chunk_upload_words(C), cudaMemcpyHostToDevice, stream);
+        if (!planned) {
+            cudaMemcpyAsync(d_up, hb, sizeof(u32) * chunk_upload_words(C), cudaMemcpyHostToDevice, stream);
+            maybe_reset_epochs(h, stream);
+        }
         // fresh epoch and tile counters for the record phase of this chunk
-        maybe_reset_epochs(h, stream);
         L.start(KIND_SMALL, 0.0);
         k_begin<<<1, 64, 0, stream>>>(h->ctl);
         L.stop();
         h->epoch_mirror += MAX_LAUNCHES;
         L.next_lookback = 0;
+        if (planned) {
+            L.start(KIND_SMALL, 0.0);
+            k_layout<M><<<1, 1024, 0, stream>>>(d_inst, C.k0, lvl_tot, qlvl_tot, C.slot_map, (int)nseg, C.T, C.Tq,
+                                                d_so, d_sbits, d_sbase, d_qsbase, h->ctl);
+            L.stop();
+        }
         L.start(KIND_SMALL, 0.0);
         k_make_tiles<<<1, 1024, 0, stream>>>(d_so, (int)nseg, SEG_TILE, d_stiles);
         L.stop();
@@ -534,18 +588,21 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         const u64 nchunk = chunk_off[C.k1] - chunk_off[C.k0];
         if (C.T > 0) {
             const unsigned grid = (unsigned)std::min<u64>((nchunk + 7) / 8, 152ull * 16);
-            L.start(KIND_EXPAND, (double)(pt_offs[C.k1] - pt_offs[C.k0]) * (4.0 * (M - 1) + 12) +
+            L.start(KIND_EXPAND, (double)(pt_offs[C.k1] - pt_offs[C.k0]) * (4.0 * (M - 1) + sizeof(Pay)) +
                                      (double)C.T * (sizeof(K) + sizeof(Pay)));
             k_expand<M, K, Pay, WT><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pj,
+                                                             (const Pay*)P[18],
                                                              chunk_base, qchunk_base, d_inst, d_sbase, d_qsbase,
                                                              (u32)C.T, keys[0], pays[0]);
             L.stop();
         }
         // records sort (6m+2): stable, each level by the bits of its prefix
         if (C.T > 0 && npass > 0) {
-            std::vector<u32> sbits_host(h_sbits, h_sbits + nseg);
-            SortSpace rs{d_so, (int)nseg, &seg_sizes, d_rtiles, (u32*)R[8], (u32*)R[9], (u64*)h->st_multi.p,
-                         (double)C.T, (u32*)R[10], sort_range_bound(seg_sizes), &sbits_host};
+            std::vector<u32> sbits_host;
+            if (!planned) sbits_host.assign(h_sbits, h_sbits + nseg);
+            SortSpace rs{d_so, (int)nseg, planned ? nullptr : &seg_sizes, d_rtiles, (u32*)R[8], (u32*)R[9],
+                         (u64*)h->st_multi.p, (double)C.T, (u32*)R[10], nrange_bound,
+                         planned ? nullptr : &sbits_host, C.T};
             const K keymask = ~(K(1) << (sizeof(K) * 8 - 1));  // all but the role bit
             sort_pairs<K, Pay>(L, rs, keys, pays, false, C.key_bits, keymask, KIND_HIST_RECORDS, KIND_SORT_RECORDS,
                                d_sbits);
@@ -572,14 +629,15 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         Tq_all += C.Tq;
         kb_all = std::max(kb_all, C.key_bits);
         passes_all = std::max(passes_all, npass);
-        if (chunks.size() > 1) {
-            e = cudaStreamSynchronize(stream);  // the next chunk reuses the record workspace's tables
+        if (chunks.size() > 1 && !planned) {
+            e = cudaStreamSynchronize(stream);  // the next chunk's host tables reuse the pinned area
             if (e != cudaSuccess) return cuda_fail(h, e, "record phase");
         }
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "launch");
     if (L.next_lookback > MAX_LAUNCHES) return fail(h, DOMAGG_ERR_UNSUPPORTED, "too many look-back launches");
+    if (planned) return DOMAGG_OK;  // the counts stay on the device
 
     domagg_stats& S = h->stats;
     S.n_points = (int64_t)N;
@@ -596,28 +654,42 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     return DOMAGG_OK;
 }
 
+typedef std::vector<PlannedChunk> Planned;
+
 template <int M, class Op>
-domagg_status run_ct(domagg_ctx* h, std::vector<Inst>& inst, domagg_dtype ct, bool negate, cudaStream_t s) {
-    return ct == DOMAGG_F32 ? run<M, Op, true>(h, inst, negate, s) : run<M, Op, false>(h, inst, negate, s);
+domagg_status run_ct(domagg_ctx* h, std::vector<Inst>& inst, domagg_dtype ct, bool negate, cudaStream_t s,
+                     const Planned* pl) {
+    return ct == DOMAGG_F32 ? run<M, Op, true>(h, inst, negate, s, pl) : run<M, Op, false>(h, inst, negate, s, pl);
 }
 
 template <class Op>
-domagg_status run_m(domagg_ctx* h, int m, std::vector<Inst>& inst, domagg_dtype ct, bool negate, cudaStream_t s) {
+domagg_status run_m(domagg_ctx* h, int m, std::vector<Inst>& inst, domagg_dtype ct, bool negate, cudaStream_t s,
+                    const Planned* pl) {
     switch (m) {
-        case 1: return run_ct<1, Op>(h, inst, ct, negate, s);
-        case 2: return run_ct<2, Op>(h, inst, ct, negate, s);
-        default: return run_ct<3, Op>(h, inst, ct, negate, s);
+        case 1: return run_ct<1, Op>(h, inst, ct, negate, s, pl);
+        case 2: return run_ct<2, Op>(h, inst, ct, negate, s, pl);
+        default: return run_ct<3, Op>(h, inst, ct, negate, s, pl);
     }
 }
 
 domagg_status dispatch(domagg_ctx* h, int m, std::vector<Inst>& inst, domagg_dtype ct, domagg_dtype wt,
-                       domagg_op op, bool negate, cudaStream_t s) {
-    if (op == DOMAGG_COUNT) return run_m<OpCount>(h, m, inst, ct, negate, s);
-    if (op == DOMAGG_SUM && wt == DOMAGG_F32) return run_m<OpSumF32>(h, m, inst, ct, negate, s);
-    if (op == DOMAGG_SUM && wt == DOMAGG_I64) return run_m<OpSumI64>(h, m, inst, ct, negate, s);
-    if (op == DOMAGG_MAX && wt == DOMAGG_I32) return run_m<OpMaxI32>(h, m, inst, ct, negate, s);
-    if (op == DOMAGG_MAX && wt == DOMAGG_F32) return run_m<OpMaxF32>(h, m, inst, ct, negate, s);
+                       domagg_op op, bool negate, cudaStream_t s, const Planned* pl = nullptr) {
+    if (op == DOMAGG_COUNT) return run_m<OpCount>(h, m, inst, ct, negate, s, pl);
+    if (op == DOMAGG_SUM && wt == DOMAGG_F32) return run_m<OpSumF32>(h, m, inst, ct, negate, s, pl);
+    if (op == DOMAGG_SUM && wt == DOMAGG_I64) return run_m<OpSumI64>(h, m, inst, ct, negate, s, pl);
+    if (op == DOMAGG_MAX && wt == DOMAGG_I32) return run_m<OpMaxI32>(h, m, inst, ct, negate, s, pl);
+    if (op == DOMAGG_MAX && wt == DOMAGG_F32) return run_m<OpMaxF32>(h, m, inst, ct, negate, s, pl);
     return fail(h, DOMAGG_ERR_INVALID_ARG, "unsupported (op, weight dtype) pair");
+}
+
+// Device bytes per record of a chunk: key and payload double-buffered, a
+// partial per (query) record and the status words, rounded up.
+size_t record_bytes(int m, domagg_dtype wt, domagg_op op) {
+    const size_t kb = m == 3 ? 8 : 4;
+    const bool wide = op == DOMAGG_SUM && wt == DOMAGG_I64;
+    const size_t pb = wide ? 8 : 4;
+    const size_t part = (op == DOMAGG_MAX || (op == DOMAGG_SUM && wt == DOMAGG_F32)) ? 4 : 8;
+    return 2 * kb + 2 * pb + part + 8;
 }
 
 domagg_status check_common(domagg_ctx* h, int m, int64_t nD, int64_t nQ, domagg_dtype ct, domagg_dtype wt,
@@ -808,15 +880,237 @@ domagg_status domagg_batch(domagg_handle h, int k, const domagg_instance* inst, 
     return DOMAGG_OK;
 }
 
-domagg_status domagg_batch_plan(domagg_handle h, int k, const domagg_instance* inst, domagg_dtype coord_dtype,
-                                domagg_dtype weight_dtype, domagg_op op) {
-    if (!h) return DOMAGG_ERR_INVALID_ARG;
-    (void)k;
-    (void)inst;
-    (void)coord_dtype;
-    (void)weight_dtype;
-    (void)op;
-    return fail(h, DOMAGG_ERR_UNSUPPORTED, "batch planning for graph capture is not available yet");
+}  // extern "C"
+
+struct domagg_plan_s {
+    struct Group {
+        int m = 0;
+        domagg_ctx* ctx = nullptr;      // private workspace of this group
+        std::vector<Inst> inst;         // as given (sizes and pointers)
+        std::vector<PlannedChunk> chunks;
+        u32 margin = 0;                 // epoch guard margin
+    };
+    int device = 0;
+    domagg_dtype ct = DOMAGG_I32, wt = DOMAGG_I32;
+    domagg_op op = DOMAGG_SUM;
+    std::vector<Group> groups;
+    std::string err;
+};
+
+namespace {
+
+void plan_free(domagg_plan p) {
+    if (!p) return;
+    cudaSetDevice(p->device);
+    for (auto& g : p->groups) {
+        for (auto& c : g.chunks)
+            if (c.d_slot_map) cudaFree(c.d_slot_map);
+        if (g.ctx) domagg_destroy(g.ctx);
+    }
+    delete p;
+}
+
+domagg_status plan_fail(domagg_plan p, domagg_status st, const std::string& msg) {
+    p->err = msg;
+    return st;
+}
+
+// One planned run of a group: the epoch guard, then the pipeline.
+domagg_status plan_group_run(domagg_plan p, domagg_plan_s::Group& g, cudaStream_t s) {
+    domagg_ctx* h = g.ctx;
+    k_epoch_clear<<<304, 256, 0, s>>>(h->ctl, (u64*)h->st_multi.p, h->st_multi.cap / sizeof(u64), (u64*)h->st_seg.p,
+                                       h->st_seg.cap / sizeof(u64), g.margin);
+    k_epoch_restart<<<1, 32, 0, s>>>(h->ctl, g.margin);
+    std::vector<Inst> I = g.inst;
+    domagg_status st = dispatch(h, g.m, I, p->ct, p->wt, p->op, false, s, &g.chunks);
+    if (st) return plan_fail(p, st, h->err);
+    return DOMAGG_OK;
+}
+
+// Largest number of levels (rank digits of the first coordinate) an
+// instance of n points can have: b = ceil(log2 U) with U <= n.
+u32 level_bound(int m, u64 n) {
+    if (m == 1) return 1u;
+    u32 b = 0;
+    while (b < 31 && (1ull << b) < n) ++b;
+    return b;
+}
+
+// Plans one group (same m, < 2^31 points): measures the record counts with an
+// unplanned run, cuts chunks with capacity (1 + headroom) x the measured
+// counts, then makes one planned run that allocates the workspace for good.
+domagg_status plan_group(domagg_plan p, int m, const std::vector<Inst>& part, double headroom, cudaStream_t s) {
+    domagg_plan_s::Group g;
+    g.m = m;
+    g.inst = part;
+    domagg_status st = domagg_create(&g.ctx, p->device, 0);
+    if (st) return plan_fail(p, st, "creating the plan's workspace");
+    p->groups.push_back(g);
+    domagg_plan_s::Group& G = p->groups.back();
+    std::vector<Inst> measured = part;
+    st = dispatch(G.ctx, m, measured, p->ct, p->wt, p->op, false, s);
+    if (st) return plan_fail(p, st, G.ctx->err);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return plan_fail(p, DOMAGG_ERR_CUDA, "measuring run");
+    // capacity budget: 2^32 positions and ~60% of the free device memory
+    const double per_rec = (double)record_bytes(m, p->wt, p->op);
+    u64 cap_limit = (1ull << 32) - (1ull << 20);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+        cap_limit = std::min<u64>(cap_limit, (u64)std::max<double>(0.6 * (double)free_b / per_rec, 1.0e6));
+    else
+        cudaGetLastError();
+    const int k = (int)part.size();
+    auto scaled = [&](u32 v) { return (u64)std::ceil((double)v * (1.0 + headroom)); };
+    PlannedChunk c{0, 0, 0, 0, 0, 0, nullptr};
+    std::vector<std::vector<u32>> maps;
+    std::vector<u32> map;
+    auto close = [&]() {
+        c.T_cap += 1024;  // never 0: the chunk's launches are the same whatever the data
+        c.Tq_cap += 1024;
+        G.chunks.push_back(c);
+        maps.push_back(map);
+        map.clear();
+    };
+    for (int i = 0; i < k; ++i) {
+        const u64 Ti = scaled(measured[i].T), Tqi = scaled(measured[i].Tq);
+        if (Ti + 1024 > cap_limit) return plan_fail(p, DOMAGG_ERR_UNSUPPORTED, "one instance exceeds a record chunk");
+        if (c.k1 > c.k0 && c.T_cap + Ti + 1024 > cap_limit) {
+            close();
+            c = PlannedChunk{i, i, 0, 0, 0, 0, nullptr};
+        }
+        c.k1 = i + 1;
+        c.T_cap += Ti;
+        c.Tq_cap += Tqi;
+        const u32 nb = level_bound(m, (u64)part[i].nD + part[i].nQ);
+        for (u32 lv = 0; lv < nb; ++lv) map.push_back(((u32)(i - c.k0) << 5) | lv);
+        c.nslot += (int)nb;
+        const int kb = m == 1 ? 0 : (m == 2 ? (int)nb - 1 : 2 * (int)nb - 1);
+        c.key_bits = std::max(c.key_bits, kb);
+    }
+    if (c.k1 > c.k0) close();
+    for (size_t ci = 0; ci < G.chunks.size(); ++ci) {
+        PlannedChunk& pc = G.chunks[ci];
+        const size_t bytes = std::max<size_t>(maps[ci].size(), 1) * sizeof(u32);
+        if (cudaMalloc(&pc.d_slot_map, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            pc.d_slot_map = nullptr;
+            return plan_fail(p, DOMAGG_ERR_OOM, "slot map");
+        }
+        if (!maps[ci].empty()) cudaMemcpy(pc.d_slot_map, maps[ci].data(), maps[ci].size() * sizeof(u32),
+                                          cudaMemcpyHostToDevice);
+    }
+    G.margin = (u32)(G.chunks.size() + 6) * MAX_LAUNCHES;
+    // the warm planned run: allocates the workspace at its final size (and
+    // loads every kernel a planned run launches)
+    st = plan_group_run(p, G, s);
+    if (st) return st;
+    st = domagg_sync_status(G.ctx, s);
+    if (st) return plan_fail(p, st, G.ctx->err);
+    G.ctx->frozen = true;
+    return DOMAGG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+domagg_status domagg_batch_plan(domagg_plan* out, int device, int k, const domagg_instance* inst,
+                                domagg_dtype coord_dtype, domagg_dtype weight_dtype, domagg_op op, double headroom,
+                                void* stream) {
+    if (!out) return DOMAGG_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (k < 0 || (k > 0 && !inst) || !(headroom >= 0.0) || headroom > 1.0e6) return DOMAGG_ERR_INVALID_ARG;
+    domagg_plan p = new (std::nothrow) domagg_plan_s();
+    if (!p) return DOMAGG_ERR_OOM;
+    p->device = device;
+    p->ct = coord_dtype;
+    p->wt = weight_dtype;
+    p->op = op;
+    domagg_ctx probe;  // argument checks only (no device resources)
+    std::vector<Inst> groups[4];
+    for (int i = 0; i < k; ++i) {
+        const domagg_instance& I = inst[i];
+        domagg_status st = check_common(&probe, I.m, I.nD, I.nQ, coord_dtype, weight_dtype, op);
+        if (st) {
+            delete p;
+            return st;
+        }
+        if ((I.nD > 0 && !I.d_coords) || (I.nQ > 0 && (!I.q_coords || !I.out)) ||
+            (op != DOMAGG_COUNT && I.nD > 0 && !I.d_weights)) {
+            delete p;
+            return DOMAGG_ERR_INVALID_ARG;
+        }
+        if (I.nQ == 0) continue;
+        groups[I.m].push_back(make_inst(I.d_coords, I.nD, I.q_coords, I.nQ, I.d_weights, I.out));
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return DOMAGG_ERR_INVALID_ARG;
+    }
+    for (int m = 1; m <= 3; ++m) {
+        std::vector<Inst> part;
+        int64_t acc = 0;
+        for (size_t i = 0; i <= groups[m].size(); ++i) {
+            const bool flush = i == groups[m].size() ||
+                               (acc + (int64_t)groups[m][i].nD + groups[m][i].nQ >= ((int64_t)1 << 31) - 1);
+            if (flush && !part.empty()) {
+                domagg_status st = plan_group(p, m, part, headroom, (cudaStream_t)stream);
+                if (st) {
+                    plan_free(p);
+                    return st;
+                }
+                part.clear();
+                acc = 0;
+            }
+            if (i < groups[m].size()) {
+                part.push_back(groups[m][i]);
+                acc += (int64_t)groups[m][i].nD + groups[m][i].nQ;
+            }
+        }
+    }
+    *out = p;
+    return DOMAGG_OK;
+}
+
+domagg_status domagg_plan_run(domagg_plan p, void* stream) {
+    if (!p) return DOMAGG_ERR_INVALID_ARG;
+    p->err.clear();
+    cudaSetDevice(p->device);
+    const cudaStream_t s = (cudaStream_t)stream;
+    for (auto& g : p->groups) {
+        domagg_status st = plan_group_run(p, g, s);
+        if (st) return st;
+    }
+    return DOMAGG_OK;
+}
+
+domagg_status domagg_plan_status(domagg_plan p, void* stream) {
+    if (!p) return DOMAGG_ERR_INVALID_ARG;
+    domagg_status first = DOMAGG_OK;
+    for (auto& g : p->groups) {
+        domagg_status st = domagg_sync_status(g.ctx, stream);
+        if (st && !first) {
+            first = st;
+            p->err = g.ctx->err;
+        }
+    }
+    return first;
+}
+
+const char* domagg_plan_last_error(domagg_plan p) { return p ? p->err.c_str() : "null plan"; }
+
+int64_t domagg_plan_workspace_bytes(domagg_plan p) {
+    if (!p) return -1;
+    int64_t b = 0;
+    for (auto& g : p->groups) b += (int64_t)g.ctx->held();
+    return b;
+}
+
+domagg_status domagg_plan_destroy(domagg_plan p) {
+    if (!p) return DOMAGG_ERR_INVALID_ARG;
+    plan_free(p);
+    return DOMAGG_OK;
 }
 
 domagg_status domagg_sync_status(domagg_handle h, void* stream) {

@@ -48,6 +48,7 @@ struct Launcher {
     double pending_bytes = 0;
     cudaEvent_t pending_a = nullptr;
     int launches = 0;  // kernels launched (all kinds)
+    bool frozen = false;  // a planned run: no allocation, no attribute changes (may be under stream capture)
 
     // Index of the next look-back launch (its tile counter and epoch).  A run
     // restarts the count at every k_begin; the clamp keeps a miscount from
@@ -85,7 +86,7 @@ struct Launcher {
 struct SortSpace {
     const u32* seg_off;         // [nseg+1] device
     int nseg;
-    const std::vector<u64>* seg_sizes;  // host copy of the segment sizes
+    const std::vector<u64>* seg_sizes;  // host copy of the segment sizes, or null (planned run: see bound_items)
     u32* tile_off;              // [nseg+1] device scratch (the sort's tile map)
     u32* hist;                  // [nseg*npass*RADIX]
     u32* digit_off;             // [nseg*npass*RADIX]
@@ -94,6 +95,7 @@ struct SortSpace {
     u32* range_scratch = nullptr;  // [range_scratch_ranges*RADIX]: first-pass bases per range
     u64 range_scratch_ranges = 0;
     const std::vector<u32>* seg_bits_host = nullptr;  // host copy of seg_bits (byte model)
+    u64 bound_items = 0;  // without seg_sizes: an upper bound on the items (the segment sizes are on the device only)
 };
 
 
@@ -111,6 +113,13 @@ inline u64 sort_range_bound(const std::vector<u64>& sizes) {
     u64 t = 0;
     for (u64 n : sizes) t += (n + SORT_MIN_TILE - 1) / SORT_MIN_TILE;
     const u64 cap = 4096 + sizes.size();  // about four ranges per resident CTA, at least one per segment
+    return t < cap ? t : cap;
+}
+
+// The same bound from the item count alone (segment sizes unknown on the host).
+inline u64 sort_range_bound_n(u64 items, u64 nseg) {
+    const u64 t = items / SORT_MIN_TILE + nseg;
+    const u64 cap = 4096 + nseg;
     return t < cap ? t : cap;
 }
 

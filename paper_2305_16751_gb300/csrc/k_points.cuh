@@ -18,6 +18,19 @@ static __global__ void k_begin(Ctl* ctl) {
     for (int i = threadIdx.x; i < MAX_LAUNCHES; i += blockDim.x) ctl->tile_ctr[i] = 0;
 }
 
+// Epoch guard of a replayed plan (no host in the loop to reset the epochs):
+// once the epoch counter comes within `margin` of its limit, the status words
+// are cleared and the counter restarts at 0 (two launches, stream-ordered).
+static __global__ void k_epoch_clear(const Ctl* ctl, u64* a, u64 na, u64* b, u64 nb, u32 margin) {
+    if (*reinterpret_cast<const volatile u32*>(&ctl->epoch_base) <= EPOCH_MASK - margin) return;
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < na; i += stride) a[i] = 0;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride) b[i] = 0;
+}
+static __global__ void k_epoch_restart(Ctl* ctl, u32 margin) {
+    if (threadIdx.x == 0 && ctl->epoch_base > EPOCH_MASK - margin) ctl->epoch_base = 0;
+}
+
 // Tiles of size `tile` over segments: tile_off[s] = sum over s' < s of
 // ceil(len(s') / tile), tile_off[nseg] = total.  One block.
 static __global__ void k_make_tiles(const u32* __restrict__ seg_off, int nseg, u32 tile, u32* __restrict__ tile_off) {
@@ -238,16 +251,20 @@ __device__ __forceinline__ u32 levels_of(const Inst& I) {
 // consecutive points.  Per instance (segmented look-back chains) it scans
 // 2 x LMAX counters: the records of every level, and the query records
 // (= partial slots) of every level.  Writes, in this order, the point's
-// ranks and index; per chunk of 32 points the exclusive count of both kinds
+// ranks (the first with the query flag in bit 31), index and weight (data
+// points; so the flat map reads them without a dependent gather); per chunk
+// of 32 points the exclusive count of both kinds
 // at the chunk's first point, for every level; per instance both totals of
 // every level.  The partial slots of a level are thereby a dense range in
 // which each query's records keep the order of the last coordinate.
 constexpr int CS_ROUNDS = 16;
-template <int M>
+constexpr u32 QUERY_BIT = 0x80000000u;  // in pr0: the point is a query (ranks are below 2^31)
+template <int M, typename Pay, int WT>
 __global__ __launch_bounds__(256) void k_count_scan(
     const u32* __restrict__ perm, const u32* __restrict__ seg_off, const u32* __restrict__ tile_off, int nseg,
     const u32* __restrict__ chunk_off, const u32* __restrict__ r0, const u32* __restrict__ r1, Inst* inst,
-    u32* __restrict__ pr0, u32* __restrict__ pr1, u32* __restrict__ pj, u32* __restrict__ chunk_base,
+    u32* __restrict__ pr0, u32* __restrict__ pr1, u32* __restrict__ pj, Pay* __restrict__ pw,
+    u32* __restrict__ chunk_base,
     u32* __restrict__ qchunk_base, u32* __restrict__ lvl_tot, u32* __restrict__ qlvl_tot, u64* status, Ctl* ctl,
     int launch_idx) {
     constexpr int WARPS = 8, C = 2 * LMAX, TILE = WARPS * CS_ROUNDS * 32;
@@ -289,9 +306,14 @@ __global__ __launch_bounds__(256) void k_count_scan(
         if (M == 1) bits0 = 1u;
         if (!valid) bits0 = 0;
         if (valid) {
-            if (M >= 2) pr0[x] = a;
+            if (M >= 2) pr0[x] = q ? (a | QUERY_BIT) : a;
             if (M >= 3) pr1[x] = c;
             pj[x] = j;
+            if (WT != 3 && !q) {
+                const u32 local = j - L.seg_begin;
+                if (WT == 1) pw[x] = (Pay)reinterpret_cast<const long long*>(I.dw)[local - nQ];
+                else pw[x] = (Pay)reinterpret_cast<const u32*>(I.dw)[local - nQ];
+            }
         }
         u32 mine = 0, mine_q = 0;
         for (u32 lv = 0; lv < nlev; ++lv) {
@@ -367,9 +389,9 @@ template <int M, typename K, typename Pay, int WT>
 __global__ __launch_bounds__(256) void k_expand(
     const u32* __restrict__ chunk_off, int k, int k0, int k1, const u32* __restrict__ pt_offs,
     const u32* __restrict__ pr0, const u32* __restrict__ pr1, const u32* __restrict__ pj,
-    const u32* __restrict__ chunk_base, const u32* __restrict__ qchunk_base, const Inst* __restrict__ inst,
-    const u32* __restrict__ seg_base /*[k1-k0][LMAX]*/, const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/,
-    u32 n_rec, K* __restrict__ kout, Pay* __restrict__ pout) {
+    const Pay* __restrict__ pw, const u32* __restrict__ chunk_base, const u32* __restrict__ qchunk_base,
+    const Inst* __restrict__ inst, const u32* __restrict__ seg_base /*[k1-k0][LMAX]*/,
+    const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/, u32 n_rec, K* __restrict__ kout, Pay* __restrict__ pout) {
     const int lane = threadIdx.x & 31;
     const u32 lt = lanemask_lt();
     const u32 c_begin = __ldg(chunk_off + k0), c_end = __ldg(chunk_off + k1);
@@ -395,24 +417,22 @@ __global__ __launch_bounds__(256) void k_expand(
         bool q = false;
         Pay w = 0;
         if (valid) {
-            u32 j = pj[p];
-            if (j - ps >= pe - ps) j = ps;  // never taken for a valid permutation
-            const u32 local = j - ps;
-            q = local < nQ;
+            // coalesced reads in the order of the last coordinate (count scan)
             if (M >= 2) {
                 a = pr0[p];
+                q = (a & QUERY_BIT) != 0u;
+                a &= ~QUERY_BIT;
                 bits0 = (q ? a : ~a) & low_mask(I.b[0]);
+            } else {
+                q = pj[p] - ps < nQ;
+                bits0 = 1u;
             }
             if (M >= 3) {
                 cc = pr1[p];
                 bits1 = (q ? cc : ~cc) & low_mask(b1);
                 c1 = (u32)__popc(bits1);
             }
-            if (M == 1) bits0 = 1u;
-            if (!q) {
-                if (WT == 1) w = (Pay)reinterpret_cast<const long long*>(I.dw)[local - nQ];
-                else if (WT == 0 || WT == 2) w = (Pay)reinterpret_cast<const u32*>(I.dw)[local - nQ];
-            }
+            if (!q && WT != 3) w = pw[p];
         }
         if (M >= 3 && c1 == 0) bits0 = 0;  // no records at all
         const u32 live = __ballot_sync(0xffffffffu, bits0 != 0u);

@@ -58,12 +58,14 @@ __device__ __forceinline__ TileLoc locate_range(u32 r, const u32* seg_off, const
 // Digit histograms of all passes, per segment: hist[(seg*npass + p)*RADIX + d].
 // One block per range of `range_items` items (ranges never straddle a
 // segment); counts are aggregated per warp with match_any before the
-// shared-memory atomics, so skewed digits do not serialise.
+// shared-memory atomics, so skewed digits do not serialise.  With seg_bits,
+// a segment only counts the passes its keys have digits for (the others
+// skip it).
 template <typename K>
 __global__ __launch_bounds__(256) void k_radix_hist(const K* __restrict__ keys, const u32* __restrict__ seg_off,
                                                     const u32* __restrict__ range_off, int nseg, u32 range_items,
                                                     int npass, int shift0, K keymask, u32* __restrict__ hist,
-                                                    u32* __restrict__ range_cnt0) {
+                                                    u32* __restrict__ range_cnt0, const u32* __restrict__ seg_bits) {
     extern __shared__ u32 sh_hist[];  // [8 warps][npass][RADIX]
     const u32 r = blockIdx.x;
     if (r >= __ldg(range_off + nseg)) return;
@@ -71,6 +73,7 @@ __global__ __launch_bounds__(256) void k_radix_hist(const K* __restrict__ keys, 
     for (int x = threadIdx.x; x < 8 * npass * RADIX; x += 256) sh_hist[x] = 0;
     __syncthreads();
     const TileLoc L = locate_range(r, seg_off, range_off, nseg, range_items);
+    const int np = seg_bits ? min(npass, (int)((__ldg(seg_bits + L.seg) + RADIX_BITS - 1) / RADIX_BITS)) : npass;
     u32* wh = sh_hist + warp * npass * RADIX;
     for (u32 base = L.start; base < L.end; base += 256u * 8u) {
         K kk[8];
@@ -82,7 +85,7 @@ __global__ __launch_bounds__(256) void k_radix_hist(const K* __restrict__ keys, 
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const bool valid = base + (u32)j * 256u + threadIdx.x < L.end;
-            for (int p = 0; p < npass; ++p)
+            for (int p = 0; p < np; ++p)
                 warp_hist_add(wh + p * RADIX, digit_of(kk[j], keymask, shift0 + p * RADIX_BITS), valid, lane);
         }
     }

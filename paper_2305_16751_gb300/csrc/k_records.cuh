@@ -7,6 +7,109 @@
 
 namespace domagg {
 
+// Record layout of a planned run, computed on the device from the count
+// scan's per-(instance, level) totals (the host-side layout of an unplanned
+// call, which needs their values on the host, as one block of 1024 threads).
+// slot_map lists the chunk's segment slots, (instance - k0) << 5 | level, with
+// every instance reserving as many slots as its rank digits can be at most;
+// slots beyond an instance's actual levels are empty.  Writes the segment
+// offsets and key bits and the per-(instance, level) record and query-slot
+// bases.  If the records exceed the reserved capacity, every segment is made
+// empty and ERR_CAPACITY is raised: the kernels after it then write nothing
+// outside their buffers (the chunk's outputs are undefined).
+template <int M>
+__global__ __launch_bounds__(1024) void k_layout(const Inst* __restrict__ inst, int k0,
+                                                 const u32* __restrict__ lvl_tot, const u32* __restrict__ qlvl_tot,
+                                                 const u32* __restrict__ slot_map, int nslot, u64 T_cap, u64 Tq_cap,
+                                                 u32* __restrict__ so, u32* __restrict__ sbits,
+                                                 u32* __restrict__ sbase, u32* __restrict__ qsbase, Ctl* ctl) {
+    __shared__ u64 w_a[32], w_q[32];
+    __shared__ u64 carry_a, carry_q;
+    __shared__ int s_over;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    auto sizes = [&](int g, u32& lv, u32& srel, u32& na, u32& nq, u32& bits) {
+        const u32 sm = __ldg(slot_map + g);
+        srel = sm >> 5;
+        lv = sm & 31u;
+        const Inst& I = inst[k0 + (int)srel];
+        const u32 nlev = M == 1 ? 1u : I.b[0];
+        na = nq = bits = 0;
+        if (lv < nlev) {
+            na = __ldg(lvl_tot + (u64)(k0 + (int)srel) * LMAX + lv);
+            nq = __ldg(qlvl_tot + (u64)(k0 + (int)srel) * LMAX + lv);
+            if (M >= 2) bits = I.b[0] - 1u - lv + (M == 3 ? I.b[1] : 0u);
+        }
+    };
+    // totals first: the capacity decides between the layout and empty segments
+    u64 ta = 0, tq = 0;
+    for (int g = tid; g < nslot; g += 1024) {
+        u32 lv, srel, na, nq, bits;
+        sizes(g, lv, srel, na, nq, bits);
+        ta += na;
+        tq += nq;
+    }
+    for (int o = 16; o >= 1; o >>= 1) {
+        ta += __shfl_xor_sync(0xffffffffu, ta, o);
+        tq += __shfl_xor_sync(0xffffffffu, tq, o);
+    }
+    if (lane == 0) {
+        w_a[warp] = ta;
+        w_q[warp] = tq;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        u64 A = 0, Q = 0;
+        for (int w = 0; w < 32; ++w) {
+            A += w_a[w];
+            Q += w_q[w];
+        }
+        s_over = (A > T_cap || Q > Tq_cap) ? 1 : 0;
+        if (s_over) atomicOr(&ctl->error, ERR_CAPACITY);
+        carry_a = carry_q = 0;
+    }
+    __syncthreads();
+    const bool over = s_over != 0;
+    for (int base = 0; base < nslot; base += 1024) {
+        const int g = base + tid;
+        u32 lv = 0, srel = 0, na = 0, nq = 0, bits = 0;
+        if (g < nslot) sizes(g, lv, srel, na, nq, bits);
+        if (over) na = nq = bits = 0;
+        u64 ia = na, iq = nq;
+        for (int o = 1; o < 32; o <<= 1) {
+            const u64 xa = __shfl_up_sync(0xffffffffu, ia, o), xq = __shfl_up_sync(0xffffffffu, iq, o);
+            if (lane >= o) {
+                ia += xa;
+                iq += xq;
+            }
+        }
+        if (lane == 31) {
+            w_a[warp] = ia;
+            w_q[warp] = iq;
+        }
+        __syncthreads();
+        u64 ea = carry_a, eq = carry_q;
+        for (int w = 0; w < warp; ++w) {
+            ea += w_a[w];
+            eq += w_q[w];
+        }
+        ea += ia - na;
+        eq += iq - nq;
+        if (g < nslot) {
+            so[g] = (u32)ea;
+            sbits[g] = bits;
+            sbase[(u64)srel * LMAX + lv] = (u32)ea;
+            qsbase[(u64)srel * LMAX + lv] = (u32)eq;
+        }
+        __syncthreads();
+        if (tid == 1023) {
+            carry_a = ea + na;
+            carry_q = eq + nq;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) so[nslot] = (u32)carry_a;
+}
+
 // Look-back status of the segmented scan.  The aggregate and the inclusive
 // prefix live in separate fields, each written once before the flag that
 // announces it (release), and read after that flag (acquire): a reader that

@@ -4,18 +4,27 @@
 #include "k_radix.cuh"
 
 #include <algorithm>
+#include <atomic>
 
 namespace domagg {
 
 // Persistent grid: as many CTAs as fit on the GPU at once (from the
 // occupancy calculator).
+// Cached per device, so that a planned run (possibly under stream capture)
+// makes no occupancy query.
 template <typename K, typename V>
 static u64 resident_ctas(size_t smem) {
+    static std::atomic<int> cache[64];
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K, V, false, true>, ONESWEEP_THREADS, smem);
-    return (u64)std::max(sms, 1) * (u64)std::max(per_sm, 1);
+    if (dev >= 0 && dev < 64) per_sm = cache[dev].load(std::memory_order_relaxed);
+    if (per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_onesweep<K, V, false, true>, ONESWEEP_THREADS, smem);
+        per_sm = std::max(per_sm, 1);
+        if (dev >= 0 && dev < 64) cache[dev].store(per_sm, std::memory_order_relaxed);
+    }
+    return (u64)std::max(sms, 1) * (u64)per_sm;
 }
 
 template <typename K, typename V, bool IOTA, bool STABLE>
@@ -33,18 +42,26 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
     constexpr u32 TILE = ONESWEEP_THREADS * onesweep_items<K, V>();
     static_assert(TILE >= SORT_MIN_TILE, "status words are sized for SORT_MIN_TILE");
     const int npass = (total_bits + RADIX_BITS - 1) / RADIX_BITS;
-    const u64 ntiles = tiles_of(*sp.seg_sizes, TILE);
+    // without host segment sizes, bounds: sum ceil(n_s / t) <= items / t + nseg
+    const u64 ntiles = sp.seg_sizes ? tiles_of(*sp.seg_sizes, TILE) : sp.bound_items / TILE + sp.nseg;
     if (npass == 0 || ntiles == 0) return 0;
     constexpr size_t smem = onesweep_smem<K, V>();
-    cudaFuncSetAttribute(k_onesweep<K, V, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_onesweep<K, V, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_onesweep<K, V, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_onesweep<K, V, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the histogram's limit is set for the most passes a key type can need, so
+    // that no later call lowers it under a captured launch that needs more
+    constexpr int hist_smem_max = 8 * (int)(sizeof(K) * 8 / RADIX_BITS) * RADIX * (int)sizeof(u32);
+    if (!L.frozen) {  // a planned run was preceded by an unfrozen one that set these
+        cudaFuncSetAttribute(k_onesweep<K, V, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_onesweep<K, V, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_onesweep<K, V, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_onesweep<K, V, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_radix_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, hist_smem_max);
+    }
     // ranges: about four per resident CTA, whole tiles, never across segments
     const u64 G = resident_ctas<K, V>(smem);
     const u64 rt = std::max<u64>(1, (ntiles + 4 * G - 1) / (4 * G));
     const u32 range_items = (u32)std::min<u64>(rt * TILE, 1ull << 30);
-    const u64 nranges = tiles_of(*sp.seg_sizes, range_items);
+    const u64 nranges =
+        sp.seg_sizes ? tiles_of(*sp.seg_sizes, range_items) : sp.bound_items / range_items + sp.nseg;
     const unsigned grid = (unsigned)std::min<u64>(G, nranges);
     // the first pass takes its range bases from the histogram (no count, no look-back)
     u32* range_base = (sp.range_scratch && nranges <= sp.range_scratch_ranges) ? sp.range_scratch : nullptr;
@@ -52,12 +69,11 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
     k_make_tiles<<<1, 1024, 0, L.stream>>>(sp.seg_off, sp.nseg, range_items, sp.tile_off);
     L.stop();
     const int hist_smem = 8 * npass * RADIX * (int)sizeof(u32);  // per-warp histograms of every pass
-    cudaFuncSetAttribute(k_radix_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, hist_smem);
     const size_t hist_bytes = (size_t)sp.nseg * npass * RADIX * sizeof(u32);
     cudaMemsetAsync(sp.hist, 0, hist_bytes, L.stream);
     L.start(kind_hist, sp.n_items * sizeof(K));
     k_radix_hist<K><<<(unsigned)nranges, 256, hist_smem, L.stream>>>(
-        keys[0], sp.seg_off, sp.tile_off, sp.nseg, range_items, npass, 0, keymask, sp.hist, range_base);
+        keys[0], sp.seg_off, sp.tile_off, sp.nseg, range_items, npass, 0, keymask, sp.hist, range_base, seg_bits);
     L.stop();
     L.start(KIND_SMALL, 0.0);
     k_radix_offsets<<<sp.nseg * npass, RADIX, 0, L.stream>>>(sp.hist, sp.seg_off, npass, sp.digit_off);
@@ -73,7 +89,7 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
         // each pass reads and writes every (key, value) pair it moves once;
         // segments whose keys have fewer digits are not moved
         double moved = sp.n_items;
-        if (seg_bits && sp.seg_bits_host) {
+        if (seg_bits && sp.seg_bits_host && sp.seg_sizes) {
             moved = 0;
             for (size_t sgi = 0; sgi < sp.seg_sizes->size(); ++sgi)
                 if ((u32)p * RADIX_BITS < (*sp.seg_bits_host)[sgi]) moved += (double)(*sp.seg_sizes)[sgi];

@@ -57,7 +57,13 @@ SIGNATURES = {
     "domagg_forward_host": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _vp], _int),
     "domagg_backward": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp], _int),
     "domagg_batch": ([_vp, _int, ctypes.POINTER(domagg_instance), _int, _int, _int, _vp], _int),
-    "domagg_batch_plan": ([_vp, _int, ctypes.POINTER(domagg_instance), _int, _int, _int], _int),
+    "domagg_batch_plan": ([ctypes.POINTER(_vp), _int, _int, ctypes.POINTER(domagg_instance), _int, _int, _int,
+                           ctypes.c_double, _vp], _int),
+    "domagg_plan_run": ([_vp, _vp], _int),
+    "domagg_plan_status": ([_vp, _vp], _int),
+    "domagg_plan_last_error": ([_vp], ctypes.c_char_p),
+    "domagg_plan_workspace_bytes": ([_vp], _i64),
+    "domagg_plan_destroy": ([_vp], _int),
     "domagg_sync_status": ([_vp, _vp], _int),
     "domagg_last_error": ([_vp], ctypes.c_char_p),
     "domagg_get_stats": ([_vp, ctypes.POINTER(domagg_stats)], _int),
@@ -126,6 +132,36 @@ def domagg_batch(h, k, inst_array, coord_dtype, weight_dtype, op, stream):
 
 def domagg_sync_status(h, stream):
     _check(h, lib().domagg_sync_status(h, stream))
+
+
+def _check_plan(p, st: int):
+    if st != 0:
+        msg = lib().domagg_plan_last_error(p).decode() if p else ""
+        raise DomaggError(st, msg)
+
+
+def domagg_batch_plan(device, k, inst_array, coord_dtype, weight_dtype, op, headroom, stream):
+    p = ctypes.c_void_p()
+    st = lib().domagg_batch_plan(ctypes.byref(p), device, k, inst_array, coord_dtype, weight_dtype, op, headroom,
+                                 stream)
+    _check_plan(None, st)
+    return p
+
+
+def domagg_plan_run(p, stream):
+    _check_plan(p, lib().domagg_plan_run(p, stream))
+
+
+def domagg_plan_status(p, stream):
+    _check_plan(p, lib().domagg_plan_status(p, stream))
+
+
+def domagg_plan_workspace_bytes(p) -> int:
+    return int(lib().domagg_plan_workspace_bytes(p))
+
+
+def domagg_plan_destroy(p):
+    _check_plan(None, lib().domagg_plan_destroy(p))
 
 
 def domagg_get_stats(h) -> dict:
@@ -282,12 +318,10 @@ def dominance_sum(D, Q, w):
     return _DominanceSum.apply(D, Q, w)
 
 
-def batch(problems, op: str = "sum"):
-    """problems: list of (D, Q, w) CUDA tensors (w ignored for count); all
-    instances share coordinate dtype, weight dtype and op.  Returns outputs."""
+def _instances(problems, op: str):
+    """ctypes descriptors for (D, Q, w) CUDA tensors, the outputs, and the
+    tensors the descriptors point into (to keep alive)."""
     torch = _torch()
-    if not problems:
-        return []
     k = len(problems)
     arr = (domagg_instance * k)()
     outs, keep = [], []
@@ -301,11 +335,61 @@ def batch(problems, op: str = "sum"):
                                  Q.data_ptr() if Q.numel() else None,
                                  w.data_ptr() if (w is not None and w.numel()) else None,
                                  out.data_ptr() if out.numel() else None)
+    return arr, outs, keep
+
+
+def batch(problems, op: str = "sum"):
+    """problems: list of (D, Q, w) CUDA tensors (w ignored for count); all
+    instances share coordinate dtype, weight dtype and op.  Returns outputs."""
+    if not problems:
+        return []
+    arr, outs, keep = _instances(problems, op)
     D0 = problems[0][0]
     w0 = problems[0][2]
     dev = D0.device.index or 0
-    domagg_batch(handle(dev), k, arr, _coord_dtype(D0), _weight_dtype(w0, op), OPS[op], _stream(D0.device))
+    domagg_batch(handle(dev), len(problems), arr, _coord_dtype(D0), _weight_dtype(w0, op), OPS[op],
+                 _stream(D0.device))
     return outs
+
+
+class BatchPlan:
+    """A planned batch (domagg_batch_plan): `run()` enqueues one run of the
+    batch on the current stream with no synchronisation, allocation or copy,
+    so it can be captured in a CUDA graph.  The problems' tensors are kept
+    alive by the plan; change their contents in place between runs.  `outs`
+    holds the outputs (written by every run)."""
+
+    def __init__(self, problems, op: str = "sum", headroom: float = 0.25):
+        if not problems:
+            raise ValueError("empty batch")
+        self.arr, self.outs, self._keep = _instances(problems, op)
+        D0 = problems[0][0]
+        self.device = D0.device
+        self._p = domagg_batch_plan(D0.device.index or 0, len(problems), self.arr, _coord_dtype(D0),
+                                    _weight_dtype(problems[0][2], op), OPS[op], float(headroom),
+                                    _stream(D0.device))
+
+    def run(self):
+        domagg_plan_run(self._p, _stream(self.device))
+
+    def status(self):
+        """Synchronises and raises DomaggError for a device-side error of the
+        runs so far (e.g. more records than reserved)."""
+        domagg_plan_status(self._p, _stream(self.device))
+
+    def workspace_bytes(self) -> int:
+        return domagg_plan_workspace_bytes(self._p)
+
+    def close(self):
+        if getattr(self, "_p", None):
+            domagg_plan_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def stats(device: int = 0) -> dict:
