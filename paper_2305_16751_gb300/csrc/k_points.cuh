@@ -33,7 +33,10 @@ static __global__ void k_epoch_restart(Ctl* ctl, u32 margin) {
 
 // Tiles of size `tile` over segments: tile_off[s] = sum over s' < s of
 // ceil(len(s') / tile), tile_off[nseg] = total.  One block.
-static __global__ void k_make_tiles(const u32* __restrict__ seg_off, int nseg, u32 tile, u32* __restrict__ tile_off) {
+// With seg_bits, segments whose keys have at most `skip_upto` bits get no
+// tiles (a radix pass starting at that bit leaves them where they are).
+static __global__ void k_make_tiles(const u32* __restrict__ seg_off, int nseg, u32 tile, u32* __restrict__ tile_off,
+                                    const u32* __restrict__ seg_bits = nullptr, u32 skip_upto = 0) {
     __shared__ u32 carry;
     __shared__ u32 warp_sum[32];
     if (threadIdx.x == 0) carry = 0;
@@ -42,7 +45,8 @@ static __global__ void k_make_tiles(const u32* __restrict__ seg_off, int nseg, u
     for (int base = 0; base < nseg; base += blockDim.x) {
         const int s = base + threadIdx.x;
         u32 v = 0;
-        if (s < nseg) v = (__ldg(seg_off + s + 1) - __ldg(seg_off + s) + tile - 1) / tile;
+        if (s < nseg && !(seg_bits && __ldg(seg_bits + s) <= skip_upto))
+            v = (__ldg(seg_off + s + 1) - __ldg(seg_off + s) + tile - 1) / tile;
         u32 inc = v;
         for (int o = 1; o < 32; o <<= 1) {
             u32 n = __shfl_up_sync(0xffffffffu, inc, o);

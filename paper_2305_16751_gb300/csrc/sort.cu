@@ -56,17 +56,33 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
         cudaFuncSetAttribute(k_onesweep<K, V, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_radix_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, hist_smem_max);
     }
-    // ranges: about four per resident CTA, whole tiles, never across segments
+    // ranges: about four per resident CTA, whole tiles, never across segments.
+    // With seg_bits, every pass ranges only the segments it moves (a segment
+    // whose keys have no digit left stays in place), so later passes, which
+    // move fewer segments, still spread over every CTA.
     const u64 G = resident_ctas<K, V>(smem);
-    const u64 rt = std::max<u64>(1, (ntiles + 4 * G - 1) / (4 * G));
-    const u32 range_items = (u32)std::min<u64>(rt * TILE, 1ull << 30);
-    const u64 nranges =
-        sp.seg_sizes ? tiles_of(*sp.seg_sizes, range_items) : sp.bound_items / range_items + sp.nseg;
-    const unsigned grid = (unsigned)std::min<u64>(G, nranges);
+    auto tiles_moved = [&](int p, u64 tile) -> u64 {
+        if (!sp.seg_sizes) return sp.bound_items / tile + sp.nseg;  // bound: sum ceil(n_s / t) <= items / t + nseg
+        if (!seg_bits || !sp.seg_bits_host) return tiles_of(*sp.seg_sizes, tile);
+        u64 t = 0;
+        for (size_t i = 0; i < sp.seg_sizes->size(); ++i)
+            if ((u32)p * RADIX_BITS < (*sp.seg_bits_host)[i]) t += ((*sp.seg_sizes)[i] + tile - 1) / tile;
+        return t;
+    };
+    auto plan_ranges = [&](int p, u32& range_items, u64& nranges) {
+        const u64 nt = tiles_moved(p, TILE);
+        const u64 rt = std::max<u64>(1, (nt + 4 * G - 1) / (4 * G));
+        range_items = (u32)std::min<u64>(rt * TILE, 1ull << 30);
+        nranges = nt == 0 ? 0 : tiles_moved(p, range_items);
+    };
+    u32 range_items = 0;
+    u64 nranges = 0;
+    plan_ranges(0, range_items, nranges);
+    if (nranges == 0) return 0;
     // the first pass takes its range bases from the histogram (no count, no look-back)
     u32* range_base = (sp.range_scratch && nranges <= sp.range_scratch_ranges) ? sp.range_scratch : nullptr;
     L.start(KIND_SMALL, 0.0);
-    k_make_tiles<<<1, 1024, 0, L.stream>>>(sp.seg_off, sp.nseg, range_items, sp.tile_off);
+    k_make_tiles<<<1, 1024, 0, L.stream>>>(sp.seg_off, sp.nseg, range_items, sp.tile_off, seg_bits, 0u);
     L.stop();
     const int hist_smem = 8 * npass * RADIX * (int)sizeof(u32);  // per-warp histograms of every pass
     const size_t hist_bytes = (size_t)sp.nseg * npass * RADIX * sizeof(u32);
@@ -85,6 +101,15 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
     }
     int cur = 0;
     for (int p = 0; p < npass; ++p) {
+        if (p > 0 && seg_bits) {  // this pass's own ranges
+            plan_ranges(p, range_items, nranges);
+            if (nranges == 0) break;  // no segment has digits left (nor will in later passes)
+            L.start(KIND_SMALL, 0.0);
+            k_make_tiles<<<1, 1024, 0, L.stream>>>(sp.seg_off, sp.nseg, range_items, sp.tile_off, seg_bits,
+                                                   (u32)p * RADIX_BITS);
+            L.stop();
+        }
+        const unsigned grid = (unsigned)std::min<u64>(G, nranges);
         const int li = L.lookback_index();
         // each pass reads and writes every (key, value) pair it moves once;
         // segments whose keys have fewer digits are not moved
