@@ -32,8 +32,10 @@
  *   - Supported (op, weight dtype) -> output dtype:
  *       SUM   int64 -> int64 (wraps modulo 2^64), float32 -> float32
  *       MAX   int32 -> int32, float32 -> float32
+ *       MIN   int32 -> int32, float32 -> float32
  *       COUNT (weights ignored, may be NULL) -> int64
- *     The empty set gives e: 0 for SUM and COUNT, INT32_MIN or -inf for MAX.
+ *     The empty set gives e: 0 for SUM and COUNT, INT32_MIN or -inf for MAX,
+ *     INT32_MAX or +inf for MIN; a NaN weight never wins a MAX or a MIN.
  *     float32 sums carry a float-float (hi, lo) accumulator through the scan
  *     and the per-query reduction; the result is within 2^-23 * sum |w(d)|
  *     over the dominated set of the exact sum.  float32 weights must be
@@ -68,7 +70,7 @@ typedef enum {
     DOMAGG_ERR_NAN = 6          /* a coordinate is NaN */
 } domagg_status;
 
-typedef enum { DOMAGG_SUM = 0, DOMAGG_MAX = 1, DOMAGG_COUNT = 2 } domagg_op;
+typedef enum { DOMAGG_SUM = 0, DOMAGG_MAX = 1, DOMAGG_COUNT = 2, DOMAGG_MIN = 3 } domagg_op;
 
 typedef enum { DOMAGG_I32 = 0, DOMAGG_I64 = 1, DOMAGG_F32 = 2 } domagg_dtype;
 

@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 # Enumerations of the C oracle (its own numbering).
 COORD = {"i32": 0, "f32": 2}
 WEIGHT = {"i32": 0, "i64": 1, "f32": 2}
-OPS = {"sum": 0, "max": 1, "count": 2}
+OPS = {"sum": 0, "max": 1, "count": 2, "min": 3}
 
 _libs: dict[int, ctypes.CDLL] = {}
 

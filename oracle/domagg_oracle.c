@@ -29,11 +29,12 @@
  * Conventions (the oracle's own; the Python test wrapper maps them):
  *   coordinate dtype: 0 = int32, 2 = float32; row-major [n][m].
  *   weight dtype    : 0 = int32, 1 = int64, 2 = float32.
- *   op              : 0 = sum, 1 = max, 2 = count.
+ *   op              : 0 = sum, 1 = max, 2 = count, 3 = min.
  *   out             : int64[nQ] for integer results (sum of int32/int64,
- *                     max of int32, count) and double[nQ] for float results
- *                     (sum / max of float32).  Empty set -> e: 0 for sums and
- *                     counts, INT32_MIN for int32 max, -inf for float max.
+ *                     max / min of int32, count) and double[nQ] for float
+ *                     results (sum / max / min of float32).  Empty set -> e:
+ *                     0 for sums and counts, INT32_MIN / -inf for max,
+ *                     INT32_MAX / +inf for min.
  *   Sums of integers wrap modulo 2^64 (associative and commutative, so the
  *   result does not depend on order).  Sums of float32 are accumulated in
  *   double.  S (optional, double[nQ]) receives sum |w(d)| over the dominated
@@ -68,6 +69,7 @@
 #define OP_SUM 0
 #define OP_MAX 1
 #define OP_COUNT 2
+#define OP_MIN 3
 
 /* ORACLE_PLANT selects a deliberately wrong variant, built only by the tests
  * that check that the pins catch such mistakes.  0 = the real oracle. */
@@ -128,6 +130,10 @@ static agg_t agg_unit(int wt, int op) {
         a.i = INT32_MIN;
         a.f = -INFINITY;
     }
+    if (op == OP_MIN) {
+        a.i = INT32_MAX;
+        a.f = INFINITY;
+    }
     (void)wt;
     return a;
 }
@@ -160,6 +166,11 @@ static agg_t agg_F(agg_t a, agg_t b, int op) {
         r.f = a.f > b.f ? a.f : b.f;
         if (a.f != a.f) r.f = b.f; /* NaN weights never win a max */
         if (b.f != b.f) r.f = a.f;
+    } else if (op == OP_MIN) {
+        r.i = a.i < b.i ? a.i : b.i;
+        r.f = a.f < b.f ? a.f : b.f;
+        if (a.f != a.f) r.f = b.f; /* NaN weights never win a min */
+        if (b.f != b.f) r.f = a.f;
     } else { /* sum and count */
         r.i = (int64_t)((uint64_t)a.i + (uint64_t)b.i);
         r.f = a.f + b.f;
@@ -175,7 +186,7 @@ static void store_out(void* out, int wt, int op, int64_t q, agg_t a) {
 static int check_args(int m, int64_t nD, int64_t nQ, int ct, int wt, int op) {
     if (m < 1 || m > 8 || nD < 0 || nQ < 0) return OR_ERR_ARG;
     if (ct != CT_I32 && ct != CT_F32) return OR_ERR_ARG;
-    if (op < OP_SUM || op > OP_COUNT) return OR_ERR_ARG;
+    if (op < OP_SUM || op > OP_MIN) return OR_ERR_ARG;
     if (op != OP_COUNT && wt != WT_I32 && wt != WT_I64 && wt != WT_F32) return OR_ERR_ARG;
     return OR_OK;
 }

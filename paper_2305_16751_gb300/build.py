@@ -43,6 +43,8 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     os.makedirs(BUILD_DIR, exist_ok=True)
     nvcc = _nvcc()
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    # tuning constants (e.g. "-DDOMAGG_SEG_THREADS=128"), for sweeps
+    extra += [f for f in os.environ.get("DOMAGG_NVCC_DEFINES", "").split() if f.startswith("-D")]
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))

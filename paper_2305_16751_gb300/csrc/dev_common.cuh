@@ -323,6 +323,30 @@ struct OpMaxF32 {
     __device__ static Acc from_part(Part p) { return p; }
     __device__ static Out to_out(Acc a) { return a; }
 };
+struct OpMinI32 {
+    typedef int Acc;
+    typedef int Part;
+    typedef int Out;
+    typedef u32 Pay;
+    __device__ static Acc e() { return 0x7fffffff; }
+    __device__ static Acc from_pay(Pay p) { return (int)p; }
+    __device__ static Acc F(Acc a, Acc b) { return a < b ? a : b; }
+    __device__ static Part to_part(Acc a) { return a; }
+    __device__ static Acc from_part(Part p) { return p; }
+    __device__ static Out to_out(Acc a) { return a; }
+};
+struct OpMinF32 {
+    typedef float Acc;
+    typedef float Part;
+    typedef float Out;
+    typedef u32 Pay;
+    __device__ static Acc e() { return __int_as_float(0x7f800000); }
+    __device__ static Acc from_pay(Pay p) { return __uint_as_float(p); }
+    __device__ static Acc F(Acc a, Acc b) { return fminf(a, b); }  // a NaN weight never wins
+    __device__ static Part to_part(Acc a) { return a; }
+    __device__ static Acc from_part(Part p) { return p; }
+    __device__ static Out to_out(Acc a) { return a; }
+};
 struct OpCount {
     typedef u32 Acc;
     typedef u32 Part;

@@ -45,6 +45,13 @@ struct Carver {
 };
 
 constexpr int SCAN_THREADS = 256, SCAN_ITEMS = 16;  // rank and count scan
+// segmented scan tiles: threads per block, items per thread for 8-byte records
+#ifndef DOMAGG_SEG_THREADS
+#define DOMAGG_SEG_THREADS 256
+#endif
+#ifndef DOMAGG_SEG_ITEMS_NARROW
+#define DOMAGG_SEG_ITEMS_NARROW 16
+#endif
 static_assert(SCAN_THREADS * SCAN_ITEMS == (int)POINT_TILE, "point scan tiles");
 
 }  // namespace
@@ -163,6 +170,14 @@ struct OpTraits<OpMaxF32> {
     static constexpr int WT = 2;
 };
 template <>
+struct OpTraits<OpMinI32> {
+    static constexpr int WT = 0;
+};
+template <>
+struct OpTraits<OpMinF32> {
+    static constexpr int WT = 2;
+};
+template <>
 struct OpTraits<OpCount> {
     static constexpr int WT = 3;
 };
@@ -202,8 +217,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     typedef typename Op::Pay Pay;
     typedef typename Op::Part Part;
     constexpr int WT = OpTraits<Op>::WT;
-    constexpr int SEG_ITEMS = (sizeof(K) + sizeof(Pay) == 8) ? 16 : 8;
-    constexpr int SEG_THREADS = 256;
+    constexpr int SEG_ITEMS = (sizeof(K) + sizeof(Pay) == 8) ? DOMAGG_SEG_ITEMS_NARROW : 8;
+    constexpr int SEG_THREADS = DOMAGG_SEG_THREADS;
     constexpr u32 SEG_TILE = SEG_THREADS * SEG_ITEMS;
     const int k = (int)inst.size();
 
@@ -679,6 +694,8 @@ domagg_status dispatch(domagg_ctx* h, int m, std::vector<Inst>& inst, domagg_dty
     if (op == DOMAGG_SUM && wt == DOMAGG_I64) return run_m<OpSumI64>(h, m, inst, ct, negate, s, pl);
     if (op == DOMAGG_MAX && wt == DOMAGG_I32) return run_m<OpMaxI32>(h, m, inst, ct, negate, s, pl);
     if (op == DOMAGG_MAX && wt == DOMAGG_F32) return run_m<OpMaxF32>(h, m, inst, ct, negate, s, pl);
+    if (op == DOMAGG_MIN && wt == DOMAGG_I32) return run_m<OpMinI32>(h, m, inst, ct, negate, s, pl);
+    if (op == DOMAGG_MIN && wt == DOMAGG_F32) return run_m<OpMinF32>(h, m, inst, ct, negate, s, pl);
     return fail(h, DOMAGG_ERR_INVALID_ARG, "unsupported (op, weight dtype) pair");
 }
 
@@ -688,7 +705,7 @@ size_t record_bytes(int m, domagg_dtype wt, domagg_op op) {
     const size_t kb = m == 3 ? 8 : 4;
     const bool wide = op == DOMAGG_SUM && wt == DOMAGG_I64;
     const size_t pb = wide ? 8 : 4;
-    const size_t part = (op == DOMAGG_MAX || (op == DOMAGG_SUM && wt == DOMAGG_F32)) ? 4 : 8;
+    const size_t part = (op == DOMAGG_MAX || op == DOMAGG_MIN || (op == DOMAGG_SUM && wt == DOMAGG_F32)) ? 4 : 8;
     return 2 * kb + 2 * pb + part + 8;
 }
 
@@ -701,10 +718,11 @@ domagg_status check_common(domagg_ctx* h, int m, int64_t nD, int64_t nQ, domagg_
     if (nD < 0 || nQ < 0) return fail(h, DOMAGG_ERR_INVALID_ARG, "negative size");
     if (nD + nQ >= (int64_t)1 << 31) return fail(h, DOMAGG_ERR_UNSUPPORTED, "nD + nQ must be below 2^31");
     if (ct != DOMAGG_I32 && ct != DOMAGG_F32) return fail(h, DOMAGG_ERR_INVALID_ARG, "coordinates must be i32 or f32");
-    if (op != DOMAGG_SUM && op != DOMAGG_MAX && op != DOMAGG_COUNT) return fail(h, DOMAGG_ERR_INVALID_ARG, "bad op");
+    if (op != DOMAGG_SUM && op != DOMAGG_MAX && op != DOMAGG_COUNT && op != DOMAGG_MIN)
+        return fail(h, DOMAGG_ERR_INVALID_ARG, "bad op");
     if (op == DOMAGG_SUM && wt != DOMAGG_I64 && wt != DOMAGG_F32)
         return fail(h, DOMAGG_ERR_INVALID_ARG, "SUM takes i64 or f32 weights");
-    if (op == DOMAGG_MAX && wt != DOMAGG_I32 && wt != DOMAGG_F32)
+    if ((op == DOMAGG_MAX || op == DOMAGG_MIN) && wt != DOMAGG_I32 && wt != DOMAGG_F32)
         return fail(h, DOMAGG_ERR_INVALID_ARG, "MAX takes i32 or f32 weights");
     return DOMAGG_OK;
 }

@@ -101,20 +101,38 @@ __global__ __launch_bounds__(256) void k_radix_hist(const K* __restrict__ keys, 
 
 // First-pass global position of every (range, digit): the digit's start in
 // the segment plus the counts of the segment's earlier ranges.  In place over
-// the per-range counts; one block per segment, one thread per digit.
-static __global__ __launch_bounds__(RADIX) void k_range_bases(const u32* __restrict__ range_off,
-                                                             const u32* __restrict__ digit_off, int npass,
-                                                             u32* __restrict__ range_cnt0) {
-    const int seg = blockIdx.x, d = threadIdx.x;
-    u32 run = __ldg(digit_off + (u64)seg * npass * RADIX + d);  // pass 0
+// the per-range counts.  Grid (segment, group of 32 digits); the 32 warps of
+// a block split the segment's ranges into 32 slices (lane = digit): slice
+// sums, an exclusive scan of them in shared memory, then the running bases.
+constexpr int RB_WARPS = 32;
+static __global__ __launch_bounds__(RB_WARPS * 32) void k_range_bases(const u32* __restrict__ range_off,
+                                                                     const u32* __restrict__ digit_off, int npass,
+                                                                     u32* __restrict__ range_cnt0) {
+    __shared__ u32 s_sum[RB_WARPS][33];
+    const int seg = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int d = blockIdx.y * 32 + lane;
     const u32 r0 = __ldg(range_off + seg), r1 = __ldg(range_off + seg + 1);
-    for (u32 r = r0; r < r1; r += 16) {  // 16 loads in flight, then the running sum
+    const u32 n = r1 - r0, per = (n + RB_WARPS - 1) / RB_WARPS;
+    const u32 a = r0 + min(n, (u32)warp * per), b = r0 + min(n, (u32)(warp + 1) * per);
+    u32 sum = 0;
+    for (u32 r = a; r < b; r += 16) {  // 16 loads in flight
         u32 c[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) c[i] = r + i < r1 ? range_cnt0[(u64)(r + i) * RADIX + d] : 0u;
+        for (int i = 0; i < 16; ++i) c[i] = r + i < b ? range_cnt0[(u64)(r + i) * RADIX + d] : 0u;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sum += c[i];
+    }
+    s_sum[warp][lane] = sum;
+    __syncthreads();
+    u32 run = __ldg(digit_off + (u64)seg * npass * RADIX + d);  // pass 0
+    for (int w = 0; w < warp; ++w) run += s_sum[w][lane];
+    for (u32 r = a; r < b; r += 16) {
+        u32 c[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) c[i] = r + i < b ? range_cnt0[(u64)(r + i) * RADIX + d] : 0u;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            if (r + i < r1) range_cnt0[(u64)(r + i) * RADIX + d] = run;
+            if (r + i < b) range_cnt0[(u64)(r + i) * RADIX + d] = run;
             run += c[i];
         }
     }

@@ -96,7 +96,8 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
     L.stop();
     if (range_base) {
         L.start(KIND_SMALL, 0.0);
-        k_range_bases<<<sp.nseg, RADIX, 0, L.stream>>>(sp.tile_off, sp.digit_off, npass, range_base);
+        k_range_bases<<<dim3(sp.nseg, RADIX / 32), RB_WARPS * 32, 0, L.stream>>>(sp.tile_off, sp.digit_off, npass,
+                                                                                  range_base);
         L.stop();
     }
     int cur = 0;

@@ -17,7 +17,7 @@ import threading
 from .build import LIB
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "NAN"}
-OPS = {"sum": 0, "max": 1, "count": 2}
+OPS = {"sum": 0, "max": 1, "count": 2, "min": 3}
 DTYPES = {"i32": 0, "i64": 1, "f32": 2}
 TIMING_KINDS = 16
 

@@ -37,7 +37,7 @@ def assert_matches_oracle(got, D, Q, w, op, want=None, S=None, qidx=None):
         bound = F32_TOL * S
         bad = np.nonzero(err > bound)[0]
         assert bad.size == 0, f"{bad.size} queries out of tolerance, first {bad[:5]}: got {got[bad[:5]]} want {want[bad[:5]]}"
-    elif op == "max" and w is not None and w.dtype == np.float32:
+    elif op in ("max", "min") and w is not None and w.dtype == np.float32:
         assert np.array_equal(got.astype(np.float64), want)
     else:
         assert np.array_equal(got.astype(np.int64), want.astype(np.int64)), \

@@ -76,7 +76,7 @@ def test_backward_full_size_sampled():
     _check_grad(got[di], want, S)
 
 
-@pytest.mark.parametrize("op,wt", [("sum", "f32"), ("sum", "i64"), ("max", "i32"), ("count", "i64")])
+@pytest.mark.parametrize("op,wt", [("sum", "f32"), ("sum", "i64"), ("max", "i32"), ("count", "i64"), ("min", "f32")])
 def test_batch_equals_single_calls(op, wt):
     rng = np.random.default_rng(77)
     probs = []

@@ -26,7 +26,8 @@ def test_record_count_equals_oracle_flat_map():
 
 
 CASES = [(m, dt, wt, op) for m in (1, 2, 3) for dt in ("i32", "f32")
-         for wt, op in (("i64", "sum"), ("f32", "sum"), ("i32", "max"), ("f32", "max"), ("i64", "count"))]
+         for wt, op in (("i64", "sum"), ("f32", "sum"), ("i32", "max"), ("f32", "max"), ("i64", "count"),
+                        ("i32", "min"), ("f32", "min"))]
 
 
 @pytest.mark.parametrize("m,dt,wt,op", CASES)
@@ -183,6 +184,8 @@ def test_full_size_m2_tied_floats_sum_and_max():
     pm = workloads.tied_floats(weights="i32")
     gotm = gpu_forward(pm.D, pm.Q, pm.w, "max")
     assert_matches_oracle(gotm, pm.D, pm.Q, pm.w, "max", qidx=qi)
+    gotn = gpu_forward(pm.D, pm.Q, pm.w, "min")
+    assert_matches_oracle(gotn, pm.D, pm.Q, pm.w, "min", qidx=qi)
 
 
 def test_full_size_m3_gaussian_mixture():

@@ -113,7 +113,8 @@ def test_m1_is_prefix_sum(dtype):
 # --- the two oracles agree on tiny tied inputs --------------------------
 
 CASES = [(m, dt, wt, op) for m in (1, 2, 3, 4) for dt in ("i32", "f32")
-         for wt, op in (("i64", "sum"), ("f32", "sum"), ("i32", "max"), ("f32", "max"), ("i64", "count"))]
+         for wt, op in (("i64", "sum"), ("f32", "sum"), ("i32", "max"), ("f32", "max"), ("i64", "count"),
+                        ("i32", "min"), ("f32", "min"))]
 
 
 @pytest.mark.parametrize("m,dt,wt,op", CASES)
@@ -147,6 +148,8 @@ def _brute_py(D, Q, w, op):
             out.append(len(dom))
         elif op == "sum":
             out.append(int(sum(int(w[i]) for i in dom)))
+        elif op == "min":
+            out.append(min([int(w[i]) for i in dom], default=np.iinfo(np.int32).max))
         else:
             out.append(max([int(w[i]) for i in dom], default=np.iinfo(np.int32).min))
     return out
@@ -157,8 +160,28 @@ def test_brute_equals_python_definition():
     for _ in range(40):
         m = int(rng.integers(1, 4))
         D, Q, w = workloads.random_small(rng, m, 25, 20, 5, "i32", "i32")
-        for op in ("sum", "max", "count"):
+        for op in ("sum", "max", "count", "min"):
             assert oracle.brute(D, Q, w, op)[0].tolist() == _brute_py(D, Q, w, op)
+
+
+def test_min_is_negated_max_of_negated_weights():
+    """min F = -max(-w) (an identity the MIN code does not use), and the
+    empty set gives +inf / INT32_MAX."""
+    rng = np.random.default_rng(31)
+    for m in (1, 2, 3):
+        D, Q, w = workloads.random_small(rng, m, 300, 200, 9, "i32", "i32")
+        w = np.maximum(w, np.iinfo(np.int32).min + 1)
+        mn = oracle.sortscan(D, Q, w, "min")[0]
+        mx = oracle.sortscan(D, Q, -w, "max")[0]
+        empty = mx == np.iinfo(np.int32).min
+        assert np.array_equal(mn[~empty], -mx[~empty])
+        assert np.all(mn[empty] == np.iinfo(np.int32).max)
+        wf = rng.standard_normal(300).astype(np.float32)
+        mnf = oracle.brute(D, Q, wf, "min")[0]
+        mxf = oracle.brute(D, Q, -wf, "max")[0]
+        assert np.array_equal(np.isposinf(mnf), np.isneginf(mxf))
+        fin = np.isfinite(mnf)
+        assert np.array_equal(mnf[fin], -mxf[fin])
 
 
 # --- record count law (Sec. 5 flat map) ----------------------------------
