@@ -97,6 +97,27 @@ domagg_status domagg_forward(domagg_handle h, int m, const void* d_coords, int64
                              const void* d_weights, domagg_dtype weight_dtype, domagg_op op,
                              void* out, void* stream);
 
+/* domagg_forward with a choice of comparison per coordinate and of variant.
+ *   nonstrict_mask  bit i set: coordinate i is compared as d_i <= q_i instead
+ *                   of d_i < q_i (bits >= m must be 0).  The paper defines
+ *                   the strict order only; a non-strict coordinate among the
+ *                   first m-1 gets ranks 2r (data) and 2r+1 (queries), one
+ *                   more rank digit, and a non-strict last coordinate puts
+ *                   data before queries on ties (the Sec. 4 order).
+ *   variant         DOMAGG_IMPROVED: the pipeline of domagg_forward (Sec. 5).
+ *                   DOMAGG_BASIC: the unimproved algorithm of Sec. 4: every
+ *                   one of the m coordinates becomes a bitstring, records are
+ *                   keyed by m node ids (n log^m n of them, data before
+ *                   queries within a node tuple); m <= 2.  Same results,
+ *                   more records: a cross-check of Lemma 2 at scale.
+ * Other arguments, layouts and errors as domagg_forward. */
+typedef enum { DOMAGG_IMPROVED = 0, DOMAGG_BASIC = 1 } domagg_variant;
+domagg_status domagg_forward_ex(domagg_handle h, int m, const void* d_coords, int64_t nD,
+                                const void* q_coords, int64_t nQ, domagg_dtype coord_dtype,
+                                const void* d_weights, domagg_dtype weight_dtype, domagg_op op,
+                                uint32_t nonstrict_mask, domagg_variant variant, void* out,
+                                void* stream);
+
 /* Same as domagg_forward with HOST buffers (pageable or pinned): copies the
  * inputs to the handle's device staging area, runs the forward on `stream`,
  * copies `out` back and synchronises before returning. */

@@ -41,6 +41,8 @@ def _lib(plant: int = 0) -> ctypes.CDLL:
         vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
         lib.oracle_brute.argtypes = [i32, vp, i64, vp, i64, i32, vp, i32, i32, vp, vp, i32]
         lib.oracle_brute.restype = i32
+        lib.oracle_brute_ns.argtypes = [i32, vp, i64, vp, i64, i32, vp, i32, i32, ctypes.c_uint32, vp, vp, i32]
+        lib.oracle_brute_ns.restype = i32
         lib.oracle_brute_transpose.argtypes = [i32, vp, i64, vp, i64, i32, vp, vp, vp, i32]
         lib.oracle_brute_transpose.restype = i32
         lib.oracle_sortscan.argtypes = [i32, vp, i64, vp, i64, i32, vp, i32, i32, vp, vp]
@@ -87,9 +89,10 @@ def _out_array(n: int, wt: int, op: str) -> np.ndarray:
     return np.empty(n, dtype=np.float64 if is_float else np.int64)
 
 
-def brute(D, Q, w, op: str, threads: int = 0, plant: int = 0):
+def brute(D, Q, w, op: str, threads: int = 0, plant: int = 0, nonstrict: int = 0):
     """Definition of Sec. 1.2 by brute force.  Returns (out, S) with
-    S[q] = sum of |w(d)| over the dominated set (float64)."""
+    S[q] = sum of |w(d)| over the dominated set (float64).  Bit i of
+    `nonstrict` compares coordinate i as d_i <= q_i."""
     m = D.shape[1]
     D, ct = _coords(D, m)
     Q, ct2 = _coords(Q, m)
@@ -98,8 +101,8 @@ def brute(D, Q, w, op: str, threads: int = 0, plant: int = 0):
     w, wt = _weights(w, D.shape[0], op)
     out = _out_array(Q.shape[0], wt, op)
     S = np.empty(Q.shape[0], dtype=np.float64)
-    st = _lib(plant).oracle_brute(m, _ptr(D), D.shape[0], _ptr(Q), Q.shape[0], ct, _ptr(w), wt,
-                                  OPS[op], _ptr(out), _ptr(S), threads)
+    st = _lib(plant).oracle_brute_ns(m, _ptr(D), D.shape[0], _ptr(Q), Q.shape[0], ct, _ptr(w), wt,
+                                     OPS[op], nonstrict, _ptr(out), _ptr(S), threads)
     if st:
         raise OracleError(st)
     return out, S

@@ -14,7 +14,9 @@
  * associative, commutative operation with unit e (Sec. 1, Sec. 1.2).
  *
  * Three independent routes are provided:
- *   oracle_brute       -- the definition written out: O(|D||Q|m) loops.
+ *   oracle_brute       -- the definition written out: O(|D||Q|m) loops
+ *                         (oracle_brute_ns: the same with chosen coordinates
+ *                         compared non-strictly, d_i <= q_i).
  *   oracle_sortscan    -- the paper's algorithm in list form, Sec. 4 with the
  *                         one-logarithm improvement of Sec. 5: dense ranks,
  *                         P0/P1 flat map, lexicographic sort, segmented scan,
@@ -98,10 +100,16 @@ static int any_nan(const void* base, int ct, int64_t n, int m) {
     return 0;
 }
 
-/* d < q coordinate-wise, strict in every coordinate (Sec. 1.2). */
-static int dominated(const void* D, int64_t d, const void* Q, int64_t q, int ct, int m) {
+/* d < q coordinate-wise, strict in every coordinate (Sec. 1.2); with bit i
+ * of `nonstrict` set, coordinate i is compared as d_i <= q_i instead (an
+ * extension: the paper defines the strict order only). */
+static int dominated_ns(const void* D, int64_t d, const void* Q, int64_t q, int ct, int m, unsigned nonstrict) {
     for (int i = 0; i < m; ++i) {
         double x = coord_at(D, ct, d, m, i), y = coord_at(Q, ct, q, m, i);
+        if ((nonstrict >> i) & 1u) {
+            if (!(x <= y)) return 0;
+            continue;
+        }
 #if ORACLE_PLANT == 1
         if (!(x <= y)) return 0; /* planted: non-strict dominance */
 #else
@@ -109,6 +117,9 @@ static int dominated(const void* D, int64_t d, const void* Q, int64_t q, int ct,
 #endif
     }
     return 1;
+}
+static int dominated(const void* D, int64_t d, const void* Q, int64_t q, int ct, int m) {
+    return dominated_ns(D, d, Q, q, ct, m, 0u);
 }
 
 /* ------------------------------------------------------------------ */
@@ -195,8 +206,8 @@ static int check_args(int m, int64_t nD, int64_t nQ, int ct, int wt, int op) {
 /* 1. brute force: the definition (Sec. 1.2)                          */
 /* ------------------------------------------------------------------ */
 
-int oracle_brute(int m, const void* D, int64_t nD, const void* Q, int64_t nQ, int ct,
-                 const void* W, int wt, int op, void* out, double* S, int nthreads) {
+int oracle_brute_ns(int m, const void* D, int64_t nD, const void* Q, int64_t nQ, int ct, const void* W, int wt,
+                    int op, unsigned nonstrict, void* out, double* S, int nthreads) {
     int st = check_args(m, nD, nQ, ct, wt, op);
     if (st) return st;
     if (any_nan(D, ct, nD, m) || any_nan(Q, ct, nQ, m)) return OR_ERR_NAN;
@@ -208,7 +219,7 @@ int oracle_brute(int m, const void* D, int64_t nD, const void* Q, int64_t nQ, in
         agg_t acc = agg_unit(wt, op);
         double s = 0.0;
         for (int64_t d = 0; d < nD; ++d) {
-            if (!dominated(D, d, Q, q, ct, m)) continue;
+            if (!dominated_ns(D, d, Q, q, ct, m, nonstrict)) continue;
             acc = agg_F(acc, weight_of(W, wt, op, d), op);
             s += abs_weight(W, wt, op, d);
         }
@@ -217,6 +228,11 @@ int oracle_brute(int m, const void* D, int64_t nD, const void* Q, int64_t nQ, in
     }
     (void)nthreads;
     return OR_OK;
+}
+
+int oracle_brute(int m, const void* D, int64_t nD, const void* Q, int64_t nQ, int ct,
+                 const void* W, int wt, int op, void* out, double* S, int nthreads) {
+    return oracle_brute_ns(m, D, nD, Q, nQ, ct, W, wt, op, 0u, out, S, nthreads);
 }
 
 /* Adjoint of the float32 dominance sum with respect to the weights:

@@ -53,8 +53,11 @@ struct Inst {
     u32 rec_off, T;    // records of this instance
     u32 qrec_off, Tq;  // query records (partial slots) of this instance
     u32 key_bits;      // bits of the node key
-    u32 pad;
+    u32 flags;         // bit i (i < 3): coordinate i compared non-strictly; FLAG_VIRTUAL_LAST
 };
+// The last of the M coordinates is not stored but constant (the basic
+// variant of Sec. 4 run as the Sec. 5 pipeline with one more coordinate).
+constexpr u32 FLAG_VIRTUAL_LAST = 1u << 8;
 
 // ---------------------------------------------------------------------
 // decoupled look-back status words: [63:34] epoch, [33:32] flag, [31:0] value
@@ -170,6 +173,20 @@ __device__ __forceinline__ void warp_hist_add(u32* h, u32 d, bool valid, u32 lan
     const u32 grp = __ballot_sync(0xffffffffu, same);
     if (valid && !same) atomicAdd(&h[d], 1u);
     else if (same && lane == (u32)(__ffs(grp) - 1)) atomicAdd(&h[d0], (u32)__popc(grp));
+}
+
+// Transpose of the warp's 32x32 bit matrix (lane l holds row l): returns the
+// lane's column, whose bit k is bit `lane` of lane k's row.  Five rounds that
+// swap off-diagonal blocks of 16, 8, 4, 2, 1 bits.
+__device__ __forceinline__ u32 warp_transpose32(u32 row, u32 lane) {
+    const u32 masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const u32 j = 16u >> s, m = masks[s];
+        const u32 x = __shfl_xor_sync(0xffffffffu, row, j);
+        row = (lane & j) ? ((row & ~m) | ((x & ~m) >> j)) : ((row & m) | ((x & m) << j));
+    }
+    return row;
 }
 
 // Index of the last entry of the non-decreasing array a[0..n) that is <= x

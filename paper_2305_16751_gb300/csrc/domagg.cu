@@ -800,6 +800,29 @@ domagg_status domagg_forward(domagg_handle h, int m, const void* d_coords, int64
     return dispatch(h, m, inst, coord_dtype, weight_dtype, op, false, (cudaStream_t)stream);
 }
 
+domagg_status domagg_forward_ex(domagg_handle h, int m, const void* d_coords, int64_t nD, const void* q_coords,
+                                int64_t nQ, domagg_dtype coord_dtype, const void* d_weights, domagg_dtype weight_dtype,
+                                domagg_op op, uint32_t nonstrict_mask, domagg_variant variant, void* out,
+                                void* stream) {
+    if (variant != DOMAGG_IMPROVED && variant != DOMAGG_BASIC) return fail(h, DOMAGG_ERR_INVALID_ARG, "bad variant");
+    const int M = variant == DOMAGG_BASIC ? m + 1 : m;  // the pipeline's coordinates
+    domagg_status st = check_common(h, M, nD, nQ, coord_dtype, weight_dtype, op);
+    if (st) return variant == DOMAGG_BASIC && M > 3 ? fail(h, DOMAGG_ERR_UNSUPPORTED, "basic variant: m <= 2") : st;
+    if (m < 1 || (nonstrict_mask >> m) != 0u) return fail(h, DOMAGG_ERR_INVALID_ARG, "nonstrict_mask has bits >= m");
+    if ((nD > 0 && !d_coords) || (nQ > 0 && (!q_coords || !out)) ||
+        (op != DOMAGG_COUNT && nD > 0 && !d_weights))
+        return fail(h, DOMAGG_ERR_INVALID_ARG, "null pointer");
+    if (nQ == 0) return DOMAGG_OK;
+    cudaSetDevice(h->device);
+    std::vector<Inst> inst{make_inst(d_coords, nD, q_coords, nQ, d_weights, out)};
+    inst[0].flags = nonstrict_mask;
+    // basic variant: all m stored coordinates become bitstrings, and a
+    // constant last coordinate compared non-strictly puts every data record
+    // of a node tuple before its queries
+    if (variant == DOMAGG_BASIC) inst[0].flags |= FLAG_VIRTUAL_LAST | (1u << m);
+    return dispatch(h, M, inst, coord_dtype, weight_dtype, op, false, (cudaStream_t)stream);
+}
+
 domagg_status domagg_forward_host(domagg_handle h, int m, const void* d_coords, int64_t nD, const void* q_coords,
                                   int64_t nQ, domagg_dtype coord_dtype, const void* d_weights,
                                   domagg_dtype weight_dtype, domagg_op op, void* out, void* stream) {

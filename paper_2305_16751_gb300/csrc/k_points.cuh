@@ -101,9 +101,16 @@ __global__ void k_encode(const Inst* __restrict__ inst, const u32* __restrict__ 
     const void* base = local < nQ ? inst[s].qco : inst[s].dco;
     const u32 row = local < nQ ? local : local - nQ;
     bool nan = false;
-    if (M >= 2) rk0[p] = coord_key<F32>(base, row, M, 0, negate, nan);
-    if (M >= 3) rk1[p] = coord_key<F32>(base, row, M, 1, negate, nan);
-    lk[p] = coord_key<F32>(base, row, M, M - 1, negate, nan);
+    const u32 flags = inst[s].flags;
+    const bool virt = (flags & FLAG_VIRTUAL_LAST) != 0u;
+    const int stride = virt ? M - 1 : M;  // stored coordinates per point
+    if (M >= 2) rk0[p] = coord_key<F32>(base, row, stride, 0, negate, nan);
+    if (M >= 3) rk1[p] = coord_key<F32>(base, row, stride, 1, negate, nan);
+    u32 key = virt ? 0u : coord_key<F32>(base, row, stride, M - 1, negate, nan);
+    // a non-strict last coordinate is sorted descending and read back in
+    // reverse, which puts data before queries on ties
+    if ((flags >> (M - 1)) & 1u) key = ~key;
+    lk[p] = key;
     if (nan) atomicOr(&ctl->error, ERR_NAN);
 }
 
@@ -157,9 +164,11 @@ __device__ __forceinline__ void block_exscan(u32 (&v)[C], u32 (&tot)[C], u32* sc
 // Dense ranks (Sec. 4, instructions 5i-2 .. 5i and 5m+i): over the keys
 // sorted per instance, flag every key that differs from its predecessor,
 // scan the flags, and scatter rank = (flags up to here) - 1 to the point's
-// own slot.  U = number of distinct keys; b = ceil(log2 U) digits.
+// own slot.  U = number of distinct keys; b = ceil(log2 U) digits.  For a
+// coordinate compared non-strictly the rank is 2r for data and 2r + 1 for
+// queries (U doubles), so that d_i <= q_i  <=>  rank(d) < rank(q).
 template <int THREADS, int ITEMS>
-__global__ __launch_bounds__(THREADS) void k_rank(const u32* __restrict__ skeys, const u32* __restrict__ sidx,
+__global__ __launch_bounds__(THREADS, 4) void k_rank(const u32* __restrict__ skeys, const u32* __restrict__ sidx,
                                                   const u32* __restrict__ seg_off, const u32* __restrict__ tile_off,
                                                   int nseg, u32* __restrict__ rank_out, Inst* inst, int dim,
                                                   u64* status, Ctl* ctl, int launch_idx) {
@@ -175,6 +184,8 @@ __global__ __launch_bounds__(THREADS) void k_rank(const u32* __restrict__ skeys,
     const u32 t = s_info[0], epoch = s_info[1];
     if (t >= __ldg(tile_off + nseg)) return;
     const TileLoc L = locate_tile<TILE>(t, seg_off, tile_off, nseg);
+    const bool nonstrict = (inst[L.seg].flags >> dim) & 1u;
+    const u32 nQ = inst[L.seg].nQ;
     u32 key[ITEMS];
     load_blocked_u32<THREADS, ITEMS>(skeys, L.start, L.end, sbuf, key, 0u);
     // predecessor of each thread's first item
@@ -183,14 +194,15 @@ __global__ __launch_bounds__(THREADS) void k_rank(const u32* __restrict__ skeys,
     bool has_prev = x0 > L.seg_begin;
     if (has_prev && x0 < L.end) prev = skeys[x0 - 1];
     u32 cnt[1] = {0};
-    u32 f[ITEMS];
+    u32 fmask = 0;  // bit i: item i starts a new key
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const u32 x = x0 + i;
-        f[i] = (x < L.end && (!has_prev || key[i] != prev)) ? 1u : 0u;
+        const u32 f = (x < L.end && (!has_prev || key[i] != prev)) ? 1u : 0u;
         has_prev = true;
         prev = key[i];
-        cnt[0] += f[i];
+        fmask |= f << i;
+        cnt[0] += f;
     }
     u32 tot[1];
     block_exscan<THREADS, 1>(cnt, tot, scratch);
@@ -208,20 +220,33 @@ __global__ __launch_bounds__(THREADS) void k_rank(const u32* __restrict__ skeys,
         s_info[2] = excl;
     }
     __syncthreads();
+    // ranks in blocked order into shared memory, then scattered by index in
+    // striped order (coalesced reads of the indices)
     u32 run = s_info[2] + cnt[0];
-    const u32 n_total = __ldg(seg_off + nseg);
+    const u32 lx0 = threadIdx.x * ITEMS;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const u32 x = x0 + i;
-        if (x < L.end) {
-            run += f[i];
-            const u32 dst = sidx[x];
-            if (dst < n_total) rank_out[dst] = run - 1u;
-            if (x + 1 == L.seg_end) {
-                const u32 U = run;
-                inst[L.seg].U[dim] = U;
-                inst[L.seg].b[dim] = U <= 1u ? 0u : 32u - __clz(U - 1u);
-            }
+        run += (fmask >> i) & 1u;
+        sbuf[pidx(lx0 + i)] = run - 1u;
+        if (x < L.end && x + 1 == L.seg_end) {
+            const u32 U = nonstrict ? 2u * run : run;
+            inst[L.seg].U[dim] = U;
+            inst[L.seg].b[dim] = U <= 1u ? 0u : 32u - __clz(U - 1u);
+        }
+    }
+    __syncthreads();
+    const u32 n_total = __ldg(seg_off + nseg);
+#pragma unroll 4
+    for (int i = 0; i < ITEMS; ++i) {
+        const u32 x = (u32)i * THREADS + threadIdx.x;
+        if (L.start + x < L.end) {
+            const u32 dst = sidx[L.start + x];
+            u32 r = sbuf[pidx(x)];
+            // non-strict coordinate: rank 2r for data, 2r + 1 for queries, so
+            // a query's rank exceeds the data ranks of its own value
+            if (nonstrict) r = 2u * r + ((dst - L.seg_begin) < nQ ? 1u : 0u);
+            if (dst < n_total) rank_out[dst] = r;
         }
     }
 }
@@ -291,6 +316,7 @@ __global__ __launch_bounds__(256) void k_count_scan(
     const u32 b0 = M >= 2 ? I.b[0] : 0u, b1 = M >= 3 ? I.b[1] : 0u;
     const u32 m0 = low_mask(b0), m1 = low_mask(b1);
     const u32 n_total = __ldg(seg_off + nseg);
+    const bool rev = (I.flags >> (M - 1)) & 1u;  // non-strict last coordinate: its order read backwards
     const u32 wstart = L.start + (u32)warp * CS_ROUNDS * 32u;
     // per lane (= level): the counts of every chunk of the warp
     u32 rc[CS_ROUNDS], qc[CS_ROUNDS];
@@ -299,7 +325,7 @@ __global__ __launch_bounds__(256) void k_count_scan(
     for (int i = 0; i < CS_ROUNDS; ++i) {
         const u32 x = wstart + (u32)i * 32u + (u32)lane;
         const bool valid = x < L.end;
-        u32 j = valid ? perm[x] : L.seg_begin;
+        u32 j = valid ? perm[rev ? L.seg_begin + (L.seg_end - 1u - x) : x] : L.seg_begin;
         if (j >= n_total) j = L.seg_begin;  // never taken for a valid permutation
         const bool q = valid && (j - L.seg_begin) < nQ;
         u32 a = 0, c = 0, bits0 = 0, c1 = 1;
@@ -320,13 +346,19 @@ __global__ __launch_bounds__(256) void k_count_scan(
             }
         }
         u32 mine = 0, mine_q = 0;
-        for (u32 lv = 0; lv < nlev; ++lv) {
-            const u32 w = ((bits0 >> lv) & 1u) ? c1 : 0u;
-            const u32 sa = __reduce_add_sync(0xffffffffu, w);
-            const u32 sq = __reduce_add_sync(0xffffffffu, q ? w : 0u);
-            if ((u32)lane == lv) {
-                mine = sa;
-                mine_q = sq;
+        if (M <= 2) {
+            // one record per level: lane lv counts the lanes with bit lv set
+            mine = (u32)__popc(warp_transpose32(bits0, (u32)lane));
+            mine_q = (u32)__popc(warp_transpose32(q ? bits0 : 0u, (u32)lane));
+        } else {
+            for (u32 lv = 0; lv < nlev; ++lv) {
+                const u32 w = ((bits0 >> lv) & 1u) ? c1 : 0u;
+                const u32 sa = __reduce_add_sync(0xffffffffu, w);
+                const u32 sq = __reduce_add_sync(0xffffffffu, q ? w : 0u);
+                if ((u32)lane == lv) {
+                    mine = sa;
+                    mine_q = sq;
+                }
             }
         }
         rc[i] = mine;

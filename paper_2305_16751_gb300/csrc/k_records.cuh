@@ -444,10 +444,7 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
         if ((u32)lane < nlev)
             s_base[warp][lane] = __ldg(qseg_base + (u64)(s - k0) * LMAX + lane) +
                                  __ldg(qchunk_base + (u64)c * LMAX + lane);
-        for (u32 lv = 0; lv < nlev; ++lv) {
-            const u32 hb = __ballot_sync(0xffffffffu, (bits0 >> lv) & 1u);
-            if ((u32)lane == lv) s_mask[warp][lv] = hb;
-        }
+        s_mask[warp][lane] = warp_transpose32(bits0, (u32)lane);  // lanes of level `lane`
         __syncwarp();
         typename Op::Acc acc = Op::e();
         if (M <= 2) {

@@ -54,6 +54,8 @@ SIGNATURES = {
     "domagg_create": ([ctypes.POINTER(_vp), _int, _sz], _int),
     "domagg_destroy": ([_vp], _int),
     "domagg_forward": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _vp], _int),
+    "domagg_forward_ex": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _int, _int, ctypes.c_uint32, _int, _vp, _vp],
+                          _int),
     "domagg_forward_host": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _vp], _int),
     "domagg_backward": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp], _int),
     "domagg_batch": ([_vp, _int, ctypes.POINTER(domagg_instance), _int, _int, _int, _vp], _int),
@@ -115,6 +117,12 @@ def domagg_destroy(h):
 def domagg_forward(h, m, d_coords, nD, q_coords, nQ, coord_dtype, d_weights, weight_dtype, op, out, stream):
     _check(h, lib().domagg_forward(h, m, d_coords, nD, q_coords, nQ, coord_dtype, d_weights, weight_dtype, op,
                                    out, stream))
+
+
+def domagg_forward_ex(h, m, d_coords, nD, q_coords, nQ, coord_dtype, d_weights, weight_dtype, op, nonstrict_mask,
+                      variant, out, stream):
+    _check(h, lib().domagg_forward_ex(h, m, d_coords, nD, q_coords, nQ, coord_dtype, d_weights, weight_dtype, op,
+                                      nonstrict_mask, variant, out, stream))
 
 
 def domagg_forward_host(h, m, d_coords, nD, q_coords, nQ, coord_dtype, d_weights, weight_dtype, op, out, stream):
@@ -244,8 +252,13 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else None
 
 
-def forward(D, Q, w=None, op: str = "sum", out=None):
-    """out[q] = F over w(d) for d < q (strict), computed on D's GPU."""
+VARIANTS = {"improved": 0, "basic": 1}
+
+
+def forward(D, Q, w=None, op: str = "sum", out=None, nonstrict: int = 0, variant: str = "improved"):
+    """out[q] = F over w(d) for d < q (strict), computed on D's GPU.  Bit i
+    of `nonstrict` compares coordinate i as d_i <= q_i; variant "basic" runs
+    the unimproved algorithm of Sec. 4 (m <= 2)."""
     torch = _torch()
     if D.device.type != "cuda":
         raise ValueError("forward expects CUDA tensors (use forward_host for host buffers)")
@@ -257,9 +270,25 @@ def forward(D, Q, w=None, op: str = "sum", out=None):
     if out is None:
         out = torch.empty(Q.shape[0], dtype=out_dtype(op, w), device=D.device)
     dev = D.device.index or 0
-    domagg_forward(handle(dev), m, _ptr(D), D.shape[0], _ptr(Q), Q.shape[0], _coord_dtype(D), _ptr(w),
-                   _weight_dtype(w, op), OPS[op], _ptr(out), _stream(D.device))
+    if nonstrict or variant != "improved":
+        domagg_forward_ex(handle(dev), m, _ptr(D), D.shape[0], _ptr(Q), Q.shape[0], _coord_dtype(D), _ptr(w),
+                          _weight_dtype(w, op), OPS[op], nonstrict, VARIANTS[variant], _ptr(out), _stream(D.device))
+    else:
+        domagg_forward(handle(dev), m, _ptr(D), D.shape[0], _ptr(Q), Q.shape[0], _coord_dtype(D), _ptr(w),
+                       _weight_dtype(w, op), OPS[op], _ptr(out), _stream(D.device))
     return out
+
+
+def ks_statistic(X, Y) -> float:
+    """Two-sample statistic max over z in X u Y of |F_X(z) - F_Y(z)|, with F
+    the empirical CDF (the fraction of a sample <= z in every coordinate):
+    two dominance counts with every coordinate non-strict, on the GPU."""
+    torch = _torch()
+    Z = torch.cat([X, Y]).contiguous()
+    full = (1 << X.shape[1]) - 1
+    fx = forward(X, Z, None, "count", nonstrict=full).double() / X.shape[0]
+    fy = forward(Y, Z, None, "count", nonstrict=full).double() / Y.shape[0]
+    return float((fx - fy).abs().max())
 
 
 def forward_host(D, Q, w=None, op: str = "sum", device: int = 0):

@@ -142,6 +142,17 @@ def batch_instances(k: int = 4096, lo: int = 256, hi: int = 2**18, seed: int | N
     return out
 
 
+def ecdf_samples(n: int = 2**20, m: int = 3, shift: float = 0.05, seed: int | None = None) -> Problem:
+    """Two samples for the empirical CDF / two-sample statistic (dominance
+    counting with every coordinate non-strict): X ~ N(0, 1)^m in D, Y ~
+    N(shift, 1)^m in Q, float32 on a 2^-8 grid (ties within and across the
+    samples)."""
+    rng = _rng(6, seed)
+    X = (np.round(rng.standard_normal((n, m)) * 256.0) / 256.0).astype(np.float32)
+    Y = (np.round((rng.standard_normal((n, m)) + shift) * 256.0) / 256.0).astype(np.float32)
+    return Problem(m=m, D=X, Q=Y, w=None, op="count", name=f"ecdf_m{m}_n{n}")
+
+
 def random_small(rng: np.random.Generator, m: int, nD: int, nQ: int, levels: int, dtype: str,
                  weights: str) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
     """Tiny random cases with heavy ties: every coordinate takes one of

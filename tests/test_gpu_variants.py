@@ -1,0 +1,117 @@
+"""Non-strict coordinates, the basic (unimproved) variant of Sec. 4, and
+dominance counting with D = Q (ECDF), on the GPU against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import assert_matches_oracle, to_dev, torch
+from paper_2305_16751_gb300 import domagg, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _forward(D, Q, w, op, nonstrict=0, variant="improved"):
+    out = domagg.forward(to_dev(D), to_dev(Q), to_dev(w), op, nonstrict=nonstrict, variant=variant)
+    torch().cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _check(got, D, Q, w, op, nonstrict):
+    want, S = oracle.brute(D, Q, w, op, nonstrict=nonstrict)
+    assert_matches_oracle(got, D, Q, w, op, want=want, S=S)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+@pytest.mark.parametrize("dt,wt,op", [("i32", "i64", "sum"), ("f32", "f32", "sum"), ("i32", "i32", "max"),
+                                      ("f32", "i64", "count")])
+def test_nonstrict_masks_match_oracle(m, dt, wt, op):
+    rng = np.random.default_rng(500 + 10 * m + len(op))
+    for mask in range(1 << m):
+        D, Q, w = workloads.random_small(rng, m, 5000, 4000, 30, dt, wt)
+        wv = None if op == "count" else w
+        _check(_forward(D, Q, wv, op, nonstrict=mask), D, Q, wv, op, mask)
+
+
+def test_all_equal_points_nonstrict_dominate_everything():
+    D = np.full((3000, 2), 5, np.int32)
+    Q = np.full((1000, 2), 5, np.int32)
+    w = np.arange(3000, dtype=np.int64)
+    assert np.all(_forward(D, Q, w, "sum", nonstrict=3) == w.sum())
+    assert np.all(_forward(D, Q, w, "sum", nonstrict=1) == 0)  # strict in the last coordinate
+
+
+def _basic_record_count(D, Q):
+    """Records of the basic variant: every coordinate a bitstring, so
+    T = sum over data of prod_i zeros(r_i) + sum over queries of prod_i ones(r_i)."""
+    P = np.concatenate([D, Q]).astype(np.float64)
+    P[P == 0] = 0.0
+    nD = D.shape[0]
+    cnt = np.ones(P.shape[0], dtype=np.int64)
+    for i in range(P.shape[1]):
+        u, r = np.unique(P[:, i], return_inverse=True)
+        b = int(np.ceil(np.log2(len(u)))) if len(u) > 1 else 0
+        ones = np.zeros(P.shape[0], np.int64)
+        for j in range(b):
+            ones += (r >> j) & 1
+        cnt *= np.where(np.arange(P.shape[0]) < nD, b - ones, ones)
+    return int(cnt.sum())
+
+
+@pytest.mark.parametrize("m", [1, 2])
+@pytest.mark.parametrize("dt,wt,op", [("i32", "i64", "sum"), ("f32", "f32", "sum"), ("i32", "i32", "max")])
+def test_basic_variant_equals_definition(m, dt, wt, op):
+    rng = np.random.default_rng(600 + m)
+    for nD, nQ, levels in ((4000, 3000, 25), (2500, 2500, 2000), (1, 5000, 3)):
+        D, Q, w = workloads.random_small(rng, m, nD, nQ, levels, dt, wt)
+        got = _forward(D, Q, w, op, variant="basic")
+        _check(got, D, Q, w, op, 0)
+        if op == "sum":
+            assert domagg.stats()["n_records"] == _basic_record_count(D, Q)
+            improved = _forward(D, Q, w, op)
+            if wt == "i64":
+                assert np.array_equal(got, improved)
+
+
+def test_basic_variant_at_scale_m2():
+    """|D| = |Q| = 2^18 uniform float32 points: the basic variant's n log^2 n
+    records give the same sums as the Sec. 5 pipeline (sampled against the
+    oracle); its record count is the basic flat-map formula."""
+    rng = np.random.default_rng(7)
+    n = 1 << 18
+    D = (rng.integers(0, 1 << 24, size=(n, 2)) * 2.0**-24).astype(np.float32)
+    Q = (rng.integers(0, 1 << 24, size=(n, 2)) * 2.0**-24).astype(np.float32)
+    w = rng.integers(-1000, 1001, size=n).astype(np.int64)
+    basic = _forward(D, Q, w, "sum", variant="basic")
+    T_basic = domagg.stats()["n_records"]
+    improved = _forward(D, Q, w, "sum")
+    T_improved = domagg.stats()["n_records"]
+    assert np.array_equal(basic, improved)
+    assert T_basic == _basic_record_count(D, Q) and T_basic > 4 * T_improved
+    qi = np.sort(rng.choice(n, 128, replace=False))
+    assert_matches_oracle(basic, D, Q, w, "sum", qidx=qi)
+
+
+def test_ecdf_counts_and_two_sample_statistic():
+    """Dominance counting with D = Q and every coordinate non-strict is the
+    empirical CDF at the sample points; the two-sample statistic
+    max |F_X - F_Y| over X u Y matches the oracle's."""
+    p = workloads.ecdf_samples(n=6000, m=3)
+    X, Y = p.D, p.Q
+    cnt = _forward(X, X, None, "count", nonstrict=7)
+    want = oracle.brute(X, X, None, "count", nonstrict=7)[0]
+    assert np.array_equal(cnt, want)
+    ks = domagg.ks_statistic(to_dev(X), to_dev(Y))
+    Z = np.concatenate([X, Y])
+    fx = oracle.brute(X, Z, None, "count", nonstrict=7)[0] / X.shape[0]
+    fy = oracle.brute(Y, Z, None, "count", nonstrict=7)[0] / Y.shape[0]
+    assert abs(ks - np.abs(fx - fy).max()) < 1e-12
+
+
+def test_variant_arguments_are_checked():
+    D = np.zeros((4, 3), np.int32)
+    with pytest.raises(domagg.DomaggError) as e:
+        _forward(D, D, np.ones(4, np.int64), "sum", variant="basic")
+    assert e.value.status == 2  # UNSUPPORTED: basic needs m <= 2
+    with pytest.raises(domagg.DomaggError) as e:
+        _forward(D[:, :2], D[:, :2], np.ones(4, np.int64), "sum", nonstrict=4)
+    assert e.value.status == 1  # INVALID_ARG: mask bit beyond m

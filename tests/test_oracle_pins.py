@@ -342,3 +342,51 @@ def test_planted_mistakes_are_caught(plant):
     # coordinate; 3: one binary digit too few per rank; 4: the last coordinate
     # also splits segments
     assert not _pins_pass(plant)
+
+
+# --- non-strict coordinates (an extension of the strict order) -----------
+
+def _brute_py_ns(D, Q, w, nonstrict):
+    out = []
+    for q in Q:
+        tot = 0
+        for i, d in enumerate(D):
+            if all((d[k] <= q[k]) if (nonstrict >> k) & 1 else (d[k] < q[k]) for k in range(len(q))):
+                tot += int(w[i])
+        out.append(tot)
+    return out
+
+
+def test_nonstrict_brute_equals_python_definition():
+    rng = np.random.default_rng(41)
+    for _ in range(30):
+        m = int(rng.integers(1, 4))
+        D, Q, w = workloads.random_small(rng, m, 25, 20, 4, "i32", "i64")
+        mask = int(rng.integers(0, 1 << m))
+        assert oracle.brute(D, Q, w, "sum", nonstrict=mask)[0].tolist() == _brute_py_ns(D, Q, w, mask)
+
+
+def test_nonstrict_on_integers_is_strict_against_the_successor():
+    """For integer coordinates d <= q  <=>  d < q + 1: shifting the queries'
+    non-strict coordinates by one turns the strict oracle into the
+    non-strict one."""
+    rng = np.random.default_rng(42)
+    for m in (1, 2, 3):
+        for mask in range(1, 1 << m):
+            D, Q, w = workloads.random_small(rng, m, 400, 300, 6, "i32", "i64")
+            Q1 = Q.copy()
+            for k in range(m):
+                if (mask >> k) & 1:
+                    Q1[:, k] += 1
+            a = oracle.brute(D, Q, w, "sum", nonstrict=mask)[0]
+            b = oracle.sortscan(D, Q1, w, "sum")[0]
+            assert a.tolist() == b.tolist()
+
+
+def test_nonstrict_without_ties_equals_strict():
+    rng = np.random.default_rng(43)
+    P = rng.permutation(2000).reshape(1000, 2).astype(np.int32)
+    D, Q = P[:600], P[600:]
+    w = rng.integers(-9, 10, 600).astype(np.int64)
+    for mask in range(4):
+        assert oracle.brute(D, Q, w, "sum", nonstrict=mask)[0].tolist() == oracle.brute(D, Q, w, "sum")[0].tolist()
