@@ -218,6 +218,42 @@ def bench_batch(args, dev, stream, torch, domagg, workloads):
                         "int32 coords U[0,2^31), f32 w, sum"}
 
 
+def bench_variants(args, dev, stream, torch, domagg, workloads):
+    """The widened rows: the basic (unimproved) variant of Sec. 4 against the
+    Sec. 5 pipeline on the same m = 2 problem, ECDF counting (D = Q, every
+    coordinate non-strict) at m = 3, and MIN."""
+    import numpy as np
+    res = {}
+    rng = np.random.default_rng(2305167517)
+    n = args.n // 16
+    D = torch.from_numpy((rng.integers(0, 1 << 24, size=(n, 2)) * 2.0**-24).astype(np.float32)).to(dev)
+    Q = torch.from_numpy((rng.integers(0, 1 << 24, size=(n, 2)) * 2.0**-24).astype(np.float32)).to(dev)
+    w = torch.from_numpy(rng.integers(-1000, 1001, size=n).astype(np.int64)).to(dev)
+    for name, variant in (("improved", "improved"), ("basic", "basic")):
+        t = timed_steps(lambda: domagg.forward(D, Q, w, "sum", variant=variant), 3, 2, stream, torch)
+        ms = statistics.mean(t)
+        res[f"m2_{name}"] = {"value": n / (ms / 1e3), "unit": "queries/s", "ms_per_step": ms,
+                             "records": domagg.stats(dev.index or 0)["n_records"]}
+    res["m2_workload"] = f"|D|=|Q|={n}, float32 U[0,1) on the 2^-24 grid, int64 sum"
+    del D, Q, w
+    p = workloads.ecdf_samples(n=args.n // 16, m=3)
+    X = torch.from_numpy(p.D).to(dev)
+    t = timed_steps(lambda: domagg.forward(X, X, None, "count", nonstrict=7), 3, 2, stream, torch)
+    ms = statistics.mean(t)
+    res["ecdf_m3"] = {"value": X.shape[0] / (ms / 1e3), "unit": "queries/s", "ms_per_step": ms,
+                      "records": domagg.stats(dev.index or 0)["n_records"],
+                      "workload": f"D=Q={X.shape[0]} points, m=3, N(0,1) on a 2^-8 grid, count, all coordinates <="}
+    del X
+    pm = workloads.tied_floats(n=args.n, weights="i32")
+    Dm, Qm, wm = (torch.from_numpy(a).to(dev) for a in (pm.D, pm.Q, pm.w))
+    om = torch.empty(Qm.shape[0], dtype=torch.int32, device=dev)
+    t = timed_steps(lambda: domagg.forward(Dm, Qm, wm, "min", out=om), 3, 2, stream, torch)
+    ms = statistics.mean(t)
+    res["min_m2"] = {"value": Qm.shape[0] / (ms / 1e3), "unit": "queries/s", "ms_per_step": ms,
+                     "workload": "tied_floats 2^24, int32 weights, min"}
+    return res
+
+
 def job_throughput(local_ms: float, units_per_rank: int, world: int, device=None):
     """Whole-job throughput: every rank's units over the slowest rank's time
     (max over ranks of the timed region).  Returns (units/s, max ms)."""
@@ -340,6 +376,7 @@ def main():
         line["m3"] = {"value": p3.Q.shape[0] / (m3_ms / 1e3), "unit": "queries/s", "ms_per_step": m3_ms,
                       "workload": "m3_nD2^21_nQ2^21_gmm_i32coords_i64w_sum", "records": st3["n_records"]}
         del D3, Q3, w3, o3
+        line["variants"] = bench_variants(args, dev, stream, torch, domagg, workloads)
         line["batch"] = bench_batch(args, dev, stream, torch, domagg, workloads)
         # end to end through the host-buffer entry point
         Dh = torch.from_numpy(p.D).pin_memory()

@@ -274,8 +274,9 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         P[22] = c.take<u32>((size_t)NC * LMAX);      // chunk bases per level
         P[23] = c.take<u32>((size_t)k * LMAX);       // records per (instance, level)
         P[24] = c.take<u32>((size_t)sort_range_bound(pt_sizes) * RADIX);  // first-pass range bases
+        P[25] = c.take<u32>(ntp);                                         // rank counts per point tile
     };
-    void* P[25];
+    void* P[26];
     {
         Carver c(nullptr);
         carve_points(c, P);
@@ -358,11 +359,17 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         // only the sorted key sequence matters for dense ranks: any order of equal digits
         const int cur = sort_pairs<u32, u32>(L, sp, keys, vals, true, 32, 0xffffffffu, KIND_HIST_POINTS,
                                              KIND_SORT_POINTS, nullptr, false);
-        const int li = L.lookback_index();
+        u32* tile_cnt = (u32*)P[25];
+        L.start(KIND_RANK, (double)N * 4);
+        k_rank_count<SCAN_THREADS, SCAN_ITEMS><<<(unsigned)ntp, SCAN_THREADS, 0, stream>>>(keys[cur], d_pt_offs,
+                                                                                        d_pt_tiles, k, tile_cnt);
+        L.stop();
+        L.start(KIND_SMALL, 0.0);
+        k_tile_exscan<<<(unsigned)((k + 7) / 8), 256, 0, stream>>>(d_pt_tiles, k, tile_cnt);
+        L.stop();
         L.start(KIND_RANK, (double)N * 12);
-        k_rank<SCAN_THREADS, SCAN_ITEMS><<<(unsigned)ntp, SCAN_THREADS, 0, stream>>>(
-            keys[cur], vals[cur], d_pt_offs, d_pt_tiles, k, i == 0 ? r0 : r1, d_inst, i, (u64*)h->st_multi.p,
-            h->ctl, li);
+        k_rank_apply<SCAN_THREADS, SCAN_ITEMS><<<(unsigned)ntp, SCAN_THREADS, 0, stream>>>(
+            keys[cur], vals[cur], d_pt_offs, d_pt_tiles, k, tile_cnt, i == 0 ? r0 : r1, d_inst, i);
         L.stop();
     }
     // ---- order of the last coordinate, queries first on ties (Sec. 5)

@@ -167,28 +167,75 @@ __device__ __forceinline__ void block_exscan(u32 (&v)[C], u32 (&tot)[C], u32* sc
 // own slot.  U = number of distinct keys; b = ceil(log2 U) digits.  For a
 // coordinate compared non-strictly the rank is 2r for data and 2r + 1 for
 // queries (U doubles), so that d_i <= q_i  <=>  rank(d) < rank(q).
+//
+// Computed in three launches without a look-back chain (one instance is a
+// single chain of thousands of tiles, whose decoupled look-back walks were
+// the cost): (1) per tile, the number of keys that differ from their
+// predecessor; (2) per instance, the exclusive scan of those counts over its
+// tiles (one warp per instance); (3) k_rank_apply: flags again, a block scan
+// plus the tile's prefix, and the scatter by index.
 template <int THREADS, int ITEMS>
-__global__ __launch_bounds__(THREADS, 4) void k_rank(const u32* __restrict__ skeys, const u32* __restrict__ sidx,
-                                                  const u32* __restrict__ seg_off, const u32* __restrict__ tile_off,
-                                                  int nseg, u32* __restrict__ rank_out, Inst* inst, int dim,
-                                                  u64* status, Ctl* ctl, int launch_idx) {
+__global__ __launch_bounds__(THREADS) void k_rank_count(const u32* __restrict__ skeys, const u32* __restrict__ seg_off,
+                                                        const u32* __restrict__ tile_off, int nseg,
+                                                        u32* __restrict__ tile_cnt) {
+    constexpr int TILE = THREADS * ITEMS;
+    __shared__ u32 warp_sum[THREADS / 32];
+    const u32 t = blockIdx.x;
+    if (t >= __ldg(tile_off + nseg)) return;
+    const TileLoc L = locate_tile<TILE>(t, seg_off, tile_off, nseg);
+    u32 c = 0;
+#pragma unroll 4
+    for (int i = 0; i < ITEMS; ++i) {  // striped: coalesced, the predecessor from the same lines
+        const u32 x = L.start + (u32)i * THREADS + threadIdx.x;
+        if (x < L.end) c += (x == L.seg_begin || __ldg(skeys + x) != __ldg(skeys + x - 1)) ? 1u : 0u;
+    }
+    for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u32 tot = 0;
+        for (int w = 0; w < THREADS / 32; ++w) tot += warp_sum[w];
+        tile_cnt[t] = tot;
+    }
+}
+
+// Exclusive scan of per-tile counts within every segment (in place), one
+// warp per segment walking its tiles 32 at a time.
+static __global__ __launch_bounds__(256) void k_tile_exscan(const u32* __restrict__ tile_off, int nseg,
+                                                           u32* __restrict__ cnt) {
+    const int seg = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (seg >= nseg) return;
+    const u32 a = __ldg(tile_off + seg), b = __ldg(tile_off + seg + 1);
+    u32 carry = 0;
+    for (u32 base = a; base < b; base += 32) {
+        const u32 x = base + (u32)lane;
+        const u32 v = x < b ? cnt[x] : 0u;
+        u32 inc = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 n = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += n;
+        }
+        if (x < b) cnt[x] = carry + inc - v;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+}
+
+template <int THREADS, int ITEMS>
+__global__ __launch_bounds__(THREADS, 4) void k_rank_apply(const u32* __restrict__ skeys, const u32* __restrict__ sidx,
+                                                        const u32* __restrict__ seg_off,
+                                                        const u32* __restrict__ tile_off, int nseg,
+                                                        const u32* __restrict__ tile_excl, u32* __restrict__ rank_out,
+                                                        Inst* inst, int dim) {
     constexpr int TILE = THREADS * ITEMS;
     __shared__ u32 sbuf[Padded<TILE>::value];
     __shared__ u32 scratch[THREADS / 32];
-    __shared__ u32 s_info[3];
-    if (threadIdx.x == 0) {
-        s_info[0] = atomicAdd(&ctl->tile_ctr[launch_idx], 1u);
-        s_info[1] = ctl->epoch_base + (u32)launch_idx;
-    }
-    __syncthreads();
-    const u32 t = s_info[0], epoch = s_info[1];
+    const u32 t = blockIdx.x;
     if (t >= __ldg(tile_off + nseg)) return;
     const TileLoc L = locate_tile<TILE>(t, seg_off, tile_off, nseg);
     const bool nonstrict = (inst[L.seg].flags >> dim) & 1u;
     const u32 nQ = inst[L.seg].nQ;
     u32 key[ITEMS];
     load_blocked_u32<THREADS, ITEMS>(skeys, L.start, L.end, sbuf, key, 0u);
-    // predecessor of each thread's first item
     const u32 x0 = L.start + threadIdx.x * ITEMS;
     u32 prev = 0;
     bool has_prev = x0 > L.seg_begin;
@@ -206,23 +253,7 @@ __global__ __launch_bounds__(THREADS, 4) void k_rank(const u32* __restrict__ ske
     }
     u32 tot[1];
     block_exscan<THREADS, 1>(cnt, tot, scratch);
-    if (threadIdx.x == 0) {
-        u64* st = status + t;
-        u32 excl = 0;
-        const u32 first_tile = t - (L.start - L.seg_begin) / (u32)TILE;
-        if (L.first) {
-            st_store(st, st_pack(epoch, ST_PREFIX, tot[0]));
-        } else {
-            st_store(st, st_pack(epoch, ST_AGG, tot[0]));
-            excl = lookback_u32(status, 1, 0, t, first_tile, epoch, ctl, 2u);
-            st_store(st, st_pack(epoch, ST_PREFIX, excl + tot[0]));
-        }
-        s_info[2] = excl;
-    }
-    __syncthreads();
-    // ranks in blocked order into shared memory, then scattered by index in
-    // striped order (coalesced reads of the indices)
-    u32 run = s_info[2] + cnt[0];
+    u32 run = __ldg(tile_excl + t) + cnt[0];
     const u32 lx0 = threadIdx.x * ITEMS;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
@@ -243,8 +274,6 @@ __global__ __launch_bounds__(THREADS, 4) void k_rank(const u32* __restrict__ ske
         if (L.start + x < L.end) {
             const u32 dst = sidx[L.start + x];
             u32 r = sbuf[pidx(x)];
-            // non-strict coordinate: rank 2r for data, 2r + 1 for queries, so
-            // a query's rank exceeds the data ranks of its own value
             if (nonstrict) r = 2u * r + ((dst - L.seg_begin) < nQ ? 1u : 0u);
             if (dst < n_total) rank_out[dst] = r;
         }
