@@ -274,7 +274,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         P[22] = c.take<u32>((size_t)NC * LMAX);      // chunk bases per level
         P[23] = c.take<u32>((size_t)k * LMAX);       // records per (instance, level)
         P[24] = c.take<u32>((size_t)sort_range_bound(pt_sizes) * RADIX);  // first-pass range bases
-        P[25] = c.take<u32>(ntp);                                         // rank counts per point tile
+        P[25] = c.take<u32>((size_t)ntp * CS_COUNTERS);                   // per point tile: rank / flat-map counts
     };
     void* P[26];
     {
@@ -383,14 +383,16 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     }
     // ---- count / offset scan of the flat map, per level
     {
-        const int li = L.lookback_index();
         // perm, gathered ranks, ranks / index / weight written in order, weight gathered
         L.start(KIND_COUNT_SCAN, (double)N * (4 + 8.0 * (M - 1) + 4 + (WT == 3 ? 0 : 2.0 * sizeof(Pay))) +
                                      (double)NC * 8 * LMAX);
         k_count_scan<M, Pay, WT><<<(unsigned)ntp, 256, 0, stream>>>(
             perm, d_pt_offs, d_pt_tiles, k, d_chunk_off, r0, r1, d_inst, pr0, pr1, pj, (Pay*)P[18], chunk_base,
-            qchunk_base, lvl_tot, qlvl_tot,
-                                                           (u64*)h->st_multi.p, h->ctl, li);
+            qchunk_base, (u32*)P[25]);
+        L.stop();
+        L.start(KIND_SMALL, 0.0);
+        k_tile_exscan_counters<<<(unsigned)(((u64)k * CS_COUNTERS + 7) / 8), 256, 0, stream>>>(
+            d_pt_tiles, k, (u32*)P[25], lvl_tot, qlvl_tot, h->ctl);
         L.stop();
     }
     // ---- record chunks: from the counts (one synchronisation) or from the plan
@@ -614,7 +616,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                                      (double)C.T * (sizeof(K) + sizeof(Pay)));
             k_expand<M, K, Pay, WT><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pj,
                                                              (const Pay*)P[18],
-                                                             chunk_base, qchunk_base, d_inst, d_sbase, d_qsbase,
+                                                             chunk_base, qchunk_base, d_pt_tiles, (const u32*)P[25],
+                                                             d_inst, d_sbase, d_qsbase,
                                                              (u32)C.T, keys[0], pays[0]);
             L.stop();
         }
@@ -644,7 +647,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             const unsigned grid = (unsigned)std::min<u64>((nchunk + 7) / 8, 152ull * 16);
             L.start(KIND_REDUCE, (double)C.Tq * sizeof(Part) + (double)(qe - qb) * (8 + sizeof(typename Op::Out)));
             k_reduce<Op, M><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pj,
-                                                      qchunk_base, d_qsbase, d_inst, partial, (u32)C.Tq);
+                                                      qchunk_base, d_pt_tiles, (const u32*)P[25], d_qsbase, d_inst,
+                                                      partial, (u32)C.Tq);
             L.stop();
         }
         T_all += C.T;

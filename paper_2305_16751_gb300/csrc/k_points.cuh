@@ -199,25 +199,43 @@ __global__ __launch_bounds__(THREADS) void k_rank_count(const u32* __restrict__ 
     }
 }
 
+// Exclusive scan, in place, of the column c[0], c[stride], ... c[(n-1)*stride]
+// by one warp: 8 consecutive entries per lane per round (their loads in
+// flight together), 256 per round.  Returns the total (64 bits).
+__device__ __forceinline__ u64 warp_exscan_column(u32* __restrict__ c, u64 stride, u32 n, int lane) {
+    u64 carry = 0;
+    for (u32 base = 0; base < n; base += 256) {
+        u32 v[8];
+        const u32 x0 = base + (u32)lane * 8u;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = x0 + i < n ? c[(u64)(x0 + i) * stride] : 0u;
+        u32 sum = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sum += v[i];
+        u32 inc = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 nb = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += nb;
+        }
+        u64 run = carry + (inc - sum);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (x0 + i < n) c[(u64)(x0 + i) * stride] = (u32)run;
+            run += v[i];
+        }
+        carry += __shfl_sync(0xffffffffu, inc, 31);  // 256 tiles hold < 2^32
+    }
+    return carry;
+}
+
 // Exclusive scan of per-tile counts within every segment (in place), one
-// warp per segment walking its tiles 32 at a time.
+// warp per segment.
 static __global__ __launch_bounds__(256) void k_tile_exscan(const u32* __restrict__ tile_off, int nseg,
                                                            u32* __restrict__ cnt) {
     const int seg = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (seg >= nseg) return;
     const u32 a = __ldg(tile_off + seg), b = __ldg(tile_off + seg + 1);
-    u32 carry = 0;
-    for (u32 base = a; base < b; base += 32) {
-        const u32 x = base + (u32)lane;
-        const u32 v = x < b ? cnt[x] : 0u;
-        u32 inc = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const u32 n = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += n;
-        }
-        if (x < b) cnt[x] = carry + inc - v;
-        carry += __shfl_sync(0xffffffffu, inc, 31);
-    }
+    warp_exscan_column(cnt + a, 1, b - a, lane);
 }
 
 template <int THREADS, int ITEMS>
@@ -306,9 +324,12 @@ __device__ __forceinline__ u32 levels_of(const Inst& I) {
 // Count and offset scan of the flat map, in the order of the last
 // coordinate (points were sorted by it, queries first on ties).  Tiles of
 // 4096 points never straddle an instance; every warp walks 16 chunks of 32
-// consecutive points.  Per instance (segmented look-back chains) it scans
-// 2 x LMAX counters: the records of every level, and the query records
-// (= partial slots) of every level.  Writes, in this order, the point's
+// consecutive points.  It counts 2 x LMAX counters: the records of every
+// level, and the query records (= partial slots) of every level.  The chunk
+// bases it writes are relative to the tile; k_tile_exscan_counters then
+// scans the tiles' totals per instance, and the flat map and the reduction
+// add the tile's prefix (no look-back chain over the thousands of tiles of
+// one instance).  Writes, in this order, the point's
 // ranks (the first with the query flag in bit 31), index and weight (data
 // points; so the flat map reads them without a dependent gather); per chunk
 // of 32 points the exclusive count of both kinds
@@ -316,27 +337,20 @@ __device__ __forceinline__ u32 levels_of(const Inst& I) {
 // every level.  The partial slots of a level are thereby a dense range in
 // which each query's records keep the order of the last coordinate.
 constexpr int CS_ROUNDS = 16;
+constexpr int CS_COUNTERS = 2 * LMAX;             // per tile: records and query records of every level
+constexpr u32 CS_CHUNKS = 8 * CS_ROUNDS;          // 32-point chunks per tile
 constexpr u32 QUERY_BIT = 0x80000000u;  // in pr0: the point is a query (ranks are below 2^31)
 template <int M, typename Pay, int WT>
 __global__ __launch_bounds__(256) void k_count_scan(
     const u32* __restrict__ perm, const u32* __restrict__ seg_off, const u32* __restrict__ tile_off, int nseg,
     const u32* __restrict__ chunk_off, const u32* __restrict__ r0, const u32* __restrict__ r1, Inst* inst,
     u32* __restrict__ pr0, u32* __restrict__ pr1, u32* __restrict__ pj, Pay* __restrict__ pw,
-    u32* __restrict__ chunk_base,
-    u32* __restrict__ qchunk_base, u32* __restrict__ lvl_tot, u32* __restrict__ qlvl_tot, u64* status, Ctl* ctl,
-    int launch_idx) {
+    u32* __restrict__ chunk_base, u32* __restrict__ qchunk_base, u32* __restrict__ tile_cnt) {
     constexpr int WARPS = 8, C = 2 * LMAX, TILE = WARPS * CS_ROUNDS * 32;
     static_assert(TILE == 4096, "point tiles");
     __shared__ u32 s_w[WARPS][C];
-    __shared__ u32 s_excl[C];
-    __shared__ u32 s_info[2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) {
-        s_info[0] = atomicAdd(&ctl->tile_ctr[launch_idx], 1u);
-        s_info[1] = ctl->epoch_base + (u32)launch_idx;
-    }
-    __syncthreads();
-    const u32 t = s_info[0], epoch = s_info[1];
+    const u32 t = blockIdx.x;
     if (t >= __ldg(tile_off + nseg)) return;
     const TileLoc L = locate_tile<TILE>(t, seg_off, tile_off, nseg);
     const Inst& I = inst[L.seg];
@@ -398,7 +412,7 @@ __global__ __launch_bounds__(256) void k_count_scan(
     s_w[warp][lane] = run_all;
     s_w[warp][LMAX + lane] = run_q;
     __syncthreads();
-    if (threadIdx.x < C) {
+    if (threadIdx.x < C) {  // exclusive over the warps; the tile's totals
         const int c = threadIdx.x;
         u32 sum = 0;
         for (int w = 0; w < WARPS; ++w) {
@@ -406,26 +420,11 @@ __global__ __launch_bounds__(256) void k_count_scan(
             s_w[w][c] = sum;
             sum += v;
         }
-        u64* st = status + (u64)t * C + c;
-        u32 excl = 0;
-        const u32 first_tile = t - (L.start - L.seg_begin) / (u32)TILE;
-        if (L.first) {
-            st_store(st, st_pack(epoch, ST_PREFIX, sum));
-        } else {
-            st_store(st, st_pack(epoch, ST_AGG, sum));
-            excl = lookback_u32(status, C, c, t, first_tile, epoch, ctl, 3u);
-            st_store(st, st_pack(epoch, ST_PREFIX, excl + sum));
-        }
-        if (excl + sum < excl) atomicOr(&ctl->error, ERR_OVERFLOW);
-        s_excl[c] = excl;
-        if (L.end == L.seg_end) {  // last tile of the instance: totals
-            if (c < LMAX) lvl_tot[(u64)L.seg * LMAX + c] = excl + sum;
-            else qlvl_tot[(u64)L.seg * LMAX + (c - LMAX)] = excl + sum;
-        }
+        tile_cnt[(u64)t * C + c] = sum;
     }
     __syncthreads();
-    const u32 base_all = s_excl[lane] + s_w[warp][lane];
-    const u32 base_q = s_excl[LMAX + lane] + s_w[warp][LMAX + lane];
+    const u32 base_all = s_w[warp][lane];  // relative to the tile
+    const u32 base_q = s_w[warp][LMAX + lane];
     const u32 cbase = __ldg(chunk_off + L.seg) + (wstart - L.seg_begin) / 32u;
     u32 ra = 0, rq = 0;
 #pragma unroll
@@ -436,6 +435,26 @@ __global__ __launch_bounds__(256) void k_count_scan(
         }
         ra += rc[i];
         rq += qc[i];
+    }
+}
+
+// Per instance and counter, the exclusive scan of the tiles' totals (in
+// place), and the instance's totals per level (lvl_tot, qlvl_tot).  One warp
+// per (instance, counter).  A total that does not fit 32 bits raises
+// ERR_OVERFLOW.
+static __global__ __launch_bounds__(256) void k_tile_exscan_counters(const u32* __restrict__ tile_off, int nseg,
+                                                                    u32* __restrict__ cnt, u32* __restrict__ lvl_tot,
+                                                                    u32* __restrict__ qlvl_tot, Ctl* ctl) {
+    const u64 gw = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= (u64)nseg * CS_COUNTERS) return;
+    const int seg = (int)(gw / CS_COUNTERS), c = (int)(gw % CS_COUNTERS);
+    const u32 a = __ldg(tile_off + seg), b = __ldg(tile_off + seg + 1);
+    const u64 carry = warp_exscan_column(cnt + (u64)a * CS_COUNTERS + c, CS_COUNTERS, b - a, lane);
+    if (lane == 0) {
+        if (carry >> 32) atomicOr(&ctl->error, ERR_OVERFLOW);
+        if (c < LMAX) lvl_tot[(u64)seg * LMAX + c] = (u32)carry;
+        else qlvl_tot[(u64)seg * LMAX + (c - LMAX)] = (u32)carry;
     }
 }
 
@@ -455,6 +474,7 @@ __global__ __launch_bounds__(256) void k_expand(
     const u32* __restrict__ chunk_off, int k, int k0, int k1, const u32* __restrict__ pt_offs,
     const u32* __restrict__ pr0, const u32* __restrict__ pr1, const u32* __restrict__ pj,
     const Pay* __restrict__ pw, const u32* __restrict__ chunk_base, const u32* __restrict__ qchunk_base,
+    const u32* __restrict__ pt_tiles, const u32* __restrict__ tile_excl,
     const Inst* __restrict__ inst, const u32* __restrict__ seg_base /*[k1-k0][LMAX]*/,
     const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/, u32 n_rec, K* __restrict__ kout, Pay* __restrict__ pout) {
     const int lane = threadIdx.x & 31;
@@ -471,12 +491,15 @@ __global__ __launch_bounds__(256) void k_expand(
         const u32 nQ = I.nQ;
         const u32 nlev = levels_of<M>(I);
         const u32 b1 = M >= 3 ? I.b[1] : 0u;
+        const u32 tile = __ldg(pt_tiles + s) + (c - __ldg(chunk_off + s)) / CS_CHUNKS;  // the count scan's tile
         // lane lv holds the bases of level lv (read once, shuffled below)
         const u32 my_all = (u32)lane < nlev ? __ldg(seg_base + (u64)(s - k0) * LMAX + lane) +
-                                                  __ldg(chunk_base + (u64)c * LMAX + lane)
+                                                  __ldg(chunk_base + (u64)c * LMAX + lane) +
+                                                  __ldg(tile_excl + (u64)tile * CS_COUNTERS + lane)
                                             : 0u;
         const u32 my_q = (u32)lane < nlev ? __ldg(qseg_base + (u64)(s - k0) * LMAX + lane) +
-                                                __ldg(qchunk_base + (u64)c * LMAX + lane)
+                                                __ldg(qchunk_base + (u64)c * LMAX + lane) +
+                                                __ldg(tile_excl + (u64)tile * CS_COUNTERS + LMAX + lane)
                                           : 0u;
         u32 a = 0, cc = 0, bits0 = 0, bits1 = 0, c1 = 1;
         bool q = false;

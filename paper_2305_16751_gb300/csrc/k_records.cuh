@@ -404,6 +404,7 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
                                                 const u32* __restrict__ pt_offs, const u32* __restrict__ pr0,
                                                 const u32* __restrict__ pr1, const u32* __restrict__ pj,
                                                 const u32* __restrict__ qchunk_base,
+                                                const u32* __restrict__ pt_tiles, const u32* __restrict__ tile_excl,
                                                 const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/,
                                                 const Inst* __restrict__ inst,
                                                 const typename Op::Part* __restrict__ partial, u32 n_partial) {
@@ -443,7 +444,9 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
         // per level: which lanes have a record there, and the level's base
         if ((u32)lane < nlev)
             s_base[warp][lane] = __ldg(qseg_base + (u64)(s - k0) * LMAX + lane) +
-                                 __ldg(qchunk_base + (u64)c * LMAX + lane);
+                                 __ldg(qchunk_base + (u64)c * LMAX + lane) +
+                                 __ldg(tile_excl + (u64)(__ldg(pt_tiles + s) + (c - __ldg(chunk_off + s)) / CS_CHUNKS) *
+                                                       CS_COUNTERS + LMAX + lane);
         s_mask[warp][lane] = warp_transpose32(bits0, (u32)lane);  // lanes of level `lane`
         __syncwarp();
         typename Op::Acc acc = Op::e();
