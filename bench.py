@@ -200,6 +200,7 @@ def bench_batch(args, dev, stream, torch, domagg, workloads):
     l_ms = statistics.mean(tl)
     # the planned batch captured once in a CUDA graph, then replayed
     plan = domagg.BatchPlan(inst, "sum", headroom=0.05)
+    tuned_ms = plan.autotune()
     side = torch.cuda.Stream(dev)
     side.wait_stream(torch.cuda.current_stream(dev))
     graph = torch.cuda.CUDAGraph()
@@ -213,7 +214,8 @@ def bench_batch(args, dev, stream, torch, domagg, workloads):
     plan.close()
     return {"value": nq / (b_ms / 1e3), "unit": "queries/s", "ms_per_step": b_ms, "instances": len(probs),
             "points": npts, "queries": nq, "per_instance_loop": {"value": nq / (l_ms / 1e3), "ms_per_step": l_ms},
-            "graph_replay": {"value": nq / (g_ms / 1e3), "ms_per_step": g_ms, "plan_workspace_gb": plan_gb},
+            "graph_replay": {"value": nq / (g_ms / 1e3), "ms_per_step": g_ms, "plan_workspace_gb": plan_gb,
+                             "autotuned_ms": tuned_ms},
             "workload": f"{len(probs)} instances, m in {{2,3}} 50/50, |D|=|Q| log-uniform [256, 2^18], "
                         "int32 coords U[0,2^31), f32 w, sum"}
 
@@ -373,8 +375,14 @@ def main():
                          torch)
         m3_ms = statistics.mean(t3)
         st3 = domagg.stats(local)
+        # one more call with the library's per-kind timing
+        domagg.domagg_timing_enable(h, True)
+        domagg.forward(D3, Q3, w3, "sum", out=o3)
+        k3 = domagg.domagg_timing_read(h)
+        domagg.domagg_timing_enable(h, False)
         line["m3"] = {"value": p3.Q.shape[0] / (m3_ms / 1e3), "unit": "queries/s", "ms_per_step": m3_ms,
-                      "workload": "m3_nD2^21_nQ2^21_gmm_i32coords_i64w_sum", "records": st3["n_records"]}
+                      "workload": "m3_nD2^21_nQ2^21_gmm_i32coords_i64w_sum", "records": st3["n_records"],
+                      "record_passes": st3["record_passes"], "phase_ms": {k: v["ms"] for k, v in k3.items()}}
         del D3, Q3, w3, o3
         line["variants"] = bench_variants(args, dev, stream, torch, domagg, workloads)
         line["batch"] = bench_batch(args, dev, stream, torch, domagg, workloads)

@@ -193,6 +193,13 @@ domagg_status domagg_batch_plan(domagg_plan* out, int device, int k, const domag
                                 domagg_dtype coord_dtype, domagg_dtype weight_dtype, domagg_op op,
                                 double headroom, void* stream);
 domagg_status domagg_plan_run(domagg_plan p, void* stream);
+/* Picks, per group of instances with the same m, the fastest of nine launch
+ * shapes (2, 4 or 8 radix-sort ranges per resident CTA x 8, 16 or 32
+ * flat-map / reduction blocks per SM) by timing planned runs on `stream`
+ * (each shape: one warm-up and two timed runs, writing the outputs); later
+ * runs use it.  Synchronises; not capturable.  *best_ms (may be NULL)
+ * receives the summed time of the chosen shapes. */
+domagg_status domagg_plan_autotune(domagg_plan p, void* stream, double* best_ms);
 domagg_status domagg_plan_status(domagg_plan p, void* stream);
 const char* domagg_plan_last_error(domagg_plan p);
 int64_t domagg_plan_workspace_bytes(domagg_plan p);
@@ -250,7 +257,7 @@ const char* domagg_timing_kind_name(int kind);
  *   all pointers are device memory on the CURRENT device, and no handle is
  *   used.
  *   Limits: nD + nQ <= 65536, and the flat map must fit the scratch (about
- *   10^6 records for m <= 2, half that for m = 3 or int64 weights); larger
+ *   10^6 records for m <= 2, about half that for m = 3); larger
  *   inputs return DOMAGG_ERR_UNSUPPORTED without running.
  *   The first call on a device sets that device's scratch up (looks its
  *   address up, clears the control block and the status words, and

@@ -290,13 +290,18 @@ __device__ __forceinline__ ff ff_add(ff x, ff y) {
 // aggregation operators F with unit e (Sec. 1)
 // ---------------------------------------------------------------------
 // Each operator defines: Acc (scan accumulator), Part (stored partial), Out
-// (output element), W (record payload type), e(), from_w(payload) for a data
-// record, F(a, b), to_part(acc), part_to_acc(p), to_out(acc).
+// (output element), Pay (32-bit record payload), W (a weight as stored in
+// the order of the last coordinate), e(), F(a, b), to_part, from_part,
+// to_out, and either from_pay (the payload is the weight's bits) or, with
+// GATHER, from_w (the payload is the position of the weight, read from the
+// L2-resident weight array: 8-byte weights do not ride through the sort).
 struct OpSumF32 {
     typedef ff Acc;
     typedef float Part;
     typedef float Out;
     typedef u32 Pay;
+    typedef u32 W;
+    static constexpr bool GATHER = false;
     __device__ static Acc e() { return {0.f, 0.f}; }
     __device__ static Acc from_pay(Pay p) { return {__uint_as_float(p), 0.f}; }
     __device__ static Acc F(Acc a, Acc b) { return ff_add(a, b); }
@@ -308,9 +313,11 @@ struct OpSumI64 {
     typedef long long Acc;
     typedef long long Part;
     typedef long long Out;
-    typedef u64 Pay;
+    typedef u32 Pay;  // a data record carries the position of its weight (GATHER)
+    typedef u64 W;
+    static constexpr bool GATHER = true;
     __device__ static Acc e() { return 0; }
-    __device__ static Acc from_pay(Pay p) { return (long long)p; }
+    __device__ static Acc from_w(W w) { return (long long)w; }
     __device__ static Acc F(Acc a, Acc b) { return (long long)((u64)a + (u64)b); }
     __device__ static Part to_part(Acc a) { return a; }
     __device__ static Acc from_part(Part p) { return p; }
@@ -321,6 +328,8 @@ struct OpMaxI32 {
     typedef int Part;
     typedef int Out;
     typedef u32 Pay;
+    typedef u32 W;
+    static constexpr bool GATHER = false;
     __device__ static Acc e() { return (int)0x80000000; }
     __device__ static Acc from_pay(Pay p) { return (int)p; }
     __device__ static Acc F(Acc a, Acc b) { return a > b ? a : b; }
@@ -333,6 +342,8 @@ struct OpMaxF32 {
     typedef float Part;
     typedef float Out;
     typedef u32 Pay;
+    typedef u32 W;
+    static constexpr bool GATHER = false;
     __device__ static Acc e() { return -__int_as_float(0x7f800000); }
     __device__ static Acc from_pay(Pay p) { return __uint_as_float(p); }
     __device__ static Acc F(Acc a, Acc b) { return fmaxf(a, b); }
@@ -345,6 +356,8 @@ struct OpMinI32 {
     typedef int Part;
     typedef int Out;
     typedef u32 Pay;
+    typedef u32 W;
+    static constexpr bool GATHER = false;
     __device__ static Acc e() { return 0x7fffffff; }
     __device__ static Acc from_pay(Pay p) { return (int)p; }
     __device__ static Acc F(Acc a, Acc b) { return a < b ? a : b; }
@@ -357,6 +370,8 @@ struct OpMinF32 {
     typedef float Part;
     typedef float Out;
     typedef u32 Pay;
+    typedef u32 W;
+    static constexpr bool GATHER = false;
     __device__ static Acc e() { return __int_as_float(0x7f800000); }
     __device__ static Acc from_pay(Pay p) { return __uint_as_float(p); }
     __device__ static Acc F(Acc a, Acc b) { return fminf(a, b); }  // a NaN weight never wins
@@ -369,6 +384,8 @@ struct OpCount {
     typedef u32 Part;
     typedef long long Out;
     typedef u32 Pay;
+    typedef u32 W;
+    static constexpr bool GATHER = false;
     __device__ static Acc e() { return 0u; }
     __device__ static Acc from_pay(Pay) { return 1u; }
     __device__ static Acc F(Acc a, Acc b) { return a + b; }

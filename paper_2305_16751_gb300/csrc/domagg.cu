@@ -71,6 +71,8 @@ struct domagg_ctx {
     size_t pool_used = 0;
     u64 epoch_mirror = 0;  // host copy of Ctl::epoch_base
     bool frozen = false;   // owned by a plan: its workspace must not grow any more
+    int sms = 152;         // multiprocessors of the device
+    int ranges_per_cta = 4, blocks_per_sm = 16;  // launch shapes (domagg_plan_autotune)
 
     size_t held() const { return pts.cap + recs.cap + st_multi.cap + st_seg.cap + stage.cap; }
 };
@@ -214,7 +216,8 @@ template <int M, class Op, bool F32>
 domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStream_t stream,
                   const std::vector<PlannedChunk>* planned = nullptr) {
     typedef typename std::conditional<M == 3, u64, u32>::type K;
-    typedef typename Op::Pay Pay;
+    typedef typename Op::Pay Pay;  // 32 bits: the weight's bits, a weight position (GATHER) or a slot
+    typedef typename Op::W W;      // a weight in the order of the last coordinate
     typedef typename Op::Part Part;
     constexpr int WT = OpTraits<Op>::WT;
     constexpr int SEG_ITEMS = (sizeof(K) + sizeof(Pay) == 8) ? DOMAGG_SEG_ITEMS_NARROW : 8;
@@ -267,7 +270,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         P[15] = c.take<u32>(k + 1);  // chunk offsets
         P[16] = c.take<u32>((size_t)NC * LMAX);  // query chunk bases per level
         P[17] = c.take<u32>((size_t)k * LMAX);   // query records per (instance, level)
-        P[18] = c.take<Pay>(WT == 3 ? 0 : N);  // weights in the order of the last coordinate
+        P[18] = c.take<W>(WT == 3 ? 0 : N);  // weights in the order of the last coordinate
         P[19] = c.take<u32>((size_t)k * 4 * RADIX);  // hist
         P[20] = c.take<u32>((size_t)k * 4 * RADIX);  // digit offsets
         P[21] = c.take<u32>(k + 1);                  // the sorts' tile map
@@ -331,6 +334,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     L.stream = stream;
     L.ctl = h->ctl;
     L.timing = h->timing && !planned;
+    L.ranges_per_cta = h->ranges_per_cta;
+    L.blocks_per_sm = h->blocks_per_sm;
     L.log = &h->log;
     L.pool = &h->pool;
     L.pool_used = &h->pool_used;
@@ -384,10 +389,10 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     // ---- count / offset scan of the flat map, per level
     {
         // perm, gathered ranks, ranks / index / weight written in order, weight gathered
-        L.start(KIND_COUNT_SCAN, (double)N * (4 + 8.0 * (M - 1) + 4 + (WT == 3 ? 0 : 2.0 * sizeof(Pay))) +
+        L.start(KIND_COUNT_SCAN, (double)N * (4 + 8.0 * (M - 1) + 4 + (WT == 3 ? 0 : 2.0 * sizeof(W))) +
                                      (double)NC * 8 * LMAX);
-        k_count_scan<M, Pay, WT><<<(unsigned)ntp, 256, 0, stream>>>(
-            perm, d_pt_offs, d_pt_tiles, k, d_chunk_off, r0, r1, d_inst, pr0, pr1, pj, (Pay*)P[18], chunk_base,
+        k_count_scan<M, W, WT><<<(unsigned)ntp, 256, 0, stream>>>(
+            perm, d_pt_offs, d_pt_tiles, k, d_chunk_off, r0, r1, d_inst, pr0, pr1, pj, (W*)P[18], chunk_base,
             qchunk_base, (u32*)P[25]);
         L.stop();
         L.start(KIND_SMALL, 0.0);
@@ -611,11 +616,11 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         // flat map (6m+1), level by level
         const u64 nchunk = chunk_off[C.k1] - chunk_off[C.k0];
         if (C.T > 0) {
-            const unsigned grid = (unsigned)std::min<u64>((nchunk + 7) / 8, 152ull * 16);
-            L.start(KIND_EXPAND, (double)(pt_offs[C.k1] - pt_offs[C.k0]) * (4.0 * (M - 1) + sizeof(Pay)) +
+            const unsigned grid = (unsigned)std::min<u64>((nchunk + 7) / 8, (u64)h->sms * L.blocks_per_sm);
+            L.start(KIND_EXPAND, (double)(pt_offs[C.k1] - pt_offs[C.k0]) * (4.0 * (M - 1) + (Op::GATHER ? 0 : sizeof(W))) +
                                      (double)C.T * (sizeof(K) + sizeof(Pay)));
-            k_expand<M, K, Pay, WT><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pj,
-                                                             (const Pay*)P[18],
+            k_expand<M, K, Pay, W, WT><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pj,
+                                                                (const W*)P[18],
                                                              chunk_base, qchunk_base, d_pt_tiles, (const u32*)P[25],
                                                              d_inst, d_sbase, d_qsbase,
                                                              (u32)C.T, keys[0], pays[0]);
@@ -635,16 +640,18 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         // segmented scan (6m+3)
         if (C.T > 0) {
             const int li = L.lookback_index();
-            L.start(KIND_SEGSCAN, (double)C.T * (sizeof(K) + sizeof(Pay)) + (double)C.Tq * sizeof(Part));
+            L.start(KIND_SEGSCAN, (double)C.T * (sizeof(K) + sizeof(Pay)) + (double)C.Tq * sizeof(Part) +
+                                      (Op::GATHER ? (double)(pt_offs[C.k1] - pt_offs[C.k0]) * sizeof(W) : 0.0));
             k_segscan<Op, K, SEG_THREADS, SEG_ITEMS><<<(unsigned)nts, SEG_THREADS, 0, stream>>>(
-                keys[0], keys[1], pays[0], pays[1], d_so, d_stiles, (int)nseg, d_sbits, partial, (u32)C.Tq,
+                keys[0], keys[1], pays[0], pays[1], d_so, d_stiles, (int)nseg, d_sbits, (const W*)P[18], partial,
+                (u32)C.Tq,
                 (SegStatus<typename Op::Acc>*)h->st_seg.p, h->ctl, li);
             L.stop();
         }
         // per-query reduction (replaces 6m+4 .. 6m+9)
         const u32 qb = q_offs[C.k0], qe = q_offs[C.k1];
         if (qe > qb) {
-            const unsigned grid = (unsigned)std::min<u64>((nchunk + 7) / 8, 152ull * 16);
+            const unsigned grid = (unsigned)std::min<u64>((nchunk + 7) / 8, (u64)h->sms * L.blocks_per_sm);
             L.start(KIND_REDUCE, (double)C.Tq * sizeof(Part) + (double)(qe - qb) * (8 + sizeof(typename Op::Out)));
             k_reduce<Op, M><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pj,
                                                       qchunk_base, d_pt_tiles, (const u32*)P[25], d_qsbase, d_inst,
@@ -714,8 +721,8 @@ domagg_status dispatch(domagg_ctx* h, int m, std::vector<Inst>& inst, domagg_dty
 // partial per (query) record and the status words, rounded up.
 size_t record_bytes(int m, domagg_dtype wt, domagg_op op) {
     const size_t kb = m == 3 ? 8 : 4;
-    const bool wide = op == DOMAGG_SUM && wt == DOMAGG_I64;
-    const size_t pb = wide ? 8 : 4;
+    const size_t pb = 4;  // every payload is 32 bits (8-byte weights are gathered by position)
+    (void)wt;
     const size_t part = (op == DOMAGG_MAX || op == DOMAGG_MIN || (op == DOMAGG_SUM && wt == DOMAGG_F32)) ? 4 : 8;
     return 2 * kb + 2 * pb + part + 8;
 }
@@ -773,6 +780,8 @@ domagg_status domagg_create(domagg_handle* out, int device, size_t max_workspace
     if (!h) return DOMAGG_ERR_OOM;
     h->device = device;
     h->max_ws = max_workspace_bytes;
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
+    if (h->sms <= 0) h->sms = 152;
     if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&h->ctl, sizeof(Ctl)) != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -1151,6 +1160,58 @@ domagg_status domagg_plan_status(domagg_plan p, void* stream) {
 }
 
 const char* domagg_plan_last_error(domagg_plan p) { return p ? p->err.c_str() : "null plan"; }
+
+domagg_status domagg_plan_autotune(domagg_plan p, void* stream, double* best_ms) {
+    if (!p) return DOMAGG_ERR_INVALID_ARG;
+    p->err.clear();
+    cudaSetDevice(p->device);
+    const cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return plan_fail(p, DOMAGG_ERR_CUDA, "cudaEventCreate");
+    }
+    static const int kRanges[3] = {2, 4, 8}, kBlocks[3] = {8, 16, 32};
+    double total = 0.0;
+    domagg_status st = DOMAGG_OK;
+    for (auto& g : p->groups) {
+        double best = 1e30;
+        int br = g.ctx->ranges_per_cta, bb = g.ctx->blocks_per_sm;
+        for (int ri = 0; ri < 3 && !st; ++ri) {
+            for (int bi = 0; bi < 3 && !st; ++bi) {
+                g.ctx->ranges_per_cta = kRanges[ri];
+                g.ctx->blocks_per_sm = kBlocks[bi];
+                st = plan_group_run(p, g, s);  // warm-up of this shape
+                double ms = 0.0;
+                for (int rep = 0; rep < 2 && !st; ++rep) {
+                    cudaEventRecord(e0, s);
+                    st = plan_group_run(p, g, s);
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) st = plan_fail(p, DOMAGG_ERR_CUDA, "autotune");
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    ms += t / 2.0;
+                }
+                if (!st && ms < best) {
+                    best = ms;
+                    br = kRanges[ri];
+                    bb = kBlocks[bi];
+                }
+            }
+        }
+        g.ctx->ranges_per_cta = br;
+        g.ctx->blocks_per_sm = bb;
+        if (!st) {
+            const domagg_status ss = domagg_sync_status(g.ctx, stream);
+            if (ss) st = plan_fail(p, ss, g.ctx->err);
+        }
+        total += best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms) *best_ms = total;
+    return st;
+}
 
 int64_t domagg_plan_workspace_bytes(domagg_plan p) {
     if (!p) return -1;

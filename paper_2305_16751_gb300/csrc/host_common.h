@@ -49,6 +49,8 @@ struct Launcher {
     cudaEvent_t pending_a = nullptr;
     int launches = 0;  // kernels launched (all kinds)
     bool frozen = false;  // a planned run: no allocation, no attribute changes (may be under stream capture)
+    int ranges_per_cta = 4;   // sort: ranges per resident CTA (tunable)
+    int blocks_per_sm = 16;   // flat map and reduction: grid-stride blocks per SM (tunable)
 
     // Index of the next look-back launch (its tile counter and epoch).  A run
     // restarts the count at every k_begin; the clamp keeps a miscount from

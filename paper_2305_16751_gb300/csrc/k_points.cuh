@@ -340,11 +340,11 @@ constexpr int CS_ROUNDS = 16;
 constexpr int CS_COUNTERS = 2 * LMAX;             // per tile: records and query records of every level
 constexpr u32 CS_CHUNKS = 8 * CS_ROUNDS;          // 32-point chunks per tile
 constexpr u32 QUERY_BIT = 0x80000000u;  // in pr0: the point is a query (ranks are below 2^31)
-template <int M, typename Pay, int WT>
+template <int M, typename W, int WT>
 __global__ __launch_bounds__(256) void k_count_scan(
     const u32* __restrict__ perm, const u32* __restrict__ seg_off, const u32* __restrict__ tile_off, int nseg,
     const u32* __restrict__ chunk_off, const u32* __restrict__ r0, const u32* __restrict__ r1, Inst* inst,
-    u32* __restrict__ pr0, u32* __restrict__ pr1, u32* __restrict__ pj, Pay* __restrict__ pw,
+    u32* __restrict__ pr0, u32* __restrict__ pr1, u32* __restrict__ pj, W* __restrict__ pw,
     u32* __restrict__ chunk_base, u32* __restrict__ qchunk_base, u32* __restrict__ tile_cnt) {
     constexpr int WARPS = 8, C = 2 * LMAX, TILE = WARPS * CS_ROUNDS * 32;
     static_assert(TILE == 4096, "point tiles");
@@ -384,8 +384,8 @@ __global__ __launch_bounds__(256) void k_count_scan(
             pj[x] = j;
             if (WT != 3 && !q) {
                 const u32 local = j - L.seg_begin;
-                if (WT == 1) pw[x] = (Pay)reinterpret_cast<const long long*>(I.dw)[local - nQ];
-                else pw[x] = (Pay)reinterpret_cast<const u32*>(I.dw)[local - nQ];
+                if (WT == 1) pw[x] = (W)reinterpret_cast<const long long*>(I.dw)[local - nQ];
+                else pw[x] = (W)reinterpret_cast<const u32*>(I.dw)[local - nQ];
             }
         }
         u32 mine = 0, mine_q = 0;
@@ -469,11 +469,11 @@ static __global__ __launch_bounds__(256) void k_tile_exscan_counters(const u32* 
 // Payload: data -> the weight's bits (Op::Pay), query -> its partial slot,
 // a dense per-level position (query slot base of the level + the chunk's
 // query count of the level + the lanes before).
-template <int M, typename K, typename Pay, int WT>
+template <int M, typename K, typename Pay, typename W, int WT>
 __global__ __launch_bounds__(256) void k_expand(
     const u32* __restrict__ chunk_off, int k, int k0, int k1, const u32* __restrict__ pt_offs,
     const u32* __restrict__ pr0, const u32* __restrict__ pr1, const u32* __restrict__ pj,
-    const Pay* __restrict__ pw, const u32* __restrict__ chunk_base, const u32* __restrict__ qchunk_base,
+    const W* __restrict__ pw, const u32* __restrict__ chunk_base, const u32* __restrict__ qchunk_base,
     const u32* __restrict__ pt_tiles, const u32* __restrict__ tile_excl,
     const Inst* __restrict__ inst, const u32* __restrict__ seg_base /*[k1-k0][LMAX]*/,
     const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/, u32 n_rec, K* __restrict__ kout, Pay* __restrict__ pout) {
@@ -520,7 +520,8 @@ __global__ __launch_bounds__(256) void k_expand(
                 bits1 = (q ? cc : ~cc) & low_mask(b1);
                 c1 = (u32)__popc(bits1);
             }
-            if (!q && WT != 3) w = pw[p];
+            // 8-byte weights stay in pw: the record carries their position
+            if (!q && WT != 3) w = WT == 1 ? (Pay)p : (Pay)pw[p];
         }
         if (M >= 3 && c1 == 0) bits0 = 0;  // no records at all
         const u32 live = __ballot_sync(0xffffffffu, bits0 != 0u);

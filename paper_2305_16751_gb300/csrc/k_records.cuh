@@ -174,6 +174,7 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys0
                                                      const u32* __restrict__ seg_off,
                                                      const u32* __restrict__ tile_off, int nseg,
                                                      const u32* __restrict__ seg_bits,
+                                                     const typename Op::W* __restrict__ wgt,
                                                      typename Op::Part* __restrict__ partial, u32 n_partial,
                                                      SegStatus<typename Op::Acc>* status, Ctl* ctl, int launch_idx) {
     typedef typename Op::Acc Acc;
@@ -237,7 +238,9 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys0
                 qmask |= 1u << i;
                 loc[i] = agg;
             } else {
-                agg = Op::F(agg, Op::from_pay(s_pays[pidx(lx0 + i)]));
+                const Pay py = s_pays[pidx(lx0 + i)];
+                if constexpr (Op::GATHER) agg = Op::F(agg, Op::from_w(__ldg(wgt + py)));
+                else agg = Op::F(agg, Op::from_pay(py));
             }
         }
     }

@@ -56,7 +56,8 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
         cudaFuncSetAttribute(k_onesweep<K, V, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(k_radix_hist<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, hist_smem_max);
     }
-    // ranges: about four per resident CTA, whole tiles, never across segments.
+    // ranges: about L.ranges_per_cta (4) per resident CTA, whole tiles, never
+    // across segments.
     // With seg_bits, every pass ranges only the segments it moves (a segment
     // whose keys have no digit left stays in place), so later passes, which
     // move fewer segments, still spread over every CTA.
@@ -71,7 +72,8 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
     };
     auto plan_ranges = [&](int p, u32& range_items, u64& nranges) {
         const u64 nt = tiles_moved(p, TILE);
-        const u64 rt = std::max<u64>(1, (nt + 4 * G - 1) / (4 * G));
+        const u64 R = (u64)std::max(1, L.ranges_per_cta) * G;
+        const u64 rt = std::max<u64>(1, (nt + R - 1) / R);
         range_items = (u32)std::min<u64>(rt * TILE, 1ull << 30);
         nranges = nt == 0 ? 0 : tiles_moved(p, range_items);
     };
@@ -141,10 +143,6 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
 template int sort_pairs<u32, u32>(Launcher&, const SortSpace&, u32**, u32**, bool, int, u32, int, int,
                                      const u32*, bool);
 template int sort_pairs<u64, u32>(Launcher&, const SortSpace&, u64**, u32**, bool, int, u64, int, int,
-                                     const u32*, bool);
-template int sort_pairs<u32, u64>(Launcher&, const SortSpace&, u32**, u64**, bool, int, u32, int, int,
-                                     const u32*, bool);
-template int sort_pairs<u64, u64>(Launcher&, const SortSpace&, u64**, u64**, bool, int, u64, int, int,
                                      const u32*, bool);
 
 }  // namespace domagg

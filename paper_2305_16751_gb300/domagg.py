@@ -63,6 +63,7 @@ SIGNATURES = {
                            ctypes.c_double, _vp], _int),
     "domagg_plan_run": ([_vp, _vp], _int),
     "domagg_plan_status": ([_vp, _vp], _int),
+    "domagg_plan_autotune": ([_vp, _vp, ctypes.POINTER(ctypes.c_double)], _int),
     "domagg_plan_last_error": ([_vp], ctypes.c_char_p),
     "domagg_plan_workspace_bytes": ([_vp], _i64),
     "domagg_plan_destroy": ([_vp], _int),
@@ -162,6 +163,12 @@ def domagg_plan_run(p, stream):
 
 def domagg_plan_status(p, stream):
     _check_plan(p, lib().domagg_plan_status(p, stream))
+
+
+def domagg_plan_autotune(p, stream) -> float:
+    ms = ctypes.c_double()
+    _check_plan(p, lib().domagg_plan_autotune(p, stream, ctypes.byref(ms)))
+    return ms.value
 
 
 def domagg_plan_workspace_bytes(p) -> int:
@@ -405,6 +412,11 @@ class BatchPlan:
         """Synchronises and raises DomaggError for a device-side error of the
         runs so far (e.g. more records than reserved)."""
         domagg_plan_status(self._p, _stream(self.device))
+
+    def autotune(self) -> float:
+        """Chooses the fastest launch shapes by timing runs (synchronises);
+        returns the chosen shapes' time in ms."""
+        return domagg_plan_autotune(self._p, _stream(self.device))
 
     def workspace_bytes(self) -> int:
         return domagg_plan_workspace_bytes(self._p)

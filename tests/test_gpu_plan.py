@@ -134,3 +134,22 @@ def test_plan_batch_workload_shape():
             assert_matches_oracle(o.cpu().numpy(), p.D, p.Q, p.w, "sum")
     finally:
         plan.close()
+
+
+def test_plan_autotune_keeps_results():
+    """The autotuner times nine launch shapes and keeps the fastest; runs
+    after it give the same (integer) results as the unplanned batch."""
+    rng = np.random.default_rng(904)
+    probs, _ = _problems(rng, 20, "i64")
+    dev = [(to_dev(D), to_dev(Q), to_dev(w)) for D, Q, w in probs]
+    want = domagg.batch(dev, "sum")
+    plan = domagg.BatchPlan(dev, "sum", headroom=0.2)
+    try:
+        ms = plan.autotune()
+        assert ms > 0
+        plan.run()
+        plan.status()
+        for o, wv in zip(plan.outs, want):
+            assert torch().equal(o, wv)
+    finally:
+        plan.close()
