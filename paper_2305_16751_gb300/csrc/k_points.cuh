@@ -552,24 +552,33 @@ __global__ __launch_bounds__(256) void k_expand(
                 ex = inc - wv;
                 exq = incq - wq;
             }
-            if (!has) continue;
             const u32 pos = base_all + ex;
             const Pay pay = q ? (Pay)(base_q + exq) : w;
             const K kv = M == 1 ? K(0) : (K)(a >> (lv + 1));
             if (M <= 2) {
-                if (pos < n_rec) {
+                if (has && pos < n_rec) {
                     kout[pos] = q ? (kv | role) : kv;
                     pout[pos] = pay;
                 }
             } else {
-                u32 rem = bits1;
-                for (u32 kk = 0; rem; ++kk) {
-                    const u32 j1 = __ffs(rem) - 1;
-                    rem &= rem - 1;
-                    const K key = (kv << b1) | (K)node_of(cc, j1);
-                    if (pos + kk < n_rec) {
-                        kout[pos + kk] = q ? (key | role) : key;
-                        pout[pos + kk] = q ? (Pay)(pay + kk) : pay;
+                // the warp writes one point's records at a time, lane j taking
+                // the record of the second rank's digit j (its rank among the
+                // point's digits is its place): contiguous, coalesced stores
+                for (u32 act = hb; act; act &= act - 1) {
+                    const int src = __ffs(act) - 1;
+                    const u32 sb = __shfl_sync(0xffffffffu, bits1, src);
+                    const u32 scc = __shfl_sync(0xffffffffu, cc, src);
+                    const K skv = __shfl_sync(0xffffffffu, kv, src);
+                    const u32 spos = __shfl_sync(0xffffffffu, pos, src);
+                    const Pay spay = __shfl_sync(0xffffffffu, pay, src);
+                    const bool sq = (qb >> src) & 1u;
+                    if ((sb >> lane) & 1u) {
+                        const u32 r = (u32)__popc(sb & lt);
+                        const K key = (skv << b1) | (K)node_of(scc, (u32)lane);
+                        if (spos + r < n_rec) {
+                            kout[spos + r] = sq ? (key | role) : key;
+                            pout[spos + r] = sq ? (Pay)(spay + r) : spay;
+                        }
                     }
                 }
             }
