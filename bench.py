@@ -43,7 +43,9 @@ def parse():
     ap.add_argument("--n3", type=int, default=2**21, help="|D| = |Q| of the m=3 workload")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the baseline sample")
     ap.add_argument("--no-extras", action="store_true", help="skip fwd_bwd, m3, batch, e2e and the CPU baseline")
-    ap.add_argument("--batch-k", type=int, default=512, help="instances of the batch workload")
+    ap.add_argument("--batch-k", type=int, default=4096, help="instances of the batch workload")
+    ap.add_argument("--only-batch", action="store_true", help="print the batch line alone (e.g. --batch-k 4096)")
+    ap.add_argument("--no-autotune", action="store_true", help="planned batch without the launch-shape autotuner")
     return ap.parse_args()
 
 
@@ -200,7 +202,7 @@ def bench_batch(args, dev, stream, torch, domagg, workloads):
     l_ms = statistics.mean(tl)
     # the planned batch captured once in a CUDA graph, then replayed
     plan = domagg.BatchPlan(inst, "sum", headroom=0.05)
-    tuned_ms = plan.autotune()
+    tuned_ms = None if args.no_autotune else plan.autotune()
     side = torch.cuda.Stream(dev)
     side.wait_stream(torch.cuda.current_stream(dev))
     graph = torch.cuda.CUDAGraph()
@@ -288,6 +290,14 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.only_batch:
+        import torch
+        from paper_2305_16751_gb300 import domagg, workloads
+        dev = torch.device("cuda", local)
+        torch.cuda.set_device(dev)
+        line = bench_batch(args, dev, torch.cuda.current_stream(dev), torch, domagg, workloads)
+        print(json.dumps({"batch": line}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         if world > 1:
