@@ -136,3 +136,18 @@ def test_batch_split_into_record_chunks():
             assert np.array_equal(o.cpu().numpy(), gpu_forward(D, Q, w, "sum"))
     finally:
         domagg.domagg_destroy(h)
+
+
+def test_batch_full_recipe_sampled():
+    """The full batch workload (4096 instances, 3.0e8 points) in one
+    domagg_batch call, as the bench times it; 24 sampled instances, 32
+    sampled queries each, against the oracle."""
+    probs = workloads.batch_instances()
+    dev = [(to_dev(p.D), to_dev(p.Q), to_dev(p.w)) for p in probs]
+    outs = domagg.batch(dev, "sum")
+    torch().cuda.synchronize()
+    rng = np.random.default_rng(11)
+    for i in np.sort(rng.choice(len(probs), 24, replace=False)):
+        p = probs[i]
+        qi = np.sort(rng.choice(p.Q.shape[0], 32, replace=False))
+        assert_matches_oracle(outs[i].cpu().numpy(), p.D, p.Q, p.w, "sum", qidx=qi)
