@@ -205,6 +205,15 @@ const char* domagg_plan_last_error(domagg_plan p);
 int64_t domagg_plan_workspace_bytes(domagg_plan p);
 domagg_status domagg_plan_destroy(domagg_plan p);
 
+/* Self-test of the device-side wait limits (the paper has no counterpart):
+ * runs one thread that waits on something that never happens -- which = 0:
+ * a decoupled look-back on a predecessor status nothing publishes; which =
+ * 1: an mbarrier phase whose bytes are never sent -- and returns what
+ * domagg_sync_status then reports: DOMAGG_ERR_TIMEOUT when the wait gave up
+ * as designed (after about a second), with the handle still usable.
+ * Synchronises `stream`. */
+domagg_status domagg_selftest_timeout(domagg_handle h, int which, void* stream);
+
 /* Synchronises `stream` and returns the first device-side error recorded by
  * this handle's kernels since the last check (DOMAGG_ERR_TIMEOUT,
  * DOMAGG_ERR_NAN), or DOMAGG_OK; clears it. */

@@ -252,12 +252,28 @@ __device__ __forceinline__ bool mbar_try_wait(u64* bar, u32 parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for phase `parity` of an mbarrier.  Returns false (and records
-// ERR_TIMEOUT) if it did not complete within the limit.
+__device__ __forceinline__ u64 globaltimer_ns() {
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for phase `parity` of an mbarrier: at most MBAR_WAIT_NS of
+// wall time (checked every 1024 polls) and MBAR_SPIN_LIMIT polls, and it
+// gives up at once when another wait of the pipeline already ran out.
+// Returns false (and records ERR_TIMEOUT) if the phase did not complete.
 constexpr u32 MBAR_SPIN_LIMIT = 1u << 22;
+constexpr u64 MBAR_WAIT_NS = 1000000000ull;
 __device__ __forceinline__ bool mbar_wait_bounded(u64* bar, u32 parity, Ctl* ctl, u32 where) {
-    for (u32 i = 0; i < MBAR_SPIN_LIMIT; ++i)
+    u64 t0 = 0;
+    for (u32 i = 0; i < MBAR_SPIN_LIMIT; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 1023u) == 1023u) {
+            const u64 now = globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > MBAR_WAIT_NS) break;
+            if (timed_out(ctl)) break;
+        }
+    }
     atomicOr(&ctl->error, ERR_TIMEOUT);
     ctl->timeout_where = where;
     return false;

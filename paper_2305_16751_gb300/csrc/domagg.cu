@@ -1226,6 +1226,21 @@ domagg_status domagg_plan_destroy(domagg_plan p) {
     return DOMAGG_OK;
 }
 
+domagg_status domagg_selftest_timeout(domagg_handle h, int which, void* stream) {
+    if (!h || (which != 0 && which != 1)) return DOMAGG_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    const cudaStream_t s = (cudaStream_t)stream;
+    domagg_status st = grow(h, h->st_multi, 4096, true);  // a zeroed status word to wait on
+    if (st) return st;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "selftest");
+    cudaMemsetAsync(&h->ctl->error, 0, sizeof(u32), s);
+    k_selftest_wait<<<1, 32, 0, s>>>(which, (const u64*)h->st_multi.p, h->ctl);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "selftest launch");
+    return domagg_sync_status(h, stream);
+}
+
 domagg_status domagg_sync_status(domagg_handle h, void* stream) {
     if (!h) return DOMAGG_ERR_INVALID_ARG;
     cudaSetDevice(h->device);

@@ -31,6 +31,25 @@ static __global__ void k_epoch_restart(Ctl* ctl, u32 margin) {
     if (threadIdx.x == 0 && ctl->epoch_base > EPOCH_MASK - margin) ctl->epoch_base = 0;
 }
 
+// Self-test of the wait limits: one thread waits on something that never
+// happens -- which = 0: a look-back on a predecessor status that nothing
+// publishes (epoch EPOCH_MASK, which no pipeline run uses); which = 1: an
+// mbarrier phase whose expected bytes are never sent (no copy is issued, so
+// nothing is in flight when the kernel returns).  Both give up, record
+// ERR_TIMEOUT and return.
+static __global__ void k_selftest_wait(int which, const u64* status, Ctl* ctl) {
+    __shared__ u64 bar;
+    if (threadIdx.x != 0) return;
+    if (which == 0) {
+        (void)lookback_u32(status, 1, 0, 1u, 0u, EPOCH_MASK, ctl, 7u);
+    } else {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(&bar, 16u);
+        (void)mbar_wait_bounded(&bar, 0u, ctl, 8u);
+    }
+}
+
 // Tiles of size `tile` over segments: tile_off[s] = sum over s' < s of
 // ceil(len(s') / tile), tile_off[nseg] = total.  One block.
 // With seg_bits, segments whose keys have at most `skip_upto` bits get no

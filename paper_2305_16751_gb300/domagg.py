@@ -68,6 +68,7 @@ SIGNATURES = {
     "domagg_plan_workspace_bytes": ([_vp], _i64),
     "domagg_plan_destroy": ([_vp], _int),
     "domagg_sync_status": ([_vp, _vp], _int),
+    "domagg_selftest_timeout": ([_vp, _int, _vp], _int),
     "domagg_last_error": ([_vp], ctypes.c_char_p),
     "domagg_get_stats": ([_vp, ctypes.POINTER(domagg_stats)], _int),
     "domagg_timing_enable": ([_vp, _int], _int),
