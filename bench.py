@@ -136,22 +136,22 @@ def profiled_traffic(bytes_per_launch: float):
 
 def cpu_baseline(p, seconds: float):
     """The oracle as it stands (brute force by the definition, OpenMP over
-    queries) on a bounded sample of the workload's queries against all data."""
+    queries) on a bounded sample of the workload's queries against all data:
+    a small probe, then one run sized to take about `seconds`."""
     import numpy as np
 
     import oracle
     threads = os.cpu_count() or 1
-    k = 8
     rng = np.random.default_rng(0)
-    spent = 0.0
-    while True:
-        qi = rng.choice(p.Q.shape[0], size=k, replace=False)
-        t0 = time.perf_counter()
-        oracle.brute(p.D, p.Q[qi], p.w, p.op, threads=threads)
-        spent = time.perf_counter() - t0
-        if spent >= seconds / 4 or k >= p.Q.shape[0]:
-            break
-        k = min(p.Q.shape[0], int(k * max(2.0, min(16.0, seconds / 4 / max(spent, 1e-3)))))
+    k = min(p.Q.shape[0], 64)
+    t0 = time.perf_counter()
+    oracle.brute(p.D, p.Q[rng.choice(p.Q.shape[0], size=k, replace=False)], p.w, p.op, threads=threads)
+    probe = max(time.perf_counter() - t0, 1e-3)
+    k = int(min(p.Q.shape[0], max(k, k * seconds / probe)))
+    qi = rng.choice(p.Q.shape[0], size=k, replace=False)
+    t0 = time.perf_counter()
+    oracle.brute(p.D, p.Q[qi], p.w, p.op, threads=threads)
+    spent = time.perf_counter() - t0
     return {"value": k / spent, "unit": "queries/s", "cores": threads, "kind": "oracle",
             "sample": f"{k} random queries of the workload, each against all {p.D.shape[0]} data points "
                       f"(brute force, {spent:.1f} s)", "seconds": spent}
