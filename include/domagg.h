@@ -40,7 +40,10 @@
  *     and the per-query reduction; the result is within 2^-23 * sum |w(d)|
  *     over the dominated set of the exact sum.  float32 weights must be
  *     finite for SUM.
- *   - m is 1, 2 or 3 (m = 1 is ordinary prefix aggregation, Sec. 1.1).
+ *   - m is 1 to 4 (m = 1 is ordinary prefix aggregation, Sec. 1.1).  For
+ *     m = 4 the node key (b_1 - 1 + b_2 + b_3 bits) must fit 63 bits, so
+ *     the first three coordinates may have at most about 2^21 distinct
+ *     values each (DOMAGG_ERR_UNSUPPORTED otherwise).
  *     nD + nQ must be below 2^31 per problem, and the number of flat-map
  *     records below 2^32 per call (DOMAGG_ERR_UNSUPPORTED otherwise).
  *   - Errors are returned, never raised or aborted on.  Errors found on the
@@ -63,7 +66,7 @@ extern "C" {
 typedef enum {
     DOMAGG_OK = 0,
     DOMAGG_ERR_INVALID_ARG = 1, /* bad pointer, size, dtype, op or m */
-    DOMAGG_ERR_UNSUPPORTED = 2, /* m > 3, more than 2^31 points, 2^32 records */
+    DOMAGG_ERR_UNSUPPORTED = 2, /* m > 4, more than 2^31 points, 2^32 records */
     DOMAGG_ERR_OOM = 3,         /* workspace could not be allocated / over the cap */
     DOMAGG_ERR_CUDA = 4,        /* a CUDA runtime call failed (see domagg_last_error) */
     DOMAGG_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
@@ -108,7 +111,7 @@ domagg_status domagg_forward(domagg_handle h, int m, const void* d_coords, int64
  *                   DOMAGG_BASIC: the unimproved algorithm of Sec. 4: every
  *                   one of the m coordinates becomes a bitstring, records are
  *                   keyed by m node ids (n log^m n of them, data before
- *                   queries within a node tuple); m <= 2.  Same results,
+ *                   queries within a node tuple); m <= 3.  Same results,
  *                   more records: a cross-check of Lemma 2 at scale.
  * Other arguments, layouts and errors as domagg_forward. */
 typedef enum { DOMAGG_IMPROVED = 0, DOMAGG_BASIC = 1 } domagg_variant;
@@ -229,8 +232,8 @@ typedef struct {
     int64_t n_records;     /* T: records of the flat map */
     int64_t n_query_records; /* records that came from queries */
     int32_t m;
-    int32_t rank_bits[2];  /* b_i = ceil(log2 U_i) for the first m-1 dimensions */
-    int64_t distinct[2];   /* U_i */
+    int32_t rank_bits[3];  /* b_i = ceil(log2 U_i) for the first m-1 dimensions */
+    int64_t distinct[3];   /* U_i */
     int32_t record_key_bits; /* bits of the node key sorted by the record sort */
     int32_t record_passes;   /* radix passes over the records */
     int64_t workspace_bytes; /* device workspace currently held by the handle */

@@ -48,8 +48,8 @@ struct Inst {
     u32 pt_off;        // first point in the concatenated point space
     u32 q_off;         // first query in the concatenated query space
     // device-computed
-    u32 U[2];          // distinct values of the first m-1 coordinates
-    u32 b[2];          // binary digits of the ranks: ceil(log2 U)
+    u32 U[3];          // distinct values of the first m-1 coordinates
+    u32 b[3];          // binary digits of the ranks: ceil(log2 U)
     u32 rec_off, T;    // records of this instance
     u32 qrec_off, Tq;  // query records (partial slots) of this instance
     u32 key_bits;      // bits of the node key

@@ -215,7 +215,7 @@ struct PlannedChunk {
 template <int M, class Op, bool F32>
 domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStream_t stream,
                   const std::vector<PlannedChunk>* planned = nullptr) {
-    typedef typename std::conditional<M == 3, u64, u32>::type K;
+    typedef typename std::conditional<M >= 3, u64, u32>::type K;
     typedef typename Op::Pay Pay;  // 32 bits: the weight's bits, a weight position (GATHER) or a slot
     typedef typename Op::W W;      // a weight in the order of the last coordinate
     typedef typename Op::Part Part;
@@ -235,7 +235,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         chunk_off[s] = (u32)NC;
         inst[s].pt_off = (u32)N;
         inst[s].q_off = (u32)NQ;
-        inst[s].U[0] = inst[s].U[1] = inst[s].b[0] = inst[s].b[1] = 0;
+        for (int i = 0; i < 3; ++i) inst[s].U[i] = inst[s].b[i] = 0;
         inst[s].T = inst[s].Tq = inst[s].rec_off = inst[s].qrec_off = inst[s].key_bits = 0;
         const u64 n = (u64)inst[s].nD + inst[s].nQ;
         pt_sizes[s] = n;
@@ -278,8 +278,11 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         P[23] = c.take<u32>((size_t)k * LMAX);       // records per (instance, level)
         P[24] = c.take<u32>((size_t)sort_range_bound(pt_sizes) * RADIX);  // first-pass range bases
         P[25] = c.take<u32>((size_t)ntp * CS_COUNTERS);                   // per point tile: rank / flat-map counts
+        P[26] = c.take<u32>(M >= 4 ? N : 0);  // rk2
+        P[27] = c.take<u32>(M >= 4 ? N : 0);  // r2
+        P[28] = c.take<u32>(M >= 4 ? N : 0);  // pr2
     };
-    void* P[26];
+    void* P[29];
     {
         Carver c(nullptr);
         carve_points(c, P);
@@ -293,6 +296,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     u32 *rk0 = (u32*)P[4], *rk1 = (u32*)P[5], *lk = (u32*)P[6], *kalt = (u32*)P[7];
     u32 *vA = (u32*)P[8], *vB = (u32*)P[9], *r0 = (u32*)P[10], *r1 = (u32*)P[11];
     u32 *pr0 = (u32*)P[12], *pr1 = (u32*)P[13], *pj = (u32*)P[14], *d_chunk_off = (u32*)P[15];
+    u32 *rk2 = (u32*)P[26], *r2 = (u32*)P[27], *pr2 = (u32*)P[28];
     u32 *qchunk_base = (u32*)P[16], *qlvl_tot = (u32*)P[17];
     u32 *hist = (u32*)P[19], *digit_off = (u32*)P[20];
     u32* d_sort_tiles = (u32*)P[21];
@@ -350,7 +354,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
 
     // ---- keys (instruction 0 and 5i-4)
     L.start(KIND_ENCODE, (double)N * M * 4 * 2);
-    k_encode<M, F32><<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(d_inst, d_pt_offs, k, (u32)N, rk0, rk1, lk,
+    k_encode<M, F32><<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(d_inst, d_pt_offs, k, (u32)N, rk0, rk1, rk2, lk,
                                                                       negate ? 1 : 0, h->ctl);
     L.stop();
 
@@ -359,7 +363,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
 
     // ---- ranks of the first m-1 coordinates (5i-3 .. 5i, 5m+i)
     for (int i = 0; i < M - 1; ++i) {
-        u32* keys[2] = {i == 0 ? rk0 : rk1, kalt};
+        u32* keys[2] = {i == 0 ? rk0 : (i == 1 ? rk1 : rk2), kalt};
         u32* vals[2] = {vA, vB};
         // only the sorted key sequence matters for dense ranks: any order of equal digits
         const int cur = sort_pairs<u32, u32>(L, sp, keys, vals, true, 32, 0xffffffffu, KIND_HIST_POINTS,
@@ -374,7 +378,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         L.stop();
         L.start(KIND_RANK, (double)N * 12);
         k_rank_apply<SCAN_THREADS, SCAN_ITEMS><<<(unsigned)ntp, SCAN_THREADS, 0, stream>>>(
-            keys[cur], vals[cur], d_pt_offs, d_pt_tiles, k, tile_cnt, i == 0 ? r0 : r1, d_inst, i);
+            keys[cur], vals[cur], d_pt_offs, d_pt_tiles, k, tile_cnt, i == 0 ? r0 : (i == 1 ? r1 : r2), d_inst, i);
         L.stop();
     }
     // ---- order of the last coordinate, queries first on ties (Sec. 5)
@@ -392,7 +396,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         L.start(KIND_COUNT_SCAN, (double)N * (4 + 8.0 * (M - 1) + 4 + (WT == 3 ? 0 : 2.0 * sizeof(W))) +
                                      (double)NC * 8 * LMAX);
         k_count_scan<M, W, WT><<<(unsigned)ntp, 256, 0, stream>>>(
-            perm, d_pt_offs, d_pt_tiles, k, d_chunk_off, r0, r1, d_inst, pr0, pr1, pj, (W*)P[18], chunk_base,
+            perm, d_pt_offs, d_pt_tiles, k, d_chunk_off, r0, r1, r2, d_inst, pr0, pr1, pr2, pj, (W*)P[18], chunk_base,
             qchunk_base, (u32*)P[25]);
         L.stop();
         L.start(KIND_SMALL, 0.0);
@@ -412,7 +416,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     auto level_bits = [&](int s, u32 lv) -> u32 {
         if (M == 1) return 0u;
         const u32 b = inst[s].b[0] - 1u - lv;  // prefix length of level lv
-        return M == 2 ? b : b + inst[s].b[1];
+        return b + (M >= 3 ? inst[s].b[1] : 0u) + (M >= 4 ? inst[s].b[2] : 0u);
     };
     // pinned upload area of every chunk: per instance record and slot bases,
     // per segment offsets and key bits, per (instance, level) segment bases
@@ -456,6 +460,9 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             Tq += qlvl[(size_t)s * LMAX + lv];
         }
         if (T >= (1ull << 32)) return fail(h, DOMAGG_ERR_UNSUPPORTED, "more than 2^32 flat-map records");
+        // the node key (and the role bit above it) must fit 64 bits
+        if (M >= 4 && nlev[s] > 0 && inst[s].b[0] - 1u + inst[s].b[1] + inst[s].b[2] > 63u)
+            return fail(h, DOMAGG_ERR_UNSUPPORTED, "node keys of more than 63 bits (m = 4, too many distinct values)");
         inst[s].T = (u32)T;
         inst[s].Tq = (u32)Tq;
     }
@@ -619,8 +626,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             const unsigned grid = (unsigned)std::min<u64>((nchunk + 7) / 8, (u64)h->sms * L.blocks_per_sm);
             L.start(KIND_EXPAND, (double)(pt_offs[C.k1] - pt_offs[C.k0]) * (4.0 * (M - 1) + (Op::GATHER ? 0 : sizeof(W))) +
                                      (double)C.T * (sizeof(K) + sizeof(Pay)));
-            k_expand<M, K, Pay, W, WT><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pj,
-                                                                (const W*)P[18],
+            k_expand<M, K, Pay, W, WT><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pr2,
+                                                                pj, (const W*)P[18],
                                                              chunk_base, qchunk_base, d_pt_tiles, (const u32*)P[25],
                                                              d_inst, d_sbase, d_qsbase,
                                                              (u32)C.T, keys[0], pays[0]);
@@ -653,7 +660,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         if (qe > qb) {
             const unsigned grid = (unsigned)std::min<u64>((nchunk + 7) / 8, (u64)h->sms * L.blocks_per_sm);
             L.start(KIND_REDUCE, (double)C.Tq * sizeof(Part) + (double)(qe - qb) * (8 + sizeof(typename Op::Out)));
-            k_reduce<Op, M><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pj,
+            k_reduce<Op, M><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pr2, pj,
                                                       qchunk_base, d_pt_tiles, (const u32*)P[25], d_qsbase, d_inst,
                                                       partial, (u32)C.Tq);
             L.stop();
@@ -677,7 +684,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     S.n_records = (int64_t)T_all;
     S.n_query_records = (int64_t)Tq_all;
     S.m = M;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 3; ++i) {
         S.rank_bits[i] = (k == 1 && i < M - 1) ? (int32_t)inst[0].b[i] : 0;
         S.distinct[i] = (k == 1 && i < M - 1) ? (int64_t)inst[0].U[i] : 0;
     }
@@ -701,7 +708,8 @@ domagg_status run_m(domagg_ctx* h, int m, std::vector<Inst>& inst, domagg_dtype 
     switch (m) {
         case 1: return run_ct<1, Op>(h, inst, ct, negate, s, pl);
         case 2: return run_ct<2, Op>(h, inst, ct, negate, s, pl);
-        default: return run_ct<3, Op>(h, inst, ct, negate, s, pl);
+        case 3: return run_ct<3, Op>(h, inst, ct, negate, s, pl);
+        default: return run_ct<4, Op>(h, inst, ct, negate, s, pl);
     }
 }
 
@@ -732,7 +740,7 @@ domagg_status check_common(domagg_ctx* h, int m, int64_t nD, int64_t nQ, domagg_
     if (!h) return DOMAGG_ERR_INVALID_ARG;
     h->err.clear();
     if (m < 1) return fail(h, DOMAGG_ERR_INVALID_ARG, "m must be >= 1");
-    if (m > 3) return fail(h, DOMAGG_ERR_UNSUPPORTED, "m > 3 is not supported");
+    if (m > 4) return fail(h, DOMAGG_ERR_UNSUPPORTED, "m > 4 is not supported");
     if (nD < 0 || nQ < 0) return fail(h, DOMAGG_ERR_INVALID_ARG, "negative size");
     if (nD + nQ >= (int64_t)1 << 31) return fail(h, DOMAGG_ERR_UNSUPPORTED, "nD + nQ must be below 2^31");
     if (ct != DOMAGG_I32 && ct != DOMAGG_F32) return fail(h, DOMAGG_ERR_INVALID_ARG, "coordinates must be i32 or f32");
@@ -827,7 +835,7 @@ domagg_status domagg_forward_ex(domagg_handle h, int m, const void* d_coords, in
     if (variant != DOMAGG_IMPROVED && variant != DOMAGG_BASIC) return fail(h, DOMAGG_ERR_INVALID_ARG, "bad variant");
     const int M = variant == DOMAGG_BASIC ? m + 1 : m;  // the pipeline's coordinates
     domagg_status st = check_common(h, M, nD, nQ, coord_dtype, weight_dtype, op);
-    if (st) return variant == DOMAGG_BASIC && M > 3 ? fail(h, DOMAGG_ERR_UNSUPPORTED, "basic variant: m <= 2") : st;
+    if (st) return variant == DOMAGG_BASIC && M > 4 ? fail(h, DOMAGG_ERR_UNSUPPORTED, "basic variant: m <= 3") : st;
     if (m < 1 || (nonstrict_mask >> m) != 0u) return fail(h, DOMAGG_ERR_INVALID_ARG, "nonstrict_mask has bits >= m");
     if ((nD > 0 && !d_coords) || (nQ > 0 && (!q_coords || !out)) ||
         (op != DOMAGG_COUNT && nD > 0 && !d_weights))
@@ -903,8 +911,8 @@ domagg_status domagg_batch(domagg_handle h, int k, const domagg_instance* inst, 
                            domagg_dtype weight_dtype, domagg_op op, void* stream) {
     if (!h) return DOMAGG_ERR_INVALID_ARG;
     if (k < 0 || (k > 0 && !inst)) return fail(h, DOMAGG_ERR_INVALID_ARG, "bad instance array");
-    std::vector<Inst> groups[4];
-    int64_t total[4] = {0, 0, 0, 0};
+    std::vector<Inst> groups[5];
+    int64_t total[5] = {0, 0, 0, 0, 0};
     for (int i = 0; i < k; ++i) {
         const domagg_instance& I = inst[i];
         domagg_status st = check_common(h, I.m, I.nD, I.nQ, coord_dtype, weight_dtype, op);
@@ -917,7 +925,7 @@ domagg_status domagg_batch(domagg_handle h, int k, const domagg_instance* inst, 
         groups[I.m].push_back(make_inst(I.d_coords, I.nD, I.q_coords, I.nQ, I.d_weights, I.out));
     }
     cudaSetDevice(h->device);
-    for (int m = 1; m <= 3; ++m) {
+    for (int m = 1; m <= 4; ++m) {
         if (groups[m].empty()) continue;
         // one call per group of at most 2^31 - 1 points
         std::vector<Inst> part;
@@ -1045,7 +1053,8 @@ domagg_status plan_group(domagg_plan p, int m, const std::vector<Inst>& part, do
         const u32 nb = level_bound(m, (u64)part[i].nD + part[i].nQ);
         for (u32 lv = 0; lv < nb; ++lv) map.push_back(((u32)(i - c.k0) << 5) | lv);
         c.nslot += (int)nb;
-        const int kb = m == 1 ? 0 : (m == 2 ? (int)nb - 1 : 2 * (int)nb - 1);
+        const int kb = m == 1 ? 0 : (int)nb * (m - 1) - 1;  // (b-1) + b + ... over the m-1 ranks
+        if (kb > 63) return plan_fail(p, DOMAGG_ERR_UNSUPPORTED, "node keys of more than 63 bits (m = 4, large instance)");
         c.key_bits = std::max(c.key_bits, kb);
     }
     if (c.k1 > c.k0) close();
@@ -1088,7 +1097,7 @@ domagg_status domagg_batch_plan(domagg_plan* out, int device, int k, const domag
     p->wt = weight_dtype;
     p->op = op;
     domagg_ctx probe;  // argument checks only (no device resources)
-    std::vector<Inst> groups[4];
+    std::vector<Inst> groups[5];
     for (int i = 0; i < k; ++i) {
         const domagg_instance& I = inst[i];
         domagg_status st = check_common(&probe, I.m, I.nD, I.nQ, coord_dtype, weight_dtype, op);
@@ -1109,7 +1118,7 @@ domagg_status domagg_batch_plan(domagg_plan* out, int device, int k, const domag
         delete p;
         return DOMAGG_ERR_INVALID_ARG;
     }
-    for (int m = 1; m <= 3; ++m) {
+    for (int m = 1; m <= 4; ++m) {
         std::vector<Inst> part;
         int64_t acc = 0;
         for (size_t i = 0; i <= groups[m].size(); ++i) {

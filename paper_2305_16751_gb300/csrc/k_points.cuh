@@ -111,7 +111,8 @@ __device__ __forceinline__ u32 coord_key(const void* base, u32 row, int m, int i
 // index p - pt_off; queries come first, then data (see Inst).
 template <int M, bool F32>
 __global__ void k_encode(const Inst* __restrict__ inst, const u32* __restrict__ pt_offs, int k, u32 N,
-                         u32* __restrict__ rk0, u32* __restrict__ rk1, u32* __restrict__ lk, int negate, Ctl* ctl) {
+                         u32* __restrict__ rk0, u32* __restrict__ rk1, u32* __restrict__ rk2, u32* __restrict__ lk,
+                         int negate, Ctl* ctl) {
     const u32 p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
     const int s = upper_index(pt_offs, k + 1, p);
@@ -125,6 +126,7 @@ __global__ void k_encode(const Inst* __restrict__ inst, const u32* __restrict__ 
     const int stride = virt ? M - 1 : M;  // stored coordinates per point
     if (M >= 2) rk0[p] = coord_key<F32>(base, row, stride, 0, negate, nan);
     if (M >= 3) rk1[p] = coord_key<F32>(base, row, stride, 1, negate, nan);
+    if (M >= 4) rk2[p] = coord_key<F32>(base, row, stride, 2, negate, nan);
     u32 key = virt ? 0u : coord_key<F32>(base, row, stride, M - 1, negate, nan);
     // a non-strict last coordinate is sorted descending and read back in
     // reverse, which puts data before queries on ties
@@ -319,13 +321,8 @@ __global__ __launch_bounds__(THREADS, 4) void k_rank_apply(const u32* __restrict
 
 // Records of a point (instruction 6m+1 with Sec. 5): the product over the
 // first m-1 dimensions of the prefix sets of its ranks -- P0 (0-digits) for a
-// data point, P1 (1-digits) for a query.  bits_i selects those digits.
-template <int M>
-__device__ __forceinline__ u32 record_count(u32 bits0, u32 bits1) {
-    if (M == 1) return 1u;
-    if (M == 2) return (u32)__popc(bits0);
-    return (u32)__popc(bits0) * (u32)__popc(bits1);
-}
+// data point, P1 (1-digits) for a query; a level of the first rank carries
+// prod_{i>0} |P(r_i)| records of the point.
 
 // Levels of the flat map (Sec. 5 records, grouped by the level of their
 // first node).  A record of the first rank dimension at bit position j
@@ -362,8 +359,9 @@ constexpr u32 QUERY_BIT = 0x80000000u;  // in pr0: the point is a query (ranks a
 template <int M, typename W, int WT>
 __global__ __launch_bounds__(256) void k_count_scan(
     const u32* __restrict__ perm, const u32* __restrict__ seg_off, const u32* __restrict__ tile_off, int nseg,
-    const u32* __restrict__ chunk_off, const u32* __restrict__ r0, const u32* __restrict__ r1, Inst* inst,
-    u32* __restrict__ pr0, u32* __restrict__ pr1, u32* __restrict__ pj, W* __restrict__ pw,
+    const u32* __restrict__ chunk_off, const u32* __restrict__ r0, const u32* __restrict__ r1,
+    const u32* __restrict__ r2, Inst* inst, u32* __restrict__ pr0, u32* __restrict__ pr1, u32* __restrict__ pr2,
+    u32* __restrict__ pj, W* __restrict__ pw,
     u32* __restrict__ chunk_base, u32* __restrict__ qchunk_base, u32* __restrict__ tile_cnt) {
     constexpr int WARPS = 8, C = 2 * LMAX, TILE = WARPS * CS_ROUNDS * 32;
     static_assert(TILE == 4096, "point tiles");
@@ -375,8 +373,8 @@ __global__ __launch_bounds__(256) void k_count_scan(
     const Inst& I = inst[L.seg];
     const u32 nQ = I.nQ;
     const u32 nlev = levels_of<M>(I);
-    const u32 b0 = M >= 2 ? I.b[0] : 0u, b1 = M >= 3 ? I.b[1] : 0u;
-    const u32 m0 = low_mask(b0), m1 = low_mask(b1);
+    const u32 b0 = M >= 2 ? I.b[0] : 0u, b1 = M >= 3 ? I.b[1] : 0u, b2 = M >= 4 ? I.b[2] : 0u;
+    const u32 m0 = low_mask(b0), m1 = low_mask(b1), m2 = low_mask(b2);
     const u32 n_total = __ldg(seg_off + nseg);
     const bool rev = (I.flags >> (M - 1)) & 1u;  // non-strict last coordinate: its order read backwards
     const u32 wstart = L.start + (u32)warp * CS_ROUNDS * 32u;
@@ -393,13 +391,17 @@ __global__ __launch_bounds__(256) void k_count_scan(
         u32 a = 0, c = 0, bits0 = 0, c1 = 1;
         if (M >= 2 && valid) a = r0[j];
         if (M >= 3 && valid) c = r1[j];
+        u32 e2 = 0;
+        if (M >= 4 && valid) e2 = r2[j];
         if (M >= 2) bits0 = (q ? a : ~a) & m0;
         if (M >= 3) c1 = (u32)__popc((q ? c : ~c) & m1);
+        if (M >= 4) c1 *= (u32)__popc((q ? e2 : ~e2) & m2);
         if (M == 1) bits0 = 1u;
         if (!valid) bits0 = 0;
         if (valid) {
             if (M >= 2) pr0[x] = q ? (a | QUERY_BIT) : a;
             if (M >= 3) pr1[x] = c;
+            if (M >= 4) pr2[x] = e2;
             pj[x] = j;
             if (WT != 3 && !q) {
                 const u32 local = j - L.seg_begin;
@@ -491,8 +493,8 @@ static __global__ __launch_bounds__(256) void k_tile_exscan_counters(const u32* 
 template <int M, typename K, typename Pay, typename W, int WT>
 __global__ __launch_bounds__(256) void k_expand(
     const u32* __restrict__ chunk_off, int k, int k0, int k1, const u32* __restrict__ pt_offs,
-    const u32* __restrict__ pr0, const u32* __restrict__ pr1, const u32* __restrict__ pj,
-    const W* __restrict__ pw, const u32* __restrict__ chunk_base, const u32* __restrict__ qchunk_base,
+    const u32* __restrict__ pr0, const u32* __restrict__ pr1, const u32* __restrict__ pr2,
+    const u32* __restrict__ pj, const W* __restrict__ pw, const u32* __restrict__ chunk_base, const u32* __restrict__ qchunk_base,
     const u32* __restrict__ pt_tiles, const u32* __restrict__ tile_excl,
     const Inst* __restrict__ inst, const u32* __restrict__ seg_base /*[k1-k0][LMAX]*/,
     const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/, u32 n_rec, K* __restrict__ kout, Pay* __restrict__ pout) {
@@ -509,7 +511,7 @@ __global__ __launch_bounds__(256) void k_expand(
         const bool valid = p < pe;
         const u32 nQ = I.nQ;
         const u32 nlev = levels_of<M>(I);
-        const u32 b1 = M >= 3 ? I.b[1] : 0u;
+        const u32 b1 = M >= 3 ? I.b[1] : 0u, b2 = M >= 4 ? I.b[2] : 0u;
         const u32 tile = __ldg(pt_tiles + s) + (c - __ldg(chunk_off + s)) / CS_CHUNKS;  // the count scan's tile
         // lane lv holds the bases of level lv (read once, shuffled below)
         const u32 my_all = (u32)lane < nlev ? __ldg(seg_base + (u64)(s - k0) * LMAX + lane) +
@@ -520,7 +522,7 @@ __global__ __launch_bounds__(256) void k_expand(
                                                 __ldg(qchunk_base + (u64)c * LMAX + lane) +
                                                 __ldg(tile_excl + (u64)tile * CS_COUNTERS + LMAX + lane)
                                           : 0u;
-        u32 a = 0, cc = 0, bits0 = 0, bits1 = 0, c1 = 1;
+        u32 a = 0, cc = 0, ee = 0, bits0 = 0, bits1 = 0, bits2 = 0, c1 = 1;
         bool q = false;
         Pay w = 0;
         if (valid) {
@@ -538,6 +540,11 @@ __global__ __launch_bounds__(256) void k_expand(
                 cc = pr1[p];
                 bits1 = (q ? cc : ~cc) & low_mask(b1);
                 c1 = (u32)__popc(bits1);
+            }
+            if (M >= 4) {
+                ee = pr2[p];
+                bits2 = (q ? ee : ~ee) & low_mask(b2);
+                c1 *= (u32)__popc(bits2);
             }
             // 8-byte weights stay in pw: the record carries their position
             if (!q && WT != 3) w = WT == 1 ? (Pay)p : (Pay)pw[p];
@@ -591,12 +598,33 @@ __global__ __launch_bounds__(256) void k_expand(
                     const u32 spos = __shfl_sync(0xffffffffu, pos, src);
                     const Pay spay = __shfl_sync(0xffffffffu, pay, src);
                     const bool sq = (qb >> src) & 1u;
-                    if ((sb >> lane) & 1u) {
-                        const u32 r = (u32)__popc(sb & lt);
-                        const K key = (skv << b1) | (K)node_of(scc, (u32)lane);
-                        if (spos + r < n_rec) {
-                            kout[spos + r] = sq ? (key | role) : key;
-                            pout[spos + r] = sq ? (Pay)(spay + r) : spay;
+                    if (M == 3) {
+                        if ((sb >> lane) & 1u) {
+                            const u32 r = (u32)__popc(sb & lt);
+                            const K key = (skv << b1) | (K)node_of(scc, (u32)lane);
+                            if (spos + r < n_rec) {
+                                kout[spos + r] = sq ? (key | role) : key;
+                                pout[spos + r] = sq ? (Pay)(spay + r) : spay;
+                            }
+                        }
+                    } else {
+                        // m = 4: the third rank's digits across the lanes, the
+                        // second rank's digits one after the other
+                        const u32 sb2 = __shfl_sync(0xffffffffu, bits2, src);
+                        const u32 see = __shfl_sync(0xffffffffu, ee, src);
+                        const u32 c2 = (u32)__popc(sb2);
+                        u32 t1 = 0;
+                        for (u32 r1 = sb; r1; r1 &= r1 - 1, ++t1) {
+                            const u32 j1 = __ffs(r1) - 1;
+                            if ((sb2 >> lane) & 1u) {
+                                const u32 r = t1 * c2 + (u32)__popc(sb2 & lt);
+                                const K key = ((((skv << b1) | (K)node_of(scc, j1)) << b2)) |
+                                              (K)node_of(see, (u32)lane);
+                                if (spos + r < n_rec) {
+                                    kout[spos + r] = sq ? (key | role) : key;
+                                    pout[spos + r] = sq ? (Pay)(spay + r) : spay;
+                                }
+                            }
                         }
                     }
                 }

@@ -37,7 +37,7 @@ __global__ __launch_bounds__(1024) void k_layout(const Inst* __restrict__ inst, 
         if (lv < nlev) {
             na = __ldg(lvl_tot + (u64)(k0 + (int)srel) * LMAX + lv);
             nq = __ldg(qlvl_tot + (u64)(k0 + (int)srel) * LMAX + lv);
-            if (M >= 2) bits = I.b[0] - 1u - lv + (M == 3 ? I.b[1] : 0u);
+            if (M >= 2) bits = I.b[0] - 1u - lv + (M >= 3 ? I.b[1] : 0u) + (M >= 4 ? I.b[2] : 0u);
         }
     };
     // totals first: the capacity decides between the layout and empty segments
@@ -405,7 +405,8 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys0
 template <class Op, int M>
 __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_off, int k, int k0, int k1,
                                                 const u32* __restrict__ pt_offs, const u32* __restrict__ pr0,
-                                                const u32* __restrict__ pr1, const u32* __restrict__ pj,
+                                                const u32* __restrict__ pr1, const u32* __restrict__ pr2,
+                                                const u32* __restrict__ pj,
                                                 const u32* __restrict__ qchunk_base,
                                                 const u32* __restrict__ pt_tiles, const u32* __restrict__ tile_excl,
                                                 const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/,
@@ -439,6 +440,7 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
                     bits1 = pr1[p] & low_mask(I.b[1]);
                     c1 = (u32)__popc(bits1);
                 }
+                if (M >= 4) c1 *= (u32)__popc(pr2[p] & low_mask(I.b[2]));
                 if (M == 1) bits0 = 1u;
                 if (M >= 3 && c1 == 0) bits0 = 0;
             }
@@ -467,7 +469,8 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
             }
         }
         if (M >= 3) {
-            // m = 3: exclusive sums of c1 over the lanes of each level (warp-uniform loop)
+            // m >= 3: exclusive sums of the records per point (c1) over the
+            // lanes of each level (warp-uniform loop)
             for (u32 lv = 0; lv < nlev; ++lv) {
                 const bool has = (bits0 >> lv) & 1u;
                 if (s_mask[warp][lv] == 0u) continue;

@@ -38,7 +38,7 @@ class domagg_instance(ctypes.Structure):
 class domagg_stats(ctypes.Structure):
     _fields_ = [("n_points", ctypes.c_int64), ("n_records", ctypes.c_int64),
                 ("n_query_records", ctypes.c_int64), ("m", ctypes.c_int32),
-                ("rank_bits", ctypes.c_int32 * 2), ("distinct", ctypes.c_int64 * 2),
+                ("rank_bits", ctypes.c_int32 * 3), ("distinct", ctypes.c_int64 * 3),
                 ("record_key_bits", ctypes.c_int32), ("record_passes", ctypes.c_int32),
                 ("workspace_bytes", ctypes.c_int64)]
 

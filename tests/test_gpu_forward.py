@@ -142,7 +142,7 @@ def test_forward_host_matches_device():
 def test_invalid_arguments_are_rejected():
     h = domagg.handle(0)
     L = domagg.lib()
-    st = L.domagg_forward(h, 4, None, 0, None, 0, 0, None, 1, 0, None, None)
+    st = L.domagg_forward(h, 5, None, 0, None, 0, 0, None, 1, 0, None, None)
     assert domagg.STATUS[st] == "UNSUPPORTED"
     st = L.domagg_forward(h, 0, None, 0, None, 0, 0, None, 1, 0, None, None)
     assert domagg.STATUS[st] == "INVALID_ARG"

@@ -108,10 +108,51 @@ def test_ecdf_counts_and_two_sample_statistic():
 
 
 def test_variant_arguments_are_checked():
-    D = np.zeros((4, 3), np.int32)
+    D = np.zeros((4, 4), np.int32)
     with pytest.raises(domagg.DomaggError) as e:
         _forward(D, D, np.ones(4, np.int64), "sum", variant="basic")
-    assert e.value.status == 2  # UNSUPPORTED: basic needs m <= 2
+    assert e.value.status == 2  # UNSUPPORTED: basic needs m <= 3
     with pytest.raises(domagg.DomaggError) as e:
         _forward(D[:, :2], D[:, :2], np.ones(4, np.int64), "sum", nonstrict=4)
     assert e.value.status == 1  # INVALID_ARG: mask bit beyond m
+
+
+# --- m = 4 (the Sec. 5 pipeline with three rank coordinates) ---------------
+
+@pytest.mark.parametrize("dt,wt,op", [("i32", "i64", "sum"), ("f32", "f32", "sum"), ("i32", "i32", "max"),
+                                      ("f32", "i64", "count")])
+def test_m4_matches_oracle(dt, wt, op):
+    rng = np.random.default_rng(700 + len(op) + len(dt))
+    for nD, nQ, levels in ((3000, 2500, 12), (1500, 1800, 300), (2, 4000, 4)):
+        D, Q, w = workloads.random_small(rng, 4, nD, nQ, levels, dt, wt)
+        wv = None if op == "count" else w
+        _check(_forward(D, Q, wv, op), D, Q, wv, op, 0)
+        if op == "sum" and dt == "i32":
+            assert domagg.stats()["n_records"] == oracle.record_count(D, Q)
+
+
+def test_m4_nonstrict_and_basic_m3():
+    rng = np.random.default_rng(710)
+    for mask in (1, 6, 8, 15):
+        D, Q, w = workloads.random_small(rng, 4, 2000, 2000, 10, "i32", "i64")
+        _check(_forward(D, Q, w, "sum", nonstrict=mask), D, Q, w, "sum", mask)
+    D, Q, w = workloads.random_small(rng, 3, 2500, 2000, 40, "i32", "i64")
+    got = _forward(D, Q, w, "sum", variant="basic")
+    _check(got, D, Q, w, "sum", 0)
+    assert domagg.stats()["n_records"] == _basic_record_count(D, Q)
+
+
+def test_m4_in_a_batch_and_key_width_limit():
+    rng = np.random.default_rng(720)
+    probs = [workloads.random_small(rng, 1 + i % 4, 800 + 50 * i, 700, 30, "i32", "i64") for i in range(12)]
+    outs = domagg.batch([(to_dev(D), to_dev(Q), to_dev(w)) for D, Q, w in probs], "sum")
+    torch().cuda.synchronize()
+    for (D, Q, w), o in zip(probs, outs):
+        _check(o.cpu().numpy(), D, Q, w, "sum", 0)
+    # 2^22 distinct values in every coordinate: b = 22, a 65-bit node key
+    n = 1 << 21
+    P = rng.permutation(np.arange(2 * n, dtype=np.int32))
+    X = np.stack([P, np.roll(P, 1), np.roll(P, 2), np.roll(P, 3)], axis=1)
+    with pytest.raises(domagg.DomaggError) as e:
+        _forward(X[:n], X[n:], np.ones(n, np.int64), "sum")
+    assert e.value.status == 2
