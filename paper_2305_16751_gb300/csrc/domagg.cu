@@ -72,6 +72,11 @@ struct domagg_ctx {
     u64 epoch_mirror = 0;  // host copy of Ctl::epoch_base
     bool frozen = false;   // owned by a plan: its workspace must not grow any more
     int sms = 152;         // multiprocessors of the device
+    // the point phase's independent sorts run on two more streams (fork /
+    // join by events); off for the allocation-free entry point
+    bool overlap = false;
+    cudaStream_t aux[2] = {nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
     int ranges_per_cta = 4, blocks_per_sm = 16;  // launch shapes (domagg_plan_autotune)
 
     size_t held() const { return pts.cap + recs.cap + st_multi.cap + st_seg.cap + stage.cap; }
@@ -281,8 +286,22 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         P[26] = c.take<u32>(M >= 4 ? N : 0);  // rk2
         P[27] = c.take<u32>(M >= 4 ? N : 0);  // r2
         P[28] = c.take<u32>(M >= 4 ? N : 0);  // pr2
+        // scratch of the sorts that run beside the first (chain 1: the last
+        // coordinate; chain 2: the second rank coordinate), when overlapping
+        for (int ch = 1; ch <= 2; ++ch) {
+            const bool used = h->overlap && (ch == 1 || M >= 3);
+            const u64 n = used ? N : 0, kk = used ? (u64)k : 0;
+            P[29 + (ch - 1) * 8 + 0] = c.take<u32>(n);                                  // key ping-pong
+            P[29 + (ch - 1) * 8 + 1] = c.take<u32>(n);                                  // values A
+            P[29 + (ch - 1) * 8 + 2] = c.take<u32>(n);                                  // values B
+            P[29 + (ch - 1) * 8 + 3] = c.take<u32>(kk + 1);                             // tile map
+            P[29 + (ch - 1) * 8 + 4] = c.take<u32>(kk * 4 * RADIX);                     // hist
+            P[29 + (ch - 1) * 8 + 5] = c.take<u32>(kk * 4 * RADIX);                     // digit offsets
+            P[29 + (ch - 1) * 8 + 6] = c.take<u32>(used ? (size_t)sort_range_bound(pt_sizes) * RADIX : 0);
+            P[29 + (ch - 1) * 8 + 7] = c.take<u32>(used ? (size_t)ntp : 0);             // rank tile counts
+        }
     };
-    void* P[29];
+    void* P[45];
     {
         Carver c(nullptr);
         carve_points(c, P);
@@ -304,8 +323,9 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
 
     // status words: point tiles x 256 digits (the records sort grows it later)
     {
-        const u64 nst = std::max<u64>(tiles_of(pt_sizes, SORT_MIN_TILE), ntp);
-        domagg_status st = grow(h, h->st_multi, (size_t)std::max<u64>(nst, 1) * RADIX * sizeof(u64), true);
+        const u64 nst = std::max<u64>(std::max<u64>(tiles_of(pt_sizes, SORT_MIN_TILE), ntp), 1);
+        const int chains = h->overlap ? (M >= 3 ? 3 : 2) : 1;
+        domagg_status st = grow(h, h->st_multi, (size_t)nst * RADIX * sizeof(u64) * chains, true);
         if (st) return st;
     }
 
@@ -358,38 +378,76 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                                                                       negate ? 1 : 0, h->ctl);
     L.stop();
 
-    SortSpace sp{d_pt_offs, k, &pt_sizes, d_sort_tiles, hist, digit_off, (u64*)h->st_multi.p, (double)N,
-                 (u32*)P[24], sort_range_bound(pt_sizes)};
-
-    // ---- ranks of the first m-1 coordinates (5i-3 .. 5i, 5m+i)
-    for (int i = 0; i < M - 1; ++i) {
-        u32* keys[2] = {i == 0 ? rk0 : (i == 1 ? rk1 : rk2), kalt};
-        u32* vals[2] = {vA, vB};
+    // ---- the point-phase sorts (5i-3 .. 5i, 5m+i, and the Sec. 5 order of the
+    // last coordinate).  They are independent: with overlap, the last
+    // coordinate's sort (chain 1) and the second rank coordinate (chain 2)
+    // run on their own streams, forked after the keys and joined before the
+    // count scan, each with its own scratch and status words.
+    const u64 nst_chain = std::max<u64>(std::max<u64>(tiles_of(pt_sizes, SORT_MIN_TILE), ntp), 1) * RADIX;
+    struct Chain {
+        cudaStream_t stream;
+        u32 *kalt, *vA, *vB, *tiles, *hist, *digit, *range, *tile_cnt;
+        u64* status;
+    };
+    auto chain = [&](int ch) -> Chain {
+        if (ch == 0 || !h->overlap)
+            return Chain{stream, kalt, vA, vB, d_sort_tiles, hist, digit_off, (u32*)P[24], (u32*)P[25],
+                         (u64*)h->st_multi.p};
+        void** Q = P + 29 + (ch - 1) * 8;
+        return Chain{h->aux[ch - 1], (u32*)Q[0], (u32*)Q[1], (u32*)Q[2], (u32*)Q[3], (u32*)Q[4], (u32*)Q[5],
+                     (u32*)Q[6], (u32*)Q[7], (u64*)h->st_multi.p + (u64)ch * nst_chain};
+    };
+    auto rank_dim = [&](int i, const Chain& C) {
+        L.stream = C.stream;
+        SortSpace sp{d_pt_offs, k, &pt_sizes, C.tiles, C.hist, C.digit, C.status, (double)N, C.range,
+                     sort_range_bound(pt_sizes)};
+        u32* keys[2] = {i == 0 ? rk0 : (i == 1 ? rk1 : rk2), C.kalt};
+        u32* vals[2] = {C.vA, C.vB};
         // only the sorted key sequence matters for dense ranks: any order of equal digits
         const int cur = sort_pairs<u32, u32>(L, sp, keys, vals, true, 32, 0xffffffffu, KIND_HIST_POINTS,
                                              KIND_SORT_POINTS, nullptr, false);
-        u32* tile_cnt = (u32*)P[25];
         L.start(KIND_RANK, (double)N * 4);
-        k_rank_count<SCAN_THREADS, SCAN_ITEMS><<<(unsigned)ntp, SCAN_THREADS, 0, stream>>>(keys[cur], d_pt_offs,
-                                                                                        d_pt_tiles, k, tile_cnt);
+        k_rank_count<SCAN_THREADS, SCAN_ITEMS><<<(unsigned)ntp, SCAN_THREADS, 0, C.stream>>>(keys[cur], d_pt_offs,
+                                                                                          d_pt_tiles, k, C.tile_cnt);
         L.stop();
         L.start(KIND_SMALL, 0.0);
-        k_tile_exscan<<<(unsigned)((k + 7) / 8), 256, 0, stream>>>(d_pt_tiles, k, tile_cnt);
+        k_tile_exscan<<<(unsigned)((k + 7) / 8), 256, 0, C.stream>>>(d_pt_tiles, k, C.tile_cnt);
         L.stop();
         L.start(KIND_RANK, (double)N * 12);
-        k_rank_apply<SCAN_THREADS, SCAN_ITEMS><<<(unsigned)ntp, SCAN_THREADS, 0, stream>>>(
-            keys[cur], vals[cur], d_pt_offs, d_pt_tiles, k, tile_cnt, i == 0 ? r0 : (i == 1 ? r1 : r2), d_inst, i);
+        k_rank_apply<SCAN_THREADS, SCAN_ITEMS><<<(unsigned)ntp, SCAN_THREADS, 0, C.stream>>>(
+            keys[cur], vals[cur], d_pt_offs, d_pt_tiles, k, C.tile_cnt, i == 0 ? r0 : (i == 1 ? r1 : r2), d_inst, i);
         L.stop();
-    }
-    // ---- order of the last coordinate, queries first on ties (Sec. 5)
-    u32* perm;
-    {
-        u32* keys[2] = {lk, kalt};
-        u32* vals[2] = {vA, vB};
+    };
+    auto last_dim = [&](const Chain& C) -> u32* {  // order of the last coordinate, queries first on ties (Sec. 5)
+        L.stream = C.stream;
+        SortSpace sp{d_pt_offs, k, &pt_sizes, C.tiles, C.hist, C.digit, C.status, (double)N, C.range,
+                     sort_range_bound(pt_sizes)};
+        u32* keys[2] = {lk, C.kalt};
+        u32* vals[2] = {C.vA, C.vB};
         const int cur = sort_pairs<u32, u32>(L, sp, keys, vals, true, 32, 0xffffffffu, KIND_HIST_POINTS,
                                              KIND_SORT_POINTS);
-        perm = vals[cur];
+        return vals[cur];
+    };
+    u32* perm;
+    if (h->overlap) {
+        cudaEventRecord(h->ev_fork, stream);
+        cudaStreamWaitEvent(h->aux[0], h->ev_fork, 0);
+        if (M >= 3) cudaStreamWaitEvent(h->aux[1], h->ev_fork, 0);
+        perm = last_dim(chain(1));
+        if (M >= 3) rank_dim(1, chain(2));
+        rank_dim(0, chain(0));
+        if (M >= 4) rank_dim(2, chain(0));
+        cudaEventRecord(h->ev_join[0], h->aux[0]);
+        cudaStreamWaitEvent(stream, h->ev_join[0], 0);
+        if (M >= 3) {
+            cudaEventRecord(h->ev_join[1], h->aux[1]);
+            cudaStreamWaitEvent(stream, h->ev_join[1], 0);
+        }
+    } else {  // one stream: the rank sorts first, the permutation last (they share buffers)
+        for (int i = 0; i < M - 1; ++i) rank_dim(i, chain(0));
+        perm = last_dim(chain(0));
     }
+    L.stream = stream;
     // ---- count / offset scan of the flat map, per level
     {
         // perm, gathered ranks, ranks / index / weight written in order, weight gathered
@@ -790,6 +848,12 @@ domagg_status domagg_create(domagg_handle* out, int device, size_t max_workspace
     h->max_ws = max_workspace_bytes;
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
     if (h->sms <= 0) h->sms = 152;
+    h->overlap = cudaStreamCreateWithFlags(&h->aux[0], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaStreamCreateWithFlags(&h->aux[1], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&h->ev_join[0], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&h->ev_join[1], cudaEventDisableTiming) == cudaSuccess;
+    cudaGetLastError();
     if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&h->ctl, sizeof(Ctl)) != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -810,6 +874,10 @@ domagg_status domagg_destroy(domagg_handle h) {
     if (h->ctl) cudaFree(h->ctl);
     if (h->h_pin) cudaFreeHost(h->h_pin);
     for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+    for (cudaStream_t s : h->aux)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : {h->ev_fork, h->ev_join[0], h->ev_join[1]})
+        if (e) cudaEventDestroy(e);
     delete h;
     return DOMAGG_OK;
 }
