@@ -203,11 +203,13 @@ void maybe_reset_epochs(domagg_ctx* h, cudaStream_t s) {
 // get a fixed capacity, laid out on the device (k_layout) instead of on the
 // host, so a planned run never reads a count back.
 struct PlannedChunk {
-    int k0, k1;
-    u64 T_cap, Tq_cap;   // reserved records and query records (>= 1)
-    int nslot;           // segment slots: every instance's largest possible level count
-    int key_bits;        // bound on the node-key bits of any level
-    u32* d_slot_map;     // device [nslot]: (instance - k0) << 5 | level
+    int k0 = 0, k1 = 0;
+    u64 T_cap = 0, Tq_cap = 0;  // reserved records (per key class) and query records (>= 1)
+    int nslot = 0;              // segment slots: every instance's largest possible level count
+    int nslot0 = 0;             // slots of class 0 (listed first); the rest are class 1 (32-bit keys, m >= 3)
+    int key_bits = 0, key_bits1 = 0;  // bounds on the node-key bits of the two classes
+    u32* d_slot_map = nullptr;  // device [nslot]: (instance - k0) << 5 | level
+    u32* d_nmask = nullptr;     // device [k1 - k0]: class-1 levels of every instance (m >= 3)
 };
 
 // ---------------------------------------------------------------------------
@@ -228,6 +230,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     constexpr int SEG_ITEMS = (sizeof(K) + sizeof(Pay) == 8) ? DOMAGG_SEG_ITEMS_NARROW : 8;
     constexpr int SEG_THREADS = DOMAGG_SEG_THREADS;
     constexpr u32 SEG_TILE = SEG_THREADS * SEG_ITEMS;
+    constexpr int SEG_ITEMS1 = (4 + sizeof(Pay) == 8) ? DOMAGG_SEG_ITEMS_NARROW : 8;  // class 1: 32-bit keys
+    constexpr u32 SEG_TILE1 = SEG_THREADS * SEG_ITEMS1;
     const int k = (int)inst.size();
 
     // ---- host-side layout of the point space
@@ -463,11 +467,17 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         L.stop();
     }
     // ---- record chunks: from the counts (one synchronisation) or from the plan
+    // Records of m >= 3 come in two key classes: levels whose node keys fit
+    // 31 bits (class 1) are sorted and scanned with 32-bit keys, the others
+    // (class 0) with 64-bit keys; for m <= 2 every level is class 0 (32-bit
+    // keys already).  Each class has its own record arrays and segment table.
     struct Chunk {
-        int k0, k1;
-        u64 T, Tq, nseg;
-        int key_bits;
-        const u32* slot_map;  // planned: the chunk's segment slots (device)
+        int k0 = 0, k1 = 0;
+        u64 T = 0, Tq = 0, nseg = 0;
+        u64 T0 = 0, T1 = 0, nseg0 = 0, nseg1 = 0;  // per class (planned: capacities and slots)
+        int key_bits = 0, key_bits1 = 0;           // per class
+        const u32* slot_map = nullptr;             // planned: the chunk's segment slots (device)
+        const u32* nmask = nullptr;                // planned: class-1 levels per instance (device)
     };
     std::vector<Chunk> chunks;
     std::vector<u32> nlev(k), lvl, qlvl;
@@ -476,17 +486,33 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         const u32 b = inst[s].b[0] - 1u - lv;  // prefix length of level lv
         return b + (M >= 3 ? inst[s].b[1] : 0u) + (M >= 4 ? inst[s].b[2] : 0u);
     };
+    auto narrow_level = [&](int s, u32 lv) -> bool { return M >= 3 && level_bits(s, lv) <= 31u; };
     // pinned upload area of every chunk: per instance record and slot bases,
     // per segment offsets and key bits, per (instance, level) segment bases
     auto chunk_upload_words = [&](const Chunk& c) -> size_t {
         const size_t kc = (size_t)(c.k1 - c.k0);
-        return 2 * (kc + 1) + (c.nseg + 1) + c.nseg + 2 * kc * LMAX;
+        return 2 * (kc + 1) + (c.nseg0 + 1) + (c.nseg1 + 1) + c.nseg + 2 * kc * LMAX + kc;
     };
     std::vector<size_t> base_pos;
     cudaError_t e = cudaSuccess;
     if (planned) {
-        for (const PlannedChunk& pc : *planned)
-            chunks.push_back(Chunk{pc.k0, pc.k1, pc.T_cap, pc.Tq_cap, (u64)pc.nslot, pc.key_bits, pc.d_slot_map});
+        for (const PlannedChunk& pc : *planned) {
+            Chunk c;
+            c.k0 = pc.k0;
+            c.k1 = pc.k1;
+            c.T = pc.T_cap;
+            c.Tq = pc.Tq_cap;
+            c.nseg = (u64)pc.nslot;
+            c.nseg0 = (u64)pc.nslot0;
+            c.nseg1 = (u64)(pc.nslot - pc.nslot0);
+            c.T0 = pc.T_cap;
+            c.T1 = pc.nslot > pc.nslot0 ? pc.T_cap : 0;
+            c.key_bits = pc.key_bits;
+            c.key_bits1 = pc.key_bits1;
+            c.slot_map = pc.d_slot_map;
+            c.nmask = pc.d_nmask;
+            chunks.push_back(c);
+        }
     } else {
     // the one synchronisation: record counts and device errors
     Inst* h_inst = (Inst*)hp;
@@ -542,18 +568,30 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         }
     }
     {
-        Chunk c{0, 0, 0, 0, 0, 0, nullptr};
+        Chunk c;
         for (int s = 0; s < k; ++s) {
             const u64 Ts = inst[s].T;
             if (c.k1 > c.k0 && c.T + Ts > chunk_cap) {
                 chunks.push_back(c);
-                c = Chunk{s, s, 0, 0, 0, 0, nullptr};
+                c = Chunk();
+                c.k0 = c.k1 = s;
             }
             c.k1 = s + 1;
             c.T += Ts;
             c.Tq += inst[s].Tq;
             c.nseg += nlev[s];
-            for (u32 lv = 0; lv < nlev[s]; ++lv) c.key_bits = std::max(c.key_bits, (int)level_bits(s, lv));
+            for (u32 lv = 0; lv < nlev[s]; ++lv) {
+                const int bits = (int)level_bits(s, lv);
+                if (narrow_level(s, lv)) {
+                    c.nseg1 += 1;
+                    c.T1 += lvl[(size_t)s * LMAX + lv];
+                    c.key_bits1 = std::max(c.key_bits1, bits);
+                } else {
+                    c.nseg0 += 1;
+                    c.T0 += lvl[(size_t)s * LMAX + lv];
+                    c.key_bits = std::max(c.key_bits, bits);
+                }
+            }
         }
         if (c.k1 > c.k0) chunks.push_back(c);
     }
@@ -576,66 +614,93 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
         const Chunk& C = chunks[ci];
         const int kc = C.k1 - C.k0;
-        const u64 nseg = C.nseg;
-        u32 *hb = nullptr, *h_rb = nullptr, *h_qb = nullptr, *h_so = nullptr, *h_sbits = nullptr, *h_sbase = nullptr,
-            *h_qsbase = nullptr;
+        const u64 nseg = C.nseg, nseg0 = C.nseg0, nseg1 = C.nseg1;
+        // host tables (unplanned): record and slot bases per instance, the two
+        // classes' segment offsets, key bits (class 0 then class 1), bases per
+        // (instance, level) within the level's class, slot bases, class-1 masks
+        u32 *hb = nullptr, *h_rb = nullptr, *h_qb = nullptr, *h_so = nullptr, *h_so1 = nullptr, *h_sbits = nullptr,
+            *h_sbase = nullptr, *h_qsbase = nullptr, *h_nmask = nullptr;
         if (!planned) {
             hb = (u32*)(hp + base_pos[ci]);
-            h_rb = hb;                            // [kc+1] record base per instance
-            h_qb = hb + kc + 1;                   // [kc+1] query-slot base per instance
-            h_so = h_qb + kc + 1;                 // [nseg+1] segment offsets
-            h_sbits = h_so + nseg + 1;            // [nseg] segment key bits
-            h_sbase = h_sbits + nseg;             // [kc][LMAX] segment base per (instance, level)
-            h_qsbase = h_sbase + (size_t)kc * LMAX;  // [kc][LMAX] query-slot base per (instance, level)
+            h_rb = hb;
+            h_qb = hb + kc + 1;
+            h_so = h_qb + kc + 1;
+            h_so1 = h_so + nseg0 + 1;
+            h_sbits = h_so1 + nseg1 + 1;
+            h_sbase = h_sbits + nseg;
+            h_qsbase = h_sbase + (size_t)kc * LMAX;
+            h_nmask = h_qsbase + (size_t)kc * LMAX;
         }
-        std::vector<u64> seg_sizes(planned ? 0 : nseg);
-        u64 nts = 0;
+        std::vector<u64> seg_sizes0(planned ? 0 : nseg0), seg_sizes1(planned ? 0 : nseg1);
+        u64 nts0 = 0, nts1 = 0;
         if (planned) {
-            nts = C.T / SEG_TILE + nseg;  // bound: sum ceil(n_s / tile) <= T / tile + nseg
+            nts0 = C.T0 / SEG_TILE + nseg0;  // bounds: sum ceil(n_s / tile) <= T / tile + nseg
+            nts1 = nseg1 ? C.T1 / SEG_TILE + nseg1 : 0;
         } else {
-            u64 a = 0, b = 0, sg = 0;
+            u64 a0 = 0, a1 = 0, b = 0, g0 = 0, g1 = 0;
             for (int s = C.k0; s < C.k1; ++s) {
-                h_rb[s - C.k0] = (u32)a;
+                h_rb[s - C.k0] = (u32)(a0 + a1);
                 h_qb[s - C.k0] = (u32)b;
+                h_nmask[s - C.k0] = 0;
                 for (u32 lv = 0; lv < LMAX; ++lv) {
                     h_sbase[(size_t)(s - C.k0) * LMAX + lv] = 0;
                     h_qsbase[(size_t)(s - C.k0) * LMAX + lv] = 0;
                 }
                 for (u32 lv = 0; lv < nlev[s]; ++lv) {
                     const u64 sz = lvl[(size_t)s * LMAX + lv];
-                    h_so[sg] = (u32)a;
-                    h_sbits[sg] = level_bits(s, lv);
+                    const bool nar = narrow_level(s, lv);
+                    u64& a = nar ? a1 : a0;
+                    const u64 g = nar ? nseg0 + g1 : g0;
+                    (nar ? h_so1[g1] : h_so[g0]) = (u32)a;
+                    h_sbits[g] = level_bits(s, lv);
                     h_sbase[(size_t)(s - C.k0) * LMAX + lv] = (u32)a;
                     h_qsbase[(size_t)(s - C.k0) * LMAX + lv] = (u32)b;
-                    seg_sizes[sg] = sz;
-                    nts += (sz + SEG_TILE - 1) / SEG_TILE;
+                    if (nar) {
+                        h_nmask[s - C.k0] |= 1u << lv;
+                        seg_sizes1[g1++] = sz;
+                        nts1 += (sz + SEG_TILE - 1) / SEG_TILE;
+                    } else {
+                        seg_sizes0[g0++] = sz;
+                        nts0 += (sz + SEG_TILE - 1) / SEG_TILE;
+                    }
                     a += sz;
                     b += qlvl[(size_t)s * LMAX + lv];
-                    ++sg;
                 }
             }
-            h_rb[kc] = (u32)a;
+            h_rb[kc] = (u32)(a0 + a1);
             h_qb[kc] = (u32)b;
-            h_so[nseg] = (u32)a;
+            h_so[nseg0] = (u32)a0;
+            h_so1[nseg1] = (u32)a1;
         }
-        const int npass = (C.key_bits + RADIX_BITS - 1) / RADIX_BITS;
-        const u64 ntr = planned ? C.T / SORT_MIN_TILE + nseg : tiles_of(seg_sizes, SORT_MIN_TILE);
-        const u64 nrange_bound = planned ? sort_range_bound_n(C.T, nseg) : sort_range_bound(seg_sizes);
+        const int npass0 = (C.key_bits + RADIX_BITS - 1) / RADIX_BITS;
+        const int npass1 = (C.key_bits1 + RADIX_BITS - 1) / RADIX_BITS;
+        const u64 ntr0 = planned ? C.T0 / SORT_MIN_TILE + nseg0 : tiles_of(seg_sizes0, SORT_MIN_TILE);
+        const u64 ntr1 = planned ? (nseg1 ? C.T1 / SORT_MIN_TILE + nseg1 : 0) : tiles_of(seg_sizes1, SORT_MIN_TILE);
+        const u64 nrb0 = planned ? sort_range_bound_n(C.T0, nseg0) : sort_range_bound(seg_sizes0);
+        const u64 nrb1 = planned ? (nseg1 ? sort_range_bound_n(C.T1, nseg1) : 0) : sort_range_bound(seg_sizes1);
+        const u64 nseg_max = std::max(nseg0, nseg1);
+        const size_t hist_words = std::max<size_t>((size_t)nseg0 * std::max(npass0, 1),
+                                                   (size_t)nseg1 * std::max(npass1, 1)) * RADIX;
         // record workspace
         auto carve_recs = [&](Carver& c, void** R) {
             R[0] = c.take<u32>(chunk_upload_words(C));  // the uploaded bases and segment tables
-            R[1] = c.take<u32>(nseg + 1);                // sort ranges
-            R[2] = c.take<u32>(nseg + 1);                // segscan tiles
-            R[3] = c.take<K>(C.T);
-            R[4] = c.take<K>(C.T);
-            R[5] = c.take<Pay>(C.T);
-            R[6] = c.take<Pay>(C.T);
+            R[1] = c.take<u32>(nseg_max + 1);            // sort ranges
+            R[2] = c.take<u32>(nseg0 + 1);               // segscan tiles, class 0
+            R[3] = c.take<K>(C.T0);
+            R[4] = c.take<K>(C.T0);
+            R[5] = c.take<Pay>(C.T0);
+            R[6] = c.take<Pay>(C.T0);
             R[7] = c.take<Part>(C.Tq);
-            R[8] = c.take<u32>((size_t)nseg * std::max(npass, 1) * RADIX);
-            R[9] = c.take<u32>((size_t)nseg * std::max(npass, 1) * RADIX);
-            R[10] = c.take<u32>((size_t)nrange_bound * RADIX);  // first-pass range bases
+            R[8] = c.take<u32>(hist_words);
+            R[9] = c.take<u32>(hist_words);
+            R[10] = c.take<u32>((size_t)std::max(nrb0, nrb1) * RADIX);  // first-pass range bases
+            R[11] = c.take<u32>(C.T1);                   // class 1: 32-bit keys
+            R[12] = c.take<u32>(C.T1);
+            R[13] = c.take<Pay>(C.T1);
+            R[14] = c.take<Pay>(C.T1);
+            R[15] = c.take<u32>(nseg1 + 1);              // segscan tiles, class 1
         };
-        void* R[11];
+        void* R[16];
         {
             Carver c(nullptr);
             carve_recs(c, R);
@@ -643,20 +708,26 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             if (st) return st;
             Carver c2(h->recs.p);
             carve_recs(c2, R);
-            st = grow(h, h->st_multi, (size_t)std::max<u64>(std::max(ntr, ntp), 1) * RADIX * sizeof(u64), true);
+            const u64 nst = std::max<u64>(std::max(std::max(ntr0, ntr1), ntp), 1);
+            st = grow(h, h->st_multi, (size_t)nst * RADIX * sizeof(u64), true);
             if (st) return st;
-            st = grow(h, h->st_seg, (size_t)std::max<u64>(nts, 1) * sizeof(SegStatus<typename Op::Acc>), true);
+            st = grow(h, h->st_seg, (size_t)std::max<u64>(std::max(nts0, nts1), 1) * sizeof(SegStatus<typename Op::Acc>),
+                      true);
             if (st) return st;
         }
         u32* d_up = (u32*)R[0];
         u32* d_qb = d_up + kc + 1;
         u32* d_so = d_qb + kc + 1;
-        u32* d_sbits = d_so + nseg + 1;
+        u32* d_so1 = d_so + nseg0 + 1;
+        u32* d_sbits = d_so1 + nseg1 + 1;
         u32* d_sbase = d_sbits + nseg;
         u32* d_qsbase = d_sbase + (size_t)kc * LMAX;
-        u32 *d_rtiles = (u32*)R[1], *d_stiles = (u32*)R[2];
+        const u32* d_nmask = planned ? C.nmask : d_qsbase + (size_t)kc * LMAX;
+        u32 *d_rtiles = (u32*)R[1], *d_stiles = (u32*)R[2], *d_stiles1 = (u32*)R[15];
         K* keys[2] = {(K*)R[3], (K*)R[4]};
         Pay* pays[2] = {(Pay*)R[5], (Pay*)R[6]};
+        u32* keys1[2] = {(u32*)R[11], (u32*)R[12]};
+        Pay* pays1[2] = {(Pay*)R[13], (Pay*)R[14]};
         Part* partial = (Part*)R[7];
         if (!planned) {
             cudaMemcpyAsync(d_up, hb, sizeof(u32) * chunk_upload_words(C), cudaMemcpyHostToDevice, stream);
@@ -670,12 +741,13 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         L.next_lookback = 0;
         if (planned) {
             L.start(KIND_SMALL, 0.0);
-            k_layout<M><<<1, 1024, 0, stream>>>(d_inst, C.k0, lvl_tot, qlvl_tot, C.slot_map, (int)nseg, C.T, C.Tq,
-                                                d_so, d_sbits, d_sbase, d_qsbase, h->ctl);
+            k_layout<M><<<1, 1024, 0, stream>>>(d_inst, C.k0, lvl_tot, qlvl_tot, C.slot_map, (int)nseg, (int)nseg0,
+                                                C.T0, C.Tq, d_so, d_sbits, d_sbase, d_qsbase, h->ctl);
             L.stop();
         }
         L.start(KIND_SMALL, 0.0);
-        k_make_tiles<<<1, 1024, 0, stream>>>(d_so, (int)nseg, SEG_TILE, d_stiles);
+        k_make_tiles<<<1, 1024, 0, stream>>>(d_so, (int)nseg0, SEG_TILE, d_stiles);
+        if (nseg1) k_make_tiles<<<1, 1024, 0, stream>>>(d_so1, (int)nseg1, SEG_TILE1, d_stiles1);
         L.stop();
 
         // flat map (6m+1), level by level
@@ -683,34 +755,48 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         if (C.T > 0) {
             const unsigned grid = (unsigned)std::min<u64>((nchunk + 7) / 8, (u64)h->sms * L.blocks_per_sm);
             L.start(KIND_EXPAND, (double)(pt_offs[C.k1] - pt_offs[C.k0]) * (4.0 * (M - 1) + (Op::GATHER ? 0 : sizeof(W))) +
-                                     (double)C.T * (sizeof(K) + sizeof(Pay)));
-            k_expand<M, K, Pay, W, WT><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pr2,
-                                                                pj, (const W*)P[18],
-                                                             chunk_base, qchunk_base, d_pt_tiles, (const u32*)P[25],
-                                                             d_inst, d_sbase, d_qsbase,
-                                                             (u32)C.T, keys[0], pays[0]);
+                                     (double)C.T0 * (sizeof(K) + sizeof(Pay)) + (double)C.T1 * (4 + sizeof(Pay)));
+            k_expand<M, K, Pay, W, WT><<<grid, 256, 0, stream>>>(
+                d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pr2, pj, (const W*)P[18], chunk_base, qchunk_base,
+                d_pt_tiles, (const u32*)P[25], d_inst, d_sbase, d_qsbase, M >= 3 ? d_nmask : nullptr, (u32)C.T0,
+                keys[0], pays[0], (u32)C.T1, keys1[0], pays1[0]);
             L.stop();
         }
-        // records sort (6m+2): stable, each level by the bits of its prefix
-        if (C.T > 0 && npass > 0) {
+        // records sort (6m+2): stable, each level by the bits of its prefix; one
+        // sort per key class
+        if (C.T0 > 0 && npass0 > 0 && nseg0 > 0) {
             std::vector<u32> sbits_host;
-            if (!planned) sbits_host.assign(h_sbits, h_sbits + nseg);
-            SortSpace rs{d_so, (int)nseg, planned ? nullptr : &seg_sizes, d_rtiles, (u32*)R[8], (u32*)R[9],
-                         (u64*)h->st_multi.p, (double)C.T, (u32*)R[10], nrange_bound,
-                         planned ? nullptr : &sbits_host, C.T};
+            if (!planned) sbits_host.assign(h_sbits, h_sbits + nseg0);
+            SortSpace rs{d_so, (int)nseg0, planned ? nullptr : &seg_sizes0, d_rtiles, (u32*)R[8], (u32*)R[9],
+                         (u64*)h->st_multi.p, (double)C.T0, (u32*)R[10], nrb0, planned ? nullptr : &sbits_host, C.T0};
             const K keymask = ~(K(1) << (sizeof(K) * 8 - 1));  // all but the role bit
             sort_pairs<K, Pay>(L, rs, keys, pays, false, C.key_bits, keymask, KIND_HIST_RECORDS, KIND_SORT_RECORDS,
                                d_sbits);
         }
-        // segmented scan (6m+3)
-        if (C.T > 0) {
+        if (C.T1 > 0 && npass1 > 0 && nseg1 > 0) {
+            std::vector<u32> sbits_host;
+            if (!planned) sbits_host.assign(h_sbits + nseg0, h_sbits + nseg);
+            SortSpace rs{d_so1, (int)nseg1, planned ? nullptr : &seg_sizes1, d_rtiles, (u32*)R[8], (u32*)R[9],
+                         (u64*)h->st_multi.p, (double)C.T1, (u32*)R[10], nrb1, planned ? nullptr : &sbits_host, C.T1};
+            sort_pairs<u32, Pay>(L, rs, keys1, pays1, false, C.key_bits1, 0x7fffffffu, KIND_HIST_RECORDS,
+                                 KIND_SORT_RECORDS, d_sbits + nseg0);
+        }
+        // segmented scan (6m+3), per key class
+        if (C.T0 > 0 && nseg0 > 0) {
             const int li = L.lookback_index();
-            L.start(KIND_SEGSCAN, (double)C.T * (sizeof(K) + sizeof(Pay)) + (double)C.Tq * sizeof(Part) +
+            L.start(KIND_SEGSCAN, (double)C.T0 * (sizeof(K) + sizeof(Pay)) + (double)C.Tq * sizeof(Part) +
                                       (Op::GATHER ? (double)(pt_offs[C.k1] - pt_offs[C.k0]) * sizeof(W) : 0.0));
-            k_segscan<Op, K, SEG_THREADS, SEG_ITEMS><<<(unsigned)nts, SEG_THREADS, 0, stream>>>(
-                keys[0], keys[1], pays[0], pays[1], d_so, d_stiles, (int)nseg, d_sbits, (const W*)P[18], partial,
-                (u32)C.Tq,
-                (SegStatus<typename Op::Acc>*)h->st_seg.p, h->ctl, li);
+            k_segscan<Op, K, SEG_THREADS, SEG_ITEMS><<<(unsigned)nts0, SEG_THREADS, 0, stream>>>(
+                keys[0], keys[1], pays[0], pays[1], d_so, d_stiles, (int)nseg0, d_sbits, (const W*)P[18], partial,
+                (u32)C.Tq, (SegStatus<typename Op::Acc>*)h->st_seg.p, h->ctl, li);
+            L.stop();
+        }
+        if (C.T1 > 0 && nseg1 > 0) {
+            const int li = L.lookback_index();
+            L.start(KIND_SEGSCAN, (double)C.T1 * (4 + sizeof(Pay)));
+            k_segscan<Op, u32, SEG_THREADS, SEG_ITEMS1><<<(unsigned)nts1, SEG_THREADS, 0, stream>>>(
+                keys1[0], keys1[1], pays1[0], pays1[1], d_so1, d_stiles1, (int)nseg1, d_sbits + nseg0,
+                (const W*)P[18], partial, (u32)C.Tq, (SegStatus<typename Op::Acc>*)h->st_seg.p, h->ctl, li);
             L.stop();
         }
         // per-query reduction (replaces 6m+4 .. 6m+9)
@@ -725,8 +811,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         }
         T_all += C.T;
         Tq_all += C.Tq;
-        kb_all = std::max(kb_all, C.key_bits);
-        passes_all = std::max(passes_all, npass);
+        kb_all = std::max(kb_all, std::max(C.key_bits, C.key_bits1));
+        passes_all = std::max(passes_all, std::max(npass0, npass1));
         if (chunks.size() > 1 && !planned) {
             e = cudaStreamSynchronize(stream);  // the next chunk's host tables reuse the pinned area
             if (e != cudaSuccess) return cuda_fail(h, e, "record phase");
@@ -790,7 +876,9 @@ size_t record_bytes(int m, domagg_dtype wt, domagg_op op) {
     const size_t pb = 4;  // every payload is 32 bits (8-byte weights are gathered by position)
     (void)wt;
     const size_t part = (op == DOMAGG_MAX || op == DOMAGG_MIN || (op == DOMAGG_SUM && wt == DOMAGG_F32)) ? 4 : 8;
-    return 2 * kb + 2 * pb + part + 8;
+    // m >= 3 plans reserve both key classes (64- and 32-bit keys) at the full capacity
+    const size_t class1 = m >= 3 ? 2 * 4 + 2 * pb : 0;
+    return 2 * kb + 2 * pb + class1 + part + 8;
 }
 
 domagg_status check_common(domagg_ctx* h, int m, int64_t nD, int64_t nQ, domagg_dtype ct, domagg_dtype wt,
@@ -1040,8 +1128,10 @@ void plan_free(domagg_plan p) {
     if (!p) return;
     cudaSetDevice(p->device);
     for (auto& g : p->groups) {
-        for (auto& c : g.chunks)
+        for (auto& c : g.chunks) {
             if (c.d_slot_map) cudaFree(c.d_slot_map);
+            if (c.d_nmask) cudaFree(c.d_nmask);
+        }
         if (g.ctx) domagg_destroy(g.ctx);
     }
     delete p;
@@ -1098,44 +1188,66 @@ domagg_status plan_group(domagg_plan p, int m, const std::vector<Inst>& part, do
         cudaGetLastError();
     const int k = (int)part.size();
     auto scaled = [&](u32 v) { return (u64)std::ceil((double)v * (1.0 + headroom)); };
-    PlannedChunk c{0, 0, 0, 0, 0, 0, nullptr};
-    std::vector<std::vector<u32>> maps;
-    std::vector<u32> map;
+    PlannedChunk c;
+    // per chunk: slots of class 0, then of class 1 (their bound fits 31 bits,
+    // m >= 3), and the class-1 level masks of its instances
+    std::vector<std::vector<u32>> maps, masks;
+    std::vector<u32> map0, map1, mask;
     auto close = [&]() {
         c.T_cap += 1024;  // never 0: the chunk's launches are the same whatever the data
         c.Tq_cap += 1024;
+        c.nslot0 = (int)map0.size();
+        c.nslot = (int)(map0.size() + map1.size());
         G.chunks.push_back(c);
-        maps.push_back(map);
-        map.clear();
+        map0.insert(map0.end(), map1.begin(), map1.end());
+        maps.push_back(map0);
+        masks.push_back(mask);
+        map0.clear();
+        map1.clear();
+        mask.clear();
     };
     for (int i = 0; i < k; ++i) {
         const u64 Ti = scaled(measured[i].T), Tqi = scaled(measured[i].Tq);
         if (Ti + 1024 > cap_limit) return plan_fail(p, DOMAGG_ERR_UNSUPPORTED, "one instance exceeds a record chunk");
         if (c.k1 > c.k0 && c.T_cap + Ti + 1024 > cap_limit) {
             close();
-            c = PlannedChunk{i, i, 0, 0, 0, 0, nullptr};
+            c = PlannedChunk();
+            c.k0 = c.k1 = i;
         }
         c.k1 = i + 1;
         c.T_cap += Ti;
         c.Tq_cap += Tqi;
         const u32 nb = level_bound(m, (u64)part[i].nD + part[i].nQ);
-        for (u32 lv = 0; lv < nb; ++lv) map.push_back(((u32)(i - c.k0) << 5) | lv);
-        c.nslot += (int)nb;
-        const int kb = m == 1 ? 0 : (int)nb * (m - 1) - 1;  // (b-1) + b + ... over the m-1 ranks
-        if (kb > 63) return plan_fail(p, DOMAGG_ERR_UNSUPPORTED, "node keys of more than 63 bits (m = 4, large instance)");
-        c.key_bits = std::max(c.key_bits, kb);
+        u32 msk = 0;
+        for (u32 lv = 0; lv < nb; ++lv) {
+            // bound on the key bits of level lv: (b - 1 - lv) + b per further rank
+            const int bits = m == 1 ? 0 : (int)(nb - 1 - lv) + (int)nb * (m - 2);
+            if (bits > 63) return plan_fail(p, DOMAGG_ERR_UNSUPPORTED, "node keys of more than 63 bits (m = 4, large instance)");
+            const u32 slot = ((u32)(i - c.k0) << 5) | lv;
+            if (m >= 3 && bits <= 31) {
+                map1.push_back(slot);
+                msk |= 1u << lv;
+                c.key_bits1 = std::max(c.key_bits1, bits);
+            } else {
+                map0.push_back(slot);
+                c.key_bits = std::max(c.key_bits, bits);
+            }
+        }
+        mask.push_back(msk);
     }
     if (c.k1 > c.k0) close();
     for (size_t ci = 0; ci < G.chunks.size(); ++ci) {
         PlannedChunk& pc = G.chunks[ci];
         const size_t bytes = std::max<size_t>(maps[ci].size(), 1) * sizeof(u32);
-        if (cudaMalloc(&pc.d_slot_map, bytes) != cudaSuccess) {
+        const size_t mbytes = std::max<size_t>(masks[ci].size(), 1) * sizeof(u32);
+        if (cudaMalloc(&pc.d_slot_map, bytes) != cudaSuccess || cudaMalloc(&pc.d_nmask, mbytes) != cudaSuccess) {
             cudaGetLastError();
-            pc.d_slot_map = nullptr;
             return plan_fail(p, DOMAGG_ERR_OOM, "slot map");
         }
         if (!maps[ci].empty()) cudaMemcpy(pc.d_slot_map, maps[ci].data(), maps[ci].size() * sizeof(u32),
                                           cudaMemcpyHostToDevice);
+        if (!masks[ci].empty()) cudaMemcpy(pc.d_nmask, masks[ci].data(), masks[ci].size() * sizeof(u32),
+                                           cudaMemcpyHostToDevice);
     }
     G.margin = (u32)(G.chunks.size() + 6) * MAX_LAUNCHES;
     // the warm planned run: allocates the workspace at its final size (and

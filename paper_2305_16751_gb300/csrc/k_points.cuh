@@ -497,7 +497,9 @@ __global__ __launch_bounds__(256) void k_expand(
     const u32* __restrict__ pj, const W* __restrict__ pw, const u32* __restrict__ chunk_base, const u32* __restrict__ qchunk_base,
     const u32* __restrict__ pt_tiles, const u32* __restrict__ tile_excl,
     const Inst* __restrict__ inst, const u32* __restrict__ seg_base /*[k1-k0][LMAX]*/,
-    const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/, u32 n_rec, K* __restrict__ kout, Pay* __restrict__ pout) {
+    const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/, const u32* __restrict__ narrow_mask /*[k1-k0] or null*/,
+    u32 n_rec, K* __restrict__ kout, Pay* __restrict__ pout, u32 n_rec1, u32* __restrict__ kout1,
+    Pay* __restrict__ pout1) {
     const int lane = threadIdx.x & 31;
     const u32 lt = lanemask_lt();
     const u32 c_begin = __ldg(chunk_off + k0), c_end = __ldg(chunk_off + k1);
@@ -513,6 +515,8 @@ __global__ __launch_bounds__(256) void k_expand(
         const u32 nlev = levels_of<M>(I);
         const u32 b1 = M >= 3 ? I.b[1] : 0u, b2 = M >= 4 ? I.b[2] : 0u;
         const u32 tile = __ldg(pt_tiles + s) + (c - __ldg(chunk_off + s)) / CS_CHUNKS;  // the count scan's tile
+        // m >= 3: levels whose node keys fit 31 bits go to the 32-bit-key records (class 1)
+        const u32 nmask = narrow_mask ? __ldg(narrow_mask + (s - k0)) : 0u;
         // lane lv holds the bases of level lv (read once, shuffled below)
         const u32 my_all = (u32)lane < nlev ? __ldg(seg_base + (u64)(s - k0) * LMAX + lane) +
                                                   __ldg(chunk_base + (u64)c * LMAX + lane) +
@@ -598,14 +602,23 @@ __global__ __launch_bounds__(256) void k_expand(
                     const u32 spos = __shfl_sync(0xffffffffu, pos, src);
                     const Pay spay = __shfl_sync(0xffffffffu, pay, src);
                     const bool sq = (qb >> src) & 1u;
+                    const bool narrow = (nmask >> lv) & 1u;
+                    // one store of a record into its class's arrays
+                    auto put = [&](u32 at, K key, u32 r) {
+                        if (narrow) {
+                            if (at < n_rec1) {
+                                kout1[at] = sq ? ((u32)key | 0x80000000u) : (u32)key;
+                                pout1[at] = sq ? (Pay)(spay + r) : spay;
+                            }
+                        } else if (at < n_rec) {
+                            kout[at] = sq ? (key | role) : key;
+                            pout[at] = sq ? (Pay)(spay + r) : spay;
+                        }
+                    };
                     if (M == 3) {
                         if ((sb >> lane) & 1u) {
                             const u32 r = (u32)__popc(sb & lt);
-                            const K key = (skv << b1) | (K)node_of(scc, (u32)lane);
-                            if (spos + r < n_rec) {
-                                kout[spos + r] = sq ? (key | role) : key;
-                                pout[spos + r] = sq ? (Pay)(spay + r) : spay;
-                            }
+                            put(spos + r, (skv << b1) | (K)node_of(scc, (u32)lane), r);
                         }
                     } else {
                         // m = 4: the third rank's digits across the lanes, the
@@ -618,12 +631,8 @@ __global__ __launch_bounds__(256) void k_expand(
                             const u32 j1 = __ffs(r1) - 1;
                             if ((sb2 >> lane) & 1u) {
                                 const u32 r = t1 * c2 + (u32)__popc(sb2 & lt);
-                                const K key = ((((skv << b1) | (K)node_of(scc, j1)) << b2)) |
-                                              (K)node_of(see, (u32)lane);
-                                if (spos + r < n_rec) {
-                                    kout[spos + r] = sq ? (key | role) : key;
-                                    pout[spos + r] = sq ? (Pay)(spay + r) : spay;
-                                }
+                                put(spos + r,
+                                    ((((skv << b1) | (K)node_of(scc, j1)) << b2)) | (K)node_of(see, (u32)lane), r);
                             }
                         }
                     }

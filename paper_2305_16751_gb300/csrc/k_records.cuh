@@ -17,11 +17,16 @@ namespace domagg {
 // bases.  If the records exceed the reserved capacity, every segment is made
 // empty and ERR_CAPACITY is raised: the kernels after it then write nothing
 // outside their buffers (the chunk's outputs are undefined).
+//
+// Slots [0, nslot0) are class 0 (the key type of the pipeline), slots
+// [nslot0, nslot) class 1 (32-bit keys, m >= 3): each class has its own
+// record arrays, so its offsets (so: class 0's nslot0 + 1, then class 1's)
+// and the bases in sbase restart at 0; query slots run on across both.
 template <int M>
 __global__ __launch_bounds__(1024) void k_layout(const Inst* __restrict__ inst, int k0,
                                                  const u32* __restrict__ lvl_tot, const u32* __restrict__ qlvl_tot,
-                                                 const u32* __restrict__ slot_map, int nslot, u64 T_cap, u64 Tq_cap,
-                                                 u32* __restrict__ so, u32* __restrict__ sbits,
+                                                 const u32* __restrict__ slot_map, int nslot, int nslot0, u64 T_cap,
+                                                 u64 Tq_cap, u32* __restrict__ so, u32* __restrict__ sbits,
                                                  u32* __restrict__ sbase, u32* __restrict__ qsbase, Ctl* ctl) {
     __shared__ u64 w_a[32], w_q[32];
     __shared__ u64 carry_a, carry_q;
@@ -40,39 +45,49 @@ __global__ __launch_bounds__(1024) void k_layout(const Inst* __restrict__ inst, 
             if (M >= 2) bits = I.b[0] - 1u - lv + (M >= 3 ? I.b[1] : 0u) + (M >= 4 ? I.b[2] : 0u);
         }
     };
-    // totals first: the capacity decides between the layout and empty segments
-    u64 ta = 0, tq = 0;
+    // totals first (per class): the capacity decides between the layout and empty segments
+    u64 ta0 = 0, ta1 = 0, tq = 0;
     for (int g = tid; g < nslot; g += 1024) {
         u32 lv, srel, na, nq, bits;
         sizes(g, lv, srel, na, nq, bits);
-        ta += na;
+        if (g < nslot0) ta0 += na;
+        else ta1 += na;
         tq += nq;
     }
     for (int o = 16; o >= 1; o >>= 1) {
-        ta += __shfl_xor_sync(0xffffffffu, ta, o);
+        ta0 += __shfl_xor_sync(0xffffffffu, ta0, o);
+        ta1 += __shfl_xor_sync(0xffffffffu, ta1, o);
         tq += __shfl_xor_sync(0xffffffffu, tq, o);
     }
+    __shared__ u64 w_b[32];
     if (lane == 0) {
-        w_a[warp] = ta;
+        w_a[warp] = ta0;
+        w_b[warp] = ta1;
         w_q[warp] = tq;
     }
     __syncthreads();
     if (tid == 0) {
-        u64 A = 0, Q = 0;
+        u64 A = 0, B = 0, Q = 0;
         for (int w = 0; w < 32; ++w) {
             A += w_a[w];
+            B += w_b[w];
             Q += w_q[w];
         }
-        s_over = (A > T_cap || Q > Tq_cap) ? 1 : 0;
+        s_over = (A > T_cap || B > T_cap || Q > Tq_cap) ? 1 : 0;
         if (s_over) atomicOr(&ctl->error, ERR_CAPACITY);
         carry_a = carry_q = 0;
     }
     __syncthreads();
     const bool over = s_over != 0;
-    for (int base = 0; base < nslot; base += 1024) {
+    for (int cls = 0; cls < 2; ++cls) {
+    const int lo = cls == 0 ? 0 : nslot0, hi = cls == 0 ? nslot0 : nslot;
+    u32* so_c = cls == 0 ? so : so + nslot0 + 1;
+    if (tid == 0) carry_a = 0;  // each class's records restart at 0
+    __syncthreads();
+    for (int base = lo; base < hi; base += 1024) {
         const int g = base + tid;
         u32 lv = 0, srel = 0, na = 0, nq = 0, bits = 0;
-        if (g < nslot) sizes(g, lv, srel, na, nq, bits);
+        if (g < hi) sizes(g, lv, srel, na, nq, bits);
         if (over) na = nq = bits = 0;
         u64 ia = na, iq = nq;
         for (int o = 1; o < 32; o <<= 1) {
@@ -94,8 +109,8 @@ __global__ __launch_bounds__(1024) void k_layout(const Inst* __restrict__ inst, 
         }
         ea += ia - na;
         eq += iq - nq;
-        if (g < nslot) {
-            so[g] = (u32)ea;
+        if (g < hi) {
+            so_c[g - lo] = (u32)ea;
             sbits[g] = bits;
             sbase[(u64)srel * LMAX + lv] = (u32)ea;
             qsbase[(u64)srel * LMAX + lv] = (u32)eq;
@@ -107,7 +122,9 @@ __global__ __launch_bounds__(1024) void k_layout(const Inst* __restrict__ inst, 
         }
         __syncthreads();
     }
-    if (tid == 0) so[nslot] = (u32)carry_a;
+    if (tid == 0) so_c[hi - lo] = (u32)carry_a;
+    __syncthreads();
+    }
 }
 
 // Look-back status of the segmented scan.  The aggregate and the inclusive
