@@ -771,7 +771,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                          (u64*)h->st_multi.p, (double)C.T0, (u32*)R[10], nrb0, planned ? nullptr : &sbits_host, C.T0};
             const K keymask = ~(K(1) << (sizeof(K) * 8 - 1));  // all but the role bit
             sort_pairs<K, Pay>(L, rs, keys, pays, false, C.key_bits, keymask, KIND_HIST_RECORDS, KIND_SORT_RECORDS,
-                               d_sbits);
+                               d_sbits, true, M <= 2);
         }
         if (C.T1 > 0 && npass1 > 0 && nseg1 > 0) {
             std::vector<u32> sbits_host;

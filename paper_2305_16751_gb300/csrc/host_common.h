@@ -136,9 +136,11 @@ constexpr u32 POINT_TILE = 4096;
 // first seg_bits[s] bits only and its result is in buffer
 // ceil(seg_bits[s] / 8) % 2; the return value is then meaningless.
 // stable = false allows any order among equal digits (for sorts whose result
-// is only the sorted key sequence).
+// is only the sorted key sequence).  uniform: the keys' digits are spread
+// evenly (m <= 2 node keys), which lets the histogram skip its skew guard.
 template <typename K, typename V>
 int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool iota, int total_bits, K keymask,
-               int kind_hist, int kind_pass, const u32* seg_bits = nullptr, bool stable = true);
+               int kind_hist, int kind_pass, const u32* seg_bits = nullptr, bool stable = true,
+               bool uniform = false);
 
 }  // namespace domagg

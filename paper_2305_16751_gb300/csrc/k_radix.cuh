@@ -60,12 +60,15 @@ __device__ __forceinline__ TileLoc locate_range(u32 r, const u32* seg_off, const
 // segment); counts are aggregated per warp with match_any before the
 // shared-memory atomics, so skewed digits do not serialise.  With seg_bits,
 // a segment only counts the passes its keys have digits for (the others
-// skip it).
+// skip it).  With `uniform` (keys whose digits are spread evenly, as the
+// m <= 2 node keys: a prefix of a dense rank), digits with at least 5
+// significant bits are counted with plain shared atomics.
 template <typename K>
 __global__ __launch_bounds__(256) void k_radix_hist(const K* __restrict__ keys, const u32* __restrict__ seg_off,
                                                     const u32* __restrict__ range_off, int nseg, u32 range_items,
                                                     int npass, int shift0, K keymask, u32* __restrict__ hist,
-                                                    u32* __restrict__ range_cnt0, const u32* __restrict__ seg_bits) {
+                                                    u32* __restrict__ range_cnt0, const u32* __restrict__ seg_bits,
+                                                    int uniform) {
     extern __shared__ u32 sh_hist[];  // [8 warps][npass][RADIX]
     const u32 r = blockIdx.x;
     if (r >= __ldg(range_off + nseg)) return;
@@ -73,7 +76,10 @@ __global__ __launch_bounds__(256) void k_radix_hist(const K* __restrict__ keys, 
     for (int x = threadIdx.x; x < 8 * npass * RADIX; x += 256) sh_hist[x] = 0;
     __syncthreads();
     const TileLoc L = locate_range(r, seg_off, range_off, nseg, range_items);
-    const int np = seg_bits ? min(npass, (int)((__ldg(seg_bits + L.seg) + RADIX_BITS - 1) / RADIX_BITS)) : npass;
+    const int sbits = seg_bits ? (int)__ldg(seg_bits + L.seg) : 0;
+    const int np = seg_bits ? min(npass, (sbits + RADIX_BITS - 1) / RADIX_BITS) : npass;
+    // passes [0, spread) have digits with at least 5 significant bits
+    const int spread = (seg_bits && uniform && sbits >= 5) ? min(np, (sbits - 5) / RADIX_BITS + 1) : 0;
     u32* wh = sh_hist + warp * npass * RADIX;
     for (u32 base = L.start; base < L.end; base += 256u * 8u) {
         K kk[8];
@@ -85,8 +91,17 @@ __global__ __launch_bounds__(256) void k_radix_hist(const K* __restrict__ keys, 
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const bool valid = base + (u32)j * 256u + threadIdx.x < L.end;
-            for (int p = 0; p < np; ++p)
-                warp_hist_add(wh + p * RADIX, digit_of(kk[j], keymask, shift0 + p * RADIX_BITS), valid, lane);
+            for (int p = 0; p < np; ++p) {
+                const u32 d = digit_of(kk[j], keymask, shift0 + p * RADIX_BITS);
+                // a digit with at least 5 significant bits of a node key is spread
+                // out: plain shared atomics; otherwise (and for point keys, whose
+                // spread is unknown) lanes sharing lane 0's digit add together
+                if (p < spread) {
+                    if (valid) atomicAdd(wh + p * RADIX + d, 1u);
+                } else {
+                    warp_hist_add(wh + p * RADIX, d, valid, lane);
+                }
+            }
         }
     }
     __syncthreads();

@@ -38,7 +38,7 @@ static void launch_pass(Launcher& L, unsigned grid, size_t smem, K* kin, V* vin,
 
 template <typename K, typename V>
 int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool iota, int total_bits, K keymask,
-               int kind_hist, int kind_pass, const u32* seg_bits, bool stable) {
+               int kind_hist, int kind_pass, const u32* seg_bits, bool stable, bool uniform) {
     constexpr u32 TILE = ONESWEEP_THREADS * onesweep_items<K, V>();
     static_assert(TILE >= SORT_MIN_TILE, "status words are sized for SORT_MIN_TILE");
     const int npass = (total_bits + RADIX_BITS - 1) / RADIX_BITS;
@@ -91,7 +91,8 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
     cudaMemsetAsync(sp.hist, 0, hist_bytes, L.stream);
     L.start(kind_hist, sp.n_items * sizeof(K));
     k_radix_hist<K><<<(unsigned)nranges, 256, hist_smem, L.stream>>>(
-        keys[0], sp.seg_off, sp.tile_off, sp.nseg, range_items, npass, 0, keymask, sp.hist, range_base, seg_bits);
+        keys[0], sp.seg_off, sp.tile_off, sp.nseg, range_items, npass, 0, keymask, sp.hist, range_base, seg_bits,
+        uniform ? 1 : 0);
     L.stop();
     L.start(KIND_SMALL, 0.0);
     k_radix_offsets<<<sp.nseg * npass, RADIX, 0, L.stream>>>(sp.hist, sp.seg_off, npass, sp.digit_off);
@@ -141,8 +142,8 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
 }
 
 template int sort_pairs<u32, u32>(Launcher&, const SortSpace&, u32**, u32**, bool, int, u32, int, int,
-                                     const u32*, bool);
+                                     const u32*, bool, bool);
 template int sort_pairs<u64, u32>(Launcher&, const SortSpace&, u64**, u32**, bool, int, u64, int, int,
-                                     const u32*, bool);
+                                     const u32*, bool, bool);
 
 }  // namespace domagg
