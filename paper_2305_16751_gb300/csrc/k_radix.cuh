@@ -234,7 +234,7 @@ __global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_oneswee
     const K* __restrict__ kin, const V* __restrict__ vin, K* __restrict__ kout, V* __restrict__ vout,
     const u32* __restrict__ seg_off, const u32* __restrict__ range_off, int nseg, u32 range_items,
     const u32* __restrict__ seg_bits, const u32* __restrict__ range_base, const u32* __restrict__ digit_off,
-    int npass, int pass, int shift, K keymask, u64* status, Ctl* ctl, int launch_idx) {
+    int npass, int pass, int shift, K keymask, u64* status, Ctl* ctl, int launch_idx, int uniform) {
     constexpr int THREADS = ONESWEEP_THREADS, ITEMS = onesweep_items<K, V>();
     constexpr int TILE = THREADS * ITEMS, WARPS = THREADS / 32;
     typedef OnesweepSmem<K, V, TILE> SM;
@@ -303,6 +303,8 @@ __global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_oneswee
             for (int d = tid; d < RADIX; d += THREADS) s_run[d] = __ldg(range_base + (u64)r * RADIX + d);
         } else {
             u32* wh = s_whist + warp * (RADIX + 1);
+            // evenly spread digits (see k_radix_hist): plain shared atomics
+            const bool plain = uniform && seg_bits && (int)__ldg(seg_bits + L.seg) - shift >= 5;
             for (u32 base = L.start; base < L.end; base += (u32)THREADS * 8u) {
                 K kk[8];
 #pragma unroll
@@ -311,9 +313,15 @@ __global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_oneswee
                     kk[j] = x < L.end ? kin[x] : K(0);
                 }
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    warp_hist_add(wh, digit_of(kk[j], keymask, shift), base + (u32)j * THREADS + (u32)tid < L.end,
-                                  (u32)lane);
+                for (int j = 0; j < 8; ++j) {
+                    const u32 d = digit_of(kk[j], keymask, shift);
+                    const bool valid = base + (u32)j * THREADS + (u32)tid < L.end;
+                    if (plain) {
+                        if (valid) atomicAdd(&wh[d], 1u);
+                    } else {
+                        warp_hist_add(wh, d, valid, (u32)lane);
+                    }
+                }
             }
             __syncthreads();
             for (int d = tid; d < RADIX; d += THREADS) {

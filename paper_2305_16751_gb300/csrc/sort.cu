@@ -30,10 +30,10 @@ static u64 resident_ctas(size_t smem) {
 template <typename K, typename V, bool IOTA, bool STABLE>
 static void launch_pass(Launcher& L, unsigned grid, size_t smem, K* kin, V* vin, K* kout, V* vout,
                         const SortSpace& sp, u32 range_items, const u32* seg_bits, const u32* range_base, int npass,
-                        int p, K keymask, int li) {
+                        int p, K keymask, int li, bool uniform) {
     k_onesweep<K, V, IOTA, STABLE><<<grid, ONESWEEP_THREADS, smem, L.stream>>>(
         kin, vin, kout, vout, sp.seg_off, sp.tile_off, sp.nseg, range_items, seg_bits, range_base, sp.digit_off,
-        npass, p, p * RADIX_BITS, keymask, sp.status, L.ctl, li);
+        npass, p, p * RADIX_BITS, keymask, sp.status, L.ctl, li, uniform ? 1 : 0);
 }
 
 template <typename K, typename V>
@@ -129,11 +129,11 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
         K *ki = keys[cur], *ko = keys[cur ^ 1];
         V *vi = vals[cur], *vo = vals[cur ^ 1];
         if (iota && p == 0) {
-            if (stable) launch_pass<K, V, true, true>(L, grid, smem, ki, vi, ko, vo, sp, range_items, seg_bits, rb, npass, p, keymask, li);
-            else launch_pass<K, V, true, false>(L, grid, smem, ki, vi, ko, vo, sp, range_items, seg_bits, rb, npass, p, keymask, li);
+            if (stable) launch_pass<K, V, true, true>(L, grid, smem, ki, vi, ko, vo, sp, range_items, seg_bits, rb, npass, p, keymask, li, uniform);
+            else launch_pass<K, V, true, false>(L, grid, smem, ki, vi, ko, vo, sp, range_items, seg_bits, rb, npass, p, keymask, li, uniform);
         } else {
-            if (stable) launch_pass<K, V, false, true>(L, grid, smem, ki, vi, ko, vo, sp, range_items, seg_bits, rb, npass, p, keymask, li);
-            else launch_pass<K, V, false, false>(L, grid, smem, ki, vi, ko, vo, sp, range_items, seg_bits, rb, npass, p, keymask, li);
+            if (stable) launch_pass<K, V, false, true>(L, grid, smem, ki, vi, ko, vo, sp, range_items, seg_bits, rb, npass, p, keymask, li, uniform);
+            else launch_pass<K, V, false, false>(L, grid, smem, ki, vi, ko, vo, sp, range_items, seg_bits, rb, npass, p, keymask, li, uniform);
         }
         L.stop();
         cur ^= 1;
