@@ -505,54 +505,83 @@ __global__ __launch_bounds__(256) void k_expand(
     const u32 c_begin = __ldg(chunk_off + k0), c_end = __ldg(chunk_off + k1);
     const u32 warps = (gridDim.x * blockDim.x) >> 5;
     const K role = K(1) << (sizeof(K) * 8 - 1);
-    for (u32 c = c_begin + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); c < c_end; c += warps) {
-        const int s = upper_index(chunk_off, k + 1, c);
-        const Inst& I = inst[s];
-        const u32 ps = __ldg(pt_offs + s), pe = __ldg(pt_offs + s + 1);
-        const u32 p = ps + (c - __ldg(chunk_off + s)) * 32u + (u32)lane;
-        const bool valid = p < pe;
+    // a warp's chunk: what its lanes read before writing records
+    struct Chunk {
+        u32 c, ps, p, nlev, b1, b2, nmask, my_all, my_q, a, cc, ee, bits0, bits1, bits2, c1;
+        int s;
+        bool q;
+        Pay w;
+    };
+    auto load = [&](u32 c) {
+        Chunk X;
+        X.c = c;
+        X.s = upper_index(chunk_off, k + 1, c);
+        const Inst& I = inst[X.s];
+        X.ps = __ldg(pt_offs + X.s);
+        const u32 pe = __ldg(pt_offs + X.s + 1);
+        X.p = X.ps + (c - __ldg(chunk_off + X.s)) * 32u + (u32)lane;
+        const bool valid = X.p < pe;
         const u32 nQ = I.nQ;
-        const u32 nlev = levels_of<M>(I);
-        const u32 b1 = M >= 3 ? I.b[1] : 0u, b2 = M >= 4 ? I.b[2] : 0u;
-        const u32 tile = __ldg(pt_tiles + s) + (c - __ldg(chunk_off + s)) / CS_CHUNKS;  // the count scan's tile
+        X.nlev = levels_of<M>(I);
+        X.b1 = M >= 3 ? I.b[1] : 0u;
+        X.b2 = M >= 4 ? I.b[2] : 0u;
+        const u32 tile = __ldg(pt_tiles + X.s) + (c - __ldg(chunk_off + X.s)) / CS_CHUNKS;  // the count scan's tile
         // m >= 3: levels whose node keys fit 31 bits go to the 32-bit-key records (class 1)
-        const u32 nmask = narrow_mask ? __ldg(narrow_mask + (s - k0)) : 0u;
+        X.nmask = narrow_mask ? __ldg(narrow_mask + (X.s - k0)) : 0u;
         // lane lv holds the bases of level lv (read once, shuffled below)
-        const u32 my_all = (u32)lane < nlev ? __ldg(seg_base + (u64)(s - k0) * LMAX + lane) +
-                                                  __ldg(chunk_base + (u64)c * LMAX + lane) +
-                                                  __ldg(tile_excl + (u64)tile * CS_COUNTERS + lane)
-                                            : 0u;
-        const u32 my_q = (u32)lane < nlev ? __ldg(qseg_base + (u64)(s - k0) * LMAX + lane) +
-                                                __ldg(qchunk_base + (u64)c * LMAX + lane) +
-                                                __ldg(tile_excl + (u64)tile * CS_COUNTERS + LMAX + lane)
-                                          : 0u;
-        u32 a = 0, cc = 0, ee = 0, bits0 = 0, bits1 = 0, bits2 = 0, c1 = 1;
-        bool q = false;
-        Pay w = 0;
+        X.my_all = (u32)lane < X.nlev ? __ldg(seg_base + (u64)(X.s - k0) * LMAX + lane) +
+                                            __ldg(chunk_base + (u64)c * LMAX + lane) +
+                                            __ldg(tile_excl + (u64)tile * CS_COUNTERS + lane)
+                                      : 0u;
+        X.my_q = (u32)lane < X.nlev ? __ldg(qseg_base + (u64)(X.s - k0) * LMAX + lane) +
+                                          __ldg(qchunk_base + (u64)c * LMAX + lane) +
+                                          __ldg(tile_excl + (u64)tile * CS_COUNTERS + LMAX + lane)
+                                    : 0u;
+        X.a = X.cc = X.ee = X.bits0 = X.bits1 = X.bits2 = 0;
+        X.c1 = 1;
+        X.q = false;
+        X.w = 0;
         if (valid) {
             // coalesced reads in the order of the last coordinate (count scan)
             if (M >= 2) {
-                a = pr0[p];
-                q = (a & QUERY_BIT) != 0u;
-                a &= ~QUERY_BIT;
-                bits0 = (q ? a : ~a) & low_mask(I.b[0]);
+                X.a = pr0[X.p];
+                X.q = (X.a & QUERY_BIT) != 0u;
+                X.a &= ~QUERY_BIT;
+                X.bits0 = (X.q ? X.a : ~X.a) & low_mask(I.b[0]);
             } else {
-                q = pj[p] - ps < nQ;
-                bits0 = 1u;
+                X.q = pj[X.p] - X.ps < nQ;
+                X.bits0 = 1u;
             }
             if (M >= 3) {
-                cc = pr1[p];
-                bits1 = (q ? cc : ~cc) & low_mask(b1);
-                c1 = (u32)__popc(bits1);
+                X.cc = pr1[X.p];
+                X.bits1 = (X.q ? X.cc : ~X.cc) & low_mask(X.b1);
+                X.c1 = (u32)__popc(X.bits1);
             }
             if (M >= 4) {
-                ee = pr2[p];
-                bits2 = (q ? ee : ~ee) & low_mask(b2);
-                c1 *= (u32)__popc(bits2);
+                X.ee = pr2[X.p];
+                X.bits2 = (X.q ? X.ee : ~X.ee) & low_mask(X.b2);
+                X.c1 *= (u32)__popc(X.bits2);
             }
             // 8-byte weights stay in pw: the record carries their position
-            if (!q && WT != 3) w = WT == 1 ? (Pay)p : (Pay)pw[p];
+            if (!X.q && WT != 3) X.w = WT == 1 ? (Pay)X.p : (Pay)pw[X.p];
         }
+        return X;
+    };
+    // the next chunk's reads are issued before this chunk's records are written
+    u32 c = c_begin + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    Chunk nxt;
+    if (c < c_end) nxt = load(c);
+    for (; c < c_end; c += warps) {
+        const Chunk X = nxt;
+        if (c + warps < c_end) nxt = load(c + warps);
+        const u32 nlev = X.nlev, b1 = X.b1, b2 = X.b2, nmask = X.nmask, my_all = X.my_all, my_q = X.my_q;
+        const u32 a = X.a, cc = X.cc, ee = X.ee, bits1 = X.bits1, bits2 = X.bits2, c1 = X.c1;
+        u32 bits0 = X.bits0;
+        const bool q = X.q;
+        const Pay w = X.w;
+        (void)b2;
+        (void)ee;
+        (void)bits2;
         if (M >= 3 && c1 == 0) bits0 = 0;  // no records at all
         const u32 live = __ballot_sync(0xffffffffu, bits0 != 0u);
         if (live == 0u) continue;
