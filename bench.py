@@ -137,21 +137,23 @@ def profiled_traffic(bytes_per_launch: float):
 def cpu_baseline(p, seconds: float):
     """The oracle as it stands (brute force by the definition, OpenMP over
     queries) on a bounded sample of the workload's queries against all data:
-    a small probe, then one run sized to take about `seconds`."""
+    runs of growing samples until one takes about `seconds` (the last is
+    reported)."""
     import numpy as np
 
     import oracle
     threads = os.cpu_count() or 1
     rng = np.random.default_rng(0)
     k = min(p.Q.shape[0], 64)
-    t0 = time.perf_counter()
-    oracle.brute(p.D, p.Q[rng.choice(p.Q.shape[0], size=k, replace=False)], p.w, p.op, threads=threads)
-    probe = max(time.perf_counter() - t0, 1e-3)
-    k = int(min(p.Q.shape[0], max(k, k * seconds / probe)))
-    qi = rng.choice(p.Q.shape[0], size=k, replace=False)
-    t0 = time.perf_counter()
-    oracle.brute(p.D, p.Q[qi], p.w, p.op, threads=threads)
-    spent = time.perf_counter() - t0
+    spent = 0.0
+    for _ in range(4):  # grow the sample until one run takes at least half the target
+        qi = rng.choice(p.Q.shape[0], size=k, replace=False)
+        t0 = time.perf_counter()
+        oracle.brute(p.D, p.Q[qi], p.w, p.op, threads=threads)
+        spent = max(time.perf_counter() - t0, 1e-3)
+        if spent >= 0.5 * seconds or k == p.Q.shape[0]:
+            break
+        k = int(min(p.Q.shape[0], max(k + 1, k * seconds / spent)))
     return {"value": k / spent, "unit": "queries/s", "cores": threads, "kind": "oracle",
             "sample": f"{k} random queries of the workload, each against all {p.D.shape[0]} data points "
                       f"(brute force, {spent:.1f} s)", "seconds": spent}
