@@ -188,6 +188,8 @@ domagg_status domagg_batch(domagg_handle h, int k, const domagg_instance* inst,
  *
  * domagg_plan_status synchronises `stream` and returns (and clears) the first
  * device-side error recorded by the plan's runs, or DOMAGG_OK.
+ * domagg_plan_last_error(p) describes the plan's last error; with p = NULL,
+ * the last failed domagg_batch_plan of the calling thread.
  * domagg_plan_workspace_bytes returns the device bytes the plan holds.
  * domagg_plan_destroy waits for the device and frees the plan. */
 typedef struct domagg_plan_s* domagg_plan;

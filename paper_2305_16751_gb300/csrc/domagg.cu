@@ -358,7 +358,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     }
 
     Launcher L;
-    L.frozen = planned != nullptr;
+    L.frozen = h->frozen;  // the first planned run (not yet frozen) sets the kernel attributes
     L.stream = stream;
     L.ctl = h->ctl;
     L.timing = h->timing && !planned;
@@ -1137,6 +1137,10 @@ void plan_free(domagg_plan p) {
     delete p;
 }
 
+// The message of the last failed domagg_batch_plan of this thread (the plan
+// itself is freed): domagg_plan_last_error(NULL) returns it.
+thread_local std::string g_plan_create_error;
+
 domagg_status plan_fail(domagg_plan p, domagg_status st, const std::string& msg) {
     p->err = msg;
     return st;
@@ -1307,6 +1311,7 @@ domagg_status domagg_batch_plan(domagg_plan* out, int device, int k, const domag
             if (flush && !part.empty()) {
                 domagg_status st = plan_group(p, m, part, headroom, (cudaStream_t)stream);
                 if (st) {
+                    g_plan_create_error = "m = " + std::to_string(m) + ": " + p->err;
                     plan_free(p);
                     return st;
                 }
@@ -1348,7 +1353,7 @@ domagg_status domagg_plan_status(domagg_plan p, void* stream) {
     return first;
 }
 
-const char* domagg_plan_last_error(domagg_plan p) { return p ? p->err.c_str() : "null plan"; }
+const char* domagg_plan_last_error(domagg_plan p) { return p ? p->err.c_str() : g_plan_create_error.c_str(); }
 
 domagg_status domagg_plan_autotune(domagg_plan p, void* stream, double* best_ms) {
     if (!p) return DOMAGG_ERR_INVALID_ARG;

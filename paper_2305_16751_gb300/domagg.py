@@ -146,8 +146,7 @@ def domagg_sync_status(h, stream):
 
 def _check_plan(p, st: int):
     if st != 0:
-        msg = lib().domagg_plan_last_error(p).decode() if p else ""
-        raise DomaggError(st, msg)
+        raise DomaggError(st, lib().domagg_plan_last_error(p).decode())
 
 
 def domagg_batch_plan(device, k, inst_array, coord_dtype, weight_dtype, op, headroom, stream):

@@ -153,3 +153,35 @@ def test_plan_autotune_keeps_results():
             assert torch().equal(o, wv)
     finally:
         plan.close()
+
+
+def test_plan_with_both_key_classes_and_m4():
+    """Planned runs with m = 3 instances large enough that some levels need
+    64-bit node keys (the rest 32-bit), and m = 4 instances, replayed from a
+    graph with new contents."""
+    t = torch()
+    rng = np.random.default_rng(905)
+    host, levels = [], []
+    for m, nD, nQ, lv in ((3, 40000, 40000, 60000), (4, 3000, 2500, 50), (3, 500, 700, 20), (2, 30000, 30000, 9000)):
+        host.append(workloads.random_small(rng, m, nD, nQ, lv, "i32", "i64"))
+        levels.append(lv)
+    dev = [(to_dev(D), to_dev(Q), to_dev(w)) for D, Q, w in host]
+    plan = domagg.BatchPlan(dev, "sum", headroom=0.5)
+    try:
+        for (D, Q, w), o in zip(host, plan.outs):
+            qi = np.sort(rng.choice(Q.shape[0], min(Q.shape[0], 300), replace=False))
+            assert_matches_oracle(o.cpu().numpy(), D, Q, w, "sum", qidx=qi)
+        side = t.cuda.Stream()
+        side.wait_stream(t.cuda.current_stream())
+        g = t.cuda.CUDAGraph()
+        with t.cuda.stream(side):
+            with t.cuda.graph(g, stream=side):
+                plan.run()
+        host = _refill(rng, dev, host, levels, "i64")
+        g.replay()
+        plan.status()
+        for (D, Q, w), o in zip(host, plan.outs):
+            qi = np.sort(rng.choice(Q.shape[0], min(Q.shape[0], 300), replace=False))
+            assert_matches_oracle(o.cpu().numpy(), D, Q, w, "sum", qidx=qi)
+    finally:
+        plan.close()
