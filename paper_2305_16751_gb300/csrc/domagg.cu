@@ -339,22 +339,20 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     const size_t ctl_pos = (lvl_pos + 2 * sizeof(u32) * k * LMAX + 63) & ~(size_t)63;  // control block (read back)
     char* hp = nullptr;
     if (!planned) {
-    {
         domagg_status st = grow_pinned(h, ctl_pos + sizeof(Ctl) + 64);
         if (st) return st;
-    }
-    hp = (char*)h->h_pin;
-    memcpy(hp, inst.data(), sizeof(Inst) * k);
-    memcpy(hp + sizeof(Inst) * k, pt_offs.data(), sizeof(u32) * (k + 1));
-    memcpy(hp + sizeof(Inst) * k + sizeof(u32) * (k + 1), q_offs.data(), sizeof(u32) * (k + 1));
-    memcpy(hp + sizeof(Inst) * k + 2 * sizeof(u32) * (k + 1), chunk_off.data(), sizeof(u32) * (k + 1));
-    cudaMemcpyAsync(d_inst, hp, sizeof(Inst) * k, cudaMemcpyHostToDevice, stream);
-    cudaMemcpyAsync(d_pt_offs, hp + sizeof(Inst) * k, sizeof(u32) * (k + 1), cudaMemcpyHostToDevice, stream);
-    cudaMemcpyAsync(d_q_offs, hp + sizeof(Inst) * k + sizeof(u32) * (k + 1), sizeof(u32) * (k + 1),
-                    cudaMemcpyHostToDevice, stream);
-    cudaMemcpyAsync(d_chunk_off, hp + sizeof(Inst) * k + 2 * sizeof(u32) * (k + 1), sizeof(u32) * (k + 1),
-                    cudaMemcpyHostToDevice, stream);
-    maybe_reset_epochs(h, stream);
+        hp = (char*)h->h_pin;
+        memcpy(hp, inst.data(), sizeof(Inst) * k);
+        memcpy(hp + sizeof(Inst) * k, pt_offs.data(), sizeof(u32) * (k + 1));
+        memcpy(hp + sizeof(Inst) * k + sizeof(u32) * (k + 1), q_offs.data(), sizeof(u32) * (k + 1));
+        memcpy(hp + sizeof(Inst) * k + 2 * sizeof(u32) * (k + 1), chunk_off.data(), sizeof(u32) * (k + 1));
+        cudaMemcpyAsync(d_inst, hp, sizeof(Inst) * k, cudaMemcpyHostToDevice, stream);
+        cudaMemcpyAsync(d_pt_offs, hp + sizeof(Inst) * k, sizeof(u32) * (k + 1), cudaMemcpyHostToDevice, stream);
+        cudaMemcpyAsync(d_q_offs, hp + sizeof(Inst) * k + sizeof(u32) * (k + 1), sizeof(u32) * (k + 1),
+                        cudaMemcpyHostToDevice, stream);
+        cudaMemcpyAsync(d_chunk_off, hp + sizeof(Inst) * k + 2 * sizeof(u32) * (k + 1), sizeof(u32) * (k + 1),
+                        cudaMemcpyHostToDevice, stream);
+        maybe_reset_epochs(h, stream);
     }
 
     Launcher L;
@@ -514,99 +512,99 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             chunks.push_back(c);
         }
     } else {
-    // the one synchronisation: record counts and device errors
-    Inst* h_inst = (Inst*)hp;
-    u32* h_lvl = (u32*)(hp + lvl_pos);
-    Ctl* h_ctl = (Ctl*)(hp + ctl_pos);
-    L.start(KIND_D2H, 0.0);
-    cudaMemcpyAsync(h_inst, d_inst, sizeof(Inst) * k, cudaMemcpyDeviceToHost, stream);
-    cudaMemcpyAsync(h_lvl, lvl_tot, sizeof(u32) * k * LMAX, cudaMemcpyDeviceToHost, stream);
-    cudaMemcpyAsync(h_lvl + (size_t)k * LMAX, qlvl_tot, sizeof(u32) * k * LMAX, cudaMemcpyDeviceToHost, stream);
-    cudaMemcpyAsync(h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream);
-    L.stop();
-    e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "point phase");
-    if (h_ctl->error) {
-        const u32 bits = h_ctl->error;
-        cudaMemsetAsync(&h->ctl->error, 0, sizeof(u32), stream);
-        cudaStreamSynchronize(stream);
-        return device_error(h, bits);
-    }
-    // per instance: its levels, their record counts and sort-key bits
-    lvl.assign(h_lvl, h_lvl + (size_t)k * LMAX);
-    qlvl.assign(h_lvl + (size_t)k * LMAX, h_lvl + (size_t)2 * k * LMAX);
-    for (int s = 0; s < k; ++s) {
-        inst[s] = h_inst[s];
-        nlev[s] = inst[s].nQ + inst[s].nD == 0 ? 0u : (M == 1 ? 1u : inst[s].b[0]);
-        u64 T = 0, Tq = 0;
-        for (u32 lv = 0; lv < nlev[s]; ++lv) {
-            T += lvl[(size_t)s * LMAX + lv];
-            Tq += qlvl[(size_t)s * LMAX + lv];
+        // the one synchronisation: record counts and device errors
+        Inst* h_inst = (Inst*)hp;
+        u32* h_lvl = (u32*)(hp + lvl_pos);
+        Ctl* h_ctl = (Ctl*)(hp + ctl_pos);
+        L.start(KIND_D2H, 0.0);
+        cudaMemcpyAsync(h_inst, d_inst, sizeof(Inst) * k, cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(h_lvl, lvl_tot, sizeof(u32) * k * LMAX, cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(h_lvl + (size_t)k * LMAX, qlvl_tot, sizeof(u32) * k * LMAX, cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream);
+        L.stop();
+        e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "point phase");
+        if (h_ctl->error) {
+            const u32 bits = h_ctl->error;
+            cudaMemsetAsync(&h->ctl->error, 0, sizeof(u32), stream);
+            cudaStreamSynchronize(stream);
+            return device_error(h, bits);
         }
-        if (T >= (1ull << 32)) return fail(h, DOMAGG_ERR_UNSUPPORTED, "more than 2^32 flat-map records");
-        // the node key (and the role bit above it) must fit 64 bits
-        if (M >= 4 && nlev[s] > 0 && inst[s].b[0] - 1u + inst[s].b[1] + inst[s].b[2] > 63u)
-            return fail(h, DOMAGG_ERR_UNSUPPORTED, "node keys of more than 63 bits (m = 4, too many distinct values)");
-        inst[s].T = (u32)T;
-        inst[s].Tq = (u32)Tq;
-    }
-
-    // chunks of instances whose records fit one record workspace: below
-    // 2^32 records and ~60% of the free memory (plus the record workspace
-    // already held)
-    u64 chunk_cap = (1ull << 32) - 65536;
-    {
-        size_t free_b = 0, total_b = 0;
-        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-            const double per_rec = 2.0 * sizeof(K) + 2.0 * sizeof(Pay) + sizeof(Part) + 8.0;
-            double budget = std::max(0.6 * (double)free_b + (double)h->recs.cap, 2.0e9);
-            // a capped handle also caps the records of one chunk
-            if (h->max_ws) budget = std::min(budget, 0.5 * (double)(h->max_ws - std::min(h->max_ws, h->held() - h->recs.cap)));
-            chunk_cap = std::max<u64>(1, std::min<u64>(chunk_cap, (u64)(budget / per_rec)));
-        } else {
-            cudaGetLastError();
-        }
-    }
-    {
-        Chunk c;
+        // per instance: its levels, their record counts and sort-key bits
+        lvl.assign(h_lvl, h_lvl + (size_t)k * LMAX);
+        qlvl.assign(h_lvl + (size_t)k * LMAX, h_lvl + (size_t)2 * k * LMAX);
         for (int s = 0; s < k; ++s) {
-            const u64 Ts = inst[s].T;
-            if (c.k1 > c.k0 && c.T + Ts > chunk_cap) {
-                chunks.push_back(c);
-                c = Chunk();
-                c.k0 = c.k1 = s;
-            }
-            c.k1 = s + 1;
-            c.T += Ts;
-            c.Tq += inst[s].Tq;
-            c.nseg += nlev[s];
+            inst[s] = h_inst[s];
+            nlev[s] = inst[s].nQ + inst[s].nD == 0 ? 0u : (M == 1 ? 1u : inst[s].b[0]);
+            u64 T = 0, Tq = 0;
             for (u32 lv = 0; lv < nlev[s]; ++lv) {
-                const int bits = (int)level_bits(s, lv);
-                if (narrow_level(s, lv)) {
-                    c.nseg1 += 1;
-                    c.T1 += lvl[(size_t)s * LMAX + lv];
-                    c.key_bits1 = std::max(c.key_bits1, bits);
-                } else {
-                    c.nseg0 += 1;
-                    c.T0 += lvl[(size_t)s * LMAX + lv];
-                    c.key_bits = std::max(c.key_bits, bits);
+                T += lvl[(size_t)s * LMAX + lv];
+                Tq += qlvl[(size_t)s * LMAX + lv];
+            }
+            if (T >= (1ull << 32)) return fail(h, DOMAGG_ERR_UNSUPPORTED, "more than 2^32 flat-map records");
+            // the node key (and the role bit above it) must fit 64 bits
+            if (M >= 4 && nlev[s] > 0 && inst[s].b[0] - 1u + inst[s].b[1] + inst[s].b[2] > 63u)
+                return fail(h, DOMAGG_ERR_UNSUPPORTED, "node keys of more than 63 bits (m = 4, too many distinct values)");
+            inst[s].T = (u32)T;
+            inst[s].Tq = (u32)Tq;
+        }
+
+        // chunks of instances whose records fit one record workspace: below
+        // 2^32 records and ~60% of the free memory (plus the record workspace
+        // already held)
+        u64 chunk_cap = (1ull << 32) - 65536;
+        {
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+                const double per_rec = 2.0 * sizeof(K) + 2.0 * sizeof(Pay) + sizeof(Part) + 8.0;
+                double budget = std::max(0.6 * (double)free_b + (double)h->recs.cap, 2.0e9);
+                // a capped handle also caps the records of one chunk
+                if (h->max_ws) budget = std::min(budget, 0.5 * (double)(h->max_ws - std::min(h->max_ws, h->held() - h->recs.cap)));
+                chunk_cap = std::max<u64>(1, std::min<u64>(chunk_cap, (u64)(budget / per_rec)));
+            } else {
+                cudaGetLastError();
+            }
+        }
+        {
+            Chunk c;
+            for (int s = 0; s < k; ++s) {
+                const u64 Ts = inst[s].T;
+                if (c.k1 > c.k0 && c.T + Ts > chunk_cap) {
+                    chunks.push_back(c);
+                    c = Chunk();
+                    c.k0 = c.k1 = s;
+                }
+                c.k1 = s + 1;
+                c.T += Ts;
+                c.Tq += inst[s].Tq;
+                c.nseg += nlev[s];
+                for (u32 lv = 0; lv < nlev[s]; ++lv) {
+                    const int bits = (int)level_bits(s, lv);
+                    if (narrow_level(s, lv)) {
+                        c.nseg1 += 1;
+                        c.T1 += lvl[(size_t)s * LMAX + lv];
+                        c.key_bits1 = std::max(c.key_bits1, bits);
+                    } else {
+                        c.nseg0 += 1;
+                        c.T0 += lvl[(size_t)s * LMAX + lv];
+                        c.key_bits = std::max(c.key_bits, bits);
+                    }
                 }
             }
+            if (c.k1 > c.k0) chunks.push_back(c);
         }
-        if (c.k1 > c.k0) chunks.push_back(c);
-    }
-    base_pos.resize(chunks.size());
-    size_t pin_need = ctl_pos + sizeof(Ctl);
-    for (size_t ci = 0; ci < chunks.size(); ++ci) {
-        base_pos[ci] = (pin_need + 63) & ~(size_t)63;
-        pin_need = base_pos[ci] + sizeof(u32) * chunk_upload_words(chunks[ci]);
-    }
-    if (pin_need > h->h_pin_cap) {
-        // grow_pinned keeps nothing; the instance table is already in `inst`
-        domagg_status st = grow_pinned(h, pin_need);
-        if (st) return st;
-        hp = (char*)h->h_pin;
-    }
+        base_pos.resize(chunks.size());
+        size_t pin_need = ctl_pos + sizeof(Ctl);
+        for (size_t ci = 0; ci < chunks.size(); ++ci) {
+            base_pos[ci] = (pin_need + 63) & ~(size_t)63;
+            pin_need = base_pos[ci] + sizeof(u32) * chunk_upload_words(chunks[ci]);
+        }
+        if (pin_need > h->h_pin_cap) {
+            // grow_pinned keeps nothing; the instance table is already in `inst`
+            domagg_status st = grow_pinned(h, pin_need);
+            if (st) return st;
+            hp = (char*)h->h_pin;
+        }
     }
 
     u64 T_all = 0, Tq_all = 0;
