@@ -1061,6 +1061,23 @@ domagg_status domagg_backward(domagg_handle h, int m, const void* d_coords, int6
     return dispatch(h, m, inst, coord_dtype, DOMAGG_F32, DOMAGG_SUM, true, (cudaStream_t)stream);
 }
 
+domagg_status domagg_backward_ex(domagg_handle h, int m, const void* d_coords, int64_t nD, const void* q_coords,
+                                 int64_t nQ, domagg_dtype coord_dtype, const float* grad_out, float* grad_w,
+                                 uint32_t nonstrict_mask, void* stream) {
+    domagg_status st = check_common(h, m, nD, nQ, coord_dtype, DOMAGG_F32, DOMAGG_SUM);
+    if (st) return st;
+    if ((nonstrict_mask >> m) != 0u) return fail(h, DOMAGG_ERR_INVALID_ARG, "nonstrict_mask has bits >= m");
+    if ((nD > 0 && (!d_coords || !grad_w)) || (nQ > 0 && (!q_coords || !grad_out)))
+        return fail(h, DOMAGG_ERR_INVALID_ARG, "null pointer");
+    if (nD == 0) return DOMAGG_OK;
+    cudaSetDevice(h->device);
+    // as domagg_backward; a non-strict coordinate stays non-strict under the
+    // swap of roles and the negated keys (d_i <= q_i  <=>  -q_i <= -d_i)
+    std::vector<Inst> inst{make_inst(q_coords, nQ, d_coords, nD, grad_out, grad_w)};
+    inst[0].flags = nonstrict_mask;
+    return dispatch(h, m, inst, coord_dtype, DOMAGG_F32, DOMAGG_SUM, true, (cudaStream_t)stream);
+}
+
 domagg_status domagg_batch(domagg_handle h, int k, const domagg_instance* inst, domagg_dtype coord_dtype,
                            domagg_dtype weight_dtype, domagg_op op, void* stream) {
     if (!h) return DOMAGG_ERR_INVALID_ARG;

@@ -58,6 +58,7 @@ SIGNATURES = {
                           _int),
     "domagg_forward_host": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _vp], _int),
     "domagg_backward": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp], _int),
+    "domagg_backward_ex": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _vp, ctypes.c_uint32, _vp], _int),
     "domagg_batch": ([_vp, _int, ctypes.POINTER(domagg_instance), _int, _int, _int, _vp], _int),
     "domagg_batch_plan": ([ctypes.POINTER(_vp), _int, _int, ctypes.POINTER(domagg_instance), _int, _int, _int,
                            ctypes.c_double, _vp], _int),
@@ -311,15 +312,21 @@ def forward_host(D, Q, w=None, op: str = "sum", device: int = 0):
     return out
 
 
-def backward(D, Q, grad_out):
-    """grad_w[d] = sum of grad_out[q] over queries q with d < q."""
+def backward(D, Q, grad_out, nonstrict: int = 0):
+    """grad_w[d] = sum of grad_out[q] over queries q with d < q (bit i of
+    `nonstrict`: d_i <= q_i)."""
     torch = _torch()
     D, Q = D.contiguous(), Q.contiguous()
     g = grad_out.contiguous().to(torch.float32)
     grad_w = torch.empty(D.shape[0], dtype=torch.float32, device=D.device)
     dev = D.device.index or 0
-    domagg_backward(handle(dev), D.shape[1], _ptr(D), D.shape[0], _ptr(Q), Q.shape[0], _coord_dtype(D), _ptr(g),
-                    _ptr(grad_w), _stream(D.device))
+    if nonstrict:
+        _check(handle(dev), lib().domagg_backward_ex(handle(dev), D.shape[1], _ptr(D), D.shape[0], _ptr(Q),
+                                                     Q.shape[0], _coord_dtype(D), _ptr(g), _ptr(grad_w),
+                                                     nonstrict, _stream(D.device)))
+    else:
+        domagg_backward(handle(dev), D.shape[1], _ptr(D), D.shape[0], _ptr(Q), Q.shape[0], _coord_dtype(D),
+                        _ptr(g), _ptr(grad_w), _stream(D.device))
     return grad_w
 
 
@@ -331,14 +338,15 @@ def _autograd_function():
         (coordinates are piecewise constant: their gradient is None)."""
 
         @staticmethod
-        def forward(ctx, D, Q, w):
+        def forward(ctx, D, Q, w, nonstrict=0):
             ctx.save_for_backward(D, Q)
-            return forward(D, Q, w, "sum")
+            ctx.nonstrict = nonstrict
+            return forward(D, Q, w, "sum", nonstrict=nonstrict)
 
         @staticmethod
         def backward(ctx, grad_out):
             D, Q = ctx.saved_tensors
-            return None, None, backward(D, Q, grad_out)
+            return None, None, backward(D, Q, grad_out, ctx.nonstrict), None
 
     return DominanceSum
 
@@ -346,12 +354,13 @@ def _autograd_function():
 _DominanceSum = None
 
 
-def dominance_sum(D, Q, w):
-    """Autograd-enabled float32 dominance sum (backward recomputes the records)."""
+def dominance_sum(D, Q, w, nonstrict: int = 0):
+    """Autograd-enabled float32 dominance sum (backward recomputes the
+    records); bit i of `nonstrict` compares coordinate i as d_i <= q_i."""
     global _DominanceSum
     if _DominanceSum is None:
         _DominanceSum = _autograd_function()
-    return _DominanceSum.apply(D, Q, w)
+    return _DominanceSum.apply(D, Q, w, nonstrict)
 
 
 def _instances(problems, op: str):

@@ -156,3 +156,24 @@ def test_m4_in_a_batch_and_key_width_limit():
     with pytest.raises(domagg.DomaggError) as e:
         _forward(X[:n], X[n:], np.ones(n, np.int64), "sum")
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_nonstrict_backward_and_autograd(m):
+    """The adjoint with non-strict coordinates: grad_w[d] = sum of g[q] over
+    q with d <= q in the masked coordinates -- against the oracle run on the
+    negated, role-swapped problem (d <= q  <=>  -q <= -d)."""
+    rng = np.random.default_rng(800 + m)
+    for mask in range(1, 1 << m):
+        D, Q, _ = workloads.random_small(rng, m, 3000, 2500, 20, "i32", "f32")
+        g = rng.standard_normal(2500).astype(np.float32)
+        got = domagg.backward(to_dev(D), to_dev(Q), to_dev(g), nonstrict=mask).cpu().numpy()
+        want, S = oracle.brute(-Q, -D, g, "sum", nonstrict=mask)
+        assert_matches_oracle(got, -Q, -D, g, "sum", want=want, S=S)
+    D, Q, w = workloads.random_small(rng, m, 2000, 1500, 15, "i32", "f32")
+    c = rng.standard_normal(1500).astype(np.float32)
+    wd = to_dev(w).requires_grad_(True)
+    out = domagg.dominance_sum(to_dev(D), to_dev(Q), wd, (1 << m) - 1)
+    (out * to_dev(c)).sum().backward()
+    want, S = oracle.brute(-Q, -D, c, "sum", nonstrict=(1 << m) - 1)
+    assert_matches_oracle(wd.grad.cpu().numpy(), -Q, -D, c, "sum", want=want, S=S)
