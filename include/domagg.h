@@ -113,8 +113,17 @@ domagg_status domagg_forward(domagg_handle h, int m, const void* d_coords, int64
  *                   keyed by m node ids (n log^m n of them, data before
  *                   queries within a node tuple); m <= 3.  Same results,
  *                   more records: a cross-check of Lemma 2 at scale.
+ *                   DOMAGG_WAVELET: m <= 2 only (else DOMAGG_ERR_UNSUPPORTED).
+ *                   The levels of the first coordinate's rank (the P0/P1
+ *                   decomposition of Sec. 5) are evaluated on the points
+ *                   themselves, two levels per pass from the top: the points,
+ *                   kept in the order (rank prefix, last coordinate), get one
+ *                   segmented scan per level and a stable partition by the
+ *                   rank digit between passes.  No flat-map records are
+ *                   materialised; every pass moves 16 bytes per point.  Same
+ *                   results (the float32 sum within the same bound).
  * Other arguments, layouts and errors as domagg_forward. */
-typedef enum { DOMAGG_IMPROVED = 0, DOMAGG_BASIC = 1 } domagg_variant;
+typedef enum { DOMAGG_IMPROVED = 0, DOMAGG_BASIC = 1, DOMAGG_WAVELET = 2 } domagg_variant;
 domagg_status domagg_forward_ex(domagg_handle h, int m, const void* d_coords, int64_t nD,
                                 const void* q_coords, int64_t nQ, domagg_dtype coord_dtype,
                                 const void* d_weights, domagg_dtype weight_dtype, domagg_op op,

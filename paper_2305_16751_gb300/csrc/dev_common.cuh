@@ -58,6 +58,9 @@ struct Inst {
 // The last of the M coordinates is not stored but constant (the basic
 // variant of Sec. 4 run as the Sec. 5 pipeline with one more coordinate).
 constexpr u32 FLAG_VIRTUAL_LAST = 1u << 8;
+// Inst::flags: evaluate the levels of the first coordinate one by one on the
+// points (the level-wise formulation, m <= 2) instead of expanding records
+constexpr u32 FLAG_WAVELET = 1u << 9;
 
 // ---------------------------------------------------------------------
 // decoupled look-back status words: [63:34] epoch, [33:32] flag, [31:0] value

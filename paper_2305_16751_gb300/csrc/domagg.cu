@@ -20,6 +20,7 @@
 #include "k_points.cuh"
 #include "k_radix.cuh"
 #include "k_records.cuh"
+#include "k_wavelet.cuh"
 
 using namespace domagg;
 
@@ -61,6 +62,7 @@ struct domagg_ctx {
     size_t max_ws = 0;
     Ctl* ctl = nullptr;
     DevBuf pts, recs, st_multi, st_seg, stage;
+    DevBuf st_wv;  // look-back records of the level-wise passes (their own layout)
     void* h_pin = nullptr;
     size_t h_pin_cap = 0;
     std::string err;
@@ -79,7 +81,7 @@ struct domagg_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
     int ranges_per_cta = 4, blocks_per_sm = 16;  // launch shapes (domagg_plan_autotune)
 
-    size_t held() const { return pts.cap + recs.cap + st_multi.cap + st_seg.cap + stage.cap; }
+    size_t held() const { return pts.cap + recs.cap + st_multi.cap + st_seg.cap + stage.cap + st_wv.cap; }
 };
 
 namespace {
@@ -195,6 +197,7 @@ void maybe_reset_epochs(domagg_ctx* h, cudaStream_t s) {
     if (h->epoch_mirror + 8 * MAX_LAUNCHES < EPOCH_MASK) return;
     if (h->st_multi.p) cudaMemsetAsync(h->st_multi.p, 0, h->st_multi.cap, s);
     if (h->st_seg.p) cudaMemsetAsync(h->st_seg.p, 0, h->st_seg.cap, s);
+    if (h->st_wv.p) cudaMemsetAsync(h->st_wv.p, 0, h->st_wv.cap, s);
     cudaMemsetAsync(&h->ctl->epoch_base, 0, sizeof(u32), s);
     h->epoch_mirror = 0;
 }
@@ -219,6 +222,110 @@ struct PlannedChunk {
 // and neither synchronises, allocates, copies from the host nor changes a
 // kernel attribute (it may be captured in a CUDA graph); the point tables were
 // uploaded by the plan's earlier runs and are still in place.
+// The level-wise formulation (m <= 2, one instance), after the point
+// phase: the passes of k_wavelet_pass over the first coordinate's rank bits,
+// two levels per pass from the top (one in the last pass when the bit count
+// is odd).  One synchronisation reads the rank bits.
+template <int M, class Op>
+domagg_status run_wavelet(domagg_ctx* h, std::vector<Inst>& inst, Inst* d_inst, const u32* perm, const u32* r0,
+                          u64 N, Launcher& L, cudaStream_t stream, char* hp, size_t ctl_pos) {
+    typedef typename Op::Acc Acc;
+    if (inst.size() != 1 || !hp) return fail(h, DOMAGG_ERR_UNSUPPORTED, "the level-wise formulation takes one problem");
+    Inst* h_inst = (Inst*)hp;
+    Ctl* h_ctl = (Ctl*)(hp + ctl_pos);
+    L.start(KIND_D2H, 0.0);
+    cudaMemcpyAsync(h_inst, d_inst, sizeof(Inst), cudaMemcpyDeviceToHost, stream);
+    cudaMemcpyAsync(h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream);
+    L.stop();
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "point phase");
+    if (h_ctl->error) {
+        const u32 bits = h_ctl->error;
+        cudaMemsetAsync(&h->ctl->error, 0, sizeof(u32), stream);
+        cudaStreamSynchronize(stream);
+        return device_error(h, bits);
+    }
+    inst[0] = h_inst[0];
+    // m = 1: the rank is the role bit (every datum below every query)
+    u32 b = M == 1 ? 1u : inst[0].b[0];
+    if (b == 0) b = 1;  // a single rank: one pass, every output e
+    if (b > 31) return fail(h, DOMAGG_ERR_UNSUPPORTED, "ranks of more than 31 bits");
+    WvPasses ps;
+    ps.n = 0;
+    for (u32 top = b; top > 0;) {
+        const u32 w = top >= 2 ? 2u : 1u;
+        ps.shift[ps.n] = top - w;
+        ps.width[ps.n] = w;
+        ++ps.n;
+        top -= w;
+    }
+    const u64 ntiles = (N + WV_TILE - 1) / WV_TILE;
+    auto carve = [&](Carver& c, void** R) {
+        R[0] = c.take<WElem>(N);
+        R[1] = c.take<WElem>(N);
+        R[2] = c.take<u32>(WV_MAX_PASSES * 4);
+    };
+    void* R[3];
+    {
+        Carver c(nullptr);
+        carve(c, R);
+        domagg_status st = grow(h, h->recs, c.off);
+        if (st) return st;
+        Carver c2(h->recs.p);
+        carve(c2, R);
+        st = grow(h, h->st_wv, (size_t)ntiles * sizeof(WvStatus<Acc>), true);
+        if (st) return st;
+    }
+    WElem* el[2] = {(WElem*)R[0], (WElem*)R[1]};
+    u32* hist = (u32*)R[2];
+    maybe_reset_epochs(h, stream);
+    L.start(KIND_SMALL, 0.0);
+    k_begin<<<1, 64, 0, stream>>>(h->ctl);
+    L.stop();
+    h->epoch_mirror += MAX_LAUNCHES;
+    L.next_lookback = 0;
+    cudaMemsetAsync(hist, 0, sizeof(u32) * WV_MAX_PASSES * 4, stream);
+    L.start(KIND_SMALL, (double)N * 4);
+    k_wavelet_hist<M><<<(unsigned)((N + 4095) / 4096), 256, 0, stream>>>(r0, d_inst, (u32)N, ps, hist);
+    L.stop();
+    const double wbytes = Op::GATHER ? 8.0 : (std::is_same<Op, OpCount>::value ? 0.0 : 4.0);
+    const double obytes = (double)sizeof(typename Op::Out);
+    int cur = 0;
+    for (int p = 0; p < ps.n; ++p) {
+        const bool first = p == 0, last = p == ps.n - 1;
+        const double bytes = (first ? (double)N * (M == 1 ? 4.0 : 8.0) + (double)inst[0].nD * wbytes
+                                    : (double)N * sizeof(WElem)) +
+                             (last ? (double)inst[0].nQ * obytes : (double)N * sizeof(WElem));
+        const int li = L.lookback_index();
+        L.start(KIND_WAVELET, bytes);
+        auto* st = (WvStatus<Acc>*)h->st_wv.p;
+        if (ps.width[p] == 2)
+            k_wavelet_pass<Op, 2, M><<<(unsigned)ntiles, WV_THREADS, 0, stream>>>(
+                el[cur], el[cur ^ 1], perm, r0, d_inst, (u32)N, ps.shift[p], first, last, hist + 4 * p, st, h->ctl, li);
+        else
+            k_wavelet_pass<Op, 1, M><<<(unsigned)ntiles, WV_THREADS, 0, stream>>>(
+                el[cur], el[cur ^ 1], perm, r0, d_inst, (u32)N, ps.shift[p], first, last, hist + 4 * p, st, h->ctl, li);
+        L.stop();
+        cur ^= 1;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "launch");
+    if (L.next_lookback > MAX_LAUNCHES) return fail(h, DOMAGG_ERR_UNSUPPORTED, "too many look-back launches");
+    domagg_stats& S = h->stats;
+    S.n_points = (int64_t)N;
+    S.n_records = 0;
+    S.n_query_records = 0;
+    S.m = M;
+    for (int i = 0; i < 3; ++i) {
+        S.rank_bits[i] = (i < M - 1) ? (int32_t)inst[0].b[i] : 0;
+        S.distinct[i] = (i < M - 1) ? (int64_t)inst[0].U[i] : 0;
+    }
+    S.record_key_bits = (int)b;
+    S.record_passes = ps.n;
+    S.workspace_bytes = (int64_t)h->held();
+    return DOMAGG_OK;
+}
+
 template <int M, class Op, bool F32>
 domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStream_t stream,
                   const std::vector<PlannedChunk>* planned = nullptr) {
@@ -437,7 +544,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         if (M >= 3) cudaStreamWaitEvent(h->aux[1], h->ev_fork, 0);
         perm = last_dim(chain(1));
         if (M >= 3) rank_dim(1, chain(2));
-        rank_dim(0, chain(0));
+        if (M >= 2) rank_dim(0, chain(0));
         if (M >= 4) rank_dim(2, chain(0));
         cudaEventRecord(h->ev_join[0], h->aux[0]);
         cudaStreamWaitEvent(stream, h->ev_join[0], 0);
@@ -450,6 +557,10 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         perm = last_dim(chain(0));
     }
     L.stream = stream;
+    if (inst[0].flags & FLAG_WAVELET) {
+        if constexpr (M <= 2) return run_wavelet<M, Op>(h, inst, d_inst, perm, r0, N, L, stream, hp, ctl_pos);
+        else return fail(h, DOMAGG_ERR_UNSUPPORTED, "the level-wise formulation takes m <= 2");
+    }
     // ---- count / offset scan of the flat map, per level
     {
         // perm, gathered ranks, ranks / index / weight written in order, weight gathered
@@ -955,7 +1066,7 @@ domagg_status domagg_destroy(domagg_handle h) {
     if (!h) return DOMAGG_ERR_INVALID_ARG;
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
-    for (DevBuf* b : {&h->pts, &h->recs, &h->st_multi, &h->st_seg, &h->stage})
+    for (DevBuf* b : {&h->pts, &h->recs, &h->st_multi, &h->st_seg, &h->stage, &h->st_wv})
         if (b->p) cudaFree(b->p);
     if (h->ctl) cudaFree(h->ctl);
     if (h->h_pin) cudaFreeHost(h->h_pin);
@@ -986,7 +1097,10 @@ domagg_status domagg_forward_ex(domagg_handle h, int m, const void* d_coords, in
                                 int64_t nQ, domagg_dtype coord_dtype, const void* d_weights, domagg_dtype weight_dtype,
                                 domagg_op op, uint32_t nonstrict_mask, domagg_variant variant, void* out,
                                 void* stream) {
-    if (variant != DOMAGG_IMPROVED && variant != DOMAGG_BASIC) return fail(h, DOMAGG_ERR_INVALID_ARG, "bad variant");
+    if (variant != DOMAGG_IMPROVED && variant != DOMAGG_BASIC && variant != DOMAGG_WAVELET)
+        return fail(h, DOMAGG_ERR_INVALID_ARG, "bad variant");
+    if (variant == DOMAGG_WAVELET && h && m > 2)
+        return fail(h, DOMAGG_ERR_UNSUPPORTED, "the level-wise formulation takes m <= 2");
     const int M = variant == DOMAGG_BASIC ? m + 1 : m;  // the pipeline's coordinates
     domagg_status st = check_common(h, M, nD, nQ, coord_dtype, weight_dtype, op);
     if (st) return variant == DOMAGG_BASIC && M > 4 ? fail(h, DOMAGG_ERR_UNSUPPORTED, "basic variant: m <= 3") : st;
@@ -1002,6 +1116,7 @@ domagg_status domagg_forward_ex(domagg_handle h, int m, const void* d_coords, in
     // constant last coordinate compared non-strictly puts every data record
     // of a node tuple before its queries
     if (variant == DOMAGG_BASIC) inst[0].flags |= FLAG_VIRTUAL_LAST | (1u << m);
+    if (variant == DOMAGG_WAVELET) inst[0].flags |= FLAG_WAVELET;
     return dispatch(h, M, inst, coord_dtype, weight_dtype, op, false, (cudaStream_t)stream);
 }
 
@@ -1503,7 +1618,7 @@ domagg_status domagg_timing_read(domagg_handle h, domagg_timing* out) {
 const char* domagg_timing_kind_name(int kind) {
     static const char* names[] = {"encode",  "hist_points",  "sort_points", "rank",     "count_scan",
                                   "expand",  "hist_records", "sort_records", "segscan", "reduce",
-                                  "small",   "h2d",          "d2h"};
+                                  "small",   "h2d",          "d2h",          "wavelet"};
     if (kind < 0 || kind >= (int)(sizeof(names) / sizeof(names[0]))) return "";
     return names[kind];
 }

@@ -27,6 +27,7 @@ enum Kind {
     KIND_SMALL,  // begin, tile maps, digit offsets
     KIND_H2D,
     KIND_D2H,
+    KIND_WAVELET,  // the level-wise passes
     KIND_COUNT_
 };
 

@@ -260,13 +260,14 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else None
 
 
-VARIANTS = {"improved": 0, "basic": 1}
+VARIANTS = {"improved": 0, "basic": 1, "wavelet": 2}
 
 
 def forward(D, Q, w=None, op: str = "sum", out=None, nonstrict: int = 0, variant: str = "improved"):
     """out[q] = F over w(d) for d < q (strict), computed on D's GPU.  Bit i
     of `nonstrict` compares coordinate i as d_i <= q_i; variant "basic" runs
-    the unimproved algorithm of Sec. 4 (m <= 2)."""
+    the unimproved algorithm of Sec. 4 (m <= 3), variant "wavelet" the
+    level-wise formulation of the first coordinate (m <= 2, no records)."""
     torch = _torch()
     if D.device.type != "cuda":
         raise ValueError("forward expects CUDA tensors (use forward_host for host buffers)")
