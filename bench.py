@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--batch-k", type=int, default=4096, help="instances of the batch workload")
     ap.add_argument("--only-batch", action="store_true", help="print the batch line alone (e.g. --batch-k 4096)")
     ap.add_argument("--no-autotune", action="store_true", help="planned batch without the launch-shape autotuner")
+    ap.add_argument("--variant", default="improved", choices=["improved", "wavelet"],
+                    help="formulation of the timed m=2 step: the Sec. 5 record pipeline (default) or the "
+                         "level-wise passes")
     return ap.parse_args()
 
 
@@ -116,14 +119,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def profiled_traffic(bytes_per_launch: float):
-    """DRAM bytes of one records radix pass: the committed ncu summary's
-    measured DRAM bytes per algorithmic byte (read + write of every key and
-    value a pass moves), times this run's algorithmic bytes per launch; None
-    if the kernel source changed since that capture."""
+def profiled_traffic(bytes_per_launch: float, source: str = "k_radix.cuh",
+                     profile: str = "k_onesweep_records_m2_n2e22.md"):
+    """DRAM bytes of one launch of the dominant kernel (a records radix pass,
+    or a level-wise pass): the committed ncu summary's measured DRAM bytes
+    per algorithmic byte, times this run's algorithmic bytes per launch;
+    None if the kernel source changed since that capture."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2305_16751_gb300", "csrc", "k_radix.cuh")
-    prof = os.path.join(ROOT, "profiles", "k_onesweep_records_m2_n2e22.md")
+    src = os.path.join(ROOT, "paper_2305_16751_gb300", "csrc", source)
+    prof = os.path.join(ROOT, "profiles", profile)
     try:
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         fields = dict(ln.split(":", 1) for ln in open(prof) if ln.startswith(("kernel_source", "traffic_per")))
@@ -260,6 +264,36 @@ def bench_variants(args, dev, stream, torch, domagg, workloads):
     return res
 
 
+def bench_wavelet(args, D, Q, w, out, dev, stream, torch, domagg):
+    """The level-wise formulation (variant "wavelet") on the headline
+    workload: no flat-map records, two rank levels per pass over 16-byte
+    points.  Its roofline: the passes' algorithmic bytes (16 B read + 16 B
+    written per point and pass; the first pass gathers ranks and weights, the
+    last writes outputs) over their summed device time."""
+    def step():
+        domagg.forward(D, Q, w, "sum", out=out, variant="wavelet")
+
+    t = timed_steps(step, max(3, args.steps // 2), 3, stream, torch)
+    ms = statistics.mean(t)
+    st = domagg.stats(dev.index or 0)
+    h = domagg.handle(dev.index or 0)
+    domagg.domagg_timing_enable(h, True)
+    domagg.domagg_timing_read(h)
+    step()
+    kinds = domagg.domagg_timing_read(h)
+    domagg.domagg_timing_enable(h, False)
+    wv = kinds.get("wavelet", {"ms": 0.0, "bytes": 0.0, "launches": 1})
+    peak, peak_src = peaks()
+    achieved = wv["bytes"] / max(wv["ms"], 1e-9) / 1e6
+    return {"value": Q.shape[0] / (ms / 1e3), "unit": "queries/s", "ms_per_step": ms,
+            "workload": WORKLOAD, "passes": st["record_passes"], "rank_bits": st["rank_bits"][0],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": peak_src, "kernel": "k_wavelet_pass (all passes)",
+                         "launch_ms": wv["ms"] / max(wv["launches"], 1),
+                         "bytes_per_launch": wv["bytes"] / max(wv["launches"], 1)},
+            "phase_ms": {k: v["ms"] for k, v in kinds.items() if v["ms"] > 0}}
+
+
 def job_throughput(local_ms: float, units_per_rank: int, world: int, device=None):
     """Whole-job throughput: every rank's units over the slowest rank's time
     (max over ranks of the timed region).  Returns (units/s, max ms)."""
@@ -323,7 +357,7 @@ def main():
     h = domagg.handle(local)
 
     def step():
-        domagg.forward(D, Q, w, "sum", out=out)
+        domagg.forward(D, Q, w, "sum", out=out, variant=args.variant)
 
     # timed region: forward steps, with per-launch events inside the library
     step()
@@ -344,7 +378,8 @@ def main():
     calls = args.warmup + args.steps
     launches = sum(v["launches"] for k, v in kinds.items() if k not in ("h2d", "d2h")) // calls * args.steps
     peak, peak_src = peaks()
-    dom = kinds.get("sort_records", {"ms": 0.0, "bytes": 0.0, "launches": 1})
+    dom_kind = "wavelet" if args.variant == "wavelet" else "sort_records"
+    dom = kinds.get(dom_kind, {"ms": 0.0, "bytes": 0.0, "launches": 1})
     achieved = dom["bytes"] / max(dom["ms"], 1e-9) / 1e6  # GB/s
     phase_ms = {k: v["ms"] / calls for k, v in kinds.items()}
 
@@ -356,9 +391,12 @@ def main():
                        "l2": f"inputs ({(p.D.nbytes + p.Q.nbytes + p.w.nbytes) >> 20} MB) and the records workspace "
                              f"({st['n_records'] * 16 >> 20} MB) exceed the 129 MB L2; no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(dom["bytes"] / max(dom["launches"], 1)),
+                         "frac": achieved / peak, "traffic": profiled_traffic(dom["bytes"] / max(dom["launches"], 1),
+                                                     *(("k_wavelet.cuh", "k_wavelet_pass_m2_n2e22.md")
+                                                       if args.variant == "wavelet" else ())),
                          "peak_source": peak_src,
-                         "kernel": "k_onesweep (records radix pass)",
+                         "kernel": "k_wavelet_pass (level-wise pass)" if args.variant == "wavelet"
+                         else "k_onesweep (records radix pass)",
                          "launch_ms": dom["ms"] / max(dom["launches"], 1),
                          "bytes_per_launch": dom["bytes"] / max(dom["launches"], 1)},
             "gpu_launches": launches,
@@ -396,6 +434,7 @@ def main():
                       "workload": "m3_nD2^21_nQ2^21_gmm_i32coords_i64w_sum", "records": st3["n_records"],
                       "record_passes": st3["record_passes"], "phase_ms": {k: v["ms"] for k, v in k3.items()}}
         del D3, Q3, w3, o3
+        line["wavelet"] = bench_wavelet(args, D, Q, w, out, dev, stream, torch, domagg)
         line["variants"] = bench_variants(args, dev, stream, torch, domagg, workloads)
         line["batch"] = bench_batch(args, dev, stream, torch, domagg, workloads)
         # end to end through the host-buffer entry point

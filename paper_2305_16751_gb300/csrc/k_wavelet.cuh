@@ -37,6 +37,10 @@ constexpr int WV_ITEMS = 8;
 constexpr u32 WV_TILE = WV_THREADS * WV_ITEMS;
 constexpr int WV_MAX_PASSES = 32;
 constexpr u32 WV_QUERY = 0x80000000u;  // in WElem::key: the point is a query
+#ifndef DOMAGG_WV_MIN_BLOCKS
+#define DOMAGG_WV_MIN_BLOCKS 3  // resident blocks per SM the register budget is cut for
+#endif
+constexpr int WV_MIN_BLOCKS = DOMAGG_WV_MIN_BLOCKS;
 
 // One point of the level-wise arrays (16 bytes, moved whole by every pass).
 struct alignas(16) WElem {
@@ -78,19 +82,14 @@ __device__ __forceinline__ typename Op::Acc wv_weight(const void* dw, u32 i) {
     }
 }
 
-// Trie channels of a D-bit digit: channel ch is trie node ch + 1 (heap
-// numbering, node 1 the root), at digit bit t = D - 1 - floor(log2(ch + 1)).
-// A digit c lies below node nd at bit t when (2^D + c) >> (t + 1) == nd.
-__host__ __device__ constexpr int wv_log2(int x) { return x <= 1 ? 0 : 1 + wv_log2(x >> 1); }
-template <int D>
-__device__ __forceinline__ bool wv_data_feeds(u32 c, int ch) {  // path turns left (bit 0)
-    const int t = D - 1 - wv_log2(ch + 1);
-    return (((1u << D) + c) >> (t + 1)) == (u32)(ch + 1) && ((c >> t) & 1u) == 0u;
-}
-template <int D>
-__device__ __forceinline__ bool wv_query_reads(u32 c, int ch) {  // path turns right (bit 1)
-    const int t = D - 1 - wv_log2(ch + 1);
-    return (((1u << D) + c) >> (t + 1)) == (u32)(ch + 1) && ((c >> t) & 1u) == 1u;
+// a[c] of a small register array without dynamic indexing
+template <int N>
+__device__ __forceinline__ u32 wv_sel(const u32 (&a)[N], u32 c) {
+    u32 v = a[0];
+#pragma unroll
+    for (int k = 1; k < N; ++k)
+        if (c == (u32)k) v = a[k];
+    return v;
 }
 
 // Look-back record of one tile: the tile's digit counts and, per channel,
@@ -150,12 +149,56 @@ __global__ __launch_bounds__(256) void k_wavelet_hist(const u32* __restrict__ r0
         if (s_h[i]) atomicAdd(hist + i, s_h[i]);
 }
 
+// Branch-free trie updates (D <= 2 levels per pass; the channels of trie
+// level t are [2^(D-1-t) - 1, 2^(D-t) - 1), selected by the digit's bits
+// above t).  feed: F the value v into the channel of every level where the
+// digit's bit is 0 (pass v = e for a query: F(x, e) = x exactly).  read: F
+// into acc the channel of every level where the digit's bit is 1.
+template <class Op, int D>
+__device__ __forceinline__ void wv_feed(typename Op::Acc (&s)[(1 << D) - 1], u32 c, typename Op::Acc v) {
+#pragma unroll
+    for (int t = D - 1; t >= 0; --t) {
+        const int lo = (1 << (D - 1 - t)) - 1, cnt = 1 << (D - 1 - t);
+        const u32 sel = c >> (t + 1);  // which channel of the level
+        typename Op::Acc cur = s[lo];
+#pragma unroll
+        for (int k = 1; k < cnt; ++k)
+            if (sel == (u32)k) cur = s[lo + k];
+        const typename Op::Acc nv = Op::F(cur, ((c >> t) & 1u) ? Op::e() : v);
+#pragma unroll
+        for (int k = 0; k < cnt; ++k)
+            if (sel == (u32)k) s[lo + k] = nv;
+    }
+}
+template <class Op, int D>
+__device__ __forceinline__ typename Op::Acc wv_read(const typename Op::Acc (&s)[(1 << D) - 1], u32 c,
+                                                    typename Op::Acc acc) {
+#pragma unroll
+    for (int t = D - 1; t >= 0; --t) {
+        const int lo = (1 << (D - 1 - t)) - 1, cnt = 1 << (D - 1 - t);
+        const u32 sel = c >> (t + 1);
+        typename Op::Acc cur = s[lo];
+#pragma unroll
+        for (int k = 1; k < cnt; ++k)
+            if (sel == (u32)k) cur = s[lo + k];
+        acc = Op::F(acc, ((c >> t) & 1u) ? cur : Op::e());
+    }
+    return acc;
+}
+
 // One pass over D levels.  first: the elements are built from the order of
 // the last coordinate (perm), the ranks and the weights; otherwise read from
 // `in`.  last: queries write their outputs; otherwise the tile is written,
 // partitioned by digit, to `out_el`.
+//
+// Within the tile every value is first computed without the carry from
+// earlier tiles (the channels of the group that continues into the tile):
+// warp 0 publishes the tile's aggregate and looks back while the other
+// warps compute, so a tile's inclusive prefix follows its aggregate by one
+// look-back only (short chains for the tiles after it); the carry is added
+// to the queries of that first group when the tile is written out.
 template <class Op, int D, int M>
-__global__ __launch_bounds__(WV_THREADS) void k_wavelet_pass(
+__global__ __launch_bounds__(WV_THREADS, WV_MIN_BLOCKS) void k_wavelet_pass(
     const WElem* __restrict__ in, WElem* __restrict__ out_el, const u32* __restrict__ perm,
     const u32* __restrict__ r0, const Inst* __restrict__ inst, u32 n, u32 shift, int first, int last,
     const u32* __restrict__ hist, WvStatus<typename Op::Acc>* status, Ctl* ctl, int launch_idx) {
@@ -167,8 +210,8 @@ __global__ __launch_bounds__(WV_THREADS) void k_wavelet_pass(
     __shared__ u32 s_whead[WARPS];
     __shared__ unsigned long long s_wcnt[WARPS];
     __shared__ Acc s_carry[NCH];
-    __shared__ u32 s_prev[NDIG], s_tstart[NDIG], s_dbase[NDIG];
-    __shared__ u32 s_info[2];
+    __shared__ u32 s_prev[NDIG], s_dbase[NDIG];
+    __shared__ u32 s_info[3];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         s_info[0] = atomicAdd(&ctl->tile_ctr[launch_idx], 1u);
@@ -224,6 +267,11 @@ __global__ __launch_bounds__(WV_THREADS) void k_wavelet_pass(
     if (has_prev && lx0 < cnt && !first)
         prevg = ((lx0 == 0 ? in[base - 1].key : s_el[wv_pidx(lx0 - 1)].x) & ~WV_QUERY) >> gshift;
     // (first pass: every rank is below 2^(shift + D), a single group)
+    if (threadIdx.x == 0) {
+        // the tile's first group continues from the previous tile unless it starts here
+        const u32 g0 = (it[0].x & ~WV_QUERY) >> gshift;
+        s_info[2] = (has_prev && g0 == prevg) ? (g0 | 0x80000000u) : 0u;  // bit 31: carry applies
+    }
 
     // thread aggregate: (group start seen, channels after the last start), digit counts
     bool head_any = false;
@@ -247,12 +295,8 @@ __global__ __launch_bounds__(WV_THREADS) void k_wavelet_pass(
                 for (int ch = 0; ch < NCH; ++ch) tsum[ch] = Op::e();
             }
             tcnt += 1ull << (16 * c);
-            if (!(it[i].x & WV_QUERY)) {
-                const Acc v = wv_acc<Acc>(((u64)it[i].w << 32) | it[i].z);
-#pragma unroll
-                for (int ch = 0; ch < NCH; ++ch)
-                    if (wv_data_feeds<D>(c, ch)) tsum[ch] = Op::F(tsum[ch], v);
-            }
+            const bool q = (it[i].x & WV_QUERY) != 0u;
+            wv_feed<Op, D>(tsum, c, q ? Op::e() : wv_acc<Acc>(((u64)it[i].w << 32) | it[i].z));
         }
     }
 
@@ -297,38 +341,47 @@ __global__ __launch_bounds__(WV_THREADS) void k_wavelet_pass(
         for (int ch = 0; ch < NCH; ++ch) lsum[ch] = Op::e();
     }
     __syncthreads();
-    // earlier warps
-    bool whead = false;
-    unsigned long long wcnt = 0;
-    Acc wsum[NCH];
+    // earlier warps, and the tile's digit counts
+    unsigned long long wcnt = 0, tc = 0;
+    Acc run[NCH];
 #pragma unroll
-    for (int ch = 0; ch < NCH; ++ch) wsum[ch] = Op::e();
-    for (int w = 0; w < warp; ++w) {
-        wcnt += s_wcnt[w];
-        if (s_whead[w]) {
-            whead = true;
+    for (int ch = 0; ch < NCH; ++ch) run[ch] = Op::e();
+    for (int w = 0; w < WARPS; ++w) {
+        const unsigned long long cw = s_wcnt[w];
+        tc += cw;
+        if (w < warp) {
+            wcnt += cw;
+            if (s_whead[w]) {
 #pragma unroll
-            for (int ch = 0; ch < NCH; ++ch) wsum[ch] = s_wsum[w][ch];
-        } else {
+                for (int ch = 0; ch < NCH; ++ch) run[ch] = s_wsum[w][ch];
+            } else {
 #pragma unroll
-            for (int ch = 0; ch < NCH; ++ch) wsum[ch] = Op::F(wsum[ch], s_wsum[w][ch]);
+                for (int ch = 0; ch < NCH; ++ch) run[ch] = Op::F(run[ch], s_wsum[w][ch]);
+            }
         }
     }
-    const bool xhead = lhead || whead;  // a group starts before me within the tile
-    Acc xsum[NCH];
+    // the running channels at my first item, without the carry of earlier tiles
 #pragma unroll
-    for (int ch = 0; ch < NCH; ++ch) xsum[ch] = lhead ? lsum[ch] : Op::F(wsum[ch], lsum[ch]);
+    for (int ch = 0; ch < NCH; ++ch) run[ch] = lhead ? lsum[ch] : Op::F(run[ch], lsum[ch]);
     unsigned long long xcnt = wcnt + lcnt;
+    u32 tstart[NDIG];
+    {
+        u32 a = 0;
+#pragma unroll
+        for (int c = 0; c < NDIG; ++c) {
+            tstart[c] = a;
+            a += (u32)(tc >> (16 * c)) & 0xffffu;
+        }
+    }
 
-    // ---- tile aggregate, look-back and publication (warp 0)
+    // ---- tile aggregate, published before anything waits (warp 0, lane 0)
+    WvStatus<Acc>* my = status + t;
+    bool thead = false;
+    Acc ts[NCH];
     if (warp == 0) {
-        bool thead = false;
-        unsigned long long tc = 0;
-        Acc ts[NCH];
 #pragma unroll
         for (int ch = 0; ch < NCH; ++ch) ts[ch] = Op::e();
         for (int w = 0; w < WARPS; ++w) {
-            tc += s_wcnt[w];
             if (s_whead[w]) {
                 thead = true;
 #pragma unroll
@@ -338,7 +391,19 @@ __global__ __launch_bounds__(WV_THREADS) void k_wavelet_pass(
                 for (int ch = 0; ch < NCH; ++ch) ts[ch] = Op::F(ts[ch], s_wsum[w][ch]);
             }
         }
-        WvStatus<Acc>* my = status + t;
+        if (lane == 0 && t > 0) {
+#pragma unroll
+            for (int c = 0; c < NDIG; ++c) my->cnt_agg[c] = (u32)(tc >> (16 * c)) & 0xffffu;
+#pragma unroll
+            for (int ch = 0; ch < NCH; ++ch) my->sum_agg[ch] = ts[ch];
+            my->has_head = thead ? 1u : 0u;
+            __threadfence();
+            st_store_release(&my->flag, ((epoch & EPOCH_MASK) << 2) | ST_AGG);
+        }
+    }
+
+    // ---- look-back (warp 0): counts of earlier tiles, carry of the first group
+    if (warp == 0) {
         u32 ecnt[NDIG];
         Acc esum[NCH];
 #pragma unroll
@@ -346,15 +411,6 @@ __global__ __launch_bounds__(WV_THREADS) void k_wavelet_pass(
 #pragma unroll
         for (int ch = 0; ch < NCH; ++ch) esum[ch] = Op::e();
         if (t > 0) {
-            if (lane == 0) {
-#pragma unroll
-                for (int c = 0; c < NDIG; ++c) my->cnt_agg[c] = (u32)(tc >> (16 * c)) & 0xffffu;
-#pragma unroll
-                for (int ch = 0; ch < NCH; ++ch) my->sum_agg[ch] = ts[ch];
-                my->has_head = thead ? 1u : 0u;
-                __threadfence();
-                st_store_release(&my->flag, ((epoch & EPOCH_MASK) << 2) | ST_AGG);
-            }
             bool sums_open = true;
             u32 u = t;  // tiles [u, t) are combined
             u32 spins = 0;
@@ -434,24 +490,13 @@ __global__ __launch_bounds__(WV_THREADS) void k_wavelet_pass(
             for (int ch = 0; ch < NCH; ++ch) my->sum_incl[ch] = thead ? ts[ch] : Op::F(esum[ch], ts[ch]);
             __threadfence();
             st_store_release(&my->flag, ((epoch & EPOCH_MASK) << 2) | ST_PREFIX);
-            u32 a = 0;
 #pragma unroll
-            for (int c = 0; c < NDIG; ++c) {
-                s_prev[c] = ecnt[c];
-                s_tstart[c] = a;
-                a += (u32)(tc >> (16 * c)) & 0xffffu;
-            }
+            for (int c = 0; c < NDIG; ++c) s_prev[c] = ecnt[c];
 #pragma unroll
             for (int ch = 0; ch < NCH; ++ch) s_carry[ch] = esum[ch];
         }
     }
-    __syncthreads();
-
-    // ---- second walk: queries receive, data feed; tile-local slots by digit
-    Acc run[NCH];
-#pragma unroll
-    for (int ch = 0; ch < NCH; ++ch) run[ch] = xhead ? xsum[ch] : Op::F(s_carry[ch], xsum[ch]);
-    typename Op::Out* outp = reinterpret_cast<typename Op::Out*>(inst[0].out);
+    // ---- second walk: queries receive, data feed; staged by digit
 #pragma unroll
     for (int i = 0; i < WV_ITEMS; ++i) {
         if (lx0 + i < cnt) {
@@ -461,40 +506,47 @@ __global__ __launch_bounds__(WV_THREADS) void k_wavelet_pass(
 #pragma unroll
                 for (int ch = 0; ch < NCH; ++ch) run[ch] = Op::e();
             }
-            Acc v = wv_acc<Acc>(((u64)it[i].w << 32) | it[i].z);
-            if (it[i].x & WV_QUERY) {
-#pragma unroll
-                for (int ch = 0; ch < NCH; ++ch)
-                    if (wv_query_reads<D>(c, ch)) v = Op::F(v, run[ch]);
-                if (last) {
-                    outp[it[i].y] = Op::to_out(v);
-                } else {
-                    const u64 b = wv_bits(v);
-                    it[i].z = (u32)b;
-                    it[i].w = (u32)(b >> 32);
-                }
-            } else {
-#pragma unroll
-                for (int ch = 0; ch < NCH; ++ch)
-                    if (wv_data_feeds<D>(c, ch)) run[ch] = Op::F(run[ch], v);
+            const bool q = (it[i].x & WV_QUERY) != 0u;
+            const Acc v = wv_acc<Acc>(((u64)it[i].w << 32) | it[i].z);
+            if (q) {
+                const u64 b = wv_bits(wv_read<Op, D>(run, c, v));
+                it[i].z = (u32)b;
+                it[i].w = (u32)(b >> 32);
             }
-            if (!last) {
-                const u32 slot = s_tstart[c] + ((u32)(xcnt >> (16 * c)) & 0xffffu);
-                xcnt += 1ull << (16 * c);
-                s_el[wv_pidx(slot)] = it[i];
-            }
+            wv_feed<Op, D>(run, c, q ? Op::e() : v);
+            const u32 slot = wv_sel<NDIG>(tstart, c) + ((u32)(xcnt >> (16 * c)) & 0xffffu);
+            xcnt += 1ull << (16 * c);
+            s_el[wv_pidx(slot)] = it[i];
         }
     }
-    if (last) return;
+
     __syncthreads();
-    // ---- write the tile out, partitioned by digit (runs of one digit are contiguous)
+
+    // ---- write the tile out, partitioned by digit (runs of one digit are
+    // contiguous); the queries of the continuing first group receive the carry
+    const u32 cont = s_info[2];
+    Acc carry[NCH];
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch) carry[ch] = s_carry[ch];
     uint4* dst = reinterpret_cast<uint4*>(out_el);
+    typename Op::Out* outp = reinterpret_cast<typename Op::Out*>(inst[0].out);
     for (int i = 0; i < WV_ITEMS; ++i) {
         const u32 x = (u32)i * WV_THREADS + threadIdx.x;
         if (x < cnt) {
-            const uint4 e = s_el[wv_pidx(x)];
-            const u32 c = ((e.x & ~WV_QUERY) >> shift) & DMASK;
-            __stcs(dst + s_dbase[c] + s_prev[c] + (x - s_tstart[c]), e);
+            uint4 e = s_el[wv_pidx(x)];
+            const u32 kn = e.x & ~WV_QUERY;
+            const u32 c = (kn >> shift) & DMASK;
+            const bool q = (e.x & WV_QUERY) != 0u;
+            if (q && (cont >> 31) && (kn >> gshift) == (cont & 0x7fffffffu)) {
+                const u64 b = wv_bits(wv_read<Op, D>(carry, c, wv_acc<Acc>(((u64)e.w << 32) | e.z)));
+                e.z = (u32)b;
+                e.w = (u32)(b >> 32);
+            }
+            if (last) {
+                if (q) outp[e.y] = Op::to_out(wv_acc<Acc>(((u64)e.w << 32) | e.z));
+            } else {
+                __stcs(dst + s_dbase[c] + s_prev[c] + (x - wv_sel<NDIG>(tstart, c)), e);
+            }
         }
     }
 }
