@@ -110,42 +110,48 @@ __device__ __forceinline__ u32 wv_pidx(u32 x) { return x + (x >> 3); }  // 16-by
 
 // Digit histogram of every pass (order-independent): hist[p * 4 + c] counts
 // the points whose rank has digit c at pass p.  For m = 1 the rank is the
-// role bit (data 0, query 1): every datum precedes every query in it.
+// role bit (data 0, query 1): every datum precedes every query in it.  A
+// thread counts its 16 points in 8-bit fields (one 32-bit word per pass,
+// the pass geometry held in registers), then warp sums go to shared memory.
+constexpr int WV_HIST_PASSES = 16;  // passes of width 2 cover ranks of up to 32 bits
 template <int M>
 __global__ __launch_bounds__(256) void k_wavelet_hist(const u32* __restrict__ r0, const Inst* __restrict__ inst,
                                                      u32 n, WvPasses ps, u32* __restrict__ hist) {
     constexpr int ITEMS = 16;
-    __shared__ u32 s_h[WV_MAX_PASSES * 4];
-    for (int i = threadIdx.x; i < WV_MAX_PASSES * 4; i += blockDim.x) s_h[i] = 0;
+    __shared__ u32 s_h[WV_HIST_PASSES * 4];
+    for (int i = threadIdx.x; i < WV_HIST_PASSES * 4; i += blockDim.x) s_h[i] = 0;
     __syncthreads();
+    const int np = ps.n < WV_HIST_PASSES ? ps.n : WV_HIST_PASSES;
+    u32 sh[WV_HIST_PASSES], mk[WV_HIST_PASSES], c[WV_HIST_PASSES];
+#pragma unroll
+    for (int p = 0; p < WV_HIST_PASSES; ++p) {
+        sh[p] = p < np ? ps.shift[p] : 0u;
+        mk[p] = p < np ? (1u << ps.width[p]) - 1u : 0u;
+        c[p] = 0;
+    }
     const u32 nQ = inst[0].nQ;
     const u32 j0 = blockIdx.x * (256u * ITEMS);
-    for (int p0 = 0; p0 < ps.n; p0 += 8) {
-        u64 c[8];
-#pragma unroll
-        for (int p = 0; p < 8; ++p) c[p] = 0;
-        for (int i = 0; i < ITEMS; ++i) {
-            const u32 j = j0 + (u32)i * 256u + threadIdx.x;
-            if (j >= n) break;
+#pragma unroll 4
+    for (int i = 0; i < ITEMS; ++i) {
+        const u32 j = j0 + (u32)i * 256u + threadIdx.x;
+        if (j < n) {
             const u32 r = M == 1 ? (j < nQ ? 1u : 0u) : r0[j];
 #pragma unroll
-            for (int p = 0; p < 8; ++p)
-                if (p0 + p < ps.n) {
-                    const u32 d = (r >> ps.shift[p0 + p]) & ((1u << ps.width[p0 + p]) - 1u);
-                    c[p] += 1ull << (16 * d);
-                }
+            for (int p = 0; p < WV_HIST_PASSES; ++p) c[p] += 1u << (8u * ((r >> sh[p]) & mk[p]));
         }
+    }
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-            if (p0 + p >= ps.n) break;
+    for (int p = 0; p < WV_HIST_PASSES; ++p) {
+        if (p < np) {
+#pragma unroll
             for (int d = 0; d < 4; ++d) {
-                const u32 v = __reduce_add_sync(0xffffffffu, (u32)(c[p] >> (16 * d)) & 0xffffu);
-                if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_h[(p0 + p) * 4 + d], v);
+                const u32 v = __reduce_add_sync(0xffffffffu, (c[p] >> (8 * d)) & 0xffu);
+                if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_h[p * 4 + d], v);
             }
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < ps.n * 4; i += blockDim.x)
+    for (int i = threadIdx.x; i < np * 4; i += blockDim.x)
         if (s_h[i]) atomicAdd(hist + i, s_h[i]);
 }
 
