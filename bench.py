@@ -416,6 +416,15 @@ def main():
         tfb = timed_steps(fb, max(3, args.steps // 2), 2, stream, torch)
         fb_ms = statistics.mean(tfb)
         line["fwd_bwd"] = {"value": p.Q.shape[0] / (fb_ms / 1e3), "unit": "queries/s", "ms_per_step": fb_ms}
+
+        def fbw():
+            o = domagg.dominance_sum(D, Q, wg, 0, "wavelet")
+            o.backward(grad_out)
+
+        tfbw = timed_steps(fbw, max(3, args.steps // 2), 2, stream, torch)
+        fbw_ms = statistics.mean(tfbw)
+        line["fwd_bwd_wavelet"] = {"value": p.Q.shape[0] / (fbw_ms / 1e3), "unit": "queries/s",
+                                   "ms_per_step": fbw_ms, "variant": "level-wise formulation"}
         del wg
         # m = 3 workload
         p3 = workloads.gaussian_mixture_i32(n=args.n3)

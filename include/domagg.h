@@ -150,11 +150,13 @@ domagg_status domagg_backward(domagg_handle h, int m, const void* d_coords, int6
 
 /* domagg_backward with coordinates compared non-strictly (bit i of
  * nonstrict_mask: d_i <= q_i), the adjoint of domagg_forward_ex's SUM with
- * the same mask (improved variant). */
+ * the same mask, computed by `variant`: DOMAGG_IMPROVED (the Sec. 5
+ * pipeline) or DOMAGG_WAVELET (the level-wise formulation, m <= 2);
+ * DOMAGG_BASIC returns DOMAGG_ERR_UNSUPPORTED. */
 domagg_status domagg_backward_ex(domagg_handle h, int m, const void* d_coords, int64_t nD,
                                  const void* q_coords, int64_t nQ, domagg_dtype coord_dtype,
                                  const float* grad_out, float* grad_w, uint32_t nonstrict_mask,
-                                 void* stream);
+                                 domagg_variant variant, void* stream);
 
 /* One problem of a batch (all pointers device memory, as in domagg_forward). */
 typedef struct {

@@ -1178,10 +1178,15 @@ domagg_status domagg_backward(domagg_handle h, int m, const void* d_coords, int6
 
 domagg_status domagg_backward_ex(domagg_handle h, int m, const void* d_coords, int64_t nD, const void* q_coords,
                                  int64_t nQ, domagg_dtype coord_dtype, const float* grad_out, float* grad_w,
-                                 uint32_t nonstrict_mask, void* stream) {
+                                 uint32_t nonstrict_mask, domagg_variant variant, void* stream) {
     domagg_status st = check_common(h, m, nD, nQ, coord_dtype, DOMAGG_F32, DOMAGG_SUM);
     if (st) return st;
     if ((nonstrict_mask >> m) != 0u) return fail(h, DOMAGG_ERR_INVALID_ARG, "nonstrict_mask has bits >= m");
+    if (variant != DOMAGG_IMPROVED && variant != DOMAGG_WAVELET)
+        return fail(h, variant == DOMAGG_BASIC ? DOMAGG_ERR_UNSUPPORTED : DOMAGG_ERR_INVALID_ARG,
+                    "backward variants: improved, wavelet");
+    if (variant == DOMAGG_WAVELET && m > 2)
+        return fail(h, DOMAGG_ERR_UNSUPPORTED, "the level-wise formulation takes m <= 2");
     if ((nD > 0 && (!d_coords || !grad_w)) || (nQ > 0 && (!q_coords || !grad_out)))
         return fail(h, DOMAGG_ERR_INVALID_ARG, "null pointer");
     if (nD == 0) return DOMAGG_OK;
@@ -1189,7 +1194,7 @@ domagg_status domagg_backward_ex(domagg_handle h, int m, const void* d_coords, i
     // as domagg_backward; a non-strict coordinate stays non-strict under the
     // swap of roles and the negated keys (d_i <= q_i  <=>  -q_i <= -d_i)
     std::vector<Inst> inst{make_inst(q_coords, nQ, d_coords, nD, grad_out, grad_w)};
-    inst[0].flags = nonstrict_mask;
+    inst[0].flags = nonstrict_mask | (variant == DOMAGG_WAVELET ? FLAG_WAVELET : 0u);
     return dispatch(h, m, inst, coord_dtype, DOMAGG_F32, DOMAGG_SUM, true, (cudaStream_t)stream);
 }
 

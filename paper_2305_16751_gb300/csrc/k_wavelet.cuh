@@ -33,7 +33,10 @@
 namespace domagg {
 
 constexpr int WV_THREADS = 256;
-constexpr int WV_ITEMS = 8;
+#ifndef DOMAGG_WV_ITEMS
+#define DOMAGG_WV_ITEMS 8  // points per thread of a tile (the tile is staged in static shared memory: <= 10)
+#endif
+constexpr int WV_ITEMS = DOMAGG_WV_ITEMS;
 constexpr u32 WV_TILE = WV_THREADS * WV_ITEMS;
 constexpr int WV_MAX_PASSES = 32;
 constexpr u32 WV_QUERY = 0x80000000u;  // in WElem::key: the point is a query

@@ -58,7 +58,7 @@ SIGNATURES = {
                           _int),
     "domagg_forward_host": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _vp], _int),
     "domagg_backward": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp], _int),
-    "domagg_backward_ex": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _vp, ctypes.c_uint32, _vp], _int),
+    "domagg_backward_ex": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _vp, ctypes.c_uint32, _int, _vp], _int),
     "domagg_batch": ([_vp, _int, ctypes.POINTER(domagg_instance), _int, _int, _int, _vp], _int),
     "domagg_batch_plan": ([ctypes.POINTER(_vp), _int, _int, ctypes.POINTER(domagg_instance), _int, _int, _int,
                            ctypes.c_double, _vp], _int),
@@ -313,18 +313,19 @@ def forward_host(D, Q, w=None, op: str = "sum", device: int = 0):
     return out
 
 
-def backward(D, Q, grad_out, nonstrict: int = 0):
+def backward(D, Q, grad_out, nonstrict: int = 0, variant: str = "improved"):
     """grad_w[d] = sum of grad_out[q] over queries q with d < q (bit i of
-    `nonstrict`: d_i <= q_i)."""
+    `nonstrict`: d_i <= q_i); variant "wavelet" (m <= 2) uses the level-wise
+    formulation."""
     torch = _torch()
     D, Q = D.contiguous(), Q.contiguous()
     g = grad_out.contiguous().to(torch.float32)
     grad_w = torch.empty(D.shape[0], dtype=torch.float32, device=D.device)
     dev = D.device.index or 0
-    if nonstrict:
+    if nonstrict or variant != "improved":
         _check(handle(dev), lib().domagg_backward_ex(handle(dev), D.shape[1], _ptr(D), D.shape[0], _ptr(Q),
                                                      Q.shape[0], _coord_dtype(D), _ptr(g), _ptr(grad_w),
-                                                     nonstrict, _stream(D.device)))
+                                                     nonstrict, VARIANTS[variant], _stream(D.device)))
     else:
         domagg_backward(handle(dev), D.shape[1], _ptr(D), D.shape[0], _ptr(Q), Q.shape[0], _coord_dtype(D),
                         _ptr(g), _ptr(grad_w), _stream(D.device))
@@ -339,15 +340,16 @@ def _autograd_function():
         (coordinates are piecewise constant: their gradient is None)."""
 
         @staticmethod
-        def forward(ctx, D, Q, w, nonstrict=0):
+        def forward(ctx, D, Q, w, nonstrict=0, variant="improved"):
             ctx.save_for_backward(D, Q)
             ctx.nonstrict = nonstrict
-            return forward(D, Q, w, "sum", nonstrict=nonstrict)
+            ctx.variant = variant
+            return forward(D, Q, w, "sum", nonstrict=nonstrict, variant=variant)
 
         @staticmethod
         def backward(ctx, grad_out):
             D, Q = ctx.saved_tensors
-            return None, None, backward(D, Q, grad_out, ctx.nonstrict), None
+            return None, None, backward(D, Q, grad_out, ctx.nonstrict, ctx.variant), None, None
 
     return DominanceSum
 
@@ -355,13 +357,13 @@ def _autograd_function():
 _DominanceSum = None
 
 
-def dominance_sum(D, Q, w, nonstrict: int = 0):
+def dominance_sum(D, Q, w, nonstrict: int = 0, variant: str = "improved"):
     """Autograd-enabled float32 dominance sum (backward recomputes the
     records); bit i of `nonstrict` compares coordinate i as d_i <= q_i."""
     global _DominanceSum
     if _DominanceSum is None:
         _DominanceSum = _autograd_function()
-    return _DominanceSum.apply(D, Q, w, nonstrict)
+    return _DominanceSum.apply(D, Q, w, nonstrict, variant)
 
 
 def _instances(problems, op: str):
