@@ -259,6 +259,7 @@ domagg_status run_wavelet(domagg_ctx* h, std::vector<Inst>& inst, Inst* d_inst, 
         ++ps.n;
         top -= w;
     }
+    if (ps.n > WV_HIST_PASSES) return fail(h, DOMAGG_ERR_UNSUPPORTED, "too many level-wise passes");
     const u64 ntiles = (N + WV_TILE - 1) / WV_TILE;
     auto carve = [&](Carver& c, void** R) {
         R[0] = c.take<WElem>(N);
