@@ -60,3 +60,33 @@ def test_no_oracle_in_the_product_path():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "domagg_oracle" not in text, f
+
+
+def _header_enum(name):
+    """{enumerator: value} of the typedef'd enum `name` in the header."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    m = re.search(r"typedef\s+enum\s*\{([^}]*)\}\s*" + name + r"\s*;", src, flags=re.S)
+    assert m, name
+    out, nxt = {}, 0
+    for item in [x.strip() for x in m.group(1).split(",") if x.strip()]:
+        k, _, v = item.partition("=")
+        nxt = int(v.strip()) if v.strip() else nxt
+        out[k.strip()] = nxt
+        nxt += 1
+    return out
+
+
+def test_binding_enums_match_the_header():
+    """The ctypes binding's op, dtype, variant and status codes are the
+    header's enumerators (the binding passes plain ints across the ABI)."""
+    from paper_2305_16751_gb300 import domagg
+    ops = _header_enum("domagg_op")
+    assert {k: ops["DOMAGG_" + k.upper()] for k in domagg.OPS} == domagg.OPS
+    dts = _header_enum("domagg_dtype")
+    assert {k: dts["DOMAGG_" + k.upper()] for k in domagg.DTYPES} == domagg.DTYPES
+    var = _header_enum("domagg_variant")
+    assert {k: var["DOMAGG_" + k.upper()] for k in domagg.VARIANTS} == domagg.VARIANTS
+    assert len(var) == len(domagg.VARIANTS)
+    st = _header_enum("domagg_status")
+    assert {v: "DOMAGG_" + ("ERR_" if v else "") + n for v, n in domagg.STATUS.items()} == \
+        {v: k for k, v in st.items()}
