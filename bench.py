@@ -288,6 +288,8 @@ def bench_wavelet(args, D, Q, w, out, dev, stream, torch, domagg):
     return {"value": Q.shape[0] / (ms / 1e3), "unit": "queries/s", "ms_per_step": ms,
             "workload": WORKLOAD, "passes": st["record_passes"], "rank_bits": st["rank_bits"][0],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": profiled_traffic(wv["bytes"] / max(wv["launches"], 1), "k_wavelet.cuh",
+                                                     "k_wavelet_pass_m2_n2e22.md"),
                          "peak_source": peak_src, "kernel": "k_wavelet_pass (all passes)",
                          "launch_ms": wv["ms"] / max(wv["launches"], 1),
                          "bytes_per_launch": wv["bytes"] / max(wv["launches"], 1)},
