@@ -139,3 +139,20 @@ def test_wavelet_backward_and_autograd(m):
     with pytest.raises(domagg.DomaggError) as e:
         domagg.backward(to_dev(D), to_dev(Q), to_dev(c), variant="basic")
     assert e.value.status == 2
+
+
+def test_wavelet_full_size_integer_results_equal_records_pipeline():
+    """At the full size (|D| = |Q| = 2^24, tied float coordinates) every one
+    of the 2^24 integer results of the level-wise formulation equals the
+    Sec. 5 record pipeline's: int64 sums, int32 max and the non-strict
+    count (each path is checked against the oracle elsewhere)."""
+    p = workloads.tied_floats(weights="i32")
+    D, Q = to_dev(p.D), to_dev(p.Q)
+    w64 = to_dev(p.w.astype(np.int64))
+    w32 = to_dev(p.w)
+    t = torch()
+    for w, op, ns in ((w64, "sum", 0), (w32, "max", 0), (None, "count", 3)):
+        a = domagg.forward(D, Q, w, op, nonstrict=ns, variant="wavelet")
+        b = domagg.forward(D, Q, w, op, nonstrict=ns, variant="improved")
+        t.cuda.synchronize()
+        assert t.equal(a, b), op
