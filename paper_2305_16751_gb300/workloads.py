@@ -155,8 +155,10 @@ def ecdf_samples(n: int = 2**20, m: int = 3, shift: float = 0.05, seed: int | No
 
 def random_small(rng: np.random.Generator, m: int, nD: int, nQ: int, levels: int, dtype: str,
                  weights: str) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
-    """Tiny random cases with heavy ties: every coordinate takes one of
-    `levels` values (negative ones included)."""
+    """Tiny random cases with heavy ties: every coordinate is an integer in
+    [-ceil(levels/2), ceil(levels/2)) -- `levels` values for even `levels`,
+    one more for odd -- as int32, or halved as float32 (negative values
+    included)."""
     vals = rng.integers(-levels // 2, levels - levels // 2, size=(nD + nQ, m))
     if dtype == "f32":
         pts = (vals.astype(np.float32) * np.float32(0.5))
