@@ -16,7 +16,7 @@ def _dense_ranks(x):
     return r.astype(np.int64)
 
 
-def _levelwise_sum(D, Q, w):
+def _levelwise(D, Q, w, F=np.add, e=0):
     nD, nQ = D.shape[0], Q.shape[0]
     P = np.concatenate([D, Q])
     isq = np.arange(nD + nQ) >= nD
@@ -25,36 +25,45 @@ def _levelwise_sum(D, Q, w):
     # order of the last coordinate, queries first on ties
     order = np.lexsort((~isq, P[:, -1]))
     key, q, idx = r[order], isq[order], order
-    val = np.where(q, 0, np.concatenate([w, np.zeros(nQ, w.dtype)])[order]).astype(np.int64)
-    acc = np.zeros(len(order), np.int64)
+    val = np.where(q, e, np.concatenate([w, np.zeros(nQ, w.dtype)])[order]).astype(np.int64)
+    acc = np.full(len(order), e, np.int64)
     top = b
     while top > 0:
         width = 2 if top >= 2 else 1
         s = top - width
         grp, dig = key >> (s + width), (key >> s) & ((1 << width) - 1)
         nch = (1 << width) - 1
-        run = np.zeros(nch, np.int64)
+        run = np.full(nch, e, np.int64)
         for i in range(len(key)):
             if i == 0 or grp[i] != grp[i - 1]:
-                run[:] = 0
+                run[:] = e
             for t in range(width - 1, -1, -1):
                 ch = ((1 << width) + int(dig[i])) >> (t + 1)  # trie node (heap numbering) at digit bit t
                 bit = (int(dig[i]) >> t) & 1
                 if q[i] and bit == 1:
-                    acc[i] += run[ch - 1]
+                    acc[i] = F(acc[i], run[ch - 1])
                 if not q[i] and bit == 0:
-                    run[ch - 1] += val[i]
+                    run[ch - 1] = F(run[ch - 1], val[i])
         perm = np.argsort(dig, kind="stable")
         key, q, val, acc, idx = key[perm], q[perm], val[perm], acc[perm], idx[perm]
         top -= width
-    out = np.zeros(nD + nQ, np.int64)
+    out = np.full(nD + nQ, e, np.int64)
     out[idx] = acc
     return out[nD:]
+
+
+def _levelwise_sum(D, Q, w):
+    return _levelwise(D, Q, w)
 
 
 def _brute(D, Q, w):
     less = np.all(D[None, :, :] < Q[:, None, :], axis=2)
     return (less * w[None, :]).sum(axis=1)
+
+
+def _brute_max(D, Q, w, e):
+    less = np.all(D[None, :, :] < Q[:, None, :], axis=2)
+    return np.where(less, w[None, :], e).max(axis=1, initial=e)
 
 
 def test_levelwise_model_equals_definition():
@@ -87,3 +96,18 @@ def test_levelwise_model_single_pass_cases():
     Q = np.array([[4, 4], [3, 9], [1, 1]])
     w = np.array([1, 10, 100, 1000])
     assert np.array_equal(_levelwise_sum(D, Q, w), [1111, 111, 1])
+
+
+def test_levelwise_model_max():
+    """The same passes with F = max (unit: the smallest int64) equal the
+    definition: only associativity, commutativity and the unit are used."""
+    rng = np.random.default_rng(2306)
+    e = np.iinfo(np.int64).min
+    for trial in range(80):
+        nD, nQ = int(rng.integers(0, 30)), int(rng.integers(1, 30))
+        levels = int(rng.integers(1, 50))
+        D = rng.integers(0, levels, size=(nD, 2))
+        Q = rng.integers(0, levels, size=(nQ, 2))
+        w = rng.integers(-99, 100, size=nD)
+        got = _levelwise(D, Q, w, F=np.maximum, e=e)
+        assert np.array_equal(got, _brute_max(D, Q, w, e)), trial
