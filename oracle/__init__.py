@@ -51,6 +51,10 @@ def _lib(plant: int = 0) -> ctypes.CDLL:
         lib.oracle_sscan_i64.restype = None
         lib.oracle_prefix_set.argtypes = [ctypes.c_uint64, i32, i32, vp, vp]
         lib.oracle_prefix_set.restype = i32
+        lib.oracle_sweep2.argtypes = [vp, i64, vp, i64, i32, vp, i32, i32, ctypes.c_uint32, vp, vp]
+        lib.oracle_sweep2.restype = i32
+        lib.oracle_sweep2_transpose.argtypes = [vp, i64, vp, i64, i32, vp, ctypes.c_uint32, vp, vp]
+        lib.oracle_sweep2_transpose.restype = i32
         lib.oracle_max_threads.argtypes = []
         lib.oracle_max_threads.restype = i32
         _libs[plant] = lib
@@ -119,6 +123,39 @@ def brute_transpose(D, Q, g, threads: int = 0, plant: int = 0):
     S = np.empty(D.shape[0], dtype=np.float64)
     st = _lib(plant).oracle_brute_transpose(m, _ptr(D), D.shape[0], _ptr(Q), Q.shape[0], ct,
                                             _ptr(g), _ptr(grad), _ptr(S), threads)
+    if st:
+        raise OracleError(st)
+    return grad, S
+
+
+def sweep2(D, Q, w, op: str, nonstrict: int = 0, plant: int = 0):
+    """m = 2 by a sweep over the last coordinate with a Fenwick tree over the
+    first coordinate's ranks (O(n log n); not the paper's algorithm, pinned to
+    brute force by the tests).  Returns (out, S) like brute()."""
+    D, ct = _coords(D, 2)
+    Q, ct2 = _coords(Q, 2)
+    if ct != ct2:
+        raise TypeError("D and Q must have the same dtype")
+    w, wt = _weights(w, D.shape[0], op)
+    out = _out_array(Q.shape[0], wt, op)
+    S = np.empty(Q.shape[0], dtype=np.float64)
+    st = _lib(plant).oracle_sweep2(_ptr(D), D.shape[0], _ptr(Q), Q.shape[0], ct, _ptr(w), wt, OPS[op],
+                                   nonstrict, _ptr(out), _ptr(S))
+    if st:
+        raise OracleError(st)
+    return out, S
+
+
+def sweep2_transpose(D, Q, g, nonstrict: int = 0, plant: int = 0):
+    """The adjoint for m = 2 by the sweep: grad[d] = sum of g[q] over queries q
+    that dominate d, and S[d] = sum of |g[q]| over the same set."""
+    D, ct = _coords(D, 2)
+    Q, _ = _coords(Q, 2)
+    g = np.ascontiguousarray(g, dtype=np.float32)
+    grad = np.empty(D.shape[0], dtype=np.float64)
+    S = np.empty(D.shape[0], dtype=np.float64)
+    st = _lib(plant).oracle_sweep2_transpose(_ptr(D), D.shape[0], _ptr(Q), Q.shape[0], ct, _ptr(g), nonstrict,
+                                             _ptr(grad), _ptr(S))
     if st:
         raise OracleError(st)
     return grad, S

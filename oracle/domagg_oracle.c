@@ -24,6 +24,12 @@
  *                         (instructions 6m+4, 6m+5) to collect each query.
  *   oracle_brute_transpose -- the adjoint with respect to the weights:
  *                         grad(d) = sum over { g(q) : q in Q, d < q }.
+ *   oracle_sweep2      -- m = 2 only: a sweep over the last coordinate with
+ *                         a Fenwick tree over the first coordinate's ranks,
+ *                         O(n log n), so full-size inputs can be checked on
+ *                         every query (oracle_sweep2_transpose: its adjoint).
+ *                         It is not the paper's algorithm; it is pinned to
+ *                         the brute force above by the tests.
  * plus the small primitives the tests pin against the paper's worked
  * examples: the segmented scan (Definition "Segmented scan", Sec. 2.2) and
  * the prefix sets P0/P1 (Sec. 3).
@@ -511,6 +517,172 @@ int oracle_sortscan(int m, const void* D, int64_t nD, const void* Q, int64_t nQ,
     free(A);
 #undef DQ_COORD
     return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* 4. m = 2 by a sweep over the last coordinate with a Fenwick tree    */
+/* ------------------------------------------------------------------ */
+
+/* A classical O(n log n) route to the definition of Sec. 1.2 for m = 2,
+ * independent of the paper's pipeline: visit the points in the order of the
+ * last coordinate; a data point is added to a Fenwick (binary indexed) tree
+ * at the dense rank of its first coordinate, and a query reads F over the
+ * tree's prefix of smaller ranks.  A tied last coordinate puts queries first
+ * (the query must not see a datum with an equal last coordinate); with
+ * bit 1 of `nonstrict` set (d_1 <= q_1) data go first.  With bit 0 set
+ * (d_0 <= q_0) the query reads the prefix up to and including its own rank.
+ * Sums of float32 weights are accumulated in double: the tree adds them in a
+ * different order than the definition does, so the result may differ from
+ * the exact sum by a few units of 2^-53 times sum |w|, far below the float32
+ * tolerance the tests use.  Integer sums wrap modulo 2^64 and max / min are
+ * exact, so those results are identical to the definition's. */
+
+typedef struct {
+    double x0, x1; /* the two coordinates (-0.0 folded into +0.0) */
+    int64_t idx;   /* data: index into D; query: nD + index into Q */
+    int64_t rank;  /* dense 0-based rank of x0 among all points */
+} sweep_pt;
+
+static int g_sweep_data_first; /* tie order of the last coordinate */
+static int64_t g_sweep_nD;
+
+static int cmp_sweep_x0(const void* pa, const void* pb) {
+    const sweep_pt* a = (const sweep_pt*)pa;
+    const sweep_pt* b = (const sweep_pt*)pb;
+    if (a->x0 != b->x0) return a->x0 < b->x0 ? -1 : 1;
+    return a->idx < b->idx ? -1 : (a->idx > b->idx ? 1 : 0);
+}
+
+static int cmp_sweep(const void* pa, const void* pb) {
+    const sweep_pt* a = (const sweep_pt*)pa;
+    const sweep_pt* b = (const sweep_pt*)pb;
+    if (a->x1 != b->x1) return a->x1 < b->x1 ? -1 : 1;
+    int aq = a->idx >= g_sweep_nD, bq = b->idx >= g_sweep_nD;
+    if (aq != bq) {
+        int q_first = aq ? -1 : 1;
+#if ORACLE_PLANT == 5
+        return -q_first; /* planted: data before queries on a tie */
+#else
+        return g_sweep_data_first ? -q_first : q_first;
+#endif
+    }
+    return a->idx < b->idx ? -1 : (a->idx > b->idx ? 1 : 0);
+}
+
+/* A node of the Fenwick tree: F over its range, and the sum of |w| there. */
+typedef struct {
+    agg_t a;
+    double s;
+} fen_t;
+
+/* Core of the sweep over points given as doubles.  xd/xq are [n][2]; the
+ * weight of data point d is taken by weight_of(W, wt, op, d). */
+static int sweep2(const double* xd, int64_t nD, const double* xq, int64_t nQ, const void* W, int wt, int op,
+                  unsigned nonstrict, void* out, double* S) {
+    int64_t N = nD + nQ;
+    sweep_pt* P = (sweep_pt*)malloc(sizeof(sweep_pt) * (size_t)(N > 0 ? N : 1));
+    if (!P) return OR_ERR_ARG;
+    for (int64_t k = 0; k < N; ++k) {
+        const double* x = k < nD ? xd + 2 * k : xq + 2 * (k - nD);
+        P[k].x0 = x[0];
+        P[k].x1 = x[1];
+        P[k].idx = k;
+    }
+    /* dense 0-based ranks of the first coordinate: sort by it, count changes */
+    qsort(P, (size_t)N, sizeof(sweep_pt), cmp_sweep_x0);
+    int64_t U = 0;
+    for (int64_t k = 0; k < N; ++k) {
+        if (k > 0 && P[k].x0 != P[k - 1].x0) ++U;
+        P[k].rank = U;
+    }
+    if (N > 0) ++U;
+    /* the order of the last coordinate */
+    g_sweep_nD = nD;
+    g_sweep_data_first = (int)((nonstrict >> 1) & 1u);
+    qsort(P, (size_t)N, sizeof(sweep_pt), cmp_sweep);
+    /* Fenwick tree over ranks 1..U (1-based inside the tree) */
+    fen_t* tree = (fen_t*)malloc(sizeof(fen_t) * (size_t)(U + 1));
+    if (!tree) {
+        free(P);
+        return OR_ERR_ARG;
+    }
+    agg_t e = agg_unit(wt, op);
+    for (int64_t k = 0; k <= U; ++k) {
+        tree[k].a = e;
+        tree[k].s = 0.0;
+    }
+#if ORACLE_PLANT == 6
+    const int incl = 1; /* planted: the query's own rank is included */
+#else
+    const int incl = (int)(nonstrict & 1u);
+#endif
+    for (int64_t k = 0; k < N; ++k) {
+        if (P[k].idx < nD) {
+            agg_t w = weight_of(W, wt, op, P[k].idx);
+            double aw = abs_weight(W, wt, op, P[k].idx);
+            for (int64_t j = P[k].rank + 1; j <= U; j += j & (-j)) {
+                tree[j].a = agg_F(tree[j].a, w, op);
+                tree[j].s += aw;
+            }
+        } else {
+            /* F over ranks [0, rank) (strict) or [0, rank] (non-strict) */
+            agg_t acc = e;
+            double s = 0.0;
+            for (int64_t j = P[k].rank + (incl ? 1 : 0); j > 0; j -= j & (-j)) {
+                acc = agg_F(acc, tree[j].a, op);
+                s += tree[j].s;
+            }
+            store_out(out, wt, op, P[k].idx - nD, acc);
+            if (S) S[P[k].idx - nD] = s;
+        }
+    }
+    free(P);
+    free(tree);
+    return OR_OK;
+}
+
+static double* coords_as_double(const void* base, int ct, int64_t n, double sign) {
+    double* x = (double*)malloc(sizeof(double) * (size_t)(2 * n > 0 ? 2 * n : 1));
+    if (!x) return NULL;
+    for (int64_t k = 0; k < n; ++k)
+        for (int i = 0; i < 2; ++i) {
+            double v = sign * coord_at(base, ct, k, 2, i);
+            x[2 * k + i] = v == 0.0 ? 0.0 : v; /* -0.0 is +0.0 */
+        }
+    return x;
+}
+
+/* out(q) = F over { w(d) : d < q } for m = 2 (bit i of nonstrict: d_i <= q_i),
+ * by the sweep above.  Same conventions as oracle_brute_ns. */
+int oracle_sweep2(const void* D, int64_t nD, const void* Q, int64_t nQ, int ct, const void* W, int wt, int op,
+                  unsigned nonstrict, void* out, double* S) {
+    int st = check_args(2, nD, nQ, ct, wt, op);
+    if (st) return st;
+    if (nonstrict > 3u) return OR_ERR_ARG;
+    if (any_nan(D, ct, nD, 2) || any_nan(Q, ct, nQ, 2)) return OR_ERR_NAN;
+    double* xd = coords_as_double(D, ct, nD, 1.0);
+    double* xq = coords_as_double(Q, ct, nQ, 1.0);
+    st = (xd && xq) ? sweep2(xd, nD, xq, nQ, W, wt, op, nonstrict, out, S) : OR_ERR_ARG;
+    free(xd);
+    free(xq);
+    return st;
+}
+
+/* The adjoint of the float32 sum for m = 2: grad(d) = sum of g(q) over
+ * queries q with d < q (bit i of nonstrict: d_i <= q_i), by the sweep on the
+ * negated problem: with every coordinate negated, q plays a data point of
+ * weight g(q) and d a query (d_i < q_i  <=>  -q_i < -d_i; negation is exact
+ * in double for int32 and float32 values). */
+int oracle_sweep2_transpose(const void* D, int64_t nD, const void* Q, int64_t nQ, int ct, const float* G,
+                            unsigned nonstrict, double* grad, double* S) {
+    if (nD < 0 || nQ < 0 || (ct != CT_I32 && ct != CT_F32) || nonstrict > 3u) return OR_ERR_ARG;
+    if (any_nan(D, ct, nD, 2) || any_nan(Q, ct, nQ, 2)) return OR_ERR_NAN;
+    double* xq = coords_as_double(Q, ct, nQ, -1.0); /* the new data points */
+    double* xd = coords_as_double(D, ct, nD, -1.0); /* the new queries */
+    int st = (xd && xq) ? sweep2(xq, nQ, xd, nD, G, WT_F32, OP_SUM, nonstrict, grad, S) : OR_ERR_ARG;
+    free(xd);
+    free(xq);
+    return st;
 }
 
 /* Number of threads OpenMP would use (1 without OpenMP). */

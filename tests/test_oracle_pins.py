@@ -140,12 +140,23 @@ def test_brute_equals_sortscan_medium():
 
 
 def _brute_py(D, Q, w, op):
-    """Pure-Python definition for tiny inputs (independent of the C code)."""
+    """Pure-Python definition for tiny inputs (independent of the C code).
+    Integer weights give Python ints; float weights give Python floats (the
+    sum in double, max / min exact, +-inf for the empty set)."""
+    is_float = w is not None and np.asarray(w).dtype.kind == "f"
     out = []
     for q in Q:
         dom = [i for i, d in enumerate(D) if all(d[k] < q[k] for k in range(len(q)))]
         if op == "count":
             out.append(len(dom))
+        elif is_float:
+            vals = [float(w[i]) for i in dom]
+            if op == "sum":
+                out.append(float(sum(vals)))
+            elif op == "min":
+                out.append(min(vals, default=float("inf")))
+            else:
+                out.append(max(vals, default=float("-inf")))
         elif op == "sum":
             out.append(int(sum(int(w[i]) for i in dom)))
         elif op == "min":
@@ -162,6 +173,21 @@ def test_brute_equals_python_definition():
         D, Q, w = workloads.random_small(rng, m, 25, 20, 5, "i32", "i32")
         for op in ("sum", "max", "count", "min"):
             assert oracle.brute(D, Q, w, op)[0].tolist() == _brute_py(D, Q, w, op)
+
+
+def test_brute_float_weights_equal_python_definition():
+    """The float branch of F (max, min and the double sum of float32
+    weights) against the pure-Python definition: the C oracle's brute force
+    and its sort-and-scan share that branch, so this pins it independently."""
+    rng = np.random.default_rng(4)
+    for _ in range(40):
+        m = int(rng.integers(1, 4))
+        D, Q, w = workloads.random_small(rng, m, 25, 20, 5, "f32", "f32")
+        for op in ("max", "min"):
+            assert oracle.brute(D, Q, w, op)[0].tolist() == _brute_py(D, Q, w, op)
+        got = oracle.brute(D, Q, w, "sum")[0]
+        want = np.array(_brute_py(D, Q, w, "sum"))
+        assert np.allclose(got, want, rtol=0, atol=1e-12 * (1 + np.abs(w).sum()))
 
 
 def test_min_is_negated_max_of_negated_weights():
@@ -390,3 +416,95 @@ def test_nonstrict_without_ties_equals_strict():
     w = rng.integers(-9, 10, 600).astype(np.int64)
     for mask in range(4):
         assert oracle.brute(D, Q, w, "sum", nonstrict=mask)[0].tolist() == oracle.brute(D, Q, w, "sum")[0].tolist()
+
+
+# --- the O(n log n) sweep for m = 2 (full-size checks) -------------------
+
+SWEEP_CASES = [(dt, wt, op) for dt in ("i32", "f32")
+               for wt, op in (("i64", "sum"), ("f32", "sum"), ("i32", "max"), ("f32", "max"), ("i64", "count"),
+                              ("i32", "min"), ("f32", "min"))]
+
+
+@pytest.mark.parametrize("dt,wt,op", SWEEP_CASES)
+def test_sweep2_equals_brute(dt, wt, op):
+    """The Fenwick-tree sweep (not the paper's algorithm) equals the
+    definition on tied inputs, for every op and comparison mask."""
+    rng = np.random.default_rng(2000 + len(dt) + len(op))
+    for _ in range(10):
+        nD, nQ = int(rng.integers(0, 300)), int(rng.integers(0, 300))
+        D, Q, w = workloads.random_small(rng, 2, nD, nQ, int(rng.integers(1, 12)), dt, wt)
+        for mask in range(4):
+            a, Sa = oracle.brute(D, Q, w, op, nonstrict=mask)
+            b, Sb = oracle.sweep2(D, Q, w, op, nonstrict=mask)
+            assert np.allclose(Sa, Sb, rtol=1e-12, atol=0)
+            if wt == "f32" and op == "sum":
+                assert np.allclose(a, b, rtol=0, atol=1e-12 * (1 + Sa.max(initial=0)))
+            else:
+                assert a.tolist() == b.tolist()
+
+
+def test_sweep2_python_definition_and_hand_case():
+    D, Q, w, want_sum, want_cnt = _hand_case()
+    assert oracle.sweep2(D, Q, w, "sum")[0].tolist() == want_sum
+    assert oracle.sweep2(D, Q, None, "count")[0].tolist() == want_cnt
+    rng = np.random.default_rng(6)
+    for _ in range(30):
+        D, Q, w = workloads.random_small(rng, 2, 30, 25, 4, "i32", "i32")
+        for op in ("sum", "max", "min", "count"):
+            assert oracle.sweep2(D, Q, w, op)[0].tolist() == _brute_py(D, Q, w, op)
+
+
+def test_sweep2_transpose_equals_brute():
+    rng = np.random.default_rng(7)
+    for _ in range(12):
+        D, Q, _ = workloads.random_small(rng, 2, int(rng.integers(0, 200)), int(rng.integers(0, 200)), 6,
+                                         "f32", "i64")
+        g = rng.standard_normal(Q.shape[0]).astype(np.float32)
+        grad, S = oracle.sweep2_transpose(D, Q, g)
+        want, Sw = oracle.brute_transpose(D, Q, g)
+        assert np.allclose(grad, want, rtol=0, atol=1e-12 * (1 + Sw.max(initial=0)))
+        assert np.allclose(S, Sw, rtol=1e-12, atol=0)
+        for mask in range(1, 4):
+            # d_i <= q_i  <=>  -q_i <= -d_i: the non-strict adjoint is the
+            # non-strict forward problem with negated coordinates, roles swapped
+            gm, _ = oracle.sweep2_transpose(D, Q, g, nonstrict=mask)
+            fm, Sm = oracle.brute(-Q, -D, g, "sum", nonstrict=mask)
+            assert np.allclose(gm, fm, rtol=0, atol=1e-12 * (1 + Sm.max(initial=0)))
+
+
+def test_sweep2_edge_cases():
+    D = np.zeros((0, 2), np.float32)
+    Q = np.array([[1, 1], [5, 5]], np.float32)
+    assert oracle.sweep2(D, Q, np.zeros(0, np.int32), "max")[0].tolist() == [np.iinfo(np.int32).min] * 2
+    assert oracle.sweep2(Q, D, np.ones(2, np.int64), "sum")[0].shape == (0,)
+    E = np.full((20, 2), 3.0, np.float32)
+    assert oracle.sweep2(E, E, np.ones(20, np.int64), "sum")[0].tolist() == [0] * 20
+    assert oracle.sweep2(E, E, np.ones(20, np.int64), "sum", nonstrict=3)[0].tolist() == [20] * 20
+    Z = np.array([[-0.0, 1.0]], np.float32)
+    assert oracle.sweep2(Z, np.array([[0.0, 2.0], [0.5, 2.0]], np.float32), np.array([3], np.int64),
+                         "sum")[0].tolist() == [0, 3]
+    with pytest.raises(oracle.OracleError):
+        oracle.sweep2(np.array([[np.nan, 1.0]], np.float32), Q, np.ones(1, np.int64), "sum")
+
+
+def _sweep_pins_pass(plant):
+    D, Q, w, want_sum, _ = _hand_case()
+    if oracle.sweep2(D, Q, w, "sum", plant=plant)[0].tolist() != want_sum:
+        return False
+    rng = np.random.default_rng(45)
+    for _ in range(20):
+        D, Q, w = workloads.random_small(rng, 2, 40, 40, 4, "i32", "i64")
+        if oracle.sweep2(D, Q, w, "sum", plant=plant)[0].tolist() != _brute_py(D, Q, w, "sum"):
+            return False
+    return True
+
+
+def test_real_sweep_passes_the_pins():
+    assert _sweep_pins_pass(0)
+
+
+@pytest.mark.parametrize("plant", [5, 6])
+def test_planted_sweep_mistakes_are_caught(plant):
+    # 5: data before queries on a tie of the last coordinate; 6: the query's
+    # own first-coordinate rank included (non-strict)
+    assert not _sweep_pins_pass(plant)
