@@ -289,9 +289,14 @@ const char* domagg_timing_kind_name(int kind);
  *   Arguments, layouts, outputs and tolerances are those of domagg_forward;
  *   all pointers are device memory on the CURRENT device, and no handle is
  *   used.
- *   Limits: nD + nQ <= 65536, and the flat map must fit the scratch (about
- *   10^6 records for m <= 2, about half that for m = 3); larger
- *   inputs return DOMAGG_ERR_UNSUPPORTED without running.
+ *   Limits: nD + nQ <= 65536 (checked before any GPU work), and the flat
+ *   map must fit the scratch (about 10^6 records for m <= 2, about half that
+ *   for m = 3).  The flat map's size is only known once the point phase has
+ *   run on the GPU and the mid-call synchronisation has read the record
+ *   counts: an input whose records do not fit then returns
+ *   DOMAGG_ERR_UNSUPPORTED without writing `out`, and the next call is
+ *   unaffected.  Errors are reported by the status code only (there is no
+ *   handle to ask domagg_last_error).
  *   The first call on a device sets that device's scratch up (looks its
  *   address up, clears the control block and the status words, and
  *   synchronises the device): make that first call before any CUDA-graph

@@ -73,6 +73,7 @@ struct domagg_ctx {
     size_t pool_used = 0;
     u64 epoch_mirror = 0;  // host copy of Ctl::epoch_base
     bool frozen = false;   // owned by a plan: its workspace must not grow any more
+    bool no_alloc = false; // buffers are fixed slices of a static array: never free or allocate
     int sms = 152;         // multiprocessors of the device
     // the point phase's independent sorts run on two more streams (fork /
     // join by events); off for the allocation-free entry point
@@ -101,6 +102,7 @@ domagg_status cuda_fail(domagg_ctx* h, cudaError_t e, const char* where) {
 // current epoch.
 domagg_status grow(domagg_ctx* h, DevBuf& b, size_t bytes, bool zero = false) {
     if (b.cap >= bytes) return DOMAGG_OK;
+    if (h->no_alloc) return fail(h, DOMAGG_ERR_OOM, "the fixed scratch is too small for this input");
     if (h->frozen) return fail(h, DOMAGG_ERR_OOM, "a planned run needs more workspace than its plan reserved");
     size_t want = std::max(bytes, b.cap + b.cap / 4);
     if (h->max_ws && h->held() - b.cap + want > h->max_ws) {
@@ -135,6 +137,7 @@ domagg_status grow(domagg_ctx* h, DevBuf& b, size_t bytes, bool zero = false) {
 
 domagg_status grow_pinned(domagg_ctx* h, size_t bytes) {
     if (h->h_pin_cap >= bytes) return DOMAGG_OK;
+    if (h->no_alloc) return fail(h, DOMAGG_ERR_OOM, "the fixed host staging area is too small for this input");
     if (h->frozen) return fail(h, DOMAGG_ERR_OOM, "a planned run needs more pinned memory than its plan reserved");
     if (h->h_pin) {
         cudaDeviceSynchronize();
@@ -1692,6 +1695,9 @@ domagg_status noalloc_setup(int dev, domagg_ctx** out) {
         }
         domagg_ctx& h = S.ctx;
         h.device = dev;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) h.sms = sms;
+        else cudaGetLastError();  // keep the default of 152
         h.ctl = reinterpret_cast<Ctl*>(ptr);
         h.pts = {ptr + NOALLOC_CTL, NOALLOC_PTS};
         h.recs = {ptr + NOALLOC_CTL + NOALLOC_PTS, NOALLOC_RECS};
@@ -1704,6 +1710,9 @@ domagg_status noalloc_setup(int dev, domagg_ctx** out) {
         h.h_pin = S.host_stage;
         h.h_pin_cap = sizeof(S.host_stage);
         h.timing = false;
+        // grow() and grow_pinned() refuse (DOMAGG_ERR_OOM, reported as
+        // UNSUPPORTED) instead of freeing these slices or allocating
+        h.no_alloc = true;
         S.ready = true;
     }
     *out = &S.ctx;

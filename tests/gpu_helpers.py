@@ -42,3 +42,20 @@ def assert_matches_oracle(got, D, Q, w, op, want=None, S=None, qidx=None):
     else:
         assert np.array_equal(got.astype(np.int64), want.astype(np.int64)), \
             f"first mismatch at {np.nonzero(got.astype(np.int64) != want)[0][:5]}"
+
+
+_FULL_CACHE = {}
+
+
+def full_size_m2_oracle(weights: str, op: str):
+    """The full-size m = 2 workload (|D| = |Q| = 2^24, float32 coordinates
+    with 25% quantised) and its oracle result on EVERY query, by the
+    O(n log n) sweep (pinned to brute force on the CPU); cached per process so
+    several GPU variants share one oracle run.  Returns (problem, want, S)."""
+    from paper_2305_16751_gb300 import workloads
+    key = (weights, op)
+    if key not in _FULL_CACHE:
+        p = workloads.tied_floats(weights=weights)
+        want, S = oracle.sweep2(p.D, p.Q, p.w, op)
+        _FULL_CACHE[key] = (p, want, S)
+    return _FULL_CACHE[key]

@@ -66,16 +66,6 @@ def test_autograd_at_512_matches_oracle_finite_differences():
     _check_grad(w.grad.cpu().numpy(), fd, S)
 
 
-def test_backward_full_size_sampled():
-    """m=2, |D|=|Q|=2^22 (the autograd workload), sampled data points."""
-    p = workloads.autograd_floats()
-    g = p.extra["c"]
-    got = domagg.backward(to_dev(p.D), to_dev(p.Q), to_dev(g)).cpu().numpy()
-    di = np.sort(np.random.default_rng(3).choice(p.D.shape[0], 256, replace=False))
-    want, S = oracle.brute_transpose(p.D[di], p.Q, g)
-    _check_grad(got[di], want, S)
-
-
 @pytest.mark.parametrize("op,wt", [("sum", "f32"), ("sum", "i64"), ("max", "i32"), ("count", "i64"), ("min", "f32")])
 def test_batch_equals_single_calls(op, wt):
     rng = np.random.default_rng(77)

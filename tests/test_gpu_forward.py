@@ -152,45 +152,3 @@ def test_invalid_arguments_are_rejected():
     assert domagg.STATUS[st] == "INVALID_ARG"
     st = L.domagg_forward(h, 2, None, 2**30, None, 2**30, 0, None, 1, 0, None, None)
     assert domagg.STATUS[st] == "UNSUPPORTED"
-
-
-# --- the full-size workloads, checked on sampled queries ----------------------
-
-def _sample(nQ, k, seed):
-    return np.sort(np.random.default_rng(seed).choice(nQ, size=k, replace=False))
-
-
-def test_full_size_m2_tied_floats_sum_and_max():
-    """m=2, |D|=|Q|=2^24, float32 coordinates with 25% quantised (ties):
-    float32 sum (tolerance) and int32 max (bit-exact), on sampled queries;
-    the record count equals the flat-map formula at full size."""
-    p = workloads.tied_floats()
-    got = gpu_forward(p.D, p.Q, p.w, "sum")
-    st = domagg.stats()
-    qi = _sample(p.Q.shape[0], 192, 1)
-    assert_matches_oracle(got, p.D, p.Q, p.w, "sum", qidx=qi)
-    # record count: sum over data of zeros(r) + over queries of ones(r), b digits
-    x = np.concatenate([p.D[:, 0], p.Q[:, 0]]).astype(np.float64)
-    x[x == 0] = 0.0
-    u, r = np.unique(x, return_inverse=True)
-    b = int(np.ceil(np.log2(len(u))))
-    ones = np.zeros(r.shape, np.int64)
-    rr = r.astype(np.uint64)
-    for j in range(b):
-        ones += ((rr >> np.uint64(j)) & np.uint64(1)).astype(np.int64)
-    nD = p.D.shape[0]
-    T = int((b - ones[:nD]).sum() + ones[nD:].sum())
-    assert st["n_records"] == T and st["rank_bits"][0] == b and st["distinct"][0] == len(u)
-    pm = workloads.tied_floats(weights="i32")
-    gotm = gpu_forward(pm.D, pm.Q, pm.w, "max")
-    assert_matches_oracle(gotm, pm.D, pm.Q, pm.w, "max", qidx=qi)
-    gotn = gpu_forward(pm.D, pm.Q, pm.w, "min")
-    assert_matches_oracle(gotn, pm.D, pm.Q, pm.w, "min", qidx=qi)
-
-
-def test_full_size_m3_gaussian_mixture():
-    """m=3, |D|=|Q|=2^21, Gaussian-mixture int32 coordinates, int64 sum."""
-    p = workloads.gaussian_mixture_i32()
-    got = gpu_forward(p.D, p.Q, p.w, "sum")
-    qi = _sample(p.Q.shape[0], 256, 2)
-    assert_matches_oracle(got, p.D, p.Q, p.w, "sum", qidx=qi)

@@ -1,0 +1,86 @@
+"""Parity at the full sizes, on every output element.
+
+The m = 2 workloads are checked against the oracle's O(n log n) sweep on all
+queries (|D| = |Q| = 2^24) and all data points of the adjoint (2^22), and
+against the brute-force definition on a seeded sample of 1024 queries; the
+m = 3 workload against brute force on 1024 sampled queries."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import assert_matches_oracle, full_size_m2_oracle, gpu_forward, to_dev, torch
+from paper_2305_16751_gb300 import domagg, workloads
+
+pytestmark = pytest.mark.gpu
+
+BRUTE_SAMPLE = 1024
+
+
+def _sample(n, k, seed):
+    return np.sort(np.random.default_rng(seed).choice(n, size=k, replace=False))
+
+
+def _fwd(D, Q, w, op, variant):
+    out = domagg.forward(to_dev(D), to_dev(Q), to_dev(w), op, variant=variant)
+    torch().cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("variant", ["improved", "wavelet"])
+def test_m2_float32_sum_every_query(variant):
+    """float32 sum within 4 * 2^-24 * sum |w| of the double-precision oracle,
+    on all 2^24 queries; brute force on a 1024-query sample as well."""
+    p, want, S = full_size_m2_oracle("f32", "sum")
+    got = _fwd(p.D, p.Q, p.w, "sum", variant)
+    assert_matches_oracle(got, p.D, p.Q, p.w, "sum", want=want, S=S)
+    qi = _sample(p.Q.shape[0], BRUTE_SAMPLE, 11)
+    assert_matches_oracle(got, p.D, p.Q, p.w, "sum", qidx=qi)
+
+
+@pytest.mark.parametrize("variant", ["improved", "wavelet"])
+@pytest.mark.parametrize("op", ["max", "min"])
+def test_m2_int32_max_min_every_query(variant, op):
+    """int32 max / min bit-exact on all 2^24 queries."""
+    p, want, _ = full_size_m2_oracle("i32", op)
+    got = _fwd(p.D, p.Q, p.w, op, variant)
+    assert_matches_oracle(got, p.D, p.Q, p.w, op, want=want)
+
+
+def test_m2_record_count_at_full_size():
+    """The flat map's record count, the rank digits and the distinct count at
+    2^24 per side equal the closed form T = sum over data of zeros(r) + sum
+    over queries of ones(r) with b = ceil(log2 U) digits."""
+    p, _, _ = full_size_m2_oracle("f32", "sum")
+    gpu_forward(p.D, p.Q, p.w, "sum")
+    st = domagg.stats()
+    x = np.concatenate([p.D[:, 0], p.Q[:, 0]]).astype(np.float64)
+    x[x == 0] = 0.0
+    u, r = np.unique(x, return_inverse=True)
+    b = int(np.ceil(np.log2(len(u))))
+    ones = np.zeros(r.shape, np.int64)
+    rr = r.astype(np.uint64)
+    for j in range(b):
+        ones += ((rr >> np.uint64(j)) & np.uint64(1)).astype(np.int64)
+    nD = p.D.shape[0]
+    T = int((b - ones[:nD]).sum() + ones[nD:].sum())
+    assert st["n_records"] == T and st["rank_bits"][0] == b and st["distinct"][0] == len(u)
+
+
+@pytest.mark.parametrize("variant", ["improved", "wavelet"])
+def test_m2_backward_every_data_point(variant):
+    """The adjoint at |D| = |Q| = 2^22 (the autograd workload): all 2^22
+    gradients against the sweep's transpose."""
+    p = workloads.autograd_floats()
+    g = p.extra["c"]
+    got = domagg.backward(to_dev(p.D), to_dev(p.Q), to_dev(g), variant=variant).cpu().numpy()
+    want, S = oracle.sweep2_transpose(p.D, p.Q, g)
+    assert_matches_oracle(got, -p.Q, -p.D, g, "sum", want=want, S=S)
+
+
+def test_m3_gaussian_mixture_brute_sample():
+    """m=3, |D|=|Q|=2^21, Gaussian-mixture int32 coordinates, int64 sum:
+    bit-exact on a 1024-query brute-force sample."""
+    p = workloads.gaussian_mixture_i32()
+    got = gpu_forward(p.D, p.Q, p.w, "sum")
+    qi = _sample(p.Q.shape[0], BRUTE_SAMPLE, 2)
+    assert_matches_oracle(got, p.D, p.Q, p.w, "sum", qidx=qi)

@@ -95,18 +95,6 @@ def test_wavelet_equals_records_pipeline_at_scale():
     assert_matches_oracle(got, pf.D, pf.Q, pf.w, "sum", qidx=qi)
 
 
-def test_wavelet_full_size_m2():
-    """The full-size workload (|D| = |Q| = 2^24, float32 coordinates with 25%
-    quantised): float32 sum and int32 max on sampled queries."""
-    p = workloads.tied_floats()
-    got = _fw(p.D, p.Q, p.w, "sum")
-    qi = np.sort(np.random.default_rng(6).choice(p.Q.shape[0], 160, replace=False))
-    assert_matches_oracle(got, p.D, p.Q, p.w, "sum", qidx=qi)
-    pm = workloads.tied_floats(weights="i32")
-    gotm = _fw(pm.D, pm.Q, pm.w, "max")
-    assert_matches_oracle(gotm, pm.D, pm.Q, pm.w, "max", qidx=qi)
-
-
 def test_wavelet_rejects_m3():
     D = np.zeros((4, 3), np.int32)
     with pytest.raises(domagg.DomaggError) as e:

@@ -61,3 +61,26 @@ def test_noalloc_rejects_inputs_beyond_its_scratch():
     w = to_dev(np.ones(40000, np.int64))
     st, _ = _noalloc(D, Q, w, "sum")
     assert domagg.STATUS[st] == "UNSUPPORTED"
+
+
+def test_noalloc_refuses_an_oversized_flat_map_then_works():
+    """Under the point limit but with a flat map too large for the scratch
+    (m = 3, 30000 points per side): refused after the point phase, with
+    `out` untouched; the next call on the same scratch is still correct."""
+    rng = np.random.default_rng(32)
+    D, Q, w = workloads.random_small(rng, 3, 30000, 30000, 1 << 20, "i32", "i64")
+    Dd, Qd, wd = to_dev(D), to_dev(Q), to_dev(w)
+    t = torch()
+    sentinel = t.full((Q.shape[0],), 12345, dtype=t.int64, device=Dd.device)
+    st = domagg.lib().domagg_forward_noalloc(
+        3, ctypes.c_void_p(Dd.data_ptr()), D.shape[0], ctypes.c_void_p(Qd.data_ptr()), Q.shape[0],
+        domagg._coord_dtype(Dd), ctypes.c_void_p(wd.data_ptr()), domagg._weight_dtype(wd, "sum"),
+        domagg.OPS["sum"], ctypes.c_void_p(sentinel.data_ptr()), ctypes.c_void_p(t.cuda.current_stream().cuda_stream))
+    t.cuda.synchronize()
+    assert domagg.STATUS[st] == "UNSUPPORTED"
+    assert bool((sentinel == 12345).all())
+    name, D2, Q2, w2, op = list(_cases())[1]
+    D2d, Q2d, w2d = to_dev(D2), to_dev(Q2), to_dev(w2)
+    st, out = _noalloc(D2d, Q2d, w2d, op)
+    assert st == 0
+    assert np.array_equal(out.cpu().numpy(), domagg.forward(D2d, Q2d, w2d, op).cpu().numpy())
