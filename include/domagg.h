@@ -258,6 +258,8 @@ typedef struct {
     int32_t record_key_bits; /* bits of the node key sorted by the record sort */
     int32_t record_passes;   /* radix passes over the records */
     int64_t workspace_bytes; /* device workspace currently held by the handle */
+    int64_t n_records_shared; /* m = 2: records of the deep rank levels, formed, sorted and
+                                 scanned in shared memory (the rest of n_records go through HBM) */
 } domagg_stats;
 
 domagg_status domagg_get_stats(domagg_handle h, domagg_stats* out);
@@ -310,6 +312,20 @@ const char* domagg_timing_kind_name(int kind);
 domagg_status domagg_forward_noalloc(int m, const void* d_coords, int64_t nD, const void* q_coords, int64_t nQ,
                                      domagg_dtype coord_dtype, const void* d_weights, domagg_dtype weight_dtype,
                                      domagg_op op, void* out, void* stream);
+
+/* Tuning knobs of a handle (the paper has no counterpart); every setting
+ * computes the same results:
+ *   "group_bits"     0 .. 12 (default 12): for m = 2, the rank levels below
+ *                    gS <= group_bits (nodes of at most 2^gS ranks) are
+ *                    formed, sorted and scanned per group of 2^gS ranks in
+ *                    shared memory; 0 sends every level's records through
+ *                    HBM;
+ *   "ranges_per_cta" 1 .. 64 (default 4): radix-sort ranges per resident CTA;
+ *   "blocks_per_sm"  1 .. 64 (default 16): flat-map / reduction blocks per SM.
+ * The environment variable DOMAGG_TUNE="name=value,..." sets the defaults of
+ * handles created afterwards.  Unknown names or values out of range return
+ * DOMAGG_ERR_INVALID_ARG. */
+domagg_status domagg_set_tuning(domagg_handle h, const char* name, int value);
 
 /* Library version string. */
 const char* domagg_version(void);

@@ -54,6 +54,10 @@ struct Inst {
     u32 qrec_off, Tq;  // query records (partial slots) of this instance
     u32 key_bits;      // bits of the node key
     u32 flags;         // bit i (i < 3): coordinate i compared non-strictly; FLAG_VIRTUAL_LAST
+    // m = 2: rank levels below gS are aggregated per group of 2^gS ranks in
+    // shared memory (k_group); G groups.  gS = 0: every level goes through
+    // the records in HBM.
+    u32 gS, G;
 };
 // The last of the M coordinates is not stored but constant (the basic
 // variant of Sec. 4 run as the Sec. 5 pipeline with one more coordinate).
@@ -311,7 +315,9 @@ __device__ __forceinline__ ff ff_add(ff x, ff y) {
 // Each operator defines: Acc (scan accumulator), Part (stored partial), Out
 // (output element), Pay (32-bit record payload), W (a weight as stored in
 // the order of the last coordinate), e(), F(a, b), to_part, from_part,
-// to_out, and either from_pay (the payload is the weight's bits) or, with
+// to_out, from_out (an output read back as an accumulator: the shared-memory
+// levels' result, completed by the records' levels), and either from_pay (the
+// payload is the weight's bits) or, with
 // GATHER, from_w (the payload is the position of the weight, read from the
 // L2-resident weight array: 8-byte weights do not ride through the sort).
 struct OpSumF32 {
@@ -327,6 +333,7 @@ struct OpSumF32 {
     __device__ static Part to_part(Acc a) { return __fadd_rn(a.hi, a.lo); }
     __device__ static Acc from_part(Part p) { return {p, 0.f}; }
     __device__ static Out to_out(Acc a) { return __fadd_rn(a.hi, a.lo); }
+    __device__ static Acc from_out(Out o) { return {o, 0.f}; }
 };
 struct OpSumI64 {
     typedef long long Acc;
@@ -341,6 +348,7 @@ struct OpSumI64 {
     __device__ static Part to_part(Acc a) { return a; }
     __device__ static Acc from_part(Part p) { return p; }
     __device__ static Out to_out(Acc a) { return a; }
+    __device__ static Acc from_out(Out o) { return o; }
 };
 struct OpMaxI32 {
     typedef int Acc;
@@ -355,6 +363,7 @@ struct OpMaxI32 {
     __device__ static Part to_part(Acc a) { return a; }
     __device__ static Acc from_part(Part p) { return p; }
     __device__ static Out to_out(Acc a) { return a; }
+    __device__ static Acc from_out(Out o) { return o; }
 };
 struct OpMaxF32 {
     typedef float Acc;
@@ -369,6 +378,7 @@ struct OpMaxF32 {
     __device__ static Part to_part(Acc a) { return a; }
     __device__ static Acc from_part(Part p) { return p; }
     __device__ static Out to_out(Acc a) { return a; }
+    __device__ static Acc from_out(Out o) { return o; }
 };
 struct OpMinI32 {
     typedef int Acc;
@@ -383,6 +393,7 @@ struct OpMinI32 {
     __device__ static Part to_part(Acc a) { return a; }
     __device__ static Acc from_part(Part p) { return p; }
     __device__ static Out to_out(Acc a) { return a; }
+    __device__ static Acc from_out(Out o) { return o; }
 };
 struct OpMinF32 {
     typedef float Acc;
@@ -397,6 +408,7 @@ struct OpMinF32 {
     __device__ static Part to_part(Acc a) { return a; }
     __device__ static Acc from_part(Part p) { return p; }
     __device__ static Out to_out(Acc a) { return a; }
+    __device__ static Acc from_out(Out o) { return o; }
 };
 struct OpCount {
     typedef u32 Acc;
@@ -411,6 +423,7 @@ struct OpCount {
     __device__ static Part to_part(Acc a) { return a; }
     __device__ static Acc from_part(Part p) { return p; }
     __device__ static Out to_out(Acc a) { return (long long)a; }
+    __device__ static Acc from_out(Out o) { return (u32)o; }
 };
 
 }  // namespace domagg

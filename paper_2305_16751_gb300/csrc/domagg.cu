@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -19,6 +20,7 @@
 #include "host_common.h"
 #include "k_points.cuh"
 #include "k_radix.cuh"
+#include "k_group.cuh"
 #include "k_records.cuh"
 #include "k_wavelet.cuh"
 
@@ -81,6 +83,9 @@ struct domagg_ctx {
     cudaStream_t aux[2] = {nullptr, nullptr};
     cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
     int ranges_per_cta = 4, blocks_per_sm = 16;  // launch shapes (domagg_plan_autotune)
+    // m = 2: the rank levels below gS <= group_bits are aggregated per group
+    // in shared memory (k_group); 0 = every level through the records in HBM
+    int group_bits = GROUP_MAX_BITS;
 
     size_t held() const { return pts.cap + recs.cap + st_multi.cap + st_seg.cap + stage.cap + st_wv.cap; }
 };
@@ -318,6 +323,7 @@ domagg_status run_wavelet(domagg_ctx* h, std::vector<Inst>& inst, Inst* d_inst, 
     domagg_stats& S = h->stats;
     S.n_points = (int64_t)N;
     S.n_records = 0;
+    S.n_records_shared = 0;
     S.n_query_records = 0;
     S.m = M;
     for (int i = 0; i < 3; ++i) {
@@ -369,6 +375,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     chunk_off[k] = (u32)NC;
     if (N >= (1ull << 31)) return fail(h, DOMAGG_ERR_UNSUPPORTED, "more than 2^31 points in one call");
     if (NQ == 0) return DOMAGG_OK;
+    // m = 2, the records path: the deep rank levels go through k_group
+    const bool use_groups = M == 2 && h->group_bits > 0 && !(inst[0].flags & FLAG_WAVELET);
 
     // ---- point workspace
     auto carve_points = [&](Carver& c, void** P) {
@@ -415,8 +423,18 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             P[29 + (ch - 1) * 8 + 6] = c.take<u32>(used ? (size_t)sort_range_bound(pt_sizes) * RADIX : 0);
             P[29 + (ch - 1) * 8 + 7] = c.take<u32>(used ? (size_t)ntp : 0);             // rank tile counts
         }
+        // m = 2 groups: rank starts, the group sort's keys and values
+        // (ping-pong), per-instance group-id bits and group slots
+        const bool grp = M == 2 && use_groups;
+        P[45] = c.take<u32>(grp ? N + k : 0);    // rank starts
+        P[46] = c.take<u32>(grp ? N : 0);        // group keys
+        P[47] = c.take<u32>(grp ? N : 0);
+        P[48] = c.take<u64>(grp ? N : 0);        // group values
+        P[49] = c.take<u64>(grp ? N : 0);
+        P[50] = c.take<u32>(grp ? k : 0);        // group-id bits per instance
+        P[51] = c.take<u32>(grp ? k + 1 : 0);    // group slot offsets
     };
-    void* P[45];
+    void* P[52];
     {
         Carver c(nullptr);
         carve_points(c, P);
@@ -435,6 +453,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     u32 *hist = (u32*)P[19], *digit_off = (u32*)P[20];
     u32* d_sort_tiles = (u32*)P[21];
     u32 *chunk_base = (u32*)P[22], *lvl_tot = (u32*)P[23];
+    u32 *rstart = (u32*)P[45], *gkey[2] = {(u32*)P[46], (u32*)P[47]}, *gbits = (u32*)P[50], *gslot = (u32*)P[51];
+    u64* gval[2] = {(u64*)P[48], (u64*)P[49]};
 
     // status words: point tiles x 256 digits (the records sort grows it later)
     {
@@ -528,7 +548,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         L.stop();
         L.start(KIND_RANK, (double)N * 12);
         k_rank_apply<SCAN_THREADS, SCAN_ITEMS><<<(unsigned)ntp, SCAN_THREADS, 0, C.stream>>>(
-            keys[cur], vals[cur], d_pt_offs, d_pt_tiles, k, C.tile_cnt, i == 0 ? r0 : (i == 1 ? r1 : r2), d_inst, i);
+            keys[cur], vals[cur], d_pt_offs, d_pt_tiles, k, C.tile_cnt, i == 0 ? r0 : (i == 1 ? r1 : r2), d_inst, i,
+            (i == 0 && use_groups) ? rstart : nullptr);
         L.stop();
     };
     auto last_dim = [&](const Chain& C) -> u32* {  // order of the last coordinate, queries first on ties (Sec. 5)
@@ -565,6 +586,12 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         if constexpr (M <= 2) return run_wavelet<M, Op>(h, inst, d_inst, perm, r0, N, L, stream, hp, ctl_pos);
         else return fail(h, DOMAGG_ERR_UNSUPPORTED, "the level-wise formulation takes m <= 2");
     }
+    // ---- m = 2: the size of the groups of ranks that k_group takes
+    if (use_groups) {
+        L.start(KIND_SMALL, 0.0);
+        k_group_plan<<<k, 1024, 0, stream>>>(d_inst, rstart, gbits, GROUP_CAP, h->group_bits);
+        L.stop();
+    }
     // ---- count / offset scan of the flat map, per level
     {
         // perm, gathered ranks, ranks / index / weight written in order, weight gathered
@@ -572,7 +599,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                                      (double)NC * 8 * LMAX);
         k_count_scan<M, W, WT><<<(unsigned)ntp, 256, 0, stream>>>(
             perm, d_pt_offs, d_pt_tiles, k, d_chunk_off, r0, r1, r2, d_inst, pr0, pr1, pr2, pj, (W*)P[18], chunk_base,
-            qchunk_base, (u32*)P[25]);
+            qchunk_base, (u32*)P[25], use_groups ? gkey[0] : nullptr, use_groups ? gval[0] : nullptr);
         L.stop();
         L.start(KIND_SMALL, 0.0);
         k_tile_exscan_counters<<<(unsigned)(((u64)k * CS_COUNTERS + 7) / 8), 256, 0, stream>>>(
@@ -594,6 +621,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     };
     std::vector<Chunk> chunks;
     std::vector<u32> nlev(k), lvl, qlvl;
+    u64 T_flat = 0, T_shared = 0;  // flat-map records in all, and those k_group forms in shared memory
     auto level_bits = [&](int s, u32 lv) -> u32 {
         if (M == 1) return 0u;
         const u32 b = inst[s].b[0] - 1u - lv;  // prefix length of level lv
@@ -653,6 +681,14 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             nlev[s] = inst[s].nQ + inst[s].nD == 0 ? 0u : (M == 1 ? 1u : inst[s].b[0]);
             u64 T = 0, Tq = 0;
             for (u32 lv = 0; lv < nlev[s]; ++lv) {
+                T_flat += lvl[(size_t)s * LMAX + lv];
+                // levels below gS are formed, sorted and scanned in shared
+                // memory (k_group): no records in HBM
+                if (M == 2 && lv < inst[s].gS) {
+                    T_shared += lvl[(size_t)s * LMAX + lv];
+                    lvl[(size_t)s * LMAX + lv] = 0;
+                    qlvl[(size_t)s * LMAX + lv] = 0;
+                }
                 T += lvl[(size_t)s * LMAX + lv];
                 Tq += qlvl[(size_t)s * LMAX + lv];
             }
@@ -720,6 +756,43 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             if (st) return st;
             hp = (char*)h->h_pin;
         }
+    }
+
+    // ---- m = 2: the deep rank levels by groups, in shared memory (k_group):
+    // a stable sort of the points (in the order of the last coordinate) by
+    // their group of ranks, then one CTA per group
+    if (use_groups) {
+        std::vector<u32> gb_host;
+        int gbits_max = 0;
+        if (!planned) {
+            gb_host.resize(k);
+            for (int s = 0; s < k; ++s) {
+                gb_host[s] = inst[s].gS ? inst[s].b[0] - inst[s].gS : 0u;
+                gbits_max = std::max(gbits_max, (int)gb_host[s]);
+            }
+        } else {  // bound: ranks below 2n (a non-strict first coordinate doubles them)
+            for (int s = 0; s < k; ++s) {
+                int bb = 0;
+                while (bb < 32 && (1ull << bb) < 2 * pt_sizes[s]) ++bb;
+                gbits_max = std::max(gbits_max, bb);
+            }
+        }
+        SortSpace gs{d_pt_offs, k, planned ? nullptr : &pt_sizes, d_sort_tiles, hist, digit_off,
+                     (u64*)h->st_multi.p, (double)N, (u32*)P[24], sort_range_bound(pt_sizes),
+                     planned ? nullptr : &gb_host, N};
+        sort_pairs<u32, u64>(L, gs, gkey, gval, false, gbits_max, 0xffffffffu, KIND_HIST_POINTS, KIND_SORT_GROUPS,
+                             gbits, true, false);
+        L.start(KIND_SMALL, 0.0);
+        k_group_slots<<<1, 1024, 0, stream>>>(d_inst, k, gslot);
+        L.stop();
+        typedef typename Op::Acc Acc;
+        constexpr size_t gsm = group_smem_bytes<Acc>();
+        if (!L.frozen) cudaFuncSetAttribute(k_group<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+        const int li = L.lookback_index();
+        L.start(KIND_GROUP, (double)N * 8.0 + (double)NQ * sizeof(typename Op::Out));
+        k_group<Op><<<(unsigned)h->sms, GROUP_THREADS, gsm, stream>>>(d_inst, k, gslot, rstart, gval[0], gval[1],
+                                                                      (const W*)P[18], h->ctl, li);
+        L.stop();
     }
 
     u64 T_all = 0, Tq_all = 0;
@@ -938,7 +1011,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
 
     domagg_stats& S = h->stats;
     S.n_points = (int64_t)N;
-    S.n_records = (int64_t)T_all;
+    S.n_records = (int64_t)(use_groups ? T_flat : T_all);
+    S.n_records_shared = (int64_t)T_shared;
     S.n_query_records = (int64_t)Tq_all;
     S.m = M;
     for (int i = 0; i < 3; ++i) {
@@ -1031,9 +1105,53 @@ Inst make_inst(const void* dco, int64_t nD, const void* qco, int64_t nQ, const v
     return I;
 }
 
+// Tuning knobs by name (domagg_set_tuning, DOMAGG_TUNE).
+bool set_tuning(domagg_ctx* h, const std::string& name, int value) {
+    if (name == "group_bits") {
+        if (value < 0 || value > GROUP_MAX_BITS) return false;
+        h->group_bits = value;
+    } else if (name == "ranges_per_cta") {
+        if (value < 1 || value > 64) return false;
+        h->ranges_per_cta = value;
+    } else if (name == "blocks_per_sm") {
+        if (value < 1 || value > 64) return false;
+        h->blocks_per_sm = value;
+    } else {
+        return false;
+    }
+    return true;
+}
+
+// DOMAGG_TUNE="name=value,name=value" overrides the defaults of a new handle
+// (malformed or unknown entries are ignored).
+void apply_tune_env(domagg_ctx* h) {
+    const char* env = std::getenv("DOMAGG_TUNE");
+    if (!env) return;
+    std::string all(env);
+    size_t pos = 0;
+    while (pos <= all.size()) {
+        size_t end = all.find(',', pos);
+        if (end == std::string::npos) end = all.size();
+        const std::string item = all.substr(pos, end - pos);
+        const size_t eq = item.find('=');
+        if (eq != std::string::npos) {
+            char* stop = nullptr;
+            const long v = std::strtol(item.c_str() + eq + 1, &stop, 10);
+            if (stop && *stop == '\0' && stop != item.c_str() + eq + 1) set_tuning(h, item.substr(0, eq), (int)v);
+        }
+        pos = end + 1;
+    }
+}
+
 }  // namespace
 
 extern "C" {
+
+domagg_status domagg_set_tuning(domagg_handle h, const char* name, int value) {
+    if (!h || !name) return DOMAGG_ERR_INVALID_ARG;
+    if (!set_tuning(h, name, value)) return fail(h, DOMAGG_ERR_INVALID_ARG, std::string("unknown tuning knob or value: ") + name);
+    return DOMAGG_OK;
+}
 
 domagg_status domagg_create(domagg_handle* out, int device, size_t max_workspace_bytes) {
     if (!out) return DOMAGG_ERR_INVALID_ARG;
@@ -1049,6 +1167,7 @@ domagg_status domagg_create(domagg_handle* out, int device, size_t max_workspace
     h->max_ws = max_workspace_bytes;
     cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
     if (h->sms <= 0) h->sms = 152;
+    apply_tune_env(h);
     h->overlap = cudaStreamCreateWithFlags(&h->aux[0], cudaStreamNonBlocking) == cudaSuccess &&
                  cudaStreamCreateWithFlags(&h->aux[1], cudaStreamNonBlocking) == cudaSuccess &&
                  cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
@@ -1627,7 +1746,8 @@ domagg_status domagg_timing_read(domagg_handle h, domagg_timing* out) {
 const char* domagg_timing_kind_name(int kind) {
     static const char* names[] = {"encode",  "hist_points",  "sort_points", "rank",     "count_scan",
                                   "expand",  "hist_records", "sort_records", "segscan", "reduce",
-                                  "small",   "h2d",          "d2h",          "wavelet"};
+                                  "small",   "h2d",          "d2h",          "wavelet",  "sort_groups",
+                                  "group"};
     if (kind < 0 || kind >= (int)(sizeof(names) / sizeof(names[0]))) return "";
     return names[kind];
 }
@@ -1653,7 +1773,7 @@ const char* domagg_version(void) { return "domagg 0.1 (sm_103a)"; }
 namespace {
 constexpr size_t NOALLOC_BYTES = (size_t)32 << 20;
 constexpr size_t NOALLOC_CTL = 4096;
-constexpr size_t NOALLOC_PTS = (size_t)6 << 20;
+constexpr size_t NOALLOC_PTS = (size_t)8 << 20;
 constexpr size_t NOALLOC_STM = (size_t)4 << 20;
 constexpr size_t NOALLOC_STS = (size_t)1 << 20;
 constexpr size_t NOALLOC_RECS = NOALLOC_BYTES - NOALLOC_CTL - NOALLOC_PTS - NOALLOC_STM - NOALLOC_STS;

@@ -28,6 +28,8 @@ enum Kind {
     KIND_H2D,
     KIND_D2H,
     KIND_WAVELET,  // the level-wise passes
+    KIND_SORT_GROUPS,  // m = 2: the points by their group of ranks
+    KIND_GROUP,        // m = 2: the deep levels in shared memory (k_group)
     KIND_COUNT_
 };
 

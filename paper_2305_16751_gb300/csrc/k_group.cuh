@@ -1,0 +1,328 @@
+// k_group.cuh -- the deep rank levels of m = 2 in shared memory.
+//
+// For m = 2 a record of level lv is keyed by the prefix r0 >> (lv+1) of the
+// first coordinate's rank (Sec. 5; the node of Sec. 3's P0/P1 sets).  All
+// records of a point share the top bits of their keys with the point's rank,
+// so the records sort (instruction 6m+2) can take its most significant
+// digits on the points, before the flat map: the points, in the order of
+// the last coordinate, are sorted stably by their group g = r0 >> gS (the
+// top bits of every key of the levels lv < gS).  A group then holds every
+// record of those levels whose node lies in it: the node of level lv covers
+// 2^(lv+1) ranks and gS >= lv+1.  One CTA takes a group of at most
+// GROUP_CAP points into shared memory and, level by level from lv = gS-1
+// down to 0, forms the level's records there, finishes their sort on the
+// remaining node-key bit and runs the segmented scan of F over them
+// (instruction 6m+3); each query keeps F over its partial results of these
+// levels (what instructions 6m+4, 6m+5 collect) and writes it to its output.
+// The levels lv >= gS go through the records in HBM as before and the
+// per-query reduction adds their partials to that output.
+//
+// Shared-memory sort, level by level.  The group's points start in the
+// order of the last coordinate, which is the order of the level gS-1
+// records (one node: the whole group).  The order of level lv-1 is the
+// order of level lv split stably by bit lv of the rank inside every node of
+// level lv -- an MSD radix sort of the node keys, one bit per level, done
+// on the points because a level's records are exactly its emitting points
+// (data with bit lv = 0: P0; queries with bit lv = 1: P1).  Within a node the
+// points keep the order of the last coordinate (queries before data on a
+// tie), which is what the segmented scan needs (Sec. 5).
+#pragma once
+#include "dev_common.cuh"
+#include "k_points.cuh"
+
+namespace domagg {
+
+constexpr int GROUP_MAX_BITS = 12;       // gS <= 12: nodes of up to 2^12 ranks
+constexpr int GROUP_THREADS = 1024;
+constexpr int GROUP_ITEMS = 16;          // points per thread
+constexpr u32 GROUP_CAP = GROUP_THREADS * GROUP_ITEMS;  // points per group in shared memory
+constexpr u32 GROUP_NODES = 1u << (GROUP_MAX_BITS - 1);  // nodes of one level in a group, at most
+
+template <typename Acc>
+__host__ __device__ constexpr size_t group_smem_bytes() {
+    return (size_t)GROUP_CAP * (sizeof(Acc) + sizeof(u32)) + 2 * GROUP_NODES * sizeof(unsigned short);
+}
+
+// Per instance (one block each): the largest gS <= min(GROUP_MAX_BITS, b0)
+// whose groups of 2^gS ranks hold at most `cap` points each, and the number
+// of groups G; gS = 0 (every level through the records in HBM) if even
+// groups of 2 ranks are too large, or if the instance takes another path.
+// rstart (per instance, at pt_off + s) holds the rank-sorted position of the
+// first point of every (undoubled) rank, and n at index U.  A non-strict
+// first coordinate doubles the ranks (2r for data, 2r+1 for queries), so a
+// group of 2^gS ranks is 2^(gS-1) undoubled ranks.  Also writes gbits[s],
+// the bits of the group id (b0 - gS) the group sort sorts.
+static __global__ __launch_bounds__(1024) void k_group_plan(Inst* inst, const u32* __restrict__ rstart,
+                                                           u32* __restrict__ gbits, u32 cap, int max_bits) {
+    __shared__ u32 s_max[32];
+    __shared__ u32 s_done;
+    const int s = blockIdx.x;
+    Inst& I = inst[s];
+    const u32 n = I.nD + I.nQ;
+    const u32 ns = I.flags & 1u;
+    const u32 U = I.U[0], b0 = I.b[0];
+    const u32 Uu = ns ? U / 2u : U;
+    const u32* rs = rstart + I.pt_off + (u32)s;
+    u32 chosen = 0, G = 0;
+    const bool eligible = n > 0 && b0 > 0 && !(I.flags & (FLAG_WAVELET | FLAG_VIRTUAL_LAST));
+    for (int S = eligible ? min(min(max_bits, GROUP_MAX_BITS), (int)b0) : 0; S >= 1; --S) {
+        const u32 us = (u32)S - ns;  // undoubled ranks per group: 2^us
+        const u32 g_n = (Uu + (1u << us) - 1u) >> us;
+        u32 mx = 0;
+        for (u32 g = threadIdx.x; g < g_n; g += blockDim.x) {
+            const u32 lo = g << us, hi = min((g + 1u) << us, Uu);
+            mx = max(mx, __ldg(rs + hi) - __ldg(rs + lo));
+        }
+        for (int o = 16; o >= 1; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            u32 m = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_max[w]);
+            s_done = m <= cap ? 1u : 0u;
+        }
+        __syncthreads();
+        const bool ok = s_done != 0u;
+        __syncthreads();
+        if (ok) {
+            chosen = (u32)S;
+            G = g_n;
+            break;
+        }
+    }
+    if (threadIdx.x == 0) {
+        I.gS = chosen;
+        I.G = chosen ? G : 0u;
+        gbits[s] = chosen ? b0 - chosen : 0u;
+    }
+}
+
+// Work list of k_group: slot offsets of the instances' groups (exclusive
+// scan of G over the instances that use groups).  One block.
+static __global__ __launch_bounds__(1024) void k_group_slots(const Inst* __restrict__ inst, int k,
+                                                            u32* __restrict__ gslot_off) {
+    __shared__ u32 carry;
+    __shared__ u32 warp_sum[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < k; base += blockDim.x) {
+        const int s = base + threadIdx.x;
+        const u32 v = s < k && inst[s].gS ? inst[s].G : 0u;
+        u32 inc = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 x = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += x;
+        }
+        if (lane == 31) warp_sum[warp] = inc;
+        __syncthreads();
+        u32 add = carry;
+        for (int w = 0; w < warp; ++w) add += warp_sum[w];
+        if (s < k) gslot_off[s] = add + inc - v;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) carry += warp_sum[w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gslot_off[k] = carry;
+}
+
+// Segmented-scan element of a level: a node head seen, F over the emitting
+// data since the last head, and the points with rank bit lv = 0 since it.
+template <typename Acc>
+struct GScan {
+    u32 hd;
+    Acc acc;
+    u32 zc;
+};
+// a precedes b
+template <class Op>
+__device__ __forceinline__ GScan<typename Op::Acc> gscan_combine(const GScan<typename Op::Acc>& a,
+                                                                const GScan<typename Op::Acc>& b) {
+    GScan<typename Op::Acc> r;
+    r.hd = a.hd | b.hd;
+    r.acc = b.hd ? b.acc : Op::F(a.acc, b.acc);
+    r.zc = b.hd ? b.zc : a.zc + b.zc;
+    return r;
+}
+template <typename Acc>
+__device__ __forceinline__ GScan<Acc> gscan_shfl_up(const GScan<Acc>& v, int o) {
+    GScan<Acc> r;
+    r.hd = __shfl_up_sync(0xffffffffu, v.hd, o);
+    r.zc = __shfl_up_sync(0xffffffffu, v.zc, o);
+    if constexpr (sizeof(Acc) == 8) {
+        unsigned long long bits = *reinterpret_cast<const unsigned long long*>(&v.acc);
+        bits = __shfl_up_sync(0xffffffffu, bits, o);
+        r.acc = *reinterpret_cast<Acc*>(&bits);
+    } else {
+        u32 bits = *reinterpret_cast<const u32*>(&v.acc);
+        bits = __shfl_up_sync(0xffffffffu, bits, o);
+        r.acc = *reinterpret_cast<Acc*>(&bits);
+    }
+    return r;
+}
+
+// The deep levels of every group (see the file comment).  Persistent CTAs
+// (one per SM) take groups from a counter.  Inputs: the group-sorted points
+// gv (per instance in buffer gv0 or gv1, by the parity of the group sort's
+// passes): (rank | QUERY_BIT) << 32 | payload, the payload being a query's
+// local index, a datum's weight bits, or (8-byte weights) the datum's
+// position in pw.  Writes out[q] = F over the query's partial results of the
+// levels below gS.
+template <class Op>
+__global__ __launch_bounds__(GROUP_THREADS, 1) void k_group(const Inst* __restrict__ inst, int k,
+                                                            const u32* __restrict__ gslot_off,
+                                                            const u32* __restrict__ rstart, const u64* __restrict__ gv0,
+                                                            const u64* __restrict__ gv1,
+                                                            const typename Op::W* __restrict__ pw, Ctl* ctl,
+                                                            int launch_idx) {
+    typedef typename Op::Acc Acc;
+    typedef GScan<Acc> E;
+    constexpr int T = GROUP_THREADS, IT = GROUP_ITEMS, WARPS = T / 32;
+    constexpr u32 NONE = 0xffffffffu;
+    extern __shared__ __align__(128) unsigned char smem[];
+    Acc* val = reinterpret_cast<Acc*>(smem);                              // by original index
+    u32* xh = reinterpret_cast<u32*>(smem + (size_t)GROUP_CAP * sizeof(Acc));  // handles, current order
+    unsigned short* nstart = reinterpret_cast<unsigned short*>(xh + GROUP_CAP);
+    unsigned short* nzero = nstart + GROUP_NODES;
+    __shared__ E s_w[WARPS];
+    __shared__ u32 s_slot;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const u32 total = __ldg(gslot_off + k);
+    const E ident{0u, Op::e(), 0u};
+    for (;;) {
+        if (tid == 0) s_slot = atomicAdd(&ctl->tile_ctr[launch_idx], 1u);
+        __syncthreads();
+        const u32 slot = s_slot;
+        if (slot >= total) break;
+        const int s = upper_index(gslot_off, k + 1, slot);
+        const Inst& I = inst[s];
+        const u32 g = slot - __ldg(gslot_off + s);
+        const u32 gS = I.gS, ns = I.flags & 1u;
+        const u32 us = gS - ns, Uu = ns ? I.U[0] / 2u : I.U[0];
+        const u32* rs = rstart + I.pt_off + (u32)s;
+        const u32 a = __ldg(rs + (g << us)), e = __ldg(rs + min((g + 1u) << us, Uu));
+        const u32 n = min(e - a, GROUP_CAP);  // k_group_plan guarantees e - a <= GROUP_CAP
+        const bool odd = ((I.b[0] - gS + RADIX_BITS - 1) / RADIX_BITS) & 1u;
+        const u64* __restrict__ gv = (odd ? gv1 : gv0) + I.pt_off + a;
+        const u32 lrmask = (1u << gS) - 1u;
+        // the group's points in the order of the last coordinate: handles
+        // (rank bits below gS | query bit | original index) and values
+        for (u32 i = tid; i < n; i += T) {
+            const u64 v = gv[i];
+            const u32 pr = (u32)(v >> 32), pv = (u32)v;
+            const bool q = (pr & QUERY_BIT) != 0u;
+            xh[i] = (pr & lrmask) | ((q ? 1u : 0u) << gS) | (i << (gS + 1u));
+            if (q) val[i] = Op::e();
+            else if constexpr (Op::GATHER) val[i] = Op::from_w(__ldg(pw + pv));
+            else val[i] = Op::from_pay(pv);
+        }
+        const u32 p0 = (u32)tid * IT;
+        for (int lv = (int)gS - 1; lv >= 0; --lv) {
+            __syncthreads();  // handles of this level's order are in xh
+            const u32 sh = (u32)lv + 1u;
+            u32 h[IT];
+#pragma unroll
+            for (int j = 0; j < IT; ++j) h[j] = p0 + j < n ? xh[p0 + j] : 0u;
+            const u32 prevnode = (p0 > 0 && p0 - 1 < n) ? ((xh[p0 - 1] & lrmask) >> sh) : NONE;
+            const u32 nextnode = (p0 + IT < n) ? ((xh[p0 + IT] & lrmask) >> sh) : NONE;
+            // thread aggregate
+            E t = ident;
+            u32 pn = prevnode;
+#pragma unroll
+            for (int j = 0; j < IT; ++j) {
+                if (p0 + j < n) {
+                    const u32 lr = h[j] & lrmask, nd = lr >> sh;
+                    if (nd != pn) {
+                        t = ident;
+                        t.hd = 1u;
+                    }
+                    pn = nd;
+                    const u32 bit = (lr >> lv) & 1u, q = (h[j] >> gS) & 1u;
+                    if (!q && !bit) t.acc = Op::F(t.acc, val[h[j] >> (gS + 1u)]);
+                    t.zc += bit ^ 1u;
+                }
+            }
+            // block-wide exclusive segmented scan of the thread aggregates
+            E inc = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const E nb = gscan_shfl_up(inc, o);
+                if (lane >= o) inc = gscan_combine<Op>(nb, inc);
+            }
+            E lex = gscan_shfl_up(inc, 1);
+            if (lane == 0) lex = ident;
+            if (lane == 31) s_w[warp] = inc;
+            __syncthreads();
+            if (warp == 0) {
+                const E wv = s_w[lane];
+                E wi = wv;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const E nb = gscan_shfl_up(wi, o);
+                    if (lane >= o) wi = gscan_combine<Op>(nb, wi);
+                }
+                E wx = gscan_shfl_up(wi, 1);
+                if (lane == 0) wx = ident;
+                s_w[lane] = wx;
+            }
+            __syncthreads();
+            const E ex = gscan_combine<Op>(s_w[warp], lex);
+            // queries receive F over the preceding data of their node; every
+            // point learns the points with bit lv = 0 before it in its node
+            Acc acc = ex.acc;
+            u32 zc = ex.zc;
+            u32 zin[IT / 2];
+#pragma unroll
+            for (int j = 0; j < IT / 2; ++j) zin[j] = 0u;
+            pn = prevnode;
+#pragma unroll
+            for (int j = 0; j < IT; ++j) {
+                const u32 p = p0 + j;
+                if (p < n) {
+                    const u32 lr = h[j] & lrmask, nd = lr >> sh;
+                    if (nd != pn) {
+                        acc = Op::e();
+                        zc = 0u;
+                        nstart[nd] = (unsigned short)p;
+                    }
+                    pn = nd;
+                    const u32 bit = (lr >> lv) & 1u, q = (h[j] >> gS) & 1u, i = h[j] >> (gS + 1u);
+                    if (q && bit) val[i] = Op::F(val[i], acc);
+                    else if (!q && !bit) acc = Op::F(acc, val[i]);
+                    zin[j >> 1] |= zc << (16 * (j & 1));
+                    zc += bit ^ 1u;
+                    const u32 nxt = j + 1 < IT ? (p + 1 < n ? (h[j + 1] & lrmask) >> sh : NONE) : nextnode;
+                    if (nxt != nd) nzero[nd] = (unsigned short)zc;
+                }
+            }
+            __syncthreads();  // node starts and zero counts known; xh read
+            if (lv == 0) break;
+            // stable split of every node by bit lv: the order of level lv-1
+#pragma unroll
+            for (int j = 0; j < IT; ++j) {
+                const u32 p = p0 + j;
+                if (p < n) {
+                    const u32 lr = h[j] & lrmask, nd = lr >> sh, bit = (lr >> lv) & 1u;
+                    const u32 st = nstart[nd], z = (zin[j >> 1] >> (16 * (j & 1))) & 0xffffu;
+                    const u32 np = bit ? st + nzero[nd] + (p - st - z) : st + z;
+                    xh[np] = h[j];
+                }
+            }
+        }
+        __syncthreads();
+        // every query of the group: F over its partial results of the levels
+        // below gS (the unit e if it has none)
+        typename Op::Out* out = reinterpret_cast<typename Op::Out*>(I.out);
+        for (u32 i = tid; i < n; i += T) {
+            const u64 v = gv[i];
+            if ((u32)(v >> 32) & QUERY_BIT) {
+                const u32 qi = (u32)v;
+                if (qi < I.nQ) out[qi] = Op::to_out(val[i]);
+            }
+        }
+        __syncthreads();  // shared memory is free for the next group
+    }
+}
+
+}  // namespace domagg

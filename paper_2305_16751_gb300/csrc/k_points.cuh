@@ -264,7 +264,7 @@ __global__ __launch_bounds__(THREADS, 4) void k_rank_apply(const u32* __restrict
                                                         const u32* __restrict__ seg_off,
                                                         const u32* __restrict__ tile_off, int nseg,
                                                         const u32* __restrict__ tile_excl, u32* __restrict__ rank_out,
-                                                        Inst* inst, int dim) {
+                                                        Inst* inst, int dim, u32* __restrict__ rstart) {
     constexpr int TILE = THREADS * ITEMS;
     __shared__ u32 sbuf[Padded<TILE>::value];
     __shared__ u32 scratch[THREADS / 32];
@@ -294,15 +294,21 @@ __global__ __launch_bounds__(THREADS, 4) void k_rank_apply(const u32* __restrict
     block_exscan<THREADS, 1>(cnt, tot, scratch);
     u32 run = __ldg(tile_excl + t) + cnt[0];
     const u32 lx0 = threadIdx.x * ITEMS;
+    // rstart (first coordinate of m = 2): per instance, at seg_begin + seg,
+    // the instance-local sorted position of every rank's first point, and
+    // the instance's size at index U (the group sizes of k_group_plan)
+    u32* rs = rstart ? rstart + L.seg_begin + (u32)L.seg : nullptr;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const u32 x = x0 + i;
         run += (fmask >> i) & 1u;
         sbuf[pidx(lx0 + i)] = run - 1u;
+        if (rs && ((fmask >> i) & 1u)) rs[run - 1u] = x - L.seg_begin;
         if (x < L.end && x + 1 == L.seg_end) {
             const u32 U = nonstrict ? 2u * run : run;
             inst[L.seg].U[dim] = U;
             inst[L.seg].b[dim] = U <= 1u ? 0u : 32u - __clz(U - 1u);
+            if (rs) rs[run] = L.seg_end - L.seg_begin;
         }
     }
     __syncthreads();
@@ -362,7 +368,8 @@ __global__ __launch_bounds__(256) void k_count_scan(
     const u32* __restrict__ chunk_off, const u32* __restrict__ r0, const u32* __restrict__ r1,
     const u32* __restrict__ r2, Inst* inst, u32* __restrict__ pr0, u32* __restrict__ pr1, u32* __restrict__ pr2,
     u32* __restrict__ pj, W* __restrict__ pw,
-    u32* __restrict__ chunk_base, u32* __restrict__ qchunk_base, u32* __restrict__ tile_cnt) {
+    u32* __restrict__ chunk_base, u32* __restrict__ qchunk_base, u32* __restrict__ tile_cnt,
+    u32* __restrict__ gkey, u64* __restrict__ gval) {
     constexpr int WARPS = 8, C = 2 * LMAX, TILE = WARPS * CS_ROUNDS * 32;
     static_assert(TILE == 4096, "point tiles");
     __shared__ u32 s_w[WARPS][C];
@@ -403,10 +410,23 @@ __global__ __launch_bounds__(256) void k_count_scan(
             if (M >= 3) pr1[x] = c;
             if (M >= 4) pr2[x] = e2;
             pj[x] = j;
+            u32 wbits = 0;
             if (WT != 3 && !q) {
                 const u32 local = j - L.seg_begin;
-                if (WT == 1) pw[x] = (W)reinterpret_cast<const long long*>(I.dw)[local - nQ];
-                else pw[x] = (W)reinterpret_cast<const u32*>(I.dw)[local - nQ];
+                if (WT == 1) {
+                    pw[x] = (W)reinterpret_cast<const long long*>(I.dw)[local - nQ];
+                } else {
+                    wbits = reinterpret_cast<const u32*>(I.dw)[local - nQ];
+                    pw[x] = (W)wbits;
+                }
+            }
+            // m = 2 with groups: the group sort's key (the group: rank >> gS)
+            // and value (rank | query bit, then the query's local index, the
+            // weight's bits, or for 8-byte weights the position in pw)
+            if (M == 2 && gkey && I.gS) {
+                const u32 pv = q ? j - L.seg_begin : (WT == 1 ? x : wbits);
+                gkey[x] = a >> I.gS;
+                gval[x] = ((u64)(q ? (a | QUERY_BIT) : a) << 32) | (u64)pv;
             }
         }
         u32 mine = 0, mine_q = 0;
@@ -548,6 +568,7 @@ __global__ __launch_bounds__(256) void k_expand(
                 X.q = (X.a & QUERY_BIT) != 0u;
                 X.a &= ~QUERY_BIT;
                 X.bits0 = (X.q ? X.a : ~X.a) & low_mask(I.b[0]);
+                if (M == 2) X.bits0 &= ~low_mask(I.gS);  // levels below gS: k_group
             } else {
                 X.q = pj[X.p] - X.ps < nQ;
                 X.bits0 = 1u;

@@ -39,7 +39,7 @@ __global__ __launch_bounds__(1024) void k_layout(const Inst* __restrict__ inst, 
         const Inst& I = inst[k0 + (int)srel];
         const u32 nlev = M == 1 ? 1u : I.b[0];
         na = nq = bits = 0;
-        if (lv < nlev) {
+        if (lv < nlev && !(M == 2 && lv < I.gS)) {  // levels below gS: k_group, no records
             na = __ldg(lvl_tot + (u64)(k0 + (int)srel) * LMAX + lv);
             nq = __ldg(qlvl_tot + (u64)(k0 + (int)srel) * LMAX + lv);
             if (M >= 2) bits = I.b[0] - 1u - lv + (M >= 3 ? I.b[1] : 0u) + (M >= 4 ? I.b[2] : 0u);
@@ -453,6 +453,7 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
             q = local < nQ;
             if (q) {
                 if (M >= 2) bits0 = pr0[p] & low_mask(I.b[0]);
+                if (M == 2) bits0 &= ~low_mask(I.gS);  // levels below gS: k_group wrote out[q]
                 if (M >= 3) {
                     bits1 = pr1[p] & low_mask(I.b[1]);
                     c1 = (u32)__popc(bits1);
@@ -472,6 +473,8 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
         s_mask[warp][lane] = warp_transpose32(bits0, (u32)lane);  // lanes of level `lane`
         __syncwarp();
         typename Op::Acc acc = Op::e();
+        // m = 2 with groups: out[q] holds F over the levels below gS already
+        if (M == 2 && q && I.gS) acc = Op::from_out(reinterpret_cast<const typename Op::Out*>(I.out)[local]);
         if (M <= 2) {
             // one partial per query and level, at the level's base plus the
             // query lanes of that level before this one; each lane walks only

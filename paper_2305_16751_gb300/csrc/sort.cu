@@ -145,5 +145,7 @@ template int sort_pairs<u32, u32>(Launcher&, const SortSpace&, u32**, u32**, boo
                                      const u32*, bool, bool);
 template int sort_pairs<u64, u32>(Launcher&, const SortSpace&, u64**, u32**, bool, int, u64, int, int,
                                      const u32*, bool, bool);
+template int sort_pairs<u32, u64>(Launcher&, const SortSpace&, u32**, u64**, bool, int, u32, int, int,
+                                     const u32*, bool, bool);
 
 }  // namespace domagg

@@ -40,7 +40,7 @@ class domagg_stats(ctypes.Structure):
                 ("n_query_records", ctypes.c_int64), ("m", ctypes.c_int32),
                 ("rank_bits", ctypes.c_int32 * 3), ("distinct", ctypes.c_int64 * 3),
                 ("record_key_bits", ctypes.c_int32), ("record_passes", ctypes.c_int32),
-                ("workspace_bytes", ctypes.c_int64)]
+                ("workspace_bytes", ctypes.c_int64), ("n_records_shared", ctypes.c_int64)]
 
 
 class domagg_timing(ctypes.Structure):
@@ -74,6 +74,7 @@ SIGNATURES = {
     "domagg_get_stats": ([_vp, ctypes.POINTER(domagg_stats)], _int),
     "domagg_timing_enable": ([_vp, _int], _int),
     "domagg_timing_read": ([_vp, ctypes.POINTER(domagg_timing)], _int),
+    "domagg_set_tuning": ([_vp, ctypes.c_char_p, _int], _int),
     "domagg_timing_kind_name": ([_int], ctypes.c_char_p),
     "domagg_version": ([], ctypes.c_char_p),
     "domagg_forward_noalloc": ([_int, _vp, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _vp], _int),
@@ -186,7 +187,13 @@ def domagg_get_stats(h) -> dict:
     return {"n_points": s.n_points, "n_records": s.n_records, "n_query_records": s.n_query_records,
             "m": s.m, "rank_bits": list(s.rank_bits), "distinct": list(s.distinct),
             "record_key_bits": s.record_key_bits, "record_passes": s.record_passes,
-            "workspace_bytes": s.workspace_bytes}
+            "workspace_bytes": s.workspace_bytes, "n_records_shared": s.n_records_shared}
+
+
+def domagg_set_tuning(h, name: str, value: int):
+    """A tuning knob of the handle (see include/domagg.h): "group_bits",
+    "ranges_per_cta" or "blocks_per_sm"."""
+    _check(h, lib().domagg_set_tuning(h, name.encode(), int(value)))
 
 
 def domagg_timing_enable(h, enable: bool):
