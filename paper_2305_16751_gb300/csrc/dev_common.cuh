@@ -303,6 +303,14 @@ __device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {
     float e = __fsub_rn(b, __fsub_rn(s, a));
     return {s, e};
 }
+// x + y without the final renormalisation (a cascaded sum): hi carries the
+// rounded sum, lo the exact rounding errors plus both low parts.  Used only
+// for short runs (a thread's few items, a query's few levels) whose pairs
+// then enter ff_add, so lo stays tiny against the sum of the magnitudes.
+__device__ __forceinline__ ff ff_add_cascade(ff x, ff y) {
+    const ff s = ff_two_sum(x.hi, y.hi);
+    return {s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
+}
 __device__ __forceinline__ ff ff_add(ff x, ff y) {
     ff s = ff_two_sum(x.hi, y.hi);
     float lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
@@ -314,7 +322,8 @@ __device__ __forceinline__ ff ff_add(ff x, ff y) {
 // ---------------------------------------------------------------------
 // Each operator defines: Acc (scan accumulator), Part (stored partial), Out
 // (output element), Pay (32-bit record payload), W (a weight as stored in
-// the order of the last coordinate), e(), F(a, b), to_part, from_part,
+// the order of the last coordinate), e(), F(a, b), Fc(a, b) (F for short
+// runs: for float-float sums without renormalisation), to_part, from_part,
 // to_out, from_out (an output read back as an accumulator: the shared-memory
 // levels' result, completed by the records' levels), and either from_pay (the
 // payload is the weight's bits) or, with
@@ -330,6 +339,7 @@ struct OpSumF32 {
     __device__ static Acc e() { return {0.f, 0.f}; }
     __device__ static Acc from_pay(Pay p) { return {__uint_as_float(p), 0.f}; }
     __device__ static Acc F(Acc a, Acc b) { return ff_add(a, b); }
+    __device__ static Acc Fc(Acc a, Acc b) { return ff_add_cascade(a, b); }
     __device__ static Part to_part(Acc a) { return __fadd_rn(a.hi, a.lo); }
     __device__ static Acc from_part(Part p) { return {p, 0.f}; }
     __device__ static Out to_out(Acc a) { return __fadd_rn(a.hi, a.lo); }
@@ -345,6 +355,7 @@ struct OpSumI64 {
     __device__ static Acc e() { return 0; }
     __device__ static Acc from_w(W w) { return (long long)w; }
     __device__ static Acc F(Acc a, Acc b) { return (long long)((u64)a + (u64)b); }
+    __device__ static Acc Fc(Acc a, Acc b) { return F(a, b); }
     __device__ static Part to_part(Acc a) { return a; }
     __device__ static Acc from_part(Part p) { return p; }
     __device__ static Out to_out(Acc a) { return a; }
@@ -360,6 +371,7 @@ struct OpMaxI32 {
     __device__ static Acc e() { return (int)0x80000000; }
     __device__ static Acc from_pay(Pay p) { return (int)p; }
     __device__ static Acc F(Acc a, Acc b) { return a > b ? a : b; }
+    __device__ static Acc Fc(Acc a, Acc b) { return F(a, b); }
     __device__ static Part to_part(Acc a) { return a; }
     __device__ static Acc from_part(Part p) { return p; }
     __device__ static Out to_out(Acc a) { return a; }
@@ -375,6 +387,7 @@ struct OpMaxF32 {
     __device__ static Acc e() { return -__int_as_float(0x7f800000); }
     __device__ static Acc from_pay(Pay p) { return __uint_as_float(p); }
     __device__ static Acc F(Acc a, Acc b) { return fmaxf(a, b); }
+    __device__ static Acc Fc(Acc a, Acc b) { return F(a, b); }
     __device__ static Part to_part(Acc a) { return a; }
     __device__ static Acc from_part(Part p) { return p; }
     __device__ static Out to_out(Acc a) { return a; }
@@ -390,6 +403,7 @@ struct OpMinI32 {
     __device__ static Acc e() { return 0x7fffffff; }
     __device__ static Acc from_pay(Pay p) { return (int)p; }
     __device__ static Acc F(Acc a, Acc b) { return a < b ? a : b; }
+    __device__ static Acc Fc(Acc a, Acc b) { return F(a, b); }
     __device__ static Part to_part(Acc a) { return a; }
     __device__ static Acc from_part(Part p) { return p; }
     __device__ static Out to_out(Acc a) { return a; }
@@ -405,6 +419,7 @@ struct OpMinF32 {
     __device__ static Acc e() { return __int_as_float(0x7f800000); }
     __device__ static Acc from_pay(Pay p) { return __uint_as_float(p); }
     __device__ static Acc F(Acc a, Acc b) { return fminf(a, b); }  // a NaN weight never wins
+    __device__ static Acc Fc(Acc a, Acc b) { return F(a, b); }
     __device__ static Part to_part(Acc a) { return a; }
     __device__ static Acc from_part(Part p) { return p; }
     __device__ static Out to_out(Acc a) { return a; }
@@ -420,6 +435,7 @@ struct OpCount {
     __device__ static Acc e() { return 0u; }
     __device__ static Acc from_pay(Pay) { return 1u; }
     __device__ static Acc F(Acc a, Acc b) { return a + b; }
+    __device__ static Acc Fc(Acc a, Acc b) { return F(a, b); }
     __device__ static Part to_part(Acc a) { return a; }
     __device__ static Acc from_part(Part p) { return p; }
     __device__ static Out to_out(Acc a) { return (long long)a; }

@@ -34,13 +34,14 @@ namespace domagg {
 
 constexpr int GROUP_MAX_BITS = 12;       // gS <= 12: nodes of up to 2^12 ranks
 constexpr int GROUP_THREADS = 1024;
-constexpr int GROUP_ITEMS = 16;          // points per thread
+constexpr int GROUP_ITEMS = 12;          // points per thread, at most
 constexpr u32 GROUP_CAP = GROUP_THREADS * GROUP_ITEMS;  // points per group in shared memory
 constexpr u32 GROUP_NODES = 1u << (GROUP_MAX_BITS - 1);  // nodes of one level in a group, at most
 
 template <typename Acc>
 __host__ __device__ constexpr size_t group_smem_bytes() {
-    return (size_t)GROUP_CAP * (sizeof(Acc) + sizeof(u32)) + 2 * GROUP_NODES * sizeof(unsigned short);
+    return (size_t)GROUP_CAP * sizeof(Acc) + (size_t)Padded<GROUP_CAP>::value * sizeof(u32) +
+           2 * GROUP_NODES * sizeof(unsigned short);
 }
 
 // Per instance (one block each): the largest gS <= min(GROUP_MAX_BITS, b0)
@@ -162,6 +163,148 @@ __device__ __forceinline__ GScan<Acc> gscan_shfl_up(const GScan<Acc>& v, int o) 
     return r;
 }
 
+// The levels below gS of one group whose points (handles in xh, padded
+// layout; values in val by original index) are in the order of the last
+// coordinate.  IT points per thread, contiguous: thread t holds positions
+// [t*IT, t*IT + IT).  Per level, one walk over a thread's points applies the
+// thread-local part of the segmented scan (queries add F over the node's
+// data before them within the thread; the exclusive count of rank bit lv = 0
+// inside the node is kept per point), a block scan of the threads' tails
+// gives each thread the part from before it, a second walk adds that part
+// to the points before the thread's first node head only, and the split
+// scatters every point to its place in the next level's order.
+template <class Op, int IT>
+__device__ __forceinline__ void group_levels(u32 n, u32 gS, typename Op::Acc* val, u32* xh,
+                                             unsigned short* nstart, unsigned short* nzero,
+                                             GScan<typename Op::Acc>* s_w) {
+    typedef typename Op::Acc Acc;
+    typedef GScan<Acc> E;
+    constexpr u32 NONE = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const E ident{0u, Op::e(), 0u};
+    const u32 p0 = (u32)tid * IT;
+    const bool active = p0 < n;
+    const u32 lrmask = (1u << gS) - 1u;
+    for (int lv = (int)gS - 1; lv >= 0; --lv) {
+        __syncthreads();  // the handles of this level's order are in xh
+        const u32 sh = (u32)lv + 1u;
+        u32 h[IT];
+        u32 zin[IT / 2];
+        E loc = ident;
+        int first_head = IT;   // first point of the thread that starts a node
+        u32 z_first = 0;       // the first (continuing) node's zero count in this thread
+        bool first_ends = false;
+        u32 first_node = NONE;
+        if (active) {
+            const u32 prevnode = p0 > 0 ? (xh[pidx(p0 - 1)] & lrmask) >> sh : NONE;
+            const u32 nextnode = p0 + IT < n ? (xh[pidx(p0 + IT)] & lrmask) >> sh : NONE;
+#pragma unroll
+            for (int j = 0; j < IT; ++j) h[j] = p0 + j < n ? xh[pidx(p0 + j)] : 0u;
+#pragma unroll
+            for (int j = 0; j < IT / 2; ++j) zin[j] = 0u;
+            Acc acc = Op::e();
+            u32 zc = 0, pn = prevnode;
+            first_node = (h[0] & lrmask) >> sh;
+#pragma unroll
+            for (int j = 0; j < IT; ++j) {
+                const u32 p = p0 + j;
+                if (p < n) {
+                    const u32 lr = h[j] & lrmask, nd = lr >> sh;
+                    if (nd != pn) {
+                        if (first_head == IT) {
+                            first_head = j;
+                            z_first = zc;
+                            first_ends = j > 0;
+                        }
+                        acc = Op::e();
+                        zc = 0u;
+                        nstart[nd] = (unsigned short)p;
+                    }
+                    pn = nd;
+                    const u32 bit = (lr >> lv) & 1u, q = (h[j] >> gS) & 1u, i = h[j] >> (gS + 1u);
+                    if (q && bit) val[i] = Op::Fc(val[i], acc);
+                    else if (!q && !bit) acc = Op::Fc(acc, val[i]);
+                    zin[j >> 1] |= zc << (16 * (j & 1));
+                    zc += bit ^ 1u;
+                    const u32 nxt = j + 1 < IT ? (p + 1 < n ? (h[j + 1] & lrmask) >> sh : NONE) : nextnode;
+                    if (nxt != nd) {
+                        if (first_head <= j) nzero[nd] = (unsigned short)zc;  // a node that began here
+                        else {
+                            z_first = zc;
+                            first_ends = true;
+                        }
+                    }
+                }
+            }
+            loc.hd = first_head < IT ? 1u : 0u;
+            loc.acc = acc;
+            loc.zc = zc;
+        }
+        // exclusive segmented scan of the threads' tails: the part of each
+        // thread's first node that lies before the thread
+        E inc = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const E nb = gscan_shfl_up(inc, o);
+            if (lane >= o) inc = gscan_combine<Op>(nb, inc);
+        }
+        E lex = gscan_shfl_up(inc, 1);
+        if (lane == 0) lex = ident;
+        if (lane == 31) s_w[warp] = inc;
+        __syncthreads();
+        E wi = s_w[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const E nb = gscan_shfl_up(wi, o);
+            if (lane >= o) wi = gscan_combine<Op>(nb, wi);
+        }
+        E wex = gscan_shfl_up(wi, 1);
+        if (lane == 0) wex = ident;
+        wex.hd = __shfl_sync(0xffffffffu, wex.hd, warp);
+        wex.zc = __shfl_sync(0xffffffffu, wex.zc, warp);
+        if constexpr (sizeof(Acc) == 8) {
+            unsigned long long b = *reinterpret_cast<unsigned long long*>(&wex.acc);
+            b = __shfl_sync(0xffffffffu, b, warp);
+            wex.acc = *reinterpret_cast<Acc*>(&b);
+        } else {
+            u32 b = *reinterpret_cast<u32*>(&wex.acc);
+            b = __shfl_sync(0xffffffffu, b, warp);
+            wex.acc = *reinterpret_cast<Acc*>(&b);
+        }
+        const E ex = gscan_combine<Op>(wex, lex);
+        // the points before the thread's first head continue a node from the left
+        if (active && first_head > 0) {
+#pragma unroll
+            for (int j = 0; j < IT; ++j) {
+                if (j < first_head && p0 + j < n) {
+                    const u32 lr = h[j] & lrmask, bit = (lr >> lv) & 1u, q = (h[j] >> gS) & 1u;
+                    if (q && bit) {
+                        const u32 i = h[j] >> (gS + 1u);
+                        val[i] = Op::Fc(val[i], ex.acc);
+                    }
+                    zin[j >> 1] += ex.zc << (16 * (j & 1));
+                }
+            }
+            if (first_ends) nzero[first_node] = (unsigned short)(ex.zc + z_first);
+        }
+        __syncthreads();  // node starts and zero counts known; xh read
+        if (lv == 0) break;
+        // stable split of every node by bit lv: the order of level lv-1
+        if (active) {
+#pragma unroll
+            for (int j = 0; j < IT; ++j) {
+                const u32 p = p0 + j;
+                if (p < n) {
+                    const u32 lr = h[j] & lrmask, nd = lr >> sh, bit = (lr >> lv) & 1u;
+                    const u32 st = nstart[nd], z = (zin[j >> 1] >> (16 * (j & 1))) & 0xffffu;
+                    const u32 np = bit ? st + nzero[nd] + (p - st - z) : st + z;
+                    xh[pidx(np)] = h[j];
+                }
+            }
+        }
+    }
+}
+
 // The deep levels of every group (see the file comment).  Persistent CTAs
 // (one per SM) take groups from a counter.  Inputs: the group-sorted points
 // gv (per instance in buffer gv0 or gv1, by the parity of the group sort's
@@ -178,18 +321,16 @@ __global__ __launch_bounds__(GROUP_THREADS, 1) void k_group(const Inst* __restri
                                                             int launch_idx) {
     typedef typename Op::Acc Acc;
     typedef GScan<Acc> E;
-    constexpr int T = GROUP_THREADS, IT = GROUP_ITEMS, WARPS = T / 32;
-    constexpr u32 NONE = 0xffffffffu;
+    constexpr int T = GROUP_THREADS;
     extern __shared__ __align__(128) unsigned char smem[];
     Acc* val = reinterpret_cast<Acc*>(smem);                              // by original index
-    u32* xh = reinterpret_cast<u32*>(smem + (size_t)GROUP_CAP * sizeof(Acc));  // handles, current order
-    unsigned short* nstart = reinterpret_cast<unsigned short*>(xh + GROUP_CAP);
+    u32* xh = reinterpret_cast<u32*>(smem + (size_t)GROUP_CAP * sizeof(Acc));  // handles, padded
+    unsigned short* nstart = reinterpret_cast<unsigned short*>(xh + Padded<GROUP_CAP>::value);
     unsigned short* nzero = nstart + GROUP_NODES;
-    __shared__ E s_w[WARPS];
+    __shared__ E s_w[T / 32];
     __shared__ u32 s_slot;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const u32 total = __ldg(gslot_off + k);
-    const E ident{0u, Op::e(), 0u};
     for (;;) {
         if (tid == 0) s_slot = atomicAdd(&ctl->tile_ctr[launch_idx], 1u);
         __syncthreads();
@@ -212,104 +353,14 @@ __global__ __launch_bounds__(GROUP_THREADS, 1) void k_group(const Inst* __restri
             const u64 v = gv[i];
             const u32 pr = (u32)(v >> 32), pv = (u32)v;
             const bool q = (pr & QUERY_BIT) != 0u;
-            xh[i] = (pr & lrmask) | ((q ? 1u : 0u) << gS) | (i << (gS + 1u));
+            xh[pidx(i)] = (pr & lrmask) | ((q ? 1u : 0u) << gS) | (i << (gS + 1u));
             if (q) val[i] = Op::e();
             else if constexpr (Op::GATHER) val[i] = Op::from_w(__ldg(pw + pv));
             else val[i] = Op::from_pay(pv);
         }
-        const u32 p0 = (u32)tid * IT;
-        for (int lv = (int)gS - 1; lv >= 0; --lv) {
-            __syncthreads();  // handles of this level's order are in xh
-            const u32 sh = (u32)lv + 1u;
-            u32 h[IT];
-#pragma unroll
-            for (int j = 0; j < IT; ++j) h[j] = p0 + j < n ? xh[p0 + j] : 0u;
-            const u32 prevnode = (p0 > 0 && p0 - 1 < n) ? ((xh[p0 - 1] & lrmask) >> sh) : NONE;
-            const u32 nextnode = (p0 + IT < n) ? ((xh[p0 + IT] & lrmask) >> sh) : NONE;
-            // thread aggregate
-            E t = ident;
-            u32 pn = prevnode;
-#pragma unroll
-            for (int j = 0; j < IT; ++j) {
-                if (p0 + j < n) {
-                    const u32 lr = h[j] & lrmask, nd = lr >> sh;
-                    if (nd != pn) {
-                        t = ident;
-                        t.hd = 1u;
-                    }
-                    pn = nd;
-                    const u32 bit = (lr >> lv) & 1u, q = (h[j] >> gS) & 1u;
-                    if (!q && !bit) t.acc = Op::F(t.acc, val[h[j] >> (gS + 1u)]);
-                    t.zc += bit ^ 1u;
-                }
-            }
-            // block-wide exclusive segmented scan of the thread aggregates
-            E inc = t;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const E nb = gscan_shfl_up(inc, o);
-                if (lane >= o) inc = gscan_combine<Op>(nb, inc);
-            }
-            E lex = gscan_shfl_up(inc, 1);
-            if (lane == 0) lex = ident;
-            if (lane == 31) s_w[warp] = inc;
-            __syncthreads();
-            if (warp == 0) {
-                const E wv = s_w[lane];
-                E wi = wv;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const E nb = gscan_shfl_up(wi, o);
-                    if (lane >= o) wi = gscan_combine<Op>(nb, wi);
-                }
-                E wx = gscan_shfl_up(wi, 1);
-                if (lane == 0) wx = ident;
-                s_w[lane] = wx;
-            }
-            __syncthreads();
-            const E ex = gscan_combine<Op>(s_w[warp], lex);
-            // queries receive F over the preceding data of their node; every
-            // point learns the points with bit lv = 0 before it in its node
-            Acc acc = ex.acc;
-            u32 zc = ex.zc;
-            u32 zin[IT / 2];
-#pragma unroll
-            for (int j = 0; j < IT / 2; ++j) zin[j] = 0u;
-            pn = prevnode;
-#pragma unroll
-            for (int j = 0; j < IT; ++j) {
-                const u32 p = p0 + j;
-                if (p < n) {
-                    const u32 lr = h[j] & lrmask, nd = lr >> sh;
-                    if (nd != pn) {
-                        acc = Op::e();
-                        zc = 0u;
-                        nstart[nd] = (unsigned short)p;
-                    }
-                    pn = nd;
-                    const u32 bit = (lr >> lv) & 1u, q = (h[j] >> gS) & 1u, i = h[j] >> (gS + 1u);
-                    if (q && bit) val[i] = Op::F(val[i], acc);
-                    else if (!q && !bit) acc = Op::F(acc, val[i]);
-                    zin[j >> 1] |= zc << (16 * (j & 1));
-                    zc += bit ^ 1u;
-                    const u32 nxt = j + 1 < IT ? (p + 1 < n ? (h[j + 1] & lrmask) >> sh : NONE) : nextnode;
-                    if (nxt != nd) nzero[nd] = (unsigned short)zc;
-                }
-            }
-            __syncthreads();  // node starts and zero counts known; xh read
-            if (lv == 0) break;
-            // stable split of every node by bit lv: the order of level lv-1
-#pragma unroll
-            for (int j = 0; j < IT; ++j) {
-                const u32 p = p0 + j;
-                if (p < n) {
-                    const u32 lr = h[j] & lrmask, nd = lr >> sh, bit = (lr >> lv) & 1u;
-                    const u32 st = nstart[nd], z = (zin[j >> 1] >> (16 * (j & 1))) & 0xffffu;
-                    const u32 np = bit ? st + nzero[nd] + (p - st - z) : st + z;
-                    xh[np] = h[j];
-                }
-            }
-        }
+        static_assert(GROUP_ITEMS == 12, "items per thread dispatched below");
+        if (n <= 8u * T) group_levels<Op, 8>(n, gS, val, xh, nstart, nzero, s_w);
+        else group_levels<Op, 12>(n, gS, val, xh, nstart, nzero, s_w);
         __syncthreads();
         // every query of the group: F over its partial results of the levels
         // below gS (the unit e if it has none)
