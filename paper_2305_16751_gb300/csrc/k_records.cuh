@@ -184,13 +184,6 @@ __device__ __forceinline__ Acc volatile_read(const Acc* p) {
 // the last coordinate, the running value at a query record is F over exactly
 // the data of its node with a smaller last coordinate; it is stored in the
 // query record's partial slot.
-// Predecessors each lane of the look-back examines per round trip.  A chain
-// of tiles in a long segment finishes its inclusive prefixes at about
-// 32*SEG_LB tiles per L2 round trip, so a wide window keeps the look-back
-// off the critical path.
-constexpr int SEG_LB = 8;
-constexpr u32 NONE_IDX = 0xffffffffu;
-
 template <class Op, typename K, int THREADS, int ITEMS>
 __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys0, const K* __restrict__ keys1,
                                                      const typename Op::Pay* __restrict__ pays0,
@@ -329,10 +322,10 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys0
     Acc texcl = lhead ? lex : Op::F(wex, lex);  // within-tile exclusive prefix
     const bool texcl_head = lhead || wex_head;  // a head occurs before me in the tile
     // tile aggregate, look-back and publication (warp 0).  The look-back is
-    // warp-cooperative: lane l examines SEG_LB predecessors, so one round trip
-    // to L2 covers 32*SEG_LB of them; the aggregates up to the first tile that
-    // ends the chain (a published prefix, or a segment head inside the tile)
-    // are combined with a masked warp reduction.
+    // warp-cooperative: lane l examines tile u-1-l, so one round trip to L2
+    // covers 32 predecessors; the aggregates up to the first tile that ends
+    // the chain (a published prefix, or a segment head inside the tile) are
+    // combined with a masked warp reduction.
     if (warp == 0) {
         Acc tagg = Op::e();
         bool thead = false;
@@ -355,46 +348,39 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys0
             u32 u = t;  // tiles [u, t) have been combined into excl
             u32 spins = 0;
             while (u > first_tile) {
-                // lane l examines tiles u-1-(SEG_LB*l + r), r < SEG_LB: one
-                // round trip to L2 covers 32*SEG_LB predecessors
-                const u32 avail = u - first_tile;
-                Acc v[SEG_LB];
-                u32 k_nr = NONE_IDX, k_tm = NONE_IDX;  // first not ready, first ending the chain
-#pragma unroll
-                for (int r = 0; r < SEG_LB; ++r) {
-                    const u32 idx = (u32)lane * SEG_LB + r;
-                    v[r] = Op::e();
-                    bool ready = false, term = false;
-                    if (idx < avail) {
-                        const SegStatus<Acc>* ps = status + (u - 1 - idx);
-                        const u32 f = st_load_acquire(&ps->flag);
-                        ready = (f >> 2) == (epoch & EPOCH_MASK) && (f & 3u);
-                        if (ready) {
-                            if ((f & 3u) == ST_PREFIX) {
-                                v[r] = volatile_read(&ps->incl);
-                                term = true;
-                            } else {
-                                v[r] = volatile_read(&ps->agg);
-                                term = *reinterpret_cast<const volatile u32*>(&ps->has_head) != 0;
-                            }
+                const bool exists = u - 1 - (u32)lane >= first_tile && (u32)lane < u - first_tile;
+                u32 f = 0, hh = 0;
+                Acc v = Op::e();
+                bool ready = true, term = false;
+                if (exists) {
+                    const SegStatus<Acc>* ps = status + (u - 1 - lane);
+                    f = st_load_acquire(&ps->flag);
+                    ready = (f >> 2) == (epoch & EPOCH_MASK) && (f & 3u);
+                    if (ready) {
+                        if ((f & 3u) == ST_PREFIX) {
+                            v = volatile_read(&ps->incl);
+                            term = true;
+                        } else {
+                            hh = *reinterpret_cast<const volatile u32*>(&ps->has_head);
+                            v = volatile_read(&ps->agg);
+                            term = hh != 0;
                         }
                     }
-                    if (!ready && k_nr == NONE_IDX) k_nr = idx;
-                    if (term && k_tm == NONE_IDX) k_tm = idx;
+                } else {
+                    ready = false;  // beyond the chain start: never consumed
                 }
-                k_nr = __reduce_min_sync(0xffffffffu, k_nr);
-                k_tm = __reduce_min_sync(0xffffffffu, k_tm);
+                const u32 nr = __ballot_sync(0xffffffffu, !ready);
+                const u32 tm = __ballot_sync(0xffffffffu, term);
+                const int k_nr = nr ? __ffs(nr) - 1 : 32;
+                const int k_tm = tm ? __ffs(tm) - 1 : 32;
                 const bool finish = k_tm < k_nr;
-                const u32 take = finish ? k_tm + 1 : k_nr;  // predecessors [0, take) are combined
+                const int take = finish ? k_tm + 1 : k_nr;  // lanes [0, take) are combined
                 if (take > 0) {
-                    Acc r_acc = Op::e();
+                    Acc r = lane < take ? v : Op::e();
 #pragma unroll
-                    for (int r = 0; r < SEG_LB; ++r)
-                        if ((u32)lane * SEG_LB + r < take) r_acc = Op::F(r_acc, v[r]);
-#pragma unroll
-                    for (int o = 16; o >= 1; o >>= 1) r_acc = Op::F(r_acc, shfl_xor_acc(r_acc, o));
-                    excl = Op::F(r_acc, excl);
-                    u -= take;
+                    for (int o = 16; o >= 1; o >>= 1) r = Op::F(r, shfl_xor_acc(r, o));
+                    excl = Op::F(r, excl);
+                    u -= (u32)take;
                 }
                 if (finish) break;
                 if (take == 0) {
