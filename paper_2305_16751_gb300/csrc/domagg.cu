@@ -897,8 +897,9 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             const u64 nst = std::max<u64>(std::max(std::max(ntr0, ntr1), ntp), 1);
             st = grow(h, h->st_multi, (size_t)nst * RADIX * sizeof(u64), true);
             if (st) return st;
-            st = grow(h, h->st_seg, (size_t)std::max<u64>(std::max(nts0, nts1), 1) * sizeof(SegStatus<typename Op::Acc>),
-                      true);
+            // the segmented scan's tile summaries and carries
+            st = grow(h, h->st_seg, (size_t)std::max<u64>(std::max(nts0, nts1), 1) *
+                                        (sizeof(TileAgg<typename Op::Acc>) + sizeof(typename Op::Acc)));
             if (st) return st;
         }
         u32* d_up = (u32*)R[0];
@@ -967,24 +968,33 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             sort_pairs<u32, Pay>(L, rs, keys1, pays1, false, C.key_bits1, 0x7fffffffu, KIND_HIST_RECORDS,
                                  KIND_SORT_RECORDS, d_sbits + nseg0);
         }
-        // segmented scan (6m+3), per key class
-        if (C.T0 > 0 && nseg0 > 0) {
-            const int li = L.lookback_index();
-            L.start(KIND_SEGSCAN, (double)C.T0 * (sizeof(K) + sizeof(Pay)) + (double)C.Tq * sizeof(Part) +
+        // segmented scan (6m+3), per key class: tile summaries, their scan, the partials
+        typedef typename Op::Acc Acc;
+        TileAgg<Acc>* tagg = (TileAgg<Acc>*)h->st_seg.p;
+        auto segscan = [&](auto kc, u64 ntiles, u32 nseg_c, const auto* k0p, const auto* k1p, const Pay* p0p,
+                           const Pay* p1p, const u32* so, const u32* stiles, const u32* sbits, double rec_bytes) {
+            typedef std::remove_cv_t<std::remove_pointer_t<decltype(k0p)>> KC;
+            constexpr int ITEMS_C = decltype(kc)::value;
+            Acc* carry = (Acc*)(tagg + ntiles);
+            L.start(KIND_SEGSCAN, rec_bytes);
+            k_segscan<Op, KC, SEG_THREADS, ITEMS_C, false><<<(unsigned)ntiles, SEG_THREADS, 0, stream>>>(
+                k0p, k1p, p0p, p1p, so, stiles, (int)nseg_c, sbits, (const W*)P[18], partial, (u32)C.Tq, tagg, carry);
+            L.stop();
+            L.start(KIND_SMALL, 0.0);
+            k_seg_carry<Op><<<1, 1024, 0, stream>>>(stiles, (int)nseg_c, tagg, carry);
+            L.stop();
+            L.start(KIND_SEGSCAN, rec_bytes + (double)C.Tq * sizeof(Part) +
                                       (Op::GATHER ? (double)(pt_offs[C.k1] - pt_offs[C.k0]) * sizeof(W) : 0.0));
-            k_segscan<Op, K, SEG_THREADS, SEG_ITEMS><<<(unsigned)nts0, SEG_THREADS, 0, stream>>>(
-                keys[0], keys[1], pays[0], pays[1], d_so, d_stiles, (int)nseg0, d_sbits, (const W*)P[18], partial,
-                (u32)C.Tq, (SegStatus<typename Op::Acc>*)h->st_seg.p, h->ctl, li);
+            k_segscan<Op, KC, SEG_THREADS, ITEMS_C, true><<<(unsigned)ntiles, SEG_THREADS, 0, stream>>>(
+                k0p, k1p, p0p, p1p, so, stiles, (int)nseg_c, sbits, (const W*)P[18], partial, (u32)C.Tq, tagg, carry);
             L.stop();
-        }
-        if (C.T1 > 0 && nseg1 > 0) {
-            const int li = L.lookback_index();
-            L.start(KIND_SEGSCAN, (double)C.T1 * (4 + sizeof(Pay)));
-            k_segscan<Op, u32, SEG_THREADS, SEG_ITEMS1><<<(unsigned)nts1, SEG_THREADS, 0, stream>>>(
-                keys1[0], keys1[1], pays1[0], pays1[1], d_so1, d_stiles1, (int)nseg1, d_sbits + nseg0,
-                (const W*)P[18], partial, (u32)C.Tq, (SegStatus<typename Op::Acc>*)h->st_seg.p, h->ctl, li);
-            L.stop();
-        }
+        };
+        if (C.T0 > 0 && nseg0 > 0)
+            segscan(std::integral_constant<int, SEG_ITEMS>(), nts0, (u32)nseg0, keys[0], keys[1], pays[0], pays[1], d_so,
+                    d_stiles, d_sbits, (double)C.T0 * (sizeof(K) + sizeof(Pay)));
+        if (C.T1 > 0 && nseg1 > 0)
+            segscan(std::integral_constant<int, SEG_ITEMS1>(), nts1, (u32)nseg1, keys1[0], keys1[1], pays1[0],
+                    pays1[1], d_so1, d_stiles1, d_sbits + nseg0, (double)C.T1 * (4 + sizeof(Pay)));
         // per-query reduction (replaces 6m+4 .. 6m+9)
         const u32 qb = q_offs[C.k0], qe = q_offs[C.k1];
         if (qe > qb) {

@@ -127,31 +127,6 @@ __global__ __launch_bounds__(1024) void k_layout(const Inst* __restrict__ inst, 
     }
 }
 
-// Look-back status of the segmented scan.  The aggregate and the inclusive
-// prefix live in separate fields, each written once before the flag that
-// announces it (release), and read after that flag (acquire): a reader that
-// saw ST_AGG never meets a half-written prefix.
-template <typename Acc>
-struct alignas(32) SegStatus {
-    u32 flag;      // (epoch << 2) | ST_AGG / ST_PREFIX
-    u32 has_head;  // a segment starts inside the tile (with ST_AGG)
-    Acc agg;       // F over the tile's items after its last head (ST_AGG)
-    Acc incl;      // inclusive prefix at the tile's end (ST_PREFIX)
-};
-
-template <typename Acc>
-__device__ __forceinline__ void seg_publish_agg(SegStatus<Acc>* s, u32 epoch, bool head, Acc v) {
-    s->has_head = head ? 1u : 0u;
-    s->agg = v;
-    __threadfence();
-    st_store_release(&s->flag, ((epoch & EPOCH_MASK) << 2) | ST_AGG);
-}
-template <typename Acc>
-__device__ __forceinline__ void seg_publish_prefix(SegStatus<Acc>* s, u32 epoch, Acc v) {
-    s->incl = v;
-    __threadfence();
-    st_store_release(&s->flag, ((epoch & EPOCH_MASK) << 2) | ST_PREFIX);
-}
 template <typename Acc>
 __device__ __forceinline__ Acc shfl_xor_acc(Acc v, int o) {
     if constexpr (sizeof(Acc) == 8) {
@@ -161,6 +136,18 @@ __device__ __forceinline__ Acc shfl_xor_acc(Acc v, int o) {
     } else {
         u32 bits = *reinterpret_cast<u32*>(&v);
         bits = __shfl_xor_sync(0xffffffffu, bits, o);
+        return *reinterpret_cast<Acc*>(&bits);
+    }
+}
+template <typename Acc>
+__device__ __forceinline__ Acc shfl_up_acc(Acc v, int o) {
+    if constexpr (sizeof(Acc) == 8) {
+        unsigned long long bits = *reinterpret_cast<unsigned long long*>(&v);
+        bits = __shfl_up_sync(0xffffffffu, bits, o);
+        return *reinterpret_cast<Acc*>(&bits);
+    } else {
+        u32 bits = *reinterpret_cast<u32*>(&v);
+        bits = __shfl_up_sync(0xffffffffu, bits, o);
         return *reinterpret_cast<Acc*>(&bits);
     }
 }
@@ -177,6 +164,14 @@ __device__ __forceinline__ Acc volatile_read(const Acc* p) {
     return v;
 }
 
+// Tile summary of the segmented scan: whether a segment starts inside the
+// tile, and F over the tile's records after its last start.
+template <typename Acc>
+struct TileAgg {
+    u32 hd;
+    Acc agg;
+};
+
 // Segmented scan of F over the sorted records of every instance (Definition
 // "Segmented scan", Sec. 2.2): a segment is a maximal run of equal node keys
 // (the role bit ignored).  Data records contribute their weight, query
@@ -184,7 +179,15 @@ __device__ __forceinline__ Acc volatile_read(const Acc* p) {
 // the last coordinate, the running value at a query record is F over exactly
 // the data of its node with a smaller last coordinate; it is stored in the
 // query record's partial slot.
-template <class Op, typename K, int THREADS, int ITEMS>
+//
+// Reduce, then scan: the kernel runs twice over the same tiles of 4096
+// records.  With APPLY = false each tile writes its summary (TileAgg);
+// k_seg_carry scans the summaries of all tiles in one block; with APPLY =
+// true each tile reads the carry from the tiles before it and writes the
+// query records' partials.  No tile waits on another (a decoupled look-back
+// made long segments wait on their predecessors' prefixes); the price is a
+// second read of the records.
+template <class Op, typename K, int THREADS, int ITEMS, bool APPLY>
 __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys0, const K* __restrict__ keys1,
                                                      const typename Op::Pay* __restrict__ pays0,
                                                      const typename Op::Pay* __restrict__ pays1,
@@ -193,7 +196,8 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys0
                                                      const u32* __restrict__ seg_bits,
                                                      const typename Op::W* __restrict__ wgt,
                                                      typename Op::Part* __restrict__ partial, u32 n_partial,
-                                                     SegStatus<typename Op::Acc>* status, Ctl* ctl, int launch_idx) {
+                                                     TileAgg<typename Op::Acc>* __restrict__ tagg,
+                                                     const typename Op::Acc* __restrict__ carry) {
     typedef typename Op::Acc Acc;
     typedef typename Op::Pay Pay;
     constexpr int TILE = THREADS * ITEMS, WARPS = THREADS / 32;
@@ -202,26 +206,33 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys0
     __shared__ Pay s_pays[Padded<TILE>::value];
     __shared__ Acc s_wacc[WARPS];
     __shared__ u32 s_whead[WARPS];
-    __shared__ Acc s_excl;
-    __shared__ u32 s_info[2];
-    if (threadIdx.x == 0) {
-        s_info[0] = atomicAdd(&ctl->tile_ctr[launch_idx], 1u);
-        s_info[1] = ctl->epoch_base + (u32)launch_idx;
-    }
-    __syncthreads();
-    const u32 t = s_info[0], epoch = s_info[1];
+    const u32 t = blockIdx.x;
     if (t >= __ldg(tile_off + nseg)) return;
     const TileLoc L = locate_tile<TILE>(t, seg_off, tile_off, nseg);
     // the sort left this segment in the buffer of its pass count's parity
     const bool odd = ((__ldg(seg_bits + L.seg) + RADIX_BITS - 1) / RADIX_BITS) & 1u;
     const K* __restrict__ keys = odd ? keys1 : keys0;
     const typename Op::Pay* __restrict__ pays = odd ? pays1 : pays0;
-    // coalesced load into shared memory, then blocked reads
-    for (int i = 0; i < ITEMS; ++i) {
-        const u32 x = (u32)i * THREADS + threadIdx.x;
-        if (L.start + x < L.end) {
-            s_keys[pidx(x)] = keys[L.start + x];
-            s_pays[pidx(x)] = pays[L.start + x];
+    // coalesced loads, all in flight together, then into shared memory
+    {
+        constexpr int HALF = ITEMS / 2;
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            K kv[HALF];
+            Pay pv[HALF];
+#pragma unroll
+            for (int i = 0; i < HALF; ++i) {
+                const u32 x = (u32)(h2 * HALF + i) * THREADS + threadIdx.x;
+                const bool in = L.start + x < L.end;
+                kv[i] = in ? keys[L.start + x] : K(0);
+                pv[i] = in ? pays[L.start + x] : Pay(0);
+            }
+#pragma unroll
+            for (int i = 0; i < HALF; ++i) {
+                const u32 x = (u32)(h2 * HALF + i) * THREADS + threadIdx.x;
+                s_keys[pidx(x)] = kv[i];
+                s_pays[pidx(x)] = pv[i];
+            }
         }
     }
     __syncthreads();
@@ -231,15 +242,12 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys0
     bool has_prev = x0 > L.seg_begin;
     if (has_prev && x0 < L.end) prev = lx0 == 0 ? keys[x0 - 1] : s_keys[pidx(lx0 - 1)];
     prev &= ~role;
-    // thread aggregate: (head seen, F over items after the last head); the
-    // running value at every query record is kept for the output pass
+    // thread aggregate: (head seen, F over items after the last head)
     bool head_any = false;
     Acc agg = Op::e();
-    u32 headmask = 0, qmask = 0;
-    Acc loc[ITEMS];
+    u32 headmask = 0;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
-        loc[i] = Op::e();
         if (x0 + i < L.end) {
             const K kx = s_keys[pidx(lx0 + i)];
             const K kn = kx & ~role;
@@ -251,33 +259,21 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys0
                 headmask |= 1u << i;
                 agg = Op::e();
             }
-            if (kx & role) {
-                qmask |= 1u << i;
-                loc[i] = agg;
-            } else {
+            if (!(kx & role)) {
                 const Pay py = s_pays[pidx(lx0 + i)];
-                if constexpr (Op::GATHER) agg = Op::F(agg, Op::from_w(__ldg(wgt + py)));
-                else agg = Op::F(agg, Op::from_pay(py));
+                if constexpr (Op::GATHER) agg = Op::Fc(agg, Op::from_w(__ldg(wgt + py)));
+                else agg = Op::Fc(agg, Op::from_pay(py));
             }
         }
     }
-    // block-wide exclusive scan of (head, agg) with the segmented operator
+    // block-wide scan of (head, agg) with the segmented operator
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     bool ihead = head_any;
     Acc iacc = agg;  // inclusive within the warp
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int nh = __shfl_up_sync(0xffffffffu, (int)ihead, o);
-        Acc na;
-        if constexpr (sizeof(Acc) == 8) {
-            unsigned long long bits = *reinterpret_cast<unsigned long long*>(&iacc);
-            bits = __shfl_up_sync(0xffffffffu, bits, o);
-            na = *reinterpret_cast<Acc*>(&bits);
-        } else {
-            u32 bits = *reinterpret_cast<u32*>(&iacc);
-            bits = __shfl_up_sync(0xffffffffu, bits, o);
-            na = *reinterpret_cast<Acc*>(&bits);
-        }
+        const Acc na = shfl_up_acc(iacc, o);
         if (lane >= o) {
             if (!ihead) iacc = Op::F(na, iacc);
             ihead = ihead || nh;
@@ -288,127 +284,120 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys0
         s_whead[warp] = ihead ? 1u : 0u;
     }
     __syncthreads();
-    // exclusive prefix of this thread within the tile
-    Acc wex = Op::e();  // prefix from earlier warps
-    bool wex_head = false;
-    for (int w = 0; w < warp; ++w) {
-        if (s_whead[w]) {
-            wex = s_wacc[w];
-            wex_head = true;
-        } else {
-            wex = Op::F(wex, s_wacc[w]);
+    if constexpr (!APPLY) {
+        // the tile's summary
+        if (threadIdx.x == 0) {
+            Acc ta = Op::e();
+            bool th = false;
+            for (int w = 0; w < WARPS; ++w) {
+                if (s_whead[w]) {
+                    ta = s_wacc[w];
+                    th = true;
+                } else {
+                    ta = Op::F(ta, s_wacc[w]);
+                }
+            }
+            tagg[t].hd = th ? 1u : 0u;
+            tagg[t].agg = ta;
         }
-    }
-    // exclusive within warp: inclusive of lane-1
-    Acc lex;
-    int lhead;
-    {
-        Acc src = iacc;
-        if constexpr (sizeof(Acc) == 8) {
-            unsigned long long bits = *reinterpret_cast<unsigned long long*>(&src);
-            bits = __shfl_up_sync(0xffffffffu, bits, 1);
-            lex = *reinterpret_cast<Acc*>(&bits);
-        } else {
-            u32 bits = *reinterpret_cast<u32*>(&src);
-            bits = __shfl_up_sync(0xffffffffu, bits, 1);
-            lex = *reinterpret_cast<Acc*>(&bits);
+        return;
+    } else {
+        // exclusive prefix of this thread within the tile
+        Acc wex = Op::e();  // prefix from earlier warps
+        bool wex_head = false;
+        for (int w = 0; w < warp; ++w) {
+            if (s_whead[w]) {
+                wex = s_wacc[w];
+                wex_head = true;
+            } else {
+                wex = Op::F(wex, s_wacc[w]);
+            }
         }
-        lhead = __shfl_up_sync(0xffffffffu, (int)ihead, 1);
+        Acc lex = shfl_up_acc(iacc, 1);
+        int lhead = __shfl_up_sync(0xffffffffu, (int)ihead, 1);
         if (lane == 0) {
             lex = Op::e();
             lhead = 0;
         }
-    }
-    Acc texcl = lhead ? lex : Op::F(wex, lex);  // within-tile exclusive prefix
-    const bool texcl_head = lhead || wex_head;  // a head occurs before me in the tile
-    // tile aggregate, look-back and publication (warp 0).  The look-back is
-    // warp-cooperative: lane l examines tile u-1-l, so one round trip to L2
-    // covers 32 predecessors; the aggregates up to the first tile that ends
-    // the chain (a published prefix, or a segment head inside the tile) are
-    // combined with a masked warp reduction.
-    if (warp == 0) {
-        Acc tagg = Op::e();
-        bool thead = false;
-        for (int w = 0; w < WARPS; ++w) {
-            if (s_whead[w]) {
-                tagg = s_wacc[w];
-                thead = true;
-            } else {
-                tagg = Op::F(tagg, s_wacc[w]);
-            }
-        }
-        SegStatus<Acc>* my = status + t;
-        const bool starts_fresh = L.first || (__shfl_sync(0xffffffffu, headmask, 0) & 1u);
-        Acc excl = Op::e();
-        if (starts_fresh) {
-            if (lane == 0) seg_publish_prefix(my, epoch, tagg);
-        } else {
-            if (lane == 0) seg_publish_agg(my, epoch, thead, tagg);
-            const u32 first_tile = t - (L.start - L.seg_begin) / (u32)TILE;
-            u32 u = t;  // tiles [u, t) have been combined into excl
-            u32 spins = 0;
-            while (u > first_tile) {
-                const bool exists = u - 1 - (u32)lane >= first_tile && (u32)lane < u - first_tile;
-                u32 f = 0, hh = 0;
-                Acc v = Op::e();
-                bool ready = true, term = false;
-                if (exists) {
-                    const SegStatus<Acc>* ps = status + (u - 1 - lane);
-                    f = st_load_acquire(&ps->flag);
-                    ready = (f >> 2) == (epoch & EPOCH_MASK) && (f & 3u);
-                    if (ready) {
-                        if ((f & 3u) == ST_PREFIX) {
-                            v = volatile_read(&ps->incl);
-                            term = true;
-                        } else {
-                            hh = *reinterpret_cast<const volatile u32*>(&ps->has_head);
-                            v = volatile_read(&ps->agg);
-                            term = hh != 0;
-                        }
-                    }
-                } else {
-                    ready = false;  // beyond the chain start: never consumed
-                }
-                const u32 nr = __ballot_sync(0xffffffffu, !ready);
-                const u32 tm = __ballot_sync(0xffffffffu, term);
-                const int k_nr = nr ? __ffs(nr) - 1 : 32;
-                const int k_tm = tm ? __ffs(tm) - 1 : 32;
-                const bool finish = k_tm < k_nr;
-                const int take = finish ? k_tm + 1 : k_nr;  // lanes [0, take) are combined
-                if (take > 0) {
-                    Acc r = lane < take ? v : Op::e();
+        const Acc texcl = lhead ? lex : Op::F(wex, lex);  // within-tile exclusive prefix
+        const bool texcl_head = lhead || wex_head;        // a head occurs before me in the tile
+        // a thread before the tile's first head continues the segment coming
+        // from the tiles before (their carry)
+        Acc run = texcl_head ? texcl : Op::F(carry[t], texcl);
+        // output walk: the running value at every query record
 #pragma unroll
-                    for (int o = 16; o >= 1; o >>= 1) r = Op::F(r, shfl_xor_acc(r, o));
-                    excl = Op::F(r, excl);
-                    u -= (u32)take;
-                }
-                if (finish) break;
-                if (take == 0) {
-                    if (++spins > SPIN_LIMIT || ((spins & 255u) == 0 && timed_out(ctl))) {
-                        if (lane == 0) {
-                            atomicOr(&ctl->error, ERR_TIMEOUT);
-                            ctl->timeout_where = 4u;
-                        }
-                        break;
-                    }
-                    if (spins > 64) __nanosleep(256);
+        for (int i = 0; i < ITEMS; ++i) {
+            if (x0 + i < L.end) {
+                if ((headmask >> i) & 1u) run = Op::e();
+                const K kx = s_keys[pidx(lx0 + i)];
+                const Pay py = s_pays[pidx(lx0 + i)];
+                if (kx & role) {
+                    if ((u32)py < n_partial) partial[py] = Op::to_part(run);
+                } else {
+                    if constexpr (Op::GATHER) run = Op::Fc(run, Op::from_w(__ldg(wgt + py)));
+                    else run = Op::Fc(run, Op::from_pay(py));
                 }
             }
-            if (lane == 0) seg_publish_prefix(my, epoch, thead ? tagg : Op::F(excl, tagg));
         }
-        if (lane == 0) s_excl = excl;
+    }
+}
+
+// Carries of the segmented scan: for every tile (over all segments, in
+// order), F over the records of its segment in the tiles before it, from the
+// tiles' summaries.  One block; each thread scans a run of consecutive tiles,
+// then a block scan joins the runs.  A segment's first tile holds a head (its
+// first record), so carries never cross segments.
+template <class Op>
+__global__ __launch_bounds__(1024) void k_seg_carry(const u32* __restrict__ tile_off, int nseg,
+                                                    const TileAgg<typename Op::Acc>* __restrict__ tagg,
+                                                    typename Op::Acc* __restrict__ carry) {
+    typedef typename Op::Acc Acc;
+    __shared__ Acc s_wacc[32];
+    __shared__ u32 s_whead[32];
+    const u32 n = __ldg(tile_off + nseg);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const u32 per = (n + blockDim.x - 1) / blockDim.x;
+    const u32 a = min(n, (u32)tid * per), b = min(n, a + per);
+    bool hd = false;
+    Acc acc = Op::e();
+    for (u32 t = a; t < b; ++t) {
+        const TileAgg<Acc> g = tagg[t];
+        if (g.hd) {
+            acc = g.agg;
+            hd = true;
+        } else {
+            acc = Op::F(acc, g.agg);
+        }
+    }
+    bool ihead = hd;
+    Acc iacc = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int nh = __shfl_up_sync(0xffffffffu, (int)ihead, o);
+        const Acc na = shfl_up_acc(iacc, o);
+        if (lane >= o) {
+            if (!ihead) iacc = Op::F(na, iacc);
+            ihead = ihead || nh;
+        }
+    }
+    if (lane == 31) {
+        s_wacc[warp] = iacc;
+        s_whead[warp] = ihead ? 1u : 0u;
     }
     __syncthreads();
-    // output: a query record before the thread's first head continues the
-    // segment coming from the left (prefix); after it, its own run suffices
-    const Acc prefix = texcl_head ? texcl : Op::F(s_excl, texcl);
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        if (qmask & (1u << i)) {
-            const u64 slot = (u64)s_pays[pidx(lx0 + i)];
-            const bool own = (headmask & ((2u << i) - 1u)) != 0;
-            if (slot < n_partial) partial[slot] = Op::to_part(own ? loc[i] : Op::F(prefix, loc[i]));
-        }
+    Acc wex = Op::e();
+    for (int w = 0; w < warp; ++w) wex = s_whead[w] ? s_wacc[w] : Op::F(wex, s_wacc[w]);
+    Acc lex = shfl_up_acc(iacc, 1);
+    int lhead = __shfl_up_sync(0xffffffffu, (int)ihead, 1);
+    if (lane == 0) {
+        lex = Op::e();
+        lhead = 0;
+    }
+    Acc run = lhead ? lex : Op::F(wex, lex);
+    for (u32 t = a; t < b; ++t) {
+        carry[t] = run;
+        const TileAgg<Acc> g = tagg[t];
+        run = g.hd ? g.agg : Op::F(run, g.agg);
     }
 }
 

@@ -86,3 +86,18 @@ def test_groups_with_nonstrict_coordinates(mask):
     assert domagg.stats()["n_records_shared"] > 0
     want, _ = oracle.brute(D, Q, w, "sum", nonstrict=mask)
     assert np.array_equal(got, want)
+
+
+def test_integer_results_repeat_exactly():
+    """Five forward calls on the same 2^20-per-side tied input give the same
+    integer results as the oracle every time (a race between tiles or groups
+    would show as a run-to-run difference)."""
+    p = workloads.tied_floats(n=1 << 20, weights="i32")
+    w64 = p.w.astype(np.int64)
+    want_c, _ = oracle.sweep2(p.D, p.Q, None, "count", nonstrict=3)
+    want_s, _ = oracle.sweep2(p.D, p.Q, w64, "sum")
+    D, Q, w = to_dev(p.D), to_dev(p.Q), to_dev(w64)
+    for _ in range(5):
+        c = domagg.forward(D, Q, None, "count", nonstrict=3).cpu().numpy()
+        s = domagg.forward(D, Q, w, "sum").cpu().numpy()
+        assert np.array_equal(c, want_c) and np.array_equal(s, want_s)
