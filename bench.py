@@ -141,6 +141,27 @@ def profiled_traffic(bytes_per_launch: float, source: str = "k_radix.cuh",
     return float(fields["traffic_per_algorithmic_byte"]) * bytes_per_launch
 
 
+def kind_roofline(kinds: dict, kind: str, peak: float, peak_src: str, kernel: str):
+    """Roofline object of one kernel kind from the library's per-launch
+    timing (CUDA events on the launching stream): its algorithmic bytes per
+    launch over its average launch time, against the measured HBM peak."""
+    k = kinds.get(kind, {"ms": 0.0, "bytes": 0.0, "launches": 0})
+    n = max(k["launches"], 1)
+    achieved = k["bytes"] / max(k["ms"], 1e-9) / 1e6
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": peak_src, "kernel": kernel, "launch_ms": k["ms"] / n,
+            "bytes_per_launch": k["bytes"] / n}
+
+
+def step_model(n_points: int, records: int, n_queries: int, ms: float, peak: float, m: int = 2):
+    """The whole step against the per-query byte model of the hot-path scope
+    (what the pipeline must move at minimum): m = 2, 4-byte keys and
+    payloads, 8-bit digits: 170 B per point, 72 B per record, 4 B per query;
+    m = 3, 8-byte keys, four 11-bit passes: 176 B per record."""
+    b = 170.0 * n_points + 72.0 * records + 4.0 * n_queries if m == 2 else 176.0 * records
+    return {"bytes": b, "ms": ms, "achieved_gbs": b / (ms * 1e6), "frac": b / (ms * 1e6) / peak}
+
+
 def _sortscan_sample(p, n: int):
     """The first n data points and n queries of the workload (the same
     distribution at a size the CPU oracle completes)."""
@@ -426,7 +447,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": args.n, "m": 2, "op": "sum", "weights": "f32",
-                       "records": st["n_records"], "record_passes": st["record_passes"],
+                       "records": st["n_records"], "records_in_shared_memory": st["n_records_shared"],
+                       "record_passes": st["record_passes"],
                        "l2": f"inputs ({(p.D.nbytes + p.Q.nbytes + p.w.nbytes) >> 20} MB) and the records workspace "
                              f"({st['n_records'] * 16 >> 20} MB) exceed the 129 MB L2; no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -439,7 +461,8 @@ def main():
                          "launch_ms": dom["ms"] / max(dom["launches"], 1),
                          "bytes_per_launch": dom["bytes"] / max(dom["launches"], 1)},
             "gpu_launches": launches,
-            "phase_ms": phase_ms}
+            "phase_ms": phase_ms,
+            "step_model": step_model(2 * args.n, st["n_records"], args.n, ms, peak)}
     clocks = clk.summary()
     line["clocks"] = clocks
 
@@ -454,7 +477,17 @@ def main():
 
         tfb = timed_steps(fb, max(3, args.steps // 2), 2, stream, torch)
         fb_ms = statistics.mean(tfb)
-        line["fwd_bwd"] = {"value": p.Q.shape[0] / (fb_ms / 1e3), "unit": "queries/s", "ms_per_step": fb_ms}
+        domagg.domagg_timing_enable(h, True)
+        domagg.domagg_timing_read(h)
+        fb()
+        kfb = domagg.domagg_timing_read(h)
+        domagg.domagg_timing_enable(h, False)
+        dom_fb = max(("sort_records", "group", "segscan"), key=lambda k: kfb.get(k, {"ms": 0.0})["ms"])
+        line["fwd_bwd"] = {"value": p.Q.shape[0] / (fb_ms / 1e3), "unit": "queries/s", "ms_per_step": fb_ms,
+                           "roofline": kind_roofline(kfb, "sort_records", peak, peak_src,
+                                                     "k_onesweep (records radix pass), forward and backward"),
+                           "largest_kind": dom_fb,
+                           "phase_ms": {k: v["ms"] for k, v in kfb.items() if v["ms"] > 0}}
 
         def fbw():
             o = domagg.dominance_sum(D, Q, wg, 0, "wavelet")
@@ -480,7 +513,10 @@ def main():
         domagg.domagg_timing_enable(h, False)
         line["m3"] = {"value": p3.Q.shape[0] / (m3_ms / 1e3), "unit": "queries/s", "ms_per_step": m3_ms,
                       "workload": "m3_nD2^21_nQ2^21_gmm_i32coords_i64w_sum", "records": st3["n_records"],
-                      "record_passes": st3["record_passes"], "phase_ms": {k: v["ms"] for k, v in k3.items()}}
+                      "record_passes": st3["record_passes"], "phase_ms": {k: v["ms"] for k, v in k3.items()},
+                      "roofline": kind_roofline(k3, "sort_records", peak, peak_src,
+                                                "k_onesweep (records radix pass, 64-bit and 32-bit key classes)"),
+                      "step_model": step_model(2 * args.n3, st3["n_records"], args.n3, m3_ms, peak, m=3)}
         del D3, Q3, w3, o3
         line["wavelet"] = bench_wavelet(args, D, Q, w, out, dev, stream, torch, domagg)
         line["variants"] = bench_variants(args, dev, stream, torch, domagg, workloads)

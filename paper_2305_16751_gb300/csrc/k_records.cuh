@@ -360,13 +360,18 @@ __global__ __launch_bounds__(1024) void k_seg_carry(const u32* __restrict__ tile
     const u32 a = min(n, (u32)tid * per), b = min(n, a + per);
     bool hd = false;
     Acc acc = Op::e();
-    for (u32 t = a; t < b; ++t) {
-        const TileAgg<Acc> g = tagg[t];
-        if (g.hd) {
-            acc = g.agg;
-            hd = true;
-        } else {
-            acc = Op::F(acc, g.agg);
+    for (u32 t0 = a; t0 < b; t0 += 8) {  // eight summaries in flight
+        TileAgg<Acc> g[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) g[j] = t0 + j < b ? tagg[t0 + j] : TileAgg<Acc>{0u, Op::e()};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (g[j].hd) {
+                acc = g[j].agg;
+                hd = true;
+            } else {
+                acc = Op::F(acc, g[j].agg);
+            }
         }
     }
     bool ihead = hd;
@@ -394,10 +399,15 @@ __global__ __launch_bounds__(1024) void k_seg_carry(const u32* __restrict__ tile
         lhead = 0;
     }
     Acc run = lhead ? lex : Op::F(wex, lex);
-    for (u32 t = a; t < b; ++t) {
-        carry[t] = run;
-        const TileAgg<Acc> g = tagg[t];
-        run = g.hd ? g.agg : Op::F(run, g.agg);
+    for (u32 t0 = a; t0 < b; t0 += 8) {
+        TileAgg<Acc> g[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) g[j] = t0 + j < b ? tagg[t0 + j] : TileAgg<Acc>{0u, Op::e()};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (t0 + j < b) carry[t0 + j] = run;
+            run = g[j].hd ? g[j].agg : Op::F(run, g[j].agg);
+        }
     }
 }
 

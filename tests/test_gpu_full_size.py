@@ -84,3 +84,21 @@ def test_m3_gaussian_mixture_brute_sample():
     got = gpu_forward(p.D, p.Q, p.w, "sum")
     qi = _sample(p.Q.shape[0], BRUTE_SAMPLE, 2)
     assert_matches_oracle(got, p.D, p.Q, p.w, "sum", qidx=qi)
+
+
+def test_m2_float32_sum_is_bit_identical_run_to_run():
+    """Two forward calls at full size give the same float32 sums bit for
+    bit: every float-float combination runs in a fixed order (tile summaries
+    scanned in tile order, fixed block scans, a fixed per-query reduction),
+    so nothing depends on which tile finishes first.  The same for the
+    backward at 2^22."""
+    p, _, _ = full_size_m2_oracle("f32", "sum")
+    a = _fwd(p.D, p.Q, p.w, "sum", "improved")
+    b = _fwd(p.D, p.Q, p.w, "sum", "improved")
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    pa = workloads.autograd_floats()
+    g = to_dev(pa.extra["c"])
+    D, Q = to_dev(pa.D), to_dev(pa.Q)
+    ga = domagg.backward(D, Q, g).cpu().numpy()
+    gb = domagg.backward(D, Q, g).cpu().numpy()
+    assert np.array_equal(ga.view(np.uint32), gb.view(np.uint32))
