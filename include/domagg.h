@@ -70,7 +70,9 @@ typedef enum {
     DOMAGG_ERR_OOM = 3,         /* workspace could not be allocated / over the cap */
     DOMAGG_ERR_CUDA = 4,        /* a CUDA runtime call failed (see domagg_last_error) */
     DOMAGG_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
-    DOMAGG_ERR_NAN = 6          /* a coordinate is NaN */
+    DOMAGG_ERR_NAN = 6,         /* a coordinate is NaN */
+    DOMAGG_ERR_BOUNDS = 7       /* checked build only: a kernel met an index outside its buffer
+                                   (the access was skipped; outputs are undefined) */
 } domagg_status;
 
 typedef enum { DOMAGG_SUM = 0, DOMAGG_MAX = 1, DOMAGG_COUNT = 2, DOMAGG_MIN = 3 } domagg_op;
@@ -129,6 +131,36 @@ domagg_status domagg_forward_ex(domagg_handle h, int m, const void* d_coords, in
                                 const void* d_weights, domagg_dtype weight_dtype, domagg_op op,
                                 uint32_t nonstrict_mask, domagg_variant variant, void* out,
                                 void* stream);
+
+/* One shard of domagg_forward, for a forward split over several GPUs (the
+ * paper's Sec. 6 reading: the flat map is partitioned and one exchange of the
+ * outputs joins the parts).  Every shard runs the point phase on all points
+ * (ranks, the order of the last coordinate); the flat map's records are
+ * split by node: with gS the rank levels taken per group of 2^gS ranks in
+ * shared memory (m = 2; 0 otherwise), shard s takes the levels lv >= gS of
+ * the first rank with (lv - gS) % nshards == s and the groups g with
+ * g % nshards == s.  The shard's outputs are F over its records only; F over
+ * the nshards outputs (domagg_combine, or a collective with F) is
+ * domagg_forward's result.
+ *   shard, nshards  0 <= shard < nshards <= 64
+ *   out             device [nQ] (output dtype as domagg_forward), overwritten
+ *   out_lo          float32 SUM only: device float32 [nQ], the low halves of
+ *                   the shard's float-float partials (out holds the high
+ *                   halves), so that joining shards adds no rounding; must be
+ *                   NULL or is ignored for other ops.
+ * Other arguments, layouts and errors as domagg_forward. */
+domagg_status domagg_forward_shard(domagg_handle h, int shard, int nshards, int m, const void* d_coords, int64_t nD,
+                                   const void* q_coords, int64_t nQ, domagg_dtype coord_dtype, const void* d_weights,
+                                   domagg_dtype weight_dtype, domagg_op op, void* out, float* out_lo, void* stream);
+
+/* out[q] = F over parts[s][q], s < nparts (1..64): joins the outputs of
+ * domagg_forward_shard.  parts and parts_lo are HOST arrays of nparts device
+ * pointers; parts_lo (float32 SUM, may be NULL) holds the low halves.  The
+ * float32 sum adds the float-float pairs in float-float and rounds once.
+ * Asynchronous on `stream`. */
+domagg_status domagg_combine(domagg_handle h, domagg_op op, domagg_dtype weight_dtype, int nparts,
+                             const void* const* parts, const float* const* parts_lo, int64_t nQ, void* out,
+                             void* stream);
 
 /* Same as domagg_forward with HOST buffers (pageable or pinned): copies the
  * inputs to the handle's device staging area, runs the forward on `stream`,
@@ -327,7 +359,10 @@ domagg_status domagg_forward_noalloc(int m, const void* d_coords, int64_t nD, co
  * DOMAGG_ERR_INVALID_ARG. */
 domagg_status domagg_set_tuning(domagg_handle h, const char* name, int value);
 
-/* Library version string. */
+/* Library version string ("checked build" when compiled with
+ * DOMAGG_CHECKED: every kernel tests the indices it loads and stores
+ * through, and an out-of-range one is reported as DOMAGG_ERR_BOUNDS by the
+ * call's mid-call synchronisation or by domagg_sync_status). */
 const char* domagg_version(void);
 
 #ifdef __cplusplus

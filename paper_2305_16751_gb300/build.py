@@ -13,6 +13,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libdomagg.so")
+# the checked build: the same sources with DOMAGG_CHECKED (every kernel tests
+# its computed indices and reports DOMAGG_ERR_BOUNDS instead of touching
+# memory outside a buffer); for tests and debugging
+LIB_CHECKED = os.path.join(HERE, "libdomagg_checked.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["domagg.cu", "sort.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -31,10 +35,13 @@ def _deps() -> list[str]:
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
-        return True
-    t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(f) > t for f in _deps())
+    for lib in (LIB, LIB_CHECKED):
+        if not os.path.exists(lib):
+            return True
+        t = os.path.getmtime(lib)
+        if any(os.path.getmtime(f) > t for f in _deps()):
+            return True
+    return False
 
 
 def build(force: bool = False, verbose_ptxas: bool = False) -> str:
@@ -46,24 +53,28 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     # tuning constants (e.g. "-DDOMAGG_SEG_THREADS=128"), for sweeps
     extra += [f for f in os.environ.get("DOMAGG_NVCC_DEFINES", "").split() if f.startswith("-D")]
 
-    def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(job) -> str:
+        src, checked = job
+        obj = os.path.join(BUILD_DIR, src.replace(".cu", "_checked.o" if checked else ".o"))
+        flags = ["-DDOMAGG_CHECKED"] if checked else []
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
-        if verbose_ptxas:
+        if verbose_ptxas and not checked:
             print(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = f"{LIB}.{os.getpid()}.tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    jobs = [(src, checked) for checked in (False, True) for src in SOURCES]
+    with cf.ThreadPoolExecutor(len(jobs)) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    for lib, these in ((LIB, objs[:len(SOURCES)]), (LIB_CHECKED, objs[len(SOURCES):])):
+        tmp = f"{lib}.{os.getpid()}.tmp"
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *these]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

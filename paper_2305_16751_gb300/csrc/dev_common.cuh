@@ -58,6 +58,13 @@ struct Inst {
     // shared memory (k_group); G groups.  gS = 0: every level goes through
     // the records in HBM.
     u32 gS, G;
+    // levels of the first rank whose records this call takes through HBM
+    // (bit lv; device-computed), and the call's shard of the flat map: shard
+    // `shard` of `nshards` takes the levels >= gS with (lv - gS) % nshards ==
+    // shard and the groups g with g % nshards == shard (host-filled; 0 of 1
+    // for a whole forward)
+    u32 lvmask, shard, nshards;
+    float* out_lo;  // float32 sums of a shard: the low halves of the float-float partials (or null)
 };
 // The last of the M coordinates is not stored but constant (the basic
 // variant of Sec. 4 run as the Sec. 5 pipeline with one more coordinate).
@@ -146,6 +153,36 @@ __device__ __forceinline__ u32 lookback_u32(const u64* status, int C, int c, u32
     }
     return excl;
 }
+
+// ---------------------------------------------------------------------
+// checked build (compiled with DOMAGG_CHECKED): every computed index the
+// kernels store through or load from is tested against its buffer; a miss
+// records which site it was in a per-translation-unit device flag, the
+// access is skipped, and the host reports DOMAGG_ERR_BOUNDS.  Nothing traps.
+// domagg_check(ok, site) guards an access that the product build bounds as
+// well (it returns ok); DOMAGG_GUARD(ok, site) adds a test that the product
+// build leaves out (it is `true` there).
+// ---------------------------------------------------------------------
+enum : u32 {
+    SITE_EXPAND = 1, SITE_SORT_SCATTER = 2, SITE_SORT_LOCAL = 3, SITE_SEGSCAN_PARTIAL = 4, SITE_REDUCE = 5,
+    SITE_GROUP_OUT = 6, SITE_GROUP_SPLIT = 7, SITE_GROUP_NODE = 8, SITE_GROUP_VAL = 9, SITE_RANK = 10,
+    SITE_WAVELET_OUT = 11, SITE_WAVELET_EL = 12, SITE_SEGSCAN_TILE = 13, SITE_COUNT_CHUNK = 14
+};
+#ifdef DOMAGG_CHECKED
+static __device__ u32 g_bounds_hit;    // one per translation unit
+static __device__ u32 g_bounds_site;
+__device__ __forceinline__ bool domagg_check(bool ok, u32 site) {
+    if (!ok) {
+        atomicOr(&g_bounds_hit, 1u);
+        g_bounds_site = site;
+    }
+    return ok;
+}
+#define DOMAGG_GUARD(ok, site) domagg::domagg_check((ok), (site))
+#else
+__device__ __forceinline__ bool domagg_check(bool ok, u32) { return ok; }
+#define DOMAGG_GUARD(ok, site) true
+#endif
 
 // ---------------------------------------------------------------------
 // small helpers

@@ -159,6 +159,31 @@ domagg_status grow_pinned(domagg_ctx* h, size_t bytes) {
     return DOMAGG_OK;
 }
 
+// Checked build: the site of the first out-of-range index any kernel met
+// (this translation unit's and sort.cu's flags), 0 if none; cleared.
+u32 bounds_site(bool clear) {
+#ifdef DOMAGG_CHECKED
+    u32 hit = 0, site = 0;
+    cudaMemcpyFromSymbol(&hit, g_bounds_hit, sizeof(u32));
+    cudaMemcpyFromSymbol(&site, g_bounds_site, sizeof(u32));
+    if (clear && hit) {
+        const u32 z = 0;
+        cudaMemcpyToSymbol(g_bounds_hit, &z, sizeof(u32));
+    }
+    cudaGetLastError();
+    const u32 mine = hit ? (site ? site : 1u) : 0u;
+    const u32 sorts = bounds_site_sort(clear);
+    return mine ? mine : sorts;
+#else
+    (void)clear;
+    return 0u;
+#endif
+}
+
+domagg_status bounds_error(domagg_ctx* h, u32 site) {
+    return fail(h, DOMAGG_ERR_BOUNDS, "checked build: an index out of range was caught (site " + std::to_string(site) + ")");
+}
+
 domagg_status device_error(domagg_ctx* h, u32 bits) {
     if (bits & ERR_NAN) return fail(h, DOMAGG_ERR_NAN, "a coordinate is NaN");
     if (bits & ERR_OVERFLOW) return fail(h, DOMAGG_ERR_UNSUPPORTED, "more than 2^32 flat-map records");
@@ -586,12 +611,12 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         if constexpr (M <= 2) return run_wavelet<M, Op>(h, inst, d_inst, perm, r0, N, L, stream, hp, ctl_pos);
         else return fail(h, DOMAGG_ERR_UNSUPPORTED, "the level-wise formulation takes m <= 2");
     }
-    // ---- m = 2: the size of the groups of ranks that k_group takes
-    if (use_groups) {
-        L.start(KIND_SMALL, 0.0);
-        k_group_plan<<<k, 1024, 0, stream>>>(d_inst, rstart, gbits, GROUP_CAP, h->group_bits);
-        L.stop();
-    }
+    // ---- the levels whose records go through HBM (this shard's, and for
+    // m = 2 the levels above the groups of ranks that k_group takes)
+    L.start(KIND_SMALL, 0.0);
+    k_group_plan<M><<<k, 1024, 0, stream>>>(d_inst, use_groups ? rstart : nullptr, use_groups ? gbits : nullptr,
+                                            GROUP_CAP, use_groups ? h->group_bits : 0);
+    L.stop();
     // ---- count / offset scan of the flat map, per level
     {
         // perm, gathered ranks, ranks / index / weight written in order, weight gathered
@@ -667,6 +692,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         L.stop();
         e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "point phase");
+        if (const u32 site = bounds_site(true)) return bounds_error(h, site);
         if (h_ctl->error) {
             const u32 bits = h_ctl->error;
             cudaMemsetAsync(&h->ctl->error, 0, sizeof(u32), stream);
@@ -683,9 +709,10 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             for (u32 lv = 0; lv < nlev[s]; ++lv) {
                 T_flat += lvl[(size_t)s * LMAX + lv];
                 // levels below gS are formed, sorted and scanned in shared
-                // memory (k_group): no records in HBM
-                if (M == 2 && lv < inst[s].gS) {
-                    T_shared += lvl[(size_t)s * LMAX + lv];
+                // memory (k_group), levels of other shards elsewhere: no
+                // records in HBM here
+                if (M == 2 && lv < inst[s].gS) T_shared += lvl[(size_t)s * LMAX + lv];
+                if (!((inst[s].lvmask >> lv) & 1u)) {
                     lvl[(size_t)s * LMAX + lv] = 0;
                     qlvl[(size_t)s * LMAX + lv] = 0;
                 }
@@ -758,6 +785,13 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         }
     }
 
+    // ---- a shard's outputs start at the unit (the group kernel and the
+    // reduction each add only this shard's part)
+    if (inst[0].nshards > 1 && NQ > 0) {
+        L.start(KIND_SMALL, 0.0);
+        k_fill_unit<Op><<<(unsigned)((NQ + 255) / 256), 256, 0, stream>>>(d_inst, d_q_offs, k, (u32)NQ);
+        L.stop();
+    }
     // ---- m = 2: the deep rank levels by groups, in shared memory (k_group):
     // a stable sort of the points (in the order of the last coordinate) by
     // their group of ranks, then one CTA per group
@@ -899,7 +933,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             if (st) return st;
             // the segmented scan's tile summaries and carries
             st = grow(h, h->st_seg, (size_t)std::max<u64>(std::max(nts0, nts1), 1) *
-                                        (sizeof(TileAgg<typename Op::Acc>) + sizeof(typename Op::Acc)));
+                                        std::max(sizeof(TileAgg<typename Op::Acc>) + sizeof(typename Op::Acc),
+                                                 sizeof(SegStatus<typename Op::Acc>)), true);
             if (st) return st;
         }
         u32* d_up = (u32*)R[0];
@@ -975,6 +1010,17 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                            const Pay* p1p, const u32* so, const u32* stiles, const u32* sbits, double rec_bytes) {
             typedef std::remove_cv_t<std::remove_pointer_t<decltype(k0p)>> KC;
             constexpr int ITEMS_C = decltype(kc)::value;
+            if constexpr (M >= 3) {
+                // short segments (node keys of two ranks): one pass, carries by look-back
+                const int li = L.lookback_index();
+                L.start(KIND_SEGSCAN, rec_bytes + (double)C.Tq * sizeof(Part) +
+                                          (Op::GATHER ? (double)(pt_offs[C.k1] - pt_offs[C.k0]) * sizeof(W) : 0.0));
+                k_segscan_lb<Op, KC, SEG_THREADS, ITEMS_C><<<(unsigned)ntiles, SEG_THREADS, 0, stream>>>(
+                    k0p, k1p, p0p, p1p, so, stiles, (int)nseg_c, sbits, (const W*)P[18], partial, (u32)C.Tq,
+                    (SegStatus<Acc>*)h->st_seg.p, h->ctl, li);
+                L.stop();
+                return;
+            }
             Acc* carry = (Acc*)(tagg + ntiles);
             L.start(KIND_SEGSCAN, rec_bytes);
             k_segscan<Op, KC, SEG_THREADS, ITEMS_C, false><<<(unsigned)ntiles, SEG_THREADS, 0, stream>>>(
@@ -1251,6 +1297,58 @@ domagg_status domagg_forward_ex(domagg_handle h, int m, const void* d_coords, in
     if (variant == DOMAGG_BASIC) inst[0].flags |= FLAG_VIRTUAL_LAST | (1u << m);
     if (variant == DOMAGG_WAVELET) inst[0].flags |= FLAG_WAVELET;
     return dispatch(h, M, inst, coord_dtype, weight_dtype, op, false, (cudaStream_t)stream);
+}
+
+domagg_status domagg_forward_shard(domagg_handle h, int shard, int nshards, int m, const void* d_coords, int64_t nD,
+                                   const void* q_coords, int64_t nQ, domagg_dtype coord_dtype, const void* d_weights,
+                                   domagg_dtype weight_dtype, domagg_op op, void* out, float* out_lo, void* stream) {
+    if (nshards < 1 || nshards > MAX_SHARDS || shard < 0 || shard >= nshards)
+        return fail(h, DOMAGG_ERR_INVALID_ARG, "shard must be in [0, nshards), nshards in [1, 64]");
+    domagg_status st = check_common(h, m, nD, nQ, coord_dtype, weight_dtype, op);
+    if (st) return st;
+    const bool ffsum = op == DOMAGG_SUM && weight_dtype == DOMAGG_F32;
+    if (ffsum && nQ > 0 && !out_lo) return fail(h, DOMAGG_ERR_INVALID_ARG, "float32 sums need out_lo");
+    if ((nD > 0 && !d_coords) || (nQ > 0 && (!q_coords || !out)) || (op != DOMAGG_COUNT && nD > 0 && !d_weights))
+        return fail(h, DOMAGG_ERR_INVALID_ARG, "null pointer");
+    if (nQ == 0) return DOMAGG_OK;
+    cudaSetDevice(h->device);
+    std::vector<Inst> inst{make_inst(d_coords, nD, q_coords, nQ, d_weights, out)};
+    inst[0].shard = (u32)shard;
+    inst[0].nshards = (u32)nshards;
+    inst[0].out_lo = ffsum ? out_lo : nullptr;
+    return dispatch(h, m, inst, coord_dtype, weight_dtype, op, false, (cudaStream_t)stream);
+}
+
+domagg_status domagg_combine(domagg_handle h, domagg_op op, domagg_dtype weight_dtype, int nparts,
+                             const void* const* parts, const float* const* parts_lo, int64_t nQ, void* out,
+                             void* stream) {
+    if (!h) return DOMAGG_ERR_INVALID_ARG;
+    if (nparts < 1 || nparts > MAX_SHARDS || !parts || nQ < 0 || (nQ > 0 && !out) || nQ >= (1ll << 31))
+        return fail(h, DOMAGG_ERR_INVALID_ARG, "bad parts, size or output");
+    ShardParts P;
+    memset(&P, 0, sizeof(P));
+    for (int s = 0; s < nparts; ++s) {
+        if (nQ > 0 && !parts[s]) return fail(h, DOMAGG_ERR_INVALID_ARG, "null part");
+        P.part[s] = parts[s];
+        P.lo[s] = parts_lo ? parts_lo[s] : nullptr;
+    }
+    if (nQ == 0) return DOMAGG_OK;
+    cudaSetDevice(h->device);
+    const unsigned grid = (unsigned)((nQ + 255) / 256);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int code = op * 8 + (op == DOMAGG_COUNT ? 0 : (int)weight_dtype);
+    switch (code) {
+        case DOMAGG_SUM * 8 + DOMAGG_F32: k_combine<OpSumF32><<<grid, 256, 0, s>>>(nparts, P, (u32)nQ, out); break;
+        case DOMAGG_SUM * 8 + DOMAGG_I64: k_combine<OpSumI64><<<grid, 256, 0, s>>>(nparts, P, (u32)nQ, out); break;
+        case DOMAGG_MAX * 8 + DOMAGG_I32: k_combine<OpMaxI32><<<grid, 256, 0, s>>>(nparts, P, (u32)nQ, out); break;
+        case DOMAGG_MAX * 8 + DOMAGG_F32: k_combine<OpMaxF32><<<grid, 256, 0, s>>>(nparts, P, (u32)nQ, out); break;
+        case DOMAGG_MIN * 8 + DOMAGG_I32: k_combine<OpMinI32><<<grid, 256, 0, s>>>(nparts, P, (u32)nQ, out); break;
+        case DOMAGG_MIN * 8 + DOMAGG_F32: k_combine<OpMinF32><<<grid, 256, 0, s>>>(nparts, P, (u32)nQ, out); break;
+        case DOMAGG_COUNT * 8: k_combine<OpCount><<<grid, 256, 0, s>>>(nparts, P, (u32)nQ, out); break;
+        default: return fail(h, DOMAGG_ERR_INVALID_ARG, "unsupported op / weight dtype");
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DOMAGG_OK : cuda_fail(h, e, "combine");
 }
 
 domagg_status domagg_forward_host(domagg_handle h, int m, const void* d_coords, int64_t nD, const void* q_coords,
@@ -1708,6 +1806,7 @@ domagg_status domagg_sync_status(domagg_handle h, void* stream) {
     cudaSetDevice(h->device);
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "sync");
+    if (const u32 site = bounds_site(true)) return bounds_error(h, site);
     u32 bits = 0;
     e = cudaMemcpy(&bits, &h->ctl->error, sizeof(u32), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(h, e, "sync");
@@ -1762,7 +1861,11 @@ const char* domagg_timing_kind_name(int kind) {
     return names[kind];
 }
 
-const char* domagg_version(void) { return "domagg 0.1 (sm_103a)"; }
+#ifdef DOMAGG_CHECKED
+const char* domagg_version(void) { return "domagg 0.2 (sm_103a, checked build)"; }
+#else
+const char* domagg_version(void) { return "domagg 0.2 (sm_103a)"; }
+#endif
 
 }  // extern "C"
 

@@ -131,6 +131,11 @@ inline u64 sort_range_bound_n(u64 items, u64 nseg) {
 // Point-phase scans (ranks, count scan) tile the points in 4096s.
 constexpr u32 POINT_TILE = 4096;
 
+// Checked build: the site of the first out-of-range index the kernels of
+// sort.cu met (0 if none), cleared when `clear`.  Always 0 in the product
+// build.
+u32 bounds_site_sort(bool clear);
+
 // Stable LSD sort of (key, value) pairs by bits [0, total_bits) of
 // (key & keymask), segment by segment.  keys[0]/vals[0] hold the input;
 // returns the index (0 or 1) of the buffers that hold the result.  With

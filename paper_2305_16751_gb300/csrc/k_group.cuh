@@ -27,6 +27,8 @@
 // points keep the order of the last coordinate (queries before data on a
 // tie), which is what the segmented scan needs (Sec. 5).
 #pragma once
+#include <type_traits>
+
 #include "dev_common.cuh"
 #include "k_points.cuh"
 
@@ -53,8 +55,9 @@ __host__ __device__ constexpr size_t group_smem_bytes() {
 // first coordinate doubles the ranks (2r for data, 2r+1 for queries), so a
 // group of 2^gS ranks is 2^(gS-1) undoubled ranks.  Also writes gbits[s],
 // the bits of the group id (b0 - gS) the group sort sorts.
-static __global__ __launch_bounds__(1024) void k_group_plan(Inst* inst, const u32* __restrict__ rstart,
-                                                           u32* __restrict__ gbits, u32 cap, int max_bits) {
+template <int M>
+__global__ __launch_bounds__(1024) void k_group_plan(Inst* inst, const u32* __restrict__ rstart,
+                                                    u32* __restrict__ gbits, u32 cap, int max_bits) {
     __shared__ u32 s_max[32];
     __shared__ u32 s_done;
     const int s = blockIdx.x;
@@ -65,7 +68,7 @@ static __global__ __launch_bounds__(1024) void k_group_plan(Inst* inst, const u3
     const u32 Uu = ns ? U / 2u : U;
     const u32* rs = rstart + I.pt_off + (u32)s;
     u32 chosen = 0, G = 0;
-    const bool eligible = n > 0 && b0 > 0 && !(I.flags & (FLAG_WAVELET | FLAG_VIRTUAL_LAST));
+    const bool eligible = M == 2 && rstart && n > 0 && b0 > 0 && !(I.flags & (FLAG_WAVELET | FLAG_VIRTUAL_LAST));
     for (int S = eligible ? min(min(max_bits, GROUP_MAX_BITS), (int)b0) : 0; S >= 1; --S) {
         const u32 us = (u32)S - ns;  // undoubled ranks per group: 2^us
         const u32 g_n = (Uu + (1u << us) - 1u) >> us;
@@ -94,7 +97,14 @@ static __global__ __launch_bounds__(1024) void k_group_plan(Inst* inst, const u3
     if (threadIdx.x == 0) {
         I.gS = chosen;
         I.G = chosen ? G : 0u;
-        gbits[s] = chosen ? b0 - chosen : 0u;
+        if (gbits) gbits[s] = chosen ? b0 - chosen : 0u;
+        // the levels this call's records take: those >= gS of this shard
+        const u32 nlev = M == 1 ? 1u : b0;
+        const u32 ns = max(I.nshards, 1u);
+        u32 mask = 0;
+        for (u32 lv = chosen; lv < nlev && lv < 32u; ++lv)
+            if ((lv - chosen) % ns == I.shard) mask |= 1u << lv;
+        I.lvmask = n > 0 ? mask : 0u;
     }
 }
 
@@ -109,7 +119,11 @@ static __global__ __launch_bounds__(1024) void k_group_slots(const Inst* __restr
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int base = 0; base < k; base += blockDim.x) {
         const int s = base + threadIdx.x;
-        const u32 v = s < k && inst[s].gS ? inst[s].G : 0u;
+        u32 v = 0;
+        if (s < k && inst[s].gS) {  // groups g with g % nshards == shard
+            const u32 ns = max(inst[s].nshards, 1u), sh = inst[s].shard, G = inst[s].G;
+            v = sh < G ? (G - sh + ns - 1) / ns : 0u;
+        }
         u32 inc = v;
         for (int o = 1; o < 32; o <<= 1) {
             const u32 x = __shfl_up_sync(0xffffffffu, inc, o);
@@ -136,13 +150,14 @@ struct GScan {
     Acc acc;
     u32 zc;
 };
-// a precedes b
+// a precedes b; float-float sums combine without renormalisation (the
+// block scan's tree is ten levels deep, so the low parts stay tiny)
 template <class Op>
 __device__ __forceinline__ GScan<typename Op::Acc> gscan_combine(const GScan<typename Op::Acc>& a,
                                                                 const GScan<typename Op::Acc>& b) {
     GScan<typename Op::Acc> r;
     r.hd = a.hd | b.hd;
-    r.acc = b.hd ? b.acc : Op::F(a.acc, b.acc);
+    r.acc = b.hd ? b.acc : Op::Fc(a.acc, b.acc);
     r.zc = b.hd ? b.zc : a.zc + b.zc;
     return r;
 }
@@ -199,7 +214,7 @@ __device__ __forceinline__ void group_levels(u32 n, u32 gS, typename Op::Acc* va
             const u32 prevnode = p0 > 0 ? (xh[pidx(p0 - 1)] & lrmask) >> sh : NONE;
             const u32 nextnode = p0 + IT < n ? (xh[pidx(p0 + IT)] & lrmask) >> sh : NONE;
 #pragma unroll
-            for (int j = 0; j < IT; ++j) h[j] = p0 + j < n ? xh[pidx(p0 + j)] : 0u;
+            for (int j = 0; j < IT; ++j) h[j] = xh[pidx(p0 + j)];
 #pragma unroll
             for (int j = 0; j < IT / 2; ++j) zin[j] = 0u;
             Acc acc = Op::e();
@@ -208,13 +223,15 @@ __device__ __forceinline__ void group_levels(u32 n, u32 gS, typename Op::Acc* va
 #pragma unroll
             for (int j = 0; j < IT; ++j) {
                 const u32 p = p0 + j;
-                if (p < n) {
+                {
                     const u32 lr = h[j] & lrmask, nd = lr >> sh;
                     if (nd != pn) {
                         if (first_head == IT) {
                             first_head = j;
                             z_first = zc;
                             first_ends = j > 0;
+                        } else {
+                            nzero[pn] = (unsigned short)zc;  // the node before ended at j-1 and began here
                         }
                         acc = Op::e();
                         zc = 0u;
@@ -222,18 +239,20 @@ __device__ __forceinline__ void group_levels(u32 n, u32 gS, typename Op::Acc* va
                     }
                     pn = nd;
                     const u32 bit = (lr >> lv) & 1u, q = (h[j] >> gS) & 1u, i = h[j] >> (gS + 1u);
-                    if (q && bit) val[i] = Op::Fc(val[i], acc);
-                    else if (!q && !bit) acc = Op::Fc(acc, val[i]);
+                    if (DOMAGG_GUARD(i < GROUP_CAP && nd < GROUP_NODES, SITE_GROUP_VAL)) {
+                        if (q && bit) val[i] = Op::Fc(val[i], acc);
+                        else if (!q && !bit) acc = Op::Fc(acc, val[i]);
+                    }
                     zin[j >> 1] |= zc << (16 * (j & 1));
                     zc += bit ^ 1u;
-                    const u32 nxt = j + 1 < IT ? (p + 1 < n ? (h[j + 1] & lrmask) >> sh : NONE) : nextnode;
-                    if (nxt != nd) {
-                        if (first_head <= j) nzero[nd] = (unsigned short)zc;  // a node that began here
-                        else {
-                            z_first = zc;
-                            first_ends = true;
-                        }
-                    }
+                }
+            }
+            // the thread's last node ends here unless the next point continues it
+            if (nextnode != pn) {
+                if (first_head < IT) nzero[pn] = (unsigned short)zc;
+                else {
+                    z_first = zc;
+                    first_ends = true;
                 }
             }
             loc.hd = first_head < IT ? 1u : 0u;
@@ -252,31 +271,25 @@ __device__ __forceinline__ void group_levels(u32 n, u32 gS, typename Op::Acc* va
         if (lane == 0) lex = ident;
         if (lane == 31) s_w[warp] = inc;
         __syncthreads();
-        E wi = s_w[lane];
+        if (warp == 0) {  // one warp scans the 32 warp totals (exclusive, in place)
+            E wi = s_w[lane];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const E nb = gscan_shfl_up(wi, o);
-            if (lane >= o) wi = gscan_combine<Op>(nb, wi);
+            for (int o = 1; o < 32; o <<= 1) {
+                const E nb = gscan_shfl_up(wi, o);
+                if (lane >= o) wi = gscan_combine<Op>(nb, wi);
+            }
+            E wx = gscan_shfl_up(wi, 1);
+            if (lane == 0) wx = ident;
+            s_w[lane] = wx;
         }
-        E wex = gscan_shfl_up(wi, 1);
-        if (lane == 0) wex = ident;
-        wex.hd = __shfl_sync(0xffffffffu, wex.hd, warp);
-        wex.zc = __shfl_sync(0xffffffffu, wex.zc, warp);
-        if constexpr (sizeof(Acc) == 8) {
-            unsigned long long b = *reinterpret_cast<unsigned long long*>(&wex.acc);
-            b = __shfl_sync(0xffffffffu, b, warp);
-            wex.acc = *reinterpret_cast<Acc*>(&b);
-        } else {
-            u32 b = *reinterpret_cast<u32*>(&wex.acc);
-            b = __shfl_sync(0xffffffffu, b, warp);
-            wex.acc = *reinterpret_cast<Acc*>(&b);
-        }
-        const E ex = gscan_combine<Op>(wex, lex);
+        __syncthreads();
+        const E ex = gscan_combine<Op>(s_w[warp], lex);
         // the points before the thread's first head continue a node from the left
         if (active && first_head > 0) {
 #pragma unroll
             for (int j = 0; j < IT; ++j) {
-                if (j < first_head && p0 + j < n) {
+                if (j >= first_head) break;
+                {
                     const u32 lr = h[j] & lrmask, bit = (lr >> lv) & 1u, q = (h[j] >> gS) & 1u;
                     if (q && bit) {
                         const u32 i = h[j] >> (gS + 1u);
@@ -294,11 +307,11 @@ __device__ __forceinline__ void group_levels(u32 n, u32 gS, typename Op::Acc* va
 #pragma unroll
             for (int j = 0; j < IT; ++j) {
                 const u32 p = p0 + j;
-                if (p < n) {
+                {
                     const u32 lr = h[j] & lrmask, nd = lr >> sh, bit = (lr >> lv) & 1u;
                     const u32 st = nstart[nd], z = (zin[j >> 1] >> (16 * (j & 1))) & 0xffffu;
                     const u32 np = bit ? st + nzero[nd] + (p - st - z) : st + z;
-                    xh[pidx(np)] = h[j];
+                    if (DOMAGG_GUARD(np < n && nd < GROUP_NODES, SITE_GROUP_SPLIT)) xh[pidx(np)] = h[j];
                 }
             }
         }
@@ -338,7 +351,7 @@ __global__ __launch_bounds__(GROUP_THREADS, 1) void k_group(const Inst* __restri
         if (slot >= total) break;
         const int s = upper_index(gslot_off, k + 1, slot);
         const Inst& I = inst[s];
-        const u32 g = slot - __ldg(gslot_off + s);
+        const u32 g = I.shard + (slot - __ldg(gslot_off + s)) * max(I.nshards, 1u);
         const u32 gS = I.gS, ns = I.flags & 1u;
         const u32 us = gS - ns, Uu = ns ? I.U[0] / 2u : I.U[0];
         const u32* rs = rstart + I.pt_off + (u32)s;
@@ -359,8 +372,17 @@ __global__ __launch_bounds__(GROUP_THREADS, 1) void k_group(const Inst* __restri
             else val[i] = Op::from_pay(pv);
         }
         static_assert(GROUP_ITEMS == 12, "items per thread dispatched below");
-        if (n <= 8u * T) group_levels<Op, 8>(n, gS, val, xh, nstart, nzero, s_w);
-        else group_levels<Op, 12>(n, gS, val, xh, nstart, nzero, s_w);
+        {
+            const u32 itp = n <= 8u * T ? 8u : 12u;
+            const u32 npad = (n + itp - 1) / itp * itp;
+            // the last thread's tail is padded with inert points (data whose rank
+            // bits are all ones: they never contribute, never receive, and stay
+            // behind every real point of their node), so no walk checks bounds
+            for (u32 i = n + tid; i < npad; i += T) xh[pidx(i)] = lrmask;
+            __syncthreads();
+            if (n <= 8u * T) group_levels<Op, 8>(npad, gS, val, xh, nstart, nzero, s_w);
+            else group_levels<Op, 12>(npad, gS, val, xh, nstart, nzero, s_w);
+        }
         __syncthreads();
         // every query of the group: F over its partial results of the levels
         // below gS (the unit e if it has none)
@@ -369,7 +391,16 @@ __global__ __launch_bounds__(GROUP_THREADS, 1) void k_group(const Inst* __restri
             const u64 v = gv[i];
             if ((u32)(v >> 32) & QUERY_BIT) {
                 const u32 qi = (u32)v;
-                if (qi < I.nQ) out[qi] = Op::to_out(val[i]);
+                if (domagg_check(qi < I.nQ, SITE_GROUP_OUT)) {
+                    if constexpr (std::is_same<Op, OpSumF32>::value) {
+                        if (I.out_lo) {  // a shard keeps the float-float pair
+                            out[qi] = val[i].hi;
+                            I.out_lo[qi] = val[i].lo;
+                            continue;
+                        }
+                    }
+                    out[qi] = Op::to_out(val[i]);
+                }
             }
         }
         __syncthreads();  // shared memory is free for the next group

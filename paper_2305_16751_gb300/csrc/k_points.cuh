@@ -320,7 +320,7 @@ __global__ __launch_bounds__(THREADS, 4) void k_rank_apply(const u32* __restrict
             const u32 dst = sidx[L.start + x];
             u32 r = sbuf[pidx(x)];
             if (nonstrict) r = 2u * r + ((dst - L.seg_begin) < nQ ? 1u : 0u);
-            if (dst < n_total) rank_out[dst] = r;
+            if (domagg_check(dst < n_total, SITE_RANK)) rank_out[dst] = r;
         }
     }
 }
@@ -568,10 +568,10 @@ __global__ __launch_bounds__(256) void k_expand(
                 X.q = (X.a & QUERY_BIT) != 0u;
                 X.a &= ~QUERY_BIT;
                 X.bits0 = (X.q ? X.a : ~X.a) & low_mask(I.b[0]);
-                if (M == 2) X.bits0 &= ~low_mask(I.gS);  // levels below gS: k_group
+                X.bits0 &= I.lvmask;  // the levels this call takes through HBM (not k_group's, this shard's)
             } else {
                 X.q = pj[X.p] - X.ps < nQ;
-                X.bits0 = 1u;
+                X.bits0 = 1u & I.lvmask;  // the single level, unless another shard takes it
             }
             if (M >= 3) {
                 X.cc = pr1[X.p];
@@ -636,7 +636,7 @@ __global__ __launch_bounds__(256) void k_expand(
             const Pay pay = q ? (Pay)(base_q + exq) : w;
             const K kv = M == 1 ? K(0) : (K)(a >> (lv + 1));
             if (M <= 2) {
-                if (has && pos < n_rec) {
+                if (has && domagg_check(pos < n_rec, SITE_EXPAND)) {
                     kout[pos] = q ? (kv | role) : kv;
                     pout[pos] = pay;
                 }
@@ -656,11 +656,11 @@ __global__ __launch_bounds__(256) void k_expand(
                     // one store of a record into its class's arrays
                     auto put = [&](u32 at, K key, u32 r) {
                         if (narrow) {
-                            if (at < n_rec1) {
+                            if (domagg_check(at < n_rec1, SITE_EXPAND)) {
                                 kout1[at] = sq ? ((u32)key | 0x80000000u) : (u32)key;
                                 pout1[at] = sq ? (Pay)(spay + r) : spay;
                             }
-                        } else if (at < n_rec) {
+                        } else if (domagg_check(at < n_rec, SITE_EXPAND)) {
                             kout[at] = sq ? (key | role) : key;
                             pout[at] = sq ? (Pay)(spay + r) : spay;
                         }

@@ -467,7 +467,7 @@ __global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_oneswee
 #pragma unroll
             for (int i = 0; i < ITEMS; ++i) {
                 const u32 x = wbase + (u32)i * 32u + (u32)lane;
-                if (x < n) sk[pos[i]] = key[i];
+                if (x < n && DOMAGG_GUARD(pos[i] < n, SITE_SORT_LOCAL)) sk[pos[i]] = key[i];
             }
             V val[ITEMS];
 #pragma unroll
@@ -479,14 +479,14 @@ __global__ __launch_bounds__(ONESWEEP_THREADS, ONESWEEP_MIN_CTAS) void k_oneswee
 #pragma unroll
             for (int i = 0; i < ITEMS; ++i) {
                 const u32 x = wbase + (u32)i * 32u + (u32)lane;
-                if (x < n) sv[pos[i]] = val[i];
+                if (x < n && DOMAGG_GUARD(pos[i] < n, SITE_SORT_LOCAL)) sv[pos[i]] = val[i];
             }
             __syncthreads();
             const u32 seg_len = L.seg_end - L.seg_begin;
             for (u32 x = tid; x < n; x += THREADS) {
                 const K k = sk[x];
                 const u32 dst = s_dstart[digit_of(k, keymask, shift)] + x;  // (global position of index 0)
-                if (dst - L.seg_begin < seg_len) {  // only fails after a timed-out wait
+                if (domagg_check(dst - L.seg_begin < seg_len, SITE_SORT_SCATTER)) {  // only fails after a timed-out wait
                     kout[dst] = k;
                     vout[dst] = sv[x];
                 }

@@ -2,6 +2,8 @@
 // scan of F (instruction 6m+3) and the per-query reduction of the partial
 // results (what instructions 6m+4, 6m+5 compute, without the ID sort).
 #pragma once
+#include <type_traits>
+
 #include "dev_common.cuh"
 #include "k_radix.cuh"
 
@@ -39,7 +41,7 @@ __global__ __launch_bounds__(1024) void k_layout(const Inst* __restrict__ inst, 
         const Inst& I = inst[k0 + (int)srel];
         const u32 nlev = M == 1 ? 1u : I.b[0];
         na = nq = bits = 0;
-        if (lv < nlev && !(M == 2 && lv < I.gS)) {  // levels below gS: k_group, no records
+        if (lv < nlev && ((I.lvmask >> lv) & 1u)) {  // other levels: k_group's or another shard's
             na = __ldg(lvl_tot + (u64)(k0 + (int)srel) * LMAX + lv);
             nq = __ldg(qlvl_tot + (u64)(k0 + (int)srel) * LMAX + lv);
             if (M >= 2) bits = I.b[0] - 1u - lv + (M >= 3 ? I.b[1] : 0u) + (M >= 4 ? I.b[2] : 0u);
@@ -127,6 +129,31 @@ __global__ __launch_bounds__(1024) void k_layout(const Inst* __restrict__ inst, 
     }
 }
 
+// Look-back status of the segmented scan.  The aggregate and the inclusive
+// prefix live in separate fields, each written once before the flag that
+// announces it (release), and read after that flag (acquire): a reader that
+// saw ST_AGG never meets a half-written prefix.
+template <typename Acc>
+struct alignas(32) SegStatus {
+    u32 flag;      // (epoch << 2) | ST_AGG / ST_PREFIX
+    u32 has_head;  // a segment starts inside the tile (with ST_AGG)
+    Acc agg;       // F over the tile's items after its last head (ST_AGG)
+    Acc incl;      // inclusive prefix at the tile's end (ST_PREFIX)
+};
+
+template <typename Acc>
+__device__ __forceinline__ void seg_publish_agg(SegStatus<Acc>* s, u32 epoch, bool head, Acc v) {
+    s->has_head = head ? 1u : 0u;
+    s->agg = v;
+    __threadfence();
+    st_store_release(&s->flag, ((epoch & EPOCH_MASK) << 2) | ST_AGG);
+}
+template <typename Acc>
+__device__ __forceinline__ void seg_publish_prefix(SegStatus<Acc>* s, u32 epoch, Acc v) {
+    s->incl = v;
+    __threadfence();
+    st_store_release(&s->flag, ((epoch & EPOCH_MASK) << 2) | ST_PREFIX);
+}
 template <typename Acc>
 __device__ __forceinline__ Acc shfl_xor_acc(Acc v, int o) {
     if constexpr (sizeof(Acc) == 8) {
@@ -332,7 +359,7 @@ __global__ __launch_bounds__(THREADS) void k_segscan(const K* __restrict__ keys0
                 const K kx = s_keys[pidx(lx0 + i)];
                 const Pay py = s_pays[pidx(lx0 + i)];
                 if (kx & role) {
-                    if ((u32)py < n_partial) partial[py] = Op::to_part(run);
+                    if (domagg_check((u32)py < n_partial, SITE_SEGSCAN_PARTIAL)) partial[py] = Op::to_part(run);
                 } else {
                     if constexpr (Op::GATHER) run = Op::Fc(run, Op::from_w(__ldg(wgt + py)));
                     else run = Op::Fc(run, Op::from_pay(py));
@@ -411,6 +438,283 @@ __global__ __launch_bounds__(1024) void k_seg_carry(const u32* __restrict__ tile
     }
 }
 
+// The same segmented scan in one pass, each tile taking its carry by a
+// decoupled look-back over the tiles before it (warp-cooperative: lane l
+// examines tile u-1-l).  Used where segments are short (m >= 3: node keys of
+// two ranks), so look-back chains stop within a few tiles and one read of
+// the records suffices; long segments (m <= 2) use k_segscan, whose
+// reduce-then-scan does not wait on chains and combines float sums in a
+// fixed order.
+template <class Op, typename K, int THREADS, int ITEMS>
+__global__ __launch_bounds__(THREADS) void k_segscan_lb(const K* __restrict__ keys0, const K* __restrict__ keys1,
+                                                     const typename Op::Pay* __restrict__ pays0,
+                                                     const typename Op::Pay* __restrict__ pays1,
+                                                     const u32* __restrict__ seg_off,
+                                                     const u32* __restrict__ tile_off, int nseg,
+                                                     const u32* __restrict__ seg_bits,
+                                                     const typename Op::W* __restrict__ wgt,
+                                                     typename Op::Part* __restrict__ partial, u32 n_partial,
+                                                     SegStatus<typename Op::Acc>* status, Ctl* ctl, int launch_idx) {
+    typedef typename Op::Acc Acc;
+    typedef typename Op::Pay Pay;
+    constexpr int TILE = THREADS * ITEMS, WARPS = THREADS / 32;
+    const K role = K(1) << (sizeof(K) * 8 - 1);
+    __shared__ K s_keys[Padded<TILE>::value];
+    __shared__ Pay s_pays[Padded<TILE>::value];
+    __shared__ Acc s_wacc[WARPS];
+    __shared__ u32 s_whead[WARPS];
+    __shared__ Acc s_excl;
+    __shared__ u32 s_info[2];
+    if (threadIdx.x == 0) {
+        s_info[0] = atomicAdd(&ctl->tile_ctr[launch_idx], 1u);
+        s_info[1] = ctl->epoch_base + (u32)launch_idx;
+    }
+    __syncthreads();
+    const u32 t = s_info[0], epoch = s_info[1];
+    if (t >= __ldg(tile_off + nseg)) return;
+    const TileLoc L = locate_tile<TILE>(t, seg_off, tile_off, nseg);
+    // the sort left this segment in the buffer of its pass count's parity
+    const bool odd = ((__ldg(seg_bits + L.seg) + RADIX_BITS - 1) / RADIX_BITS) & 1u;
+    const K* __restrict__ keys = odd ? keys1 : keys0;
+    const typename Op::Pay* __restrict__ pays = odd ? pays1 : pays0;
+    // coalesced load into shared memory, then blocked reads
+    for (int i = 0; i < ITEMS; ++i) {
+        const u32 x = (u32)i * THREADS + threadIdx.x;
+        if (L.start + x < L.end) {
+            s_keys[pidx(x)] = keys[L.start + x];
+            s_pays[pidx(x)] = pays[L.start + x];
+        }
+    }
+    __syncthreads();
+    const u32 lx0 = threadIdx.x * ITEMS;  // tile-local index of my first item
+    const u32 x0 = L.start + lx0;
+    K prev = 0;
+    bool has_prev = x0 > L.seg_begin;
+    if (has_prev && x0 < L.end) prev = lx0 == 0 ? keys[x0 - 1] : s_keys[pidx(lx0 - 1)];
+    prev &= ~role;
+    // thread aggregate: (head seen, F over items after the last head); the
+    // running value at every query record is kept for the output pass
+    bool head_any = false;
+    Acc agg = Op::e();
+    u32 headmask = 0, qmask = 0;
+    Acc loc[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        loc[i] = Op::e();
+        if (x0 + i < L.end) {
+            const K kx = s_keys[pidx(lx0 + i)];
+            const K kn = kx & ~role;
+            const bool head = !has_prev || kn != prev;
+            has_prev = true;
+            prev = kn;
+            if (head) {
+                head_any = true;
+                headmask |= 1u << i;
+                agg = Op::e();
+            }
+            if (kx & role) {
+                qmask |= 1u << i;
+                loc[i] = agg;
+            } else {
+                const Pay py = s_pays[pidx(lx0 + i)];
+                if constexpr (Op::GATHER) agg = Op::F(agg, Op::from_w(__ldg(wgt + py)));
+                else agg = Op::F(agg, Op::from_pay(py));
+            }
+        }
+    }
+    // block-wide exclusive scan of (head, agg) with the segmented operator
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool ihead = head_any;
+    Acc iacc = agg;  // inclusive within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int nh = __shfl_up_sync(0xffffffffu, (int)ihead, o);
+        Acc na;
+        if constexpr (sizeof(Acc) == 8) {
+            unsigned long long bits = *reinterpret_cast<unsigned long long*>(&iacc);
+            bits = __shfl_up_sync(0xffffffffu, bits, o);
+            na = *reinterpret_cast<Acc*>(&bits);
+        } else {
+            u32 bits = *reinterpret_cast<u32*>(&iacc);
+            bits = __shfl_up_sync(0xffffffffu, bits, o);
+            na = *reinterpret_cast<Acc*>(&bits);
+        }
+        if (lane >= o) {
+            if (!ihead) iacc = Op::F(na, iacc);
+            ihead = ihead || nh;
+        }
+    }
+    if (lane == 31) {
+        s_wacc[warp] = iacc;
+        s_whead[warp] = ihead ? 1u : 0u;
+    }
+    __syncthreads();
+    // exclusive prefix of this thread within the tile
+    Acc wex = Op::e();  // prefix from earlier warps
+    bool wex_head = false;
+    for (int w = 0; w < warp; ++w) {
+        if (s_whead[w]) {
+            wex = s_wacc[w];
+            wex_head = true;
+        } else {
+            wex = Op::F(wex, s_wacc[w]);
+        }
+    }
+    // exclusive within warp: inclusive of lane-1
+    Acc lex;
+    int lhead;
+    {
+        Acc src = iacc;
+        if constexpr (sizeof(Acc) == 8) {
+            unsigned long long bits = *reinterpret_cast<unsigned long long*>(&src);
+            bits = __shfl_up_sync(0xffffffffu, bits, 1);
+            lex = *reinterpret_cast<Acc*>(&bits);
+        } else {
+            u32 bits = *reinterpret_cast<u32*>(&src);
+            bits = __shfl_up_sync(0xffffffffu, bits, 1);
+            lex = *reinterpret_cast<Acc*>(&bits);
+        }
+        lhead = __shfl_up_sync(0xffffffffu, (int)ihead, 1);
+        if (lane == 0) {
+            lex = Op::e();
+            lhead = 0;
+        }
+    }
+    Acc texcl = lhead ? lex : Op::F(wex, lex);  // within-tile exclusive prefix
+    const bool texcl_head = lhead || wex_head;  // a head occurs before me in the tile
+    // tile aggregate, look-back and publication (warp 0).  The look-back is
+    // warp-cooperative: lane l examines tile u-1-l, so one round trip to L2
+    // covers 32 predecessors; the aggregates up to the first tile that ends
+    // the chain (a published prefix, or a segment head inside the tile) are
+    // combined with a masked warp reduction.
+    if (warp == 0) {
+        Acc tagg = Op::e();
+        bool thead = false;
+        for (int w = 0; w < WARPS; ++w) {
+            if (s_whead[w]) {
+                tagg = s_wacc[w];
+                thead = true;
+            } else {
+                tagg = Op::F(tagg, s_wacc[w]);
+            }
+        }
+        SegStatus<Acc>* my = status + t;
+        const bool starts_fresh = L.first || (__shfl_sync(0xffffffffu, headmask, 0) & 1u);
+        Acc excl = Op::e();
+        if (starts_fresh) {
+            if (lane == 0) seg_publish_prefix(my, epoch, tagg);
+        } else {
+            if (lane == 0) seg_publish_agg(my, epoch, thead, tagg);
+            const u32 first_tile = t - (L.start - L.seg_begin) / (u32)TILE;
+            u32 u = t;  // tiles [u, t) have been combined into excl
+            u32 spins = 0;
+            while (u > first_tile) {
+                const bool exists = u - 1 - (u32)lane >= first_tile && (u32)lane < u - first_tile;
+                u32 f = 0, hh = 0;
+                Acc v = Op::e();
+                bool ready = true, term = false;
+                if (exists) {
+                    const SegStatus<Acc>* ps = status + (u - 1 - lane);
+                    f = st_load_acquire(&ps->flag);
+                    ready = (f >> 2) == (epoch & EPOCH_MASK) && (f & 3u);
+                    if (ready) {
+                        if ((f & 3u) == ST_PREFIX) {
+                            v = volatile_read(&ps->incl);
+                            term = true;
+                        } else {
+                            hh = *reinterpret_cast<const volatile u32*>(&ps->has_head);
+                            v = volatile_read(&ps->agg);
+                            term = hh != 0;
+                        }
+                    }
+                } else {
+                    ready = false;  // beyond the chain start: never consumed
+                }
+                const u32 nr = __ballot_sync(0xffffffffu, !ready);
+                const u32 tm = __ballot_sync(0xffffffffu, term);
+                const int k_nr = nr ? __ffs(nr) - 1 : 32;
+                const int k_tm = tm ? __ffs(tm) - 1 : 32;
+                const bool finish = k_tm < k_nr;
+                const int take = finish ? k_tm + 1 : k_nr;  // lanes [0, take) are combined
+                if (take > 0) {
+                    Acc r = lane < take ? v : Op::e();
+#pragma unroll
+                    for (int o = 16; o >= 1; o >>= 1) r = Op::F(r, shfl_xor_acc(r, o));
+                    excl = Op::F(r, excl);
+                    u -= (u32)take;
+                }
+                if (finish) break;
+                if (take == 0) {
+                    if (++spins > SPIN_LIMIT || ((spins & 255u) == 0 && timed_out(ctl))) {
+                        if (lane == 0) {
+                            atomicOr(&ctl->error, ERR_TIMEOUT);
+                            ctl->timeout_where = 4u;
+                        }
+                        break;
+                    }
+                    if (spins > 64) __nanosleep(256);
+                }
+            }
+            if (lane == 0) seg_publish_prefix(my, epoch, thead ? tagg : Op::F(excl, tagg));
+        }
+        if (lane == 0) s_excl = excl;
+    }
+    __syncthreads();
+    // output: a query record before the thread's first head continues the
+    // segment coming from the left (prefix); after it, its own run suffices
+    const Acc prefix = texcl_head ? texcl : Op::F(s_excl, texcl);
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        if (qmask & (1u << i)) {
+            const u64 slot = (u64)s_pays[pidx(lx0 + i)];
+            const bool own = (headmask & ((2u << i) - 1u)) != 0;
+            if (domagg_check(slot < n_partial, SITE_SEGSCAN_PARTIAL)) partial[slot] = Op::to_part(own ? loc[i] : Op::F(prefix, loc[i]));
+        }
+    }
+}
+
+// A shard's outputs start at the unit e (k_group writes only its own
+// groups' queries; the reduction then adds this shard's levels).
+template <class Op>
+__global__ void k_fill_unit(const Inst* __restrict__ inst, const u32* __restrict__ q_offs, int k, u32 NQ) {
+    const u32 g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= NQ) return;
+    const int s = upper_index(q_offs, k + 1, g);
+    const Inst& I = inst[s];
+    const u32 q = g - __ldg(q_offs + s);
+    if (q >= I.nQ) return;
+    bool done = false;
+    if constexpr (std::is_same<Op, OpSumF32>::value) {
+        if (I.out_lo) {
+            reinterpret_cast<float*>(I.out)[q] = 0.f;
+            I.out_lo[q] = 0.f;
+            done = true;
+        }
+    }
+    if (!done) reinterpret_cast<typename Op::Out*>(I.out)[q] = Op::to_out(Op::e());
+}
+
+// out[q] = F over the shards' partial outputs (float32 sums: the shards'
+// float-float pairs added in float-float, rounded once).
+constexpr int MAX_SHARDS = 64;
+struct ShardParts {
+    const void* part[MAX_SHARDS];
+    const float* lo[MAX_SHARDS];
+};
+template <class Op>
+__global__ void k_combine(int nparts, const ShardParts parts, u32 nQ, void* __restrict__ out) {
+    const u32 q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nQ) return;
+    typename Op::Acc acc = Op::e();
+    for (int s = 0; s < nparts; ++s) {
+        typename Op::Acc v = Op::from_out(reinterpret_cast<const typename Op::Out*>(parts.part[s])[q]);
+        if constexpr (std::is_same<Op, OpSumF32>::value)
+            if (parts.lo[s]) v.lo = parts.lo[s][q];
+        acc = Op::F(acc, v);
+    }
+    reinterpret_cast<typename Op::Out*>(out)[q] = Op::to_out(acc);
+}
+
 // Per-query reduction: out[q] = F over the query's partial results.  This
 // replaces the sort by ID and the ID-segmented scan of instructions 6m+4,
 // 6m+5 (the broadcast of 6m+6 .. 6m+9 is not needed for one output per
@@ -452,13 +756,13 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
             q = local < nQ;
             if (q) {
                 if (M >= 2) bits0 = pr0[p] & low_mask(I.b[0]);
-                if (M == 2) bits0 &= ~low_mask(I.gS);  // levels below gS: k_group wrote out[q]
+                if (M >= 2) bits0 &= I.lvmask;  // this call's levels (k_group wrote out[q] for the others)
                 if (M >= 3) {
                     bits1 = pr1[p] & low_mask(I.b[1]);
                     c1 = (u32)__popc(bits1);
                 }
                 if (M >= 4) c1 *= (u32)__popc(pr2[p] & low_mask(I.b[2]));
-                if (M == 1) bits0 = 1u;
+                if (M == 1) bits0 = 1u & I.lvmask;
                 if (M >= 3 && c1 == 0) bits0 = 0;
             }
         }
@@ -473,7 +777,12 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
         __syncwarp();
         typename Op::Acc acc = Op::e();
         // m = 2 with groups: out[q] holds F over the levels below gS already
-        if (M == 2 && q && I.gS) acc = Op::from_out(reinterpret_cast<const typename Op::Out*>(I.out)[local]);
+        // (a shard of a float32 sum: the float-float pair)
+        if (M == 2 && q && I.gS) {
+            acc = Op::from_out(reinterpret_cast<const typename Op::Out*>(I.out)[local]);
+            if constexpr (std::is_same<Op, OpSumF32>::value)
+                if (I.out_lo) acc.lo = I.out_lo[local];
+        }
         if (M <= 2) {
             // one partial per query and level, at the level's base plus the
             // query lanes of that level before this one; each lane walks only
@@ -484,7 +793,7 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
                 const u32 lv = __ffs(rem) - 1;
                 rem &= rem - 1;
                 const u32 slot = s_base[warp][lv] + (u32)__popc(s_mask[warp][lv] & lt);
-                if (slot < n_partial) acc = Op::F(acc, Op::from_part(partial[slot]));
+                if (domagg_check(slot < n_partial, SITE_REDUCE)) acc = Op::F(acc, Op::from_part(partial[slot]));
             }
         }
         if (M >= 3) {
@@ -507,7 +816,17 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
                 }
             }
         }
-        if (q) reinterpret_cast<typename Op::Out*>(I.out)[local] = Op::to_out(acc);
+        if (q) {
+            bool done = false;
+            if constexpr (std::is_same<Op, OpSumF32>::value) {
+                if (I.out_lo) {  // a shard keeps the float-float pair
+                    reinterpret_cast<float*>(I.out)[local] = acc.hi;
+                    I.out_lo[local] = acc.lo;
+                    done = true;
+                }
+            }
+            if (!done) reinterpret_cast<typename Op::Out*>(I.out)[local] = Op::to_out(acc);
+        }
         __syncwarp();
     }
 }

@@ -552,9 +552,11 @@ __global__ __launch_bounds__(WV_THREADS, WV_MIN_BLOCKS) void k_wavelet_pass(
                 e.w = (u32)(b >> 32);
             }
             if (last) {
-                if (q) outp[e.y] = Op::to_out(wv_acc<Acc>(((u64)e.w << 32) | e.z));
+                if (q && DOMAGG_GUARD(e.y < inst[0].nQ, SITE_WAVELET_OUT))
+                    outp[e.y] = Op::to_out(wv_acc<Acc>(((u64)e.w << 32) | e.z));
             } else {
-                __stcs(dst + s_dbase[c] + s_prev[c] + (x - wv_sel<NDIG>(tstart, c)), e);
+                const u32 at = s_dbase[c] + s_prev[c] + (x - wv_sel<NDIG>(tstart, c));
+                if (DOMAGG_GUARD(at < n, SITE_WAVELET_EL)) __stcs(dst + at, e);
             }
         }
     }

@@ -141,6 +141,23 @@ int sort_pairs(Launcher& L, const SortSpace& sp, K* keys[2], V* vals[2], bool io
     return cur;
 }
 
+u32 bounds_site_sort(bool clear) {
+#ifdef DOMAGG_CHECKED
+    u32 hit = 0, site = 0;
+    cudaMemcpyFromSymbol(&hit, g_bounds_hit, sizeof(u32));
+    cudaMemcpyFromSymbol(&site, g_bounds_site, sizeof(u32));
+    if (clear && hit) {
+        const u32 z = 0;
+        cudaMemcpyToSymbol(g_bounds_hit, &z, sizeof(u32));
+    }
+    cudaGetLastError();
+    return hit ? (site ? site : 1u) : 0u;
+#else
+    (void)clear;
+    return 0u;
+#endif
+}
+
 template int sort_pairs<u32, u32>(Launcher&, const SortSpace&, u32**, u32**, bool, int, u32, int, int,
                                      const u32*, bool, bool);
 template int sort_pairs<u64, u32>(Launcher&, const SortSpace&, u64**, u32**, bool, int, u64, int, int,

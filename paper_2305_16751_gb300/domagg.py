@@ -14,9 +14,9 @@ import ctypes
 import os
 import threading
 
-from .build import LIB
+from .build import LIB, LIB_CHECKED
 
-STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "NAN"}
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "NAN", 7: "BOUNDS"}
 OPS = {"sum": 0, "max": 1, "count": 2, "min": 3}
 DTYPES = {"i32": 0, "i64": 1, "f32": 2}
 TIMING_KINDS = 16
@@ -57,6 +57,9 @@ SIGNATURES = {
     "domagg_forward_ex": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _int, _int, ctypes.c_uint32, _int, _vp, _vp],
                           _int),
     "domagg_forward_host": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _vp], _int),
+    "domagg_forward_shard": ([_vp, _int, _int, _int, _vp, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _vp, _vp],
+                             _int),
+    "domagg_combine": ([_vp, _int, _int, _int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64, _vp, _vp], _int),
     "domagg_backward": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp], _int),
     "domagg_backward_ex": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _vp, ctypes.c_uint32, _int, _vp], _int),
     "domagg_batch": ([_vp, _int, ctypes.POINTER(domagg_instance), _int, _int, _int, _vp], _int),
@@ -85,13 +88,16 @@ _lock = threading.Lock()
 
 
 def lib() -> ctypes.CDLL:
-    """Loads the in-tree library; raises if it has not been built."""
+    """Loads the in-tree library; raises if it has not been built.  With the
+    environment variable DOMAGG_CHECKED=1 the checked build is loaded instead
+    (kernels test every computed index; a miss returns DOMAGG_ERR_BOUNDS)."""
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(LIB):
-                raise RuntimeError(f"{LIB} is missing: build it with __graft_entry__.build()")
-            L = ctypes.CDLL(LIB)
+            path = LIB_CHECKED if os.environ.get("DOMAGG_CHECKED") == "1" else LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+            L = ctypes.CDLL(path)
             for name, (args, res) in SIGNATURES.items():
                 fn = getattr(L, name)
                 fn.argtypes = args
@@ -292,6 +298,40 @@ def forward(D, Q, w=None, op: str = "sum", out=None, nonstrict: int = 0, variant
     else:
         domagg_forward(handle(dev), m, _ptr(D), D.shape[0], _ptr(Q), Q.shape[0], _coord_dtype(D), _ptr(w),
                        _weight_dtype(w, op), OPS[op], _ptr(out), _stream(D.device))
+    return out
+
+
+def forward_shard(D, Q, w, op: str, shard: int, nshards: int):
+    """Shard `shard` of `nshards` of forward(D, Q, w, op) (domagg_forward_shard):
+    F over the shard's part of the flat map.  Returns (out, out_lo); out_lo
+    holds the low halves of the float-float partials of a float32 sum (None
+    for other ops)."""
+    torch = _torch()
+    D, Q = D.contiguous(), Q.contiguous()
+    w = None if op == "count" else w.contiguous()
+    out = torch.empty(Q.shape[0], dtype=out_dtype(op, w), device=D.device)
+    out_lo = torch.empty(Q.shape[0], dtype=torch.float32, device=D.device) \
+        if (op == "sum" and w is not None and w.dtype == torch.float32) else None
+    dev = D.device.index or 0
+    _check(handle(dev), lib().domagg_forward_shard(
+        handle(dev), shard, nshards, D.shape[1], _ptr(D), D.shape[0], _ptr(Q), Q.shape[0], _coord_dtype(D), _ptr(w),
+        _weight_dtype(w, op), OPS[op], _ptr(out), _ptr(out_lo), _stream(D.device)))
+    return out, out_lo
+
+
+def combine(parts, parts_lo, op: str, weight_dtype=None, out=None):
+    """F over the shards' outputs (domagg_combine): parts are the `out`
+    tensors of forward_shard, parts_lo their `out_lo` (or None)."""
+    torch = _torch()
+    n = len(parts)
+    dev = parts[0].device
+    if out is None:
+        out = torch.empty_like(parts[0])
+    wd = {None: 1, torch.int32: 0, torch.int64: 1, torch.float32: 2}[weight_dtype if op != "count" else None]
+    P = (_vp * n)(*[p.data_ptr() for p in parts])
+    lo = (_vp * n)(*[x.data_ptr() for x in parts_lo]) if parts_lo is not None and parts_lo[0] is not None else None
+    _check(handle(dev.index or 0), lib().domagg_combine(handle(dev.index or 0), OPS[op], wd, n, P, lo,
+                                                        parts[0].shape[0], _ptr(out), _stream(dev)))
     return out
 
 
