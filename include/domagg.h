@@ -139,8 +139,9 @@ domagg_status domagg_forward_ex(domagg_handle h, int m, const void* d_coords, in
  * split by node: with gS the rank levels taken per group of 2^gS ranks in
  * shared memory (m = 2; 0 otherwise), shard s takes the levels lv >= gS of
  * the first rank with (lv - gS) % nshards == s and the groups g with
- * g % nshards == s.  The shard's outputs are F over its records only; F over
- * the nshards outputs (domagg_combine, or a collective with F) is
+ * g % nshards == s (m = 1 has a single level: shard 0 takes it and the
+ * others return the unit).  The shard's outputs are F over its records only;
+ * F over the nshards outputs (domagg_combine, or a collective with F) is
  * domagg_forward's result.
  *   shard, nshards  0 <= shard < nshards <= 64
  *   out             device [nQ] (output dtype as domagg_forward), overwritten
@@ -347,7 +348,7 @@ domagg_status domagg_forward_noalloc(int m, const void* d_coords, int64_t nD, co
 
 /* Tuning knobs of a handle (the paper has no counterpart); every setting
  * computes the same results:
- *   "group_bits"     0 .. 12 (default 12): for m = 2, the rank levels below
+ *   "group_bits"     0 .. 13 (default 13): for m = 2, the rank levels below
  *                    gS <= group_bits (nodes of at most 2^gS ranks) are
  *                    formed, sorted and scanned per group of 2^gS ranks in
  *                    shared memory; 0 sends every level's records through

@@ -34,7 +34,7 @@
 
 namespace domagg {
 
-constexpr int GROUP_MAX_BITS = 12;       // gS <= 12: nodes of up to 2^12 ranks
+constexpr int GROUP_MAX_BITS = 13;       // gS <= 13: nodes of up to 2^13 ranks
 constexpr int GROUP_THREADS = 1024;
 constexpr int GROUP_ITEMS = 12;          // points per thread, at most
 constexpr u32 GROUP_CAP = GROUP_THREADS * GROUP_ITEMS;  // points per group in shared memory

@@ -20,7 +20,7 @@ def group_bits(v):
     try:
         yield
     finally:
-        domagg.domagg_set_tuning(h, "group_bits", 12)
+        domagg.domagg_set_tuning(h, "group_bits", 13)
 
 
 CASES = [("i32", "i64", "sum"), ("f32", "i32", "max"), ("f32", "i64", "count"), ("i32", "i32", "min"),
@@ -49,12 +49,12 @@ def test_every_group_width_gives_the_same_sums():
     D, Q, w = workloads.random_small(rng, 2, 20000, 18000, 1 << 16, "i32", "i64")
     want, _ = oracle.brute(D, Q, w, "sum")
     shared = []
-    for g in range(0, 13):
+    for g in range(0, 14):
         with group_bits(g):
             got = gpu_forward(D, Q, w, "sum")
             shared.append(domagg.stats()["n_records_shared"])
         assert np.array_equal(got, want), g
-    assert shared[0] == 0 and all(b >= a for a, b in zip(shared, shared[1:])) and shared[12] > 0
+    assert shared[0] == 0 and all(b >= a for a, b in zip(shared, shared[1:])) and shared[13] > 0
 
 
 def test_heavy_ties_fall_back_to_records_in_hbm():
