@@ -303,7 +303,7 @@ domagg_status domagg_get_stats(domagg_handle h, domagg_stats* out);
  * device time (ms) and the summed algorithmic bytes (the bytes each launch
  * must read and write at minimum), and resets the counters.  Kinds are
  * indexed as in domagg_timing_kind_name. */
-#define DOMAGG_TIMING_KINDS 16
+#define DOMAGG_TIMING_KINDS 20
 typedef struct {
     int32_t launches[DOMAGG_TIMING_KINDS];
     double ms[DOMAGG_TIMING_KINDS];

@@ -58,6 +58,10 @@ struct Inst {
     // shared memory (k_group); G groups.  gS = 0: every level goes through
     // the records in HBM.
     u32 gS, G;
+    // m = 2: rank levels tS .. b0-1 (at most TOP_MAX_BITS) are taken per tile
+    // of points in the order of the last coordinate (k_top); topmask: those
+    // of this call's shard (bit lv; device-computed)
+    u32 tS, topmask;
     // levels of the first rank whose records this call takes through HBM
     // (bit lv; device-computed), and the call's shard of the flat map: shard
     // `shard` of `nshards` takes the levels >= gS with (lv - gS) % nshards ==

@@ -22,6 +22,7 @@
 #include "k_radix.cuh"
 #include "k_group.cuh"
 #include "k_records.cuh"
+#include "k_top.cuh"
 #include "k_wavelet.cuh"
 
 using namespace domagg;
@@ -86,6 +87,10 @@ struct domagg_ctx {
     // m = 2: the rank levels below gS <= group_bits are aggregated per group
     // in shared memory (k_group); 0 = every level through the records in HBM
     int group_bits = GROUP_MAX_BITS;
+    // m = 2: the top top_bits rank levels (at most 2^(top_bits-1) nodes
+    // each) per tile in shared memory (k_top); 0 = every level from gS up
+    // through the records in HBM
+    int top_bits = TOP_MAX_BITS;
 
     size_t held() const { return pts.cap + recs.cap + st_multi.cap + st_seg.cap + stage.cap + st_wv.cap; }
 };
@@ -402,6 +407,26 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     if (NQ == 0) return DOMAGG_OK;
     // m = 2, the records path: the deep rank levels go through k_group
     const bool use_groups = M == 2 && h->group_bits > 0 && !(inst[0].flags & FLAG_WAVELET);
+    // m = 2: the top rank levels per range of whole tiles (k_top): about
+    // ranges_per_cta ranges per SM over all points; prange_off[s] is instance
+    // s's first range; `multi` lists the instances of two or more ranges
+    const bool use_top = M == 2 && h->top_bits > 0 && !(inst[0].flags & FLAG_WAVELET);
+    u32 range_pts = TOP_TILE;
+    std::vector<u32> prange_off(k + 1, 0), multi;
+    if (use_top) {
+        const u64 want = (u64)std::max(1, h->ranges_per_cta) * (u64)std::max(h->sms, 1);
+        const u64 tiles = (N + TOP_TILE - 1) / TOP_TILE;
+        range_pts = (u32)std::min<u64>(TOP_TILE * std::max<u64>(1, (tiles + want - 1) / want), 1ull << 30);
+        u64 nr = 0;
+        for (int s = 0; s < k; ++s) {
+            prange_off[s] = (u32)nr;
+            const u64 r = (pt_sizes[s] + range_pts - 1) / range_pts;
+            if (r >= 2) multi.push_back((u32)s);
+            nr += r;
+        }
+        prange_off[k] = (u32)nr;
+    }
+    const u64 nranges = prange_off[k];
 
     // ---- point workspace
     auto carve_points = [&](Carver& c, void** P) {
@@ -458,8 +483,15 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         P[49] = c.take<u64>(grp ? N : 0);
         P[50] = c.take<u32>(grp ? k : 0);        // group-id bits per instance
         P[51] = c.take<u32>(grp ? k + 1 : 0);    // group slot offsets
+        // m = 2 top levels: per query F over its range's top levels, per range
+        // F of every top-level node (then the carries), the range table, the
+        // instances of several ranges
+        P[52] = c.take<typename Op::Part>(use_top ? N : 0);
+        P[53] = c.take<typename Op::Acc>(use_top ? (size_t)nranges * TOP_STRIDE : 0);
+        P[54] = c.take<u32>(use_top ? k + 1 : 0);
+        P[55] = c.take<u32>(use_top ? std::max<size_t>(multi.size(), 1) : 0);
     };
-    void* P[52];
+    void* P[56];
     {
         Carver c(nullptr);
         carve_points(c, P);
@@ -480,6 +512,9 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     u32 *chunk_base = (u32*)P[22], *lvl_tot = (u32*)P[23];
     u32 *rstart = (u32*)P[45], *gkey[2] = {(u32*)P[46], (u32*)P[47]}, *gbits = (u32*)P[50], *gslot = (u32*)P[51];
     u64* gval[2] = {(u64*)P[48], (u64*)P[49]};
+    typename Op::Part* topv = (typename Op::Part*)P[52];
+    typename Op::Acc* top_agg = (typename Op::Acc*)P[53];
+    u32 *d_prange = (u32*)P[54], *d_multi = (u32*)P[55];
 
     // status words: point tiles x 256 digits (the records sort grows it later)
     {
@@ -490,7 +525,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     }
 
     // ---- upload the instance table and offsets
-    const size_t up_bytes = sizeof(Inst) * k + 3 * sizeof(u32) * (k + 1);
+    const size_t up_bytes = sizeof(Inst) * k + 3 * sizeof(u32) * (k + 1) + (use_top ? sizeof(u32) * (2 * k + 2) : 0);
     const size_t lvl_pos = (up_bytes + 63) & ~(size_t)63;                          // level totals (read back)
     const size_t ctl_pos = (lvl_pos + 2 * sizeof(u32) * k * LMAX + 63) & ~(size_t)63;  // control block (read back)
     char* hp = nullptr;
@@ -508,6 +543,14 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                         cudaMemcpyHostToDevice, stream);
         cudaMemcpyAsync(d_chunk_off, hp + sizeof(Inst) * k + 2 * sizeof(u32) * (k + 1), sizeof(u32) * (k + 1),
                         cudaMemcpyHostToDevice, stream);
+        if (use_top) {  // (a planned run reuses the tables its measuring run uploaded)
+            u32* hr = (u32*)(hp + sizeof(Inst) * k + 3 * sizeof(u32) * (k + 1));
+            memcpy(hr, prange_off.data(), sizeof(u32) * (k + 1));
+            memcpy(hr + k + 1, multi.data(), sizeof(u32) * multi.size());
+            cudaMemcpyAsync(d_prange, hr, sizeof(u32) * (k + 1), cudaMemcpyHostToDevice, stream);
+            if (!multi.empty())
+                cudaMemcpyAsync(d_multi, hr + k + 1, sizeof(u32) * multi.size(), cudaMemcpyHostToDevice, stream);
+        }
         maybe_reset_epochs(h, stream);
     }
 
@@ -615,7 +658,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     // m = 2 the levels above the groups of ranks that k_group takes)
     L.start(KIND_SMALL, 0.0);
     k_group_plan<M><<<k, 1024, 0, stream>>>(d_inst, use_groups ? rstart : nullptr, use_groups ? gbits : nullptr,
-                                            GROUP_CAP, use_groups ? h->group_bits : 0);
+                                            GROUP_CAP, use_groups ? h->group_bits : 0, use_top ? h->top_bits : 0);
     L.stop();
     // ---- count / offset scan of the flat map, per level
     {
@@ -708,10 +751,10 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             u64 T = 0, Tq = 0;
             for (u32 lv = 0; lv < nlev[s]; ++lv) {
                 T_flat += lvl[(size_t)s * LMAX + lv];
-                // levels below gS are formed, sorted and scanned in shared
-                // memory (k_group), levels of other shards elsewhere: no
-                // records in HBM here
-                if (M == 2 && lv < inst[s].gS) T_shared += lvl[(size_t)s * LMAX + lv];
+                // levels below gS (k_group) and from tS up (k_top) are
+                // formed, sorted and scanned in shared memory, levels of
+                // other shards elsewhere: no records in HBM here
+                if (M == 2 && (lv < inst[s].gS || lv >= inst[s].tS)) T_shared += lvl[(size_t)s * LMAX + lv];
                 if (!((inst[s].lvmask >> lv) & 1u)) {
                     lvl[(size_t)s * LMAX + lv] = 0;
                     qlvl[(size_t)s * LMAX + lv] = 0;
@@ -828,8 +871,27 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                                                                       (const W*)P[18], h->ctl, li);
         L.stop();
     }
+    // ---- m = 2: the top levels per range of tiles in the order of the last
+    // coordinate (k_top), then the nodes' carries across the ranges
+    if (use_top && nranges > 0) {
+        typedef typename Op::Acc Acc;
+        constexpr size_t tsm = TopSmem<Acc>::TOTAL;
+        if (!L.frozen) cudaFuncSetAttribute(k_top<Op, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
+        const int li = L.lookback_index();
+        L.start(KIND_TOP, (double)N * (4.0 + (WT == 3 ? 0.0 : sizeof(W))) + (double)NQ * sizeof(Part) +
+                              (double)nranges * TOP_STRIDE * sizeof(Acc));
+        k_top<Op, WT><<<(unsigned)h->sms, TOP_THREADS, tsm, stream>>>(d_inst, k, d_prange, d_pt_offs, range_pts, pr0,
+                                                                      (const W*)P[18], topv, top_agg, h->ctl, li);
+        L.stop();
+        if (!multi.empty()) {
+            L.start(KIND_SMALL, 0.0);
+            k_top_carry<Op><<<dim3((unsigned)multi.size(), TOP_STRIDE / 32), 1024, 0, stream>>>(d_multi, d_prange,
+                                                                                               d_inst, top_agg);
+            L.stop();
+        }
+    }
 
-    u64 T_all = 0, Tq_all = 0;
+    u64 Tq_all = 0;
     int kb_all = 0, passes_all = 0;
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
         const Chunk& C = chunks[ci];
@@ -1043,7 +1105,16 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                     pays1[1], d_so1, d_stiles1, d_sbits + nseg0, (double)C.T1 * (4 + sizeof(Pay)));
         // per-query reduction (replaces 6m+4 .. 6m+9)
         const u32 qb = q_offs[C.k0], qe = q_offs[C.k1];
-        if (qe > qb) {
+        if (qe > qb && use_top) {
+            // m = 2 with top levels: one block per range of the chunk's instances
+            const unsigned grid = prange_off[C.k1] - prange_off[C.k0];
+            L.start(KIND_REDUCE, (double)C.Tq * sizeof(Part) + (double)(qe - qb) * (12 + sizeof(typename Op::Out)));
+            if (grid)
+                k_reduce_top<Op><<<grid, 256, 0, stream>>>(k, C.k0, d_prange, range_pts, d_chunk_off, d_pt_offs, pr0, pj,
+                                                           qchunk_base, d_pt_tiles, (const u32*)P[25], d_qsbase, d_inst,
+                                                           partial, (u32)C.Tq, topv, top_agg);
+            L.stop();
+        } else if (qe > qb) {
             const unsigned grid = (unsigned)std::min<u64>((nchunk + 7) / 8, (u64)h->sms * L.blocks_per_sm);
             L.start(KIND_REDUCE, (double)C.Tq * sizeof(Part) + (double)(qe - qb) * (8 + sizeof(typename Op::Out)));
             k_reduce<Op, M><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pr2, pj,
@@ -1051,7 +1122,6 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                                                       partial, (u32)C.Tq);
             L.stop();
         }
-        T_all += C.T;
         Tq_all += C.Tq;
         kb_all = std::max(kb_all, std::max(C.key_bits, C.key_bits1));
         passes_all = std::max(passes_all, std::max(npass0, npass1));
@@ -1067,7 +1137,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
 
     domagg_stats& S = h->stats;
     S.n_points = (int64_t)N;
-    S.n_records = (int64_t)(use_groups ? T_flat : T_all);
+    S.n_records = (int64_t)T_flat;  // every record of the flat map, wherever it is formed
     S.n_records_shared = (int64_t)T_shared;
     S.n_query_records = (int64_t)Tq_all;
     S.m = M;
@@ -1166,6 +1236,9 @@ bool set_tuning(domagg_ctx* h, const std::string& name, int value) {
     if (name == "group_bits") {
         if (value < 0 || value > GROUP_MAX_BITS) return false;
         h->group_bits = value;
+    } else if (name == "top_bits") {
+        if (value < 0 || value > TOP_MAX_BITS) return false;
+        h->top_bits = value;
     } else if (name == "ranges_per_cta") {
         if (value < 1 || value > 64) return false;
         h->ranges_per_cta = value;
@@ -1856,7 +1929,7 @@ const char* domagg_timing_kind_name(int kind) {
     static const char* names[] = {"encode",  "hist_points",  "sort_points", "rank",     "count_scan",
                                   "expand",  "hist_records", "sort_records", "segscan", "reduce",
                                   "small",   "h2d",          "d2h",          "wavelet",  "sort_groups",
-                                  "group"};
+                                  "group",   "top"};
     if (kind < 0 || kind >= (int)(sizeof(names) / sizeof(names[0]))) return "";
     return names[kind];
 }

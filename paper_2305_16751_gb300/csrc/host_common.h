@@ -30,6 +30,7 @@ enum Kind {
     KIND_WAVELET,  // the level-wise passes
     KIND_SORT_GROUPS,  // m = 2: the points by their group of ranks
     KIND_GROUP,        // m = 2: the deep levels in shared memory (k_group)
+    KIND_TOP,          // m = 2: the top levels per tile (k_top)
     KIND_COUNT_
 };
 

@@ -48,8 +48,11 @@ __host__ __device__ constexpr size_t group_smem_bytes() {
 
 // Per instance (one block each): the largest gS <= min(GROUP_MAX_BITS, b0)
 // whose groups of 2^gS ranks hold at most `cap` points each, and the number
-// of groups G; gS = 0 (every level through the records in HBM) if even
-// groups of 2 ranks are too large, or if the instance takes another path.
+// of groups G; gS = 0 (no level in groups) if even groups of 2 ranks are too
+// large, or if the instance takes another path.  With top_bits > 0, the
+// levels from tS = max(gS, b0 - top_bits) up go to k_top, and the levels
+// [gS, tS) through the records in HBM (lvmask); both masks hold this
+// shard's levels only.
 // rstart (per instance, at pt_off + s) holds the rank-sorted position of the
 // first point of every (undoubled) rank, and n at index U.  A non-strict
 // first coordinate doubles the ranks (2r for data, 2r+1 for queries), so a
@@ -57,7 +60,7 @@ __host__ __device__ constexpr size_t group_smem_bytes() {
 // the bits of the group id (b0 - gS) the group sort sorts.
 template <int M>
 __global__ __launch_bounds__(1024) void k_group_plan(Inst* inst, const u32* __restrict__ rstart,
-                                                    u32* __restrict__ gbits, u32 cap, int max_bits) {
+                                                    u32* __restrict__ gbits, u32 cap, int max_bits, int top_bits) {
     __shared__ u32 s_max[32];
     __shared__ u32 s_done;
     const int s = blockIdx.x;
@@ -98,12 +101,20 @@ __global__ __launch_bounds__(1024) void k_group_plan(Inst* inst, const u32* __re
         I.gS = chosen;
         I.G = chosen ? G : 0u;
         if (gbits) gbits[s] = chosen ? b0 - chosen : 0u;
-        // the levels this call's records take: those >= gS of this shard
+        // the levels >= gS of this shard: from tS up per tile (k_top), below
+        // tS through the records in HBM
         const u32 nlev = M == 1 ? 1u : b0;
         const u32 ns = max(I.nshards, 1u);
-        u32 mask = 0;
+        const bool top = M == 2 && top_bits > 0 && n > 0 && b0 > 0 && !(I.flags & (FLAG_WAVELET | FLAG_VIRTUAL_LAST));
+        const u32 tS = top ? max(chosen, b0 > (u32)top_bits ? b0 - (u32)top_bits : 0u) : nlev;
+        u32 mask = 0, tmask = 0;
         for (u32 lv = chosen; lv < nlev && lv < 32u; ++lv)
-            if ((lv - chosen) % ns == I.shard) mask |= 1u << lv;
+            if ((lv - chosen) % ns == I.shard) {
+                if (lv >= tS) tmask |= 1u << lv;
+                else mask |= 1u << lv;
+            }
+        I.tS = tS;
+        I.topmask = n > 0 ? tmask : 0u;
         I.lvmask = n > 0 ? mask : 0u;
     }
 }
@@ -178,20 +189,31 @@ __device__ __forceinline__ GScan<Acc> gscan_shfl_up(const GScan<Acc>& v, int o) 
     return r;
 }
 
-// The levels below gS of one group whose points (handles in xh, padded
-// layout; values in val by original index) are in the order of the last
-// coordinate.  IT points per thread, contiguous: thread t holds positions
+// The nb rank levels d = nb-1 .. 0 of one block of points (handles in xh,
+// padded layout: the nb rank bits of the levels, the query bit above them,
+// the point's index above that; values in val by that index), in the order
+// of the last coordinate.  A group (k_group) is nb = gS levels of nodes that
+// lie wholly inside it; with TOP (k_top) the block is a tile of a range of
+// points in the order of the last coordinate, the nodes continue across the
+// range's tiles, and frun (heap order: level d's nodes from (1 << (nb-1-d))
+// - 1) holds F over each node's data in the range's earlier tiles; only the
+// levels in scan_mask are scanned (the others are only split).
+// IT points per thread, contiguous: thread t holds positions
 // [t*IT, t*IT + IT).  Per level, one walk over a thread's points applies the
 // thread-local part of the segmented scan (queries add F over the node's
-// data before them within the thread; the exclusive count of rank bit lv = 0
+// data before them within the thread; the exclusive count of rank bit d = 0
 // inside the node is kept per point), a block scan of the threads' tails
 // gives each thread the part from before it, a second walk adds that part
 // to the points before the thread's first node head only, and the split
-// scatters every point to its place in the next level's order.
-template <class Op, int IT>
-__device__ __forceinline__ void group_levels(u32 n, u32 gS, typename Op::Acc* val, u32* xh,
+// scatters every point to its place in the next level's order.  With TOP,
+// each node's F over the tile (ntot, written where the node ends; two
+// halves of 2^(nb-1) entries taken by alternate levels, so that a level's
+// reset never meets the previous level's readers) then advances frun.
+template <class Op, int IT, bool TOP>
+__device__ __forceinline__ void group_levels(u32 n, u32 nb, u32 scan_mask, typename Op::Acc* val, u32* xh,
                                              unsigned short* nstart, unsigned short* nzero,
-                                             GScan<typename Op::Acc>* s_w) {
+                                             GScan<typename Op::Acc>* s_w, typename Op::Acc* frun,
+                                             typename Op::Acc* ntot) {
     typedef typename Op::Acc Acc;
     typedef GScan<Acc> E;
     constexpr u32 NONE = 0xffffffffu;
@@ -199,8 +221,14 @@ __device__ __forceinline__ void group_levels(u32 n, u32 gS, typename Op::Acc* va
     const E ident{0u, Op::e(), 0u};
     const u32 p0 = (u32)tid * IT;
     const bool active = p0 < n;
-    const u32 lrmask = (1u << gS) - 1u;
-    for (int lv = (int)gS - 1; lv >= 0; --lv) {
+    const u32 lrmask = (1u << nb) - 1u;
+    const u32 gS = nb;  // the query bit sits above the rank bits
+    for (int lv = (int)nb - 1; lv >= 0; --lv) {
+        const bool scan = !TOP || ((scan_mask >> lv) & 1u);
+        const u32 nnodes = 1u << (nb - 1u - (u32)lv), hoff = nnodes - 1u;  // (TOP) the level's nodes in frun
+        Acc* lnt = TOP ? ntot + ((u32)(lv & 1) << (nb - 1u)) : nullptr;
+        if (TOP && scan)
+            for (u32 x = (u32)tid; x < nnodes; x += blockDim.x) lnt[x] = Op::e();
         __syncthreads();  // the handles of this level's order are in xh
         const u32 sh = (u32)lv + 1u;
         u32 h[IT];
@@ -208,6 +236,7 @@ __device__ __forceinline__ void group_levels(u32 n, u32 gS, typename Op::Acc* va
         E loc = ident;
         int first_head = IT;   // first point of the thread that starts a node
         u32 z_first = 0;       // the first (continuing) node's zero count in this thread
+        Acc a_first = Op::e();  // (TOP) and its F over the thread's data
         bool first_ends = false;
         u32 first_node = NONE;
         if (active) {
@@ -229,9 +258,11 @@ __device__ __forceinline__ void group_levels(u32 n, u32 gS, typename Op::Acc* va
                         if (first_head == IT) {
                             first_head = j;
                             z_first = zc;
+                            if (TOP) a_first = acc;
                             first_ends = j > 0;
                         } else {
                             nzero[pn] = (unsigned short)zc;  // the node before ended at j-1 and began here
+                            if (TOP && scan) lnt[pn] = acc;
                         }
                         acc = Op::e();
                         zc = 0u;
@@ -239,8 +270,8 @@ __device__ __forceinline__ void group_levels(u32 n, u32 gS, typename Op::Acc* va
                     }
                     pn = nd;
                     const u32 bit = (lr >> lv) & 1u, q = (h[j] >> gS) & 1u, i = h[j] >> (gS + 1u);
-                    if (DOMAGG_GUARD(i < GROUP_CAP && nd < GROUP_NODES, SITE_GROUP_VAL)) {
-                        if (q && bit) val[i] = Op::Fc(val[i], acc);
+                    if (scan && DOMAGG_GUARD(i < GROUP_CAP && nd < GROUP_NODES, SITE_GROUP_VAL)) {
+                        if (q && bit) val[i] = TOP ? Op::Fc(val[i], Op::F(frun[hoff + nd], acc)) : Op::Fc(val[i], acc);
                         else if (!q && !bit) acc = Op::Fc(acc, val[i]);
                     }
                     zin[j >> 1] |= zc << (16 * (j & 1));
@@ -249,9 +280,12 @@ __device__ __forceinline__ void group_levels(u32 n, u32 gS, typename Op::Acc* va
             }
             // the thread's last node ends here unless the next point continues it
             if (nextnode != pn) {
-                if (first_head < IT) nzero[pn] = (unsigned short)zc;
-                else {
+                if (first_head < IT) {
+                    nzero[pn] = (unsigned short)zc;
+                    if (TOP && scan) lnt[pn] = acc;
+                } else {
                     z_first = zc;
+                    if (TOP) a_first = acc;
                     first_ends = true;
                 }
             }
@@ -291,16 +325,21 @@ __device__ __forceinline__ void group_levels(u32 n, u32 gS, typename Op::Acc* va
                 if (j >= first_head) break;
                 {
                     const u32 lr = h[j] & lrmask, bit = (lr >> lv) & 1u, q = (h[j] >> gS) & 1u;
-                    if (q && bit) {
+                    if (scan && q && bit) {
                         const u32 i = h[j] >> (gS + 1u);
                         val[i] = Op::Fc(val[i], ex.acc);
                     }
                     zin[j >> 1] += ex.zc << (16 * (j & 1));
                 }
             }
-            if (first_ends) nzero[first_node] = (unsigned short)(ex.zc + z_first);
+            if (first_ends) {
+                nzero[first_node] = (unsigned short)(ex.zc + z_first);
+                if (TOP && scan) lnt[first_node] = Op::Fc(ex.acc, a_first);
+            }
         }
         __syncthreads();  // node starts and zero counts known; xh read
+        if (TOP && scan)  // the range's running F per node takes in this tile
+            for (u32 x = (u32)tid; x < nnodes; x += blockDim.x) frun[hoff + x] = Op::F(frun[hoff + x], lnt[x]);
         if (lv == 0) break;
         // stable split of every node by bit lv: the order of level lv-1
         if (active) {
@@ -380,8 +419,8 @@ __global__ __launch_bounds__(GROUP_THREADS, 1) void k_group(const Inst* __restri
             // behind every real point of their node), so no walk checks bounds
             for (u32 i = n + tid; i < npad; i += T) xh[pidx(i)] = lrmask;
             __syncthreads();
-            if (n <= 8u * T) group_levels<Op, 8>(npad, gS, val, xh, nstart, nzero, s_w);
-            else group_levels<Op, 12>(npad, gS, val, xh, nstart, nzero, s_w);
+            if (n <= 8u * T) group_levels<Op, 8, false>(npad, gS, ~0u, val, xh, nstart, nzero, s_w, nullptr, nullptr);
+            else group_levels<Op, 12, false>(npad, gS, ~0u, val, xh, nstart, nzero, s_w, nullptr, nullptr);
         }
         __syncthreads();
         // every query of the group: F over its partial results of the levels

@@ -19,7 +19,7 @@ from .build import LIB, LIB_CHECKED
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "OOM", 4: "CUDA", 5: "TIMEOUT", 6: "NAN", 7: "BOUNDS"}
 OPS = {"sum": 0, "max": 1, "count": 2, "min": 3}
 DTYPES = {"i32": 0, "i64": 1, "f32": 2}
-TIMING_KINDS = 16
+TIMING_KINDS = 20
 
 
 class DomaggError(RuntimeError):

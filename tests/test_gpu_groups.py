@@ -1,6 +1,7 @@
 """The m = 2 deep rank levels taken per group of ranks in shared memory
 (k_group) against the same pipeline with every level's records in HBM
-(tuning knob group_bits = 0), and both against the oracle."""
+(tuning knob group_bits = 0; the top levels' tiles are off here), and both
+against the oracle."""
 import contextlib
 
 import numpy as np
@@ -11,6 +12,16 @@ from gpu_helpers import assert_matches_oracle, gpu_forward, to_dev, torch
 from paper_2305_16751_gb300 import domagg, workloads
 
 pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def records_above_the_groups():
+    """These tests compare the groups with the records in HBM: the levels
+    above the groups go through the records too (top_bits = 0)."""
+    h = domagg.handle(0)
+    domagg.domagg_set_tuning(h, "top_bits", 0)
+    yield
+    domagg.domagg_set_tuning(h, "top_bits", 12)
 
 
 @contextlib.contextmanager
