@@ -5,8 +5,11 @@ m = 2, |D| = |Q| = 2^24, float32 coordinates uniform in [0, 1) with 25% of
 the points quantised to a 2^-16 grid (ties), float32 weights N(0, 1),
 F = sum.  value = queries per second (whole job: all ranks' queries / the
 slowest rank's time).  The line also carries:
-  roofline      the dominant kernel (the records radix sort pass) against the
-                measured HBM copy bandwidth;
+  roofline      the dominant HBM-bound kernel (the points' radix pass: the
+                records of this workload never reach HBM) against the
+                measured HBM copy bandwidth; largest_kinds lists the kernel
+                kinds by device time (the shared-memory level kernels k_top
+                and k_group among them);
   cpu_baseline  the CPU oracle on bounded samples: its sort-and-scan (the
                 paper's pipeline in list form, one thread) and its brute force
                 (all host cores);
@@ -123,11 +126,11 @@ class ClockSampler:
 
 
 def profiled_traffic(bytes_per_launch: float, source: str = "k_radix.cuh",
-                     profile: str = "k_onesweep_records_m2_n2e22.md"):
-    """DRAM bytes of one launch of the dominant kernel (a records radix pass,
-    or a level-wise pass): the committed ncu summary's measured DRAM bytes
-    per algorithmic byte, times this run's algorithmic bytes per launch;
-    None if the kernel source changed since that capture."""
+                     profile: str = "k_onesweep_points_m2_n2e22.md"):
+    """DRAM bytes of one launch of the dominant HBM-bound kernel (a radix
+    pass, or a level-wise pass): the committed ncu summary's measured DRAM
+    bytes per algorithmic byte, times this run's algorithmic bytes per
+    launch; None if the kernel source changed since that capture."""
     import hashlib
     src = os.path.join(ROOT, "paper_2305_16751_gb300", "csrc", source)
     prof = os.path.join(ROOT, "profiles", profile)
@@ -447,7 +450,7 @@ def main():
     calls = args.warmup + args.steps
     launches = sum(v["launches"] for k, v in kinds.items() if k not in ("h2d", "d2h")) // calls * args.steps
     peak, peak_src = peaks()
-    dom_kind = "wavelet" if args.variant == "wavelet" else "sort_records"
+    dom_kind = "wavelet" if args.variant == "wavelet" else "sort_points"
     dom = kinds.get(dom_kind, {"ms": 0.0, "bytes": 0.0, "launches": 1})
     achieved = dom["bytes"] / max(dom["ms"], 1e-9) / 1e6  # GB/s
     phase_ms = {k: v["ms"] / calls for k, v in kinds.items()}
@@ -461,19 +464,21 @@ def main():
                        if world > 1 else "1 GPU",
                        "records": st["n_records"], "records_in_shared_memory": st["n_records_shared"],
                        "record_passes": st["record_passes"],
-                       "l2": f"inputs ({(p.D.nbytes + p.Q.nbytes + p.w.nbytes) >> 20} MB) and the records workspace "
-                             f"({st['n_records'] * 16 >> 20} MB) exceed the 129 MB L2; no flush"},
+                       "l2": f"inputs ({(p.D.nbytes + p.Q.nbytes + p.w.nbytes) >> 20} MB) and the library's "
+                             f"workspace ({st['workspace_bytes'] >> 20} MB) exceed the 129 MB L2; no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": profiled_traffic(dom["bytes"] / max(dom["launches"], 1),
                                                      *(("k_wavelet.cuh", "k_wavelet_pass_m2_n2e22.md")
                                                        if args.variant == "wavelet" else ())),
                          "peak_source": peak_src,
                          "kernel": "k_wavelet_pass (level-wise pass)" if args.variant == "wavelet"
-                         else "k_onesweep (records radix pass)",
+                         else "k_onesweep (point radix pass: first coordinate and last coordinate)",
                          "launch_ms": dom["ms"] / max(dom["launches"], 1),
                          "bytes_per_launch": dom["bytes"] / max(dom["launches"], 1)},
             "gpu_launches": launches,
             "phase_ms": phase_ms,
+            "largest_kinds": sorted(((k, round(v, 4)) for k, v in phase_ms.items() if k not in ("h2d", "d2h")),
+                                    key=lambda kv: -kv[1])[:4],
             "step_model": step_model(2 * args.n, st["n_records"], args.n, ms, peak)}
     clocks = clk.summary()
     line["clocks"] = clocks
@@ -494,10 +499,10 @@ def main():
         fb()
         kfb = domagg.domagg_timing_read(h)
         domagg.domagg_timing_enable(h, False)
-        dom_fb = max(("sort_records", "group", "segscan"), key=lambda k: kfb.get(k, {"ms": 0.0})["ms"])
+        dom_fb = max((k for k in kfb if k not in ("h2d", "d2h", "small")), key=lambda k: kfb[k]["ms"])
         line["fwd_bwd"] = {"value": p.Q.shape[0] / (fb_ms / 1e3), "unit": "queries/s", "ms_per_step": fb_ms,
-                           "roofline": kind_roofline(kfb, "sort_records", peak, peak_src,
-                                                     "k_onesweep (records radix pass), forward and backward"),
+                           "roofline": kind_roofline(kfb, "sort_points", peak, peak_src,
+                                                     "k_onesweep (point radix pass), forward and backward"),
                            "largest_kind": dom_fb,
                            "phase_ms": {k: v["ms"] for k, v in kfb.items() if v["ms"] > 0}}
 

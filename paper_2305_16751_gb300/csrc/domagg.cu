@@ -486,12 +486,15 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         // m = 2 top levels: per query F over its range's top levels, per range
         // F of every top-level node (then the carries), the range table, the
         // instances of several ranges
-        P[52] = c.take<typename Op::Part>(use_top ? N : 0);
+        P[52] = c.take<typename Op::Acc>(use_top ? N : 0);
         P[53] = c.take<typename Op::Acc>(use_top ? (size_t)nranges * TOP_STRIDE : 0);
         P[54] = c.take<u32>(use_top ? k + 1 : 0);
         P[55] = c.take<u32>(use_top ? std::max<size_t>(multi.size(), 1) : 0);
+        // m = 2 groups: per query (by position in the order of the last
+        // coordinate) F over the levels below gS
+        P[56] = c.take<typename Op::Acc>(grp ? N : 0);
     };
-    void* P[56];
+    void* P[57];
     {
         Carver c(nullptr);
         carve_points(c, P);
@@ -512,7 +515,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     u32 *chunk_base = (u32*)P[22], *lvl_tot = (u32*)P[23];
     u32 *rstart = (u32*)P[45], *gkey[2] = {(u32*)P[46], (u32*)P[47]}, *gbits = (u32*)P[50], *gslot = (u32*)P[51];
     u64* gval[2] = {(u64*)P[48], (u64*)P[49]};
-    typename Op::Part* topv = (typename Op::Part*)P[52];
+    typename Op::Acc* topv = (typename Op::Acc*)P[52];
+    typename Op::Acc* gacc = (typename Op::Acc*)P[56];
     typename Op::Acc* top_agg = (typename Op::Acc*)P[53];
     u32 *d_prange = (u32*)P[54], *d_multi = (u32*)P[55];
 
@@ -828,11 +832,11 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         }
     }
 
-    // ---- a shard's outputs start at the unit (the group kernel and the
-    // reduction each add only this shard's part)
-    if (inst[0].nshards > 1 && NQ > 0) {
+    // ---- a shard's group parts start at the unit (its group kernel writes
+    // only its own groups' queries)
+    if (use_groups && inst[0].nshards > 1 && N > 0) {
         L.start(KIND_SMALL, 0.0);
-        k_fill_unit<Op><<<(unsigned)((NQ + 255) / 256), 256, 0, stream>>>(d_inst, d_q_offs, k, (u32)NQ);
+        k_fill_e<Op><<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(gacc, (u32)N);
         L.stop();
     }
     // ---- m = 2: the deep rank levels by groups, in shared memory (k_group):
@@ -866,9 +870,9 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         constexpr size_t gsm = group_smem_bytes<Acc>();
         if (!L.frozen) cudaFuncSetAttribute(k_group<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
         const int li = L.lookback_index();
-        L.start(KIND_GROUP, (double)N * 8.0 + (double)NQ * sizeof(typename Op::Out));
+        L.start(KIND_GROUP, (double)N * 8.0 + (double)NQ * sizeof(typename Op::Acc));
         k_group<Op><<<(unsigned)h->sms, GROUP_THREADS, gsm, stream>>>(d_inst, k, gslot, rstart, gval[0], gval[1],
-                                                                      (const W*)P[18], h->ctl, li);
+                                                                      (const W*)P[18], gacc, h->ctl, li);
         L.stop();
     }
     // ---- m = 2: the top levels per range of tiles in the order of the last
@@ -878,10 +882,12 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         constexpr size_t tsm = TopSmem<Acc>::TOTAL;
         if (!L.frozen) cudaFuncSetAttribute(k_top<Op, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
         const int li = L.lookback_index();
-        L.start(KIND_TOP, (double)N * (4.0 + (WT == 3 ? 0.0 : sizeof(W))) + (double)NQ * sizeof(Part) +
+        L.start(KIND_TOP, (double)N * (4.0 + (WT == 3 ? 0.0 : sizeof(W))) +
+                              (double)NQ * sizeof(Acc) * (use_groups ? 2.0 : 1.0) +
                               (double)nranges * TOP_STRIDE * sizeof(Acc));
         k_top<Op, WT><<<(unsigned)h->sms, TOP_THREADS, tsm, stream>>>(d_inst, k, d_prange, d_pt_offs, range_pts, pr0,
-                                                                      (const W*)P[18], topv, top_agg, h->ctl, li);
+                                                                      (const W*)P[18], gacc, topv, top_agg, h->ctl,
+                                                                      li);
         L.stop();
         if (!multi.empty()) {
             L.start(KIND_SMALL, 0.0);
@@ -1108,18 +1114,20 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         if (qe > qb && use_top) {
             // m = 2 with top levels: one block per range of the chunk's instances
             const unsigned grid = prange_off[C.k1] - prange_off[C.k0];
-            L.start(KIND_REDUCE, (double)C.Tq * sizeof(Part) + (double)(qe - qb) * (12 + sizeof(typename Op::Out)));
+            // every point's index; a query's rank, top-level value and output
+            L.start(KIND_REDUCE, (double)C.Tq * sizeof(Part) + (double)(pt_offs[C.k1] - pt_offs[C.k0]) * 4 +
+                                     (double)(qe - qb) * (4 + sizeof(typename Op::Acc) + sizeof(typename Op::Out)));
             if (grid)
-                k_reduce_top<Op><<<grid, 256, 0, stream>>>(k, C.k0, d_prange, range_pts, d_chunk_off, d_pt_offs, pr0, pj,
-                                                           qchunk_base, d_pt_tiles, (const u32*)P[25], d_qsbase, d_inst,
-                                                           partial, (u32)C.Tq, topv, top_agg);
+                k_reduce_top<Op><<<grid, TOP_RED_THREADS, 0, stream>>>(
+                    k, C.k0, d_prange, range_pts, d_chunk_off, d_pt_offs, pr0, pj, qchunk_base, d_pt_tiles,
+                    (const u32*)P[25], d_qsbase, d_inst, partial, (u32)C.Tq, gacc, topv, top_agg);
             L.stop();
         } else if (qe > qb) {
             const unsigned grid = (unsigned)std::min<u64>((nchunk + 7) / 8, (u64)h->sms * L.blocks_per_sm);
             L.start(KIND_REDUCE, (double)C.Tq * sizeof(Part) + (double)(qe - qb) * (8 + sizeof(typename Op::Out)));
             k_reduce<Op, M><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pr2, pj,
                                                       qchunk_base, d_pt_tiles, (const u32*)P[25], d_qsbase, d_inst,
-                                                      partial, (u32)C.Tq);
+                                                      partial, (u32)C.Tq, gacc);
             L.stop();
         }
         Tq_all += C.Tq;

@@ -206,9 +206,14 @@ __device__ __forceinline__ GScan<Acc> gscan_shfl_up(const GScan<Acc>& v, int o) 
 // gives each thread the part from before it, a second walk adds that part
 // to the points before the thread's first node head only, and the split
 // scatters every point to its place in the next level's order.  With TOP,
-// each node's F over the tile (ntot, written where the node ends; two
-// halves of 2^(nb-1) entries taken by alternate levels, so that a level's
-// reset never meets the previous level's readers) then advances frun.
+// a node's scan starts at its head from frun (so every query of the node
+// receives the earlier tiles' part with the rest), and F at the node's end
+// (ntot, preset to frun for nodes the tile does not hold; two halves of
+// 2^(nb-1) entries taken by alternate levels, so that a level's preset
+// never meets the previous level's readers) becomes the new frun.
+// One walk combines every point's value with the running F (the sum of a
+// datum is kept, a query's own value takes it): the same operation for
+// both roles, so a warp does not run the two one after the other.
 template <class Op, int IT, bool TOP>
 __device__ __forceinline__ void group_levels(u32 n, u32 nb, u32 scan_mask, typename Op::Acc* val, u32* xh,
                                              unsigned short* nstart, unsigned short* nzero,
@@ -228,7 +233,7 @@ __device__ __forceinline__ void group_levels(u32 n, u32 nb, u32 scan_mask, typen
         const u32 nnodes = 1u << (nb - 1u - (u32)lv), hoff = nnodes - 1u;  // (TOP) the level's nodes in frun
         Acc* lnt = TOP ? ntot + ((u32)(lv & 1) << (nb - 1u)) : nullptr;
         if (TOP && scan)
-            for (u32 x = (u32)tid; x < nnodes; x += blockDim.x) lnt[x] = Op::e();
+            for (u32 x = (u32)tid; x < nnodes; x += blockDim.x) lnt[x] = frun[hoff + x];
         __syncthreads();  // the handles of this level's order are in xh
         const u32 sh = (u32)lv + 1u;
         u32 h[IT];
@@ -264,15 +269,17 @@ __device__ __forceinline__ void group_levels(u32 n, u32 nb, u32 scan_mask, typen
                             nzero[pn] = (unsigned short)zc;  // the node before ended at j-1 and began here
                             if (TOP && scan) lnt[pn] = acc;
                         }
-                        acc = Op::e();
+                        acc = (TOP && scan) ? frun[hoff + nd] : Op::e();
                         zc = 0u;
                         nstart[nd] = (unsigned short)p;
                     }
                     pn = nd;
                     const u32 bit = (lr >> lv) & 1u, q = (h[j] >> gS) & 1u, i = h[j] >> (gS + 1u);
                     if (scan && DOMAGG_GUARD(i < GROUP_CAP && nd < GROUP_NODES, SITE_GROUP_VAL)) {
-                        if (q && bit) val[i] = TOP ? Op::Fc(val[i], Op::F(frun[hoff + nd], acc)) : Op::Fc(val[i], acc);
-                        else if (!q && !bit) acc = Op::Fc(acc, val[i]);
+                        // F(acc, v) serves both roles (a datum's sum, a query's value)
+                        const Acc v = val[i], sum = Op::Fc(acc, v);
+                        if (q && bit) val[i] = sum;
+                        acc = (!q && !bit) ? sum : acc;
                     }
                     zin[j >> 1] |= zc << (16 * (j & 1));
                     zc += bit ^ 1u;
@@ -338,8 +345,8 @@ __device__ __forceinline__ void group_levels(u32 n, u32 nb, u32 scan_mask, typen
             }
         }
         __syncthreads();  // node starts and zero counts known; xh read
-        if (TOP && scan)  // the range's running F per node takes in this tile
-            for (u32 x = (u32)tid; x < nnodes; x += blockDim.x) frun[hoff + x] = Op::F(frun[hoff + x], lnt[x]);
+        if (TOP && scan)  // the range's running F per node, renormalised
+            for (u32 x = (u32)tid; x < nnodes; x += blockDim.x) frun[hoff + x] = Op::F(Op::e(), lnt[x]);
         if (lv == 0) break;
         // stable split of every node by bit lv: the order of level lv-1
         if (active) {
@@ -361,15 +368,17 @@ __device__ __forceinline__ void group_levels(u32 n, u32 nb, u32 scan_mask, typen
 // (one per SM) take groups from a counter.  Inputs: the group-sorted points
 // gv (per instance in buffer gv0 or gv1, by the parity of the group sort's
 // passes): (rank | QUERY_BIT) << 32 | payload, the payload being a query's
-// local index, a datum's weight bits, or (8-byte weights) the datum's
-// position in pw.  Writes out[q] = F over the query's partial results of the
-// levels below gS.
+// position x in the order of the last coordinate, a datum's weight bits, or
+// (8-byte weights) the datum's position in pw.  Writes gacc[x] = F over the
+// query's partial results of the levels below gS (read in that order by
+// k_top and the per-query reduction).
 template <class Op>
 __global__ __launch_bounds__(GROUP_THREADS, 1) void k_group(const Inst* __restrict__ inst, int k,
                                                             const u32* __restrict__ gslot_off,
                                                             const u32* __restrict__ rstart, const u64* __restrict__ gv0,
                                                             const u64* __restrict__ gv1,
-                                                            const typename Op::W* __restrict__ pw, Ctl* ctl,
+                                                            const typename Op::W* __restrict__ pw,
+                                                            typename Op::Acc* __restrict__ gacc, Ctl* ctl,
                                                             int launch_idx) {
     typedef typename Op::Acc Acc;
     typedef GScan<Acc> E;
@@ -424,22 +433,12 @@ __global__ __launch_bounds__(GROUP_THREADS, 1) void k_group(const Inst* __restri
         }
         __syncthreads();
         // every query of the group: F over its partial results of the levels
-        // below gS (the unit e if it has none)
-        typename Op::Out* out = reinterpret_cast<typename Op::Out*>(I.out);
+        // below gS (the unit e if it has none), at its position
         for (u32 i = tid; i < n; i += T) {
             const u64 v = gv[i];
             if ((u32)(v >> 32) & QUERY_BIT) {
-                const u32 qi = (u32)v;
-                if (domagg_check(qi < I.nQ, SITE_GROUP_OUT)) {
-                    if constexpr (std::is_same<Op, OpSumF32>::value) {
-                        if (I.out_lo) {  // a shard keeps the float-float pair
-                            out[qi] = val[i].hi;
-                            I.out_lo[qi] = val[i].lo;
-                            continue;
-                        }
-                    }
-                    out[qi] = Op::to_out(val[i]);
-                }
+                const u32 x = (u32)v;
+                if (domagg_check(x - I.pt_off < I.nD + I.nQ, SITE_GROUP_OUT)) gacc[x] = val[i];
             }
         }
         __syncthreads();  // shared memory is free for the next group

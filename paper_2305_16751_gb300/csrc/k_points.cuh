@@ -421,10 +421,11 @@ __global__ __launch_bounds__(256) void k_count_scan(
                 }
             }
             // m = 2 with groups: the group sort's key (the group: rank >> gS)
-            // and value (rank | query bit, then the query's local index, the
-            // weight's bits, or for 8-byte weights the position in pw)
+            // and value (rank | query bit, then a query's position in this
+            // order, a datum's weight bits or, for 8-byte weights, its
+            // position in pw)
             if (M == 2 && gkey && I.gS) {
-                const u32 pv = q ? j - L.seg_begin : (WT == 1 ? x : wbits);
+                const u32 pv = (q || WT == 1) ? x : wbits;
                 gkey[x] = a >> I.gS;
                 gval[x] = ((u64)(q ? (a | QUERY_BIT) : a) << 32) | (u64)pv;
             }

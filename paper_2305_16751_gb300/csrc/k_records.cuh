@@ -673,25 +673,12 @@ __global__ __launch_bounds__(THREADS) void k_segscan_lb(const K* __restrict__ ke
     }
 }
 
-// A shard's outputs start at the unit e (k_group writes only its own
-// groups' queries; the reduction then adds this shard's levels).
+// a[0 .. n) = e: a shard's group parts start at the unit (k_group writes
+// only its own groups' queries).
 template <class Op>
-__global__ void k_fill_unit(const Inst* __restrict__ inst, const u32* __restrict__ q_offs, int k, u32 NQ) {
+__global__ void k_fill_e(typename Op::Acc* __restrict__ a, u32 n) {
     const u32 g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= NQ) return;
-    const int s = upper_index(q_offs, k + 1, g);
-    const Inst& I = inst[s];
-    const u32 q = g - __ldg(q_offs + s);
-    if (q >= I.nQ) return;
-    bool done = false;
-    if constexpr (std::is_same<Op, OpSumF32>::value) {
-        if (I.out_lo) {
-            reinterpret_cast<float*>(I.out)[q] = 0.f;
-            I.out_lo[q] = 0.f;
-            done = true;
-        }
-    }
-    if (!done) reinterpret_cast<typename Op::Out*>(I.out)[q] = Op::to_out(Op::e());
+    if (g < n) a[g] = Op::e();
 }
 
 // out[q] = F over the shards' partial outputs (float32 sums: the shards'
@@ -731,7 +718,8 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
                                                 const u32* __restrict__ pt_tiles, const u32* __restrict__ tile_excl,
                                                 const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/,
                                                 const Inst* __restrict__ inst,
-                                                const typename Op::Part* __restrict__ partial, u32 n_partial) {
+                                                const typename Op::Part* __restrict__ partial, u32 n_partial,
+                                                const typename Op::Acc* __restrict__ gacc) {
     typedef typename Op::Part Part;
     __shared__ u32 s_mask[8][LMAX];  // per warp: query lanes holding a record of level lv
     __shared__ u32 s_base[8][LMAX];  // per warp: first partial slot of level lv in this chunk
@@ -776,13 +764,8 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
         s_mask[warp][lane] = warp_transpose32(bits0, (u32)lane);  // lanes of level `lane`
         __syncwarp();
         typename Op::Acc acc = Op::e();
-        // m = 2 with groups: out[q] holds F over the levels below gS already
-        // (a shard of a float32 sum: the float-float pair)
-        if (M == 2 && q && I.gS) {
-            acc = Op::from_out(reinterpret_cast<const typename Op::Out*>(I.out)[local]);
-            if constexpr (std::is_same<Op, OpSumF32>::value)
-                if (I.out_lo) acc.lo = I.out_lo[local];
-        }
+        // m = 2 with groups: F over the levels below gS, by position
+        if (M == 2 && q && I.gS) acc = gacc[p];
         if (M <= 2) {
             // one partial per query and level, at the level's base plus the
             // query lanes of that level before this one; each lane walks only

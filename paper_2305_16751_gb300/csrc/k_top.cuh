@@ -12,7 +12,8 @@
 // order, instructions 6m+1 .. 6m+3).  A node's records continue across
 // tiles and ranges, so the scan carries, per node, F over the node's data in
 // the range's earlier tiles (frun, in shared memory), and every query keeps
-// F over its partial results of the range's top levels (topv).  What the
+// F over its partial results of the range's top levels and of the levels
+// below gS (those from k_group, by position: gacc) in topv.  What the
 // range's nodes gathered (agg) is then scanned across the ranges of the
 // instance in a fixed order (k_top_carry), and the per-query reduction adds
 // to each query, for every top level where it has a record, the carry of its
@@ -65,17 +66,20 @@ __device__ __forceinline__ TopRange top_range(u32 r, const u32* prange_off, int 
 
 // The top levels of every range (see the file comment).  Persistent CTAs
 // (one per SM) take ranges from a counter.  Inputs, in the order of the last
-// coordinate: pr0 (rank | QUERY_BIT) and pw (a datum's weight bits, or its
-// 8-byte weight for WT = 1).  Writes topv[x] (queries: F over their partial
-// results of the range's top levels, the unit if none) and agg[r][h] (F over
-// the range's data of node h, heap order).
+// coordinate: pr0 (rank | QUERY_BIT), pw (a datum's weight bits, or its
+// 8-byte weight for WT = 1) and, for an instance with groups, gacc (a
+// query's F over the levels below gS).  Writes topv[x] (queries: F over
+// their partial results of the range's top levels and the levels below gS,
+// the unit if none) and agg[r][h] (F over the range's data of node h, heap
+// order).
 template <class Op, int WT>
 __global__ __launch_bounds__(TOP_THREADS, 1) void k_top(const Inst* __restrict__ inst, int k,
                                                         const u32* __restrict__ prange_off,
                                                         const u32* __restrict__ pt_offs, u32 range_pts,
                                                         const u32* __restrict__ pr0,
                                                         const typename Op::W* __restrict__ pw,
-                                                        typename Op::Part* __restrict__ topv,
+                                                        const typename Op::Acc* __restrict__ gacc,
+                                                        typename Op::Acc* __restrict__ topv,
                                                         typename Op::Acc* __restrict__ agg, Ctl* ctl, int launch_idx) {
     typedef typename Op::Acc Acc;
     typedef TopSmem<Acc> SM;
@@ -99,6 +103,7 @@ __global__ __launch_bounds__(TOP_THREADS, 1) void k_top(const Inst* __restrict__
         const TopRange R = top_range(r, prange_off, k, pt_offs, range_pts);
         const Inst& I = inst[R.s];
         const u32 tmask = I.topmask, tS = I.tS, b0 = I.b[0];
+        const bool grouped = I.gS != 0u;
         // (the instance's levels from tS up: nb <= TOP_MAX_BITS by k_group_plan)
         const u32 nb = tmask ? b0 - tS : 0u;
         if (nb > 0u && DOMAGG_GUARD(nb <= (u32)TOP_MAX_BITS, SITE_GROUP_NODE)) {
@@ -111,7 +116,7 @@ __global__ __launch_bounds__(TOP_THREADS, 1) void k_top(const Inst* __restrict__
                     const u32 v = pr0[a0 + i];
                     const bool q = (v & QUERY_BIT) != 0u;
                     xh[pidx(i)] = (((v & ~QUERY_BIT) >> tS) & lrmask) | ((q ? 1u : 0u) << nb) | (i << (nb + 1u));
-                    if (q) val[i] = Op::e();
+                    if (q) val[i] = grouped ? gacc[a0 + i] : Op::e();
                     else if constexpr (Op::GATHER) val[i] = Op::from_w(pw[a0 + i]);
                     else if constexpr (WT == 3) val[i] = Op::from_pay(0u);
                     else val[i] = Op::from_pay((typename Op::Pay)pw[a0 + i]);
@@ -125,7 +130,7 @@ __global__ __launch_bounds__(TOP_THREADS, 1) void k_top(const Inst* __restrict__
                 else group_levels<Op, 12, true>(npad, nb, tmask >> tS, val, xh, nstart, nzero, s_w, frun, ntot);
                 __syncthreads();
                 for (u32 i = tid; i < n; i += T)
-                    if (pr0[a0 + i] & QUERY_BIT) topv[a0 + i] = Op::to_part(val[i]);
+                    if (pr0[a0 + i] & QUERY_BIT) topv[a0 + i] = val[i];
             }
             __syncthreads();  // the last tile's node totals are in frun
             for (u32 h = tid; h < stride; h += T) agg[(u64)r * TOP_STRIDE + h] = frun[h];
@@ -181,14 +186,15 @@ __global__ __launch_bounds__(1024) void k_top_carry(const u32* __restrict__ mult
 }
 
 // Per-query reduction of m = 2 with top levels (replaces k_reduce there):
-// one block per range of the chunk's instances [k0, k1).  For each query:
-// F over what k_group wrote to out (the levels below gS), its partials of
-// the levels that went through the records in HBM (slots as in k_reduce),
-// topv (the range's top levels) and, for every top level where it has a
-// record, the carry of its node from the instance's earlier ranges (staged
-// in shared memory).
+// one block of TOP_RED_THREADS per range of the chunk's instances [k0, k1).
+// For each query: F over topv (the range's top levels and the levels below
+// gS; gacc alone for an instance without top levels), its partials of the
+// levels that went through the records in HBM (slots as in k_reduce) and,
+// for every top level where it has a record, the carry of its node from the
+// instance's earlier ranges (staged in shared memory).
+constexpr int TOP_RED_THREADS = 1024;
 template <class Op>
-__global__ __launch_bounds__(256) void k_reduce_top(int k, int k0, const u32* __restrict__ prange_off, u32 range_pts,
+__global__ __launch_bounds__(TOP_RED_THREADS) void k_reduce_top(int k, int k0, const u32* __restrict__ prange_off, u32 range_pts,
                                                     const u32* __restrict__ chunk_off, const u32* __restrict__ pt_offs,
                                                     const u32* __restrict__ pr0, const u32* __restrict__ pj,
                                                     const u32* __restrict__ qchunk_base,
@@ -196,12 +202,14 @@ __global__ __launch_bounds__(256) void k_reduce_top(int k, int k0, const u32* __
                                                     const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/,
                                                     const Inst* __restrict__ inst,
                                                     const typename Op::Part* __restrict__ partial, u32 n_partial,
-                                                    const typename Op::Part* __restrict__ topv,
+                                                    const typename Op::Acc* __restrict__ gacc,
+                                                    const typename Op::Acc* __restrict__ topv,
                                                     const typename Op::Acc* __restrict__ carry) {
     typedef typename Op::Acc Acc;
     __shared__ Acc s_carry[TOP_STRIDE];
-    __shared__ u32 s_mask[8][LMAX];  // per warp: query lanes holding a record of level lv
-    __shared__ u32 s_base[8][LMAX];  // per warp: first partial slot of level lv in this chunk
+    constexpr u32 WARPS = TOP_RED_THREADS / 32;
+    __shared__ u32 s_mask[WARPS][LMAX];  // per warp: query lanes holding a record of level lv
+    __shared__ u32 s_base[WARPS][LMAX];  // per warp: first partial slot of level lv in this chunk
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const u32 lt = lanemask_lt();
     const u32 r = __ldg(prange_off + k0) + blockIdx.x;
@@ -218,7 +226,7 @@ __global__ __launch_bounds__(256) void k_reduce_top(int k, int k0, const u32* __
     const u32 nQ = I.nQ;
     const u32 c0 = __ldg(chunk_off + s);
     const u32 cb = c0 + (R.start - R.ps) / 32u, ce = c0 + (R.end - R.ps + 31u) / 32u;
-    for (u32 c = cb + (u32)warp; c < ce; c += 8u) {
+    for (u32 c = cb + (u32)warp; c < ce; c += WARPS) {
         const u32 p = R.ps + (c - c0) * 32u + (u32)lane;
         const bool valid = p < R.end;
         u32 local = 0, a = 0, bits0 = 0;
@@ -243,11 +251,7 @@ __global__ __launch_bounds__(256) void k_reduce_top(int k, int k0, const u32* __
         s_mask[warp][lane] = warp_transpose32(rec, (u32)lane);  // lanes of level `lane`
         __syncwarp();
         Acc acc = Op::e();
-        if (q && I.gS) {  // out[q] holds F over the levels below gS (a shard: the float-float pair)
-            acc = Op::from_out(reinterpret_cast<const typename Op::Out*>(I.out)[local]);
-            if constexpr (std::is_same<Op, OpSumF32>::value)
-                if (I.out_lo) acc.lo = I.out_lo[local];
-        }
+        if (q) acc = tmask ? topv[p] : (I.gS ? gacc[p] : Op::e());
         u32 rem = rec;
 #pragma unroll 4
         while (rem) {
@@ -256,13 +260,10 @@ __global__ __launch_bounds__(256) void k_reduce_top(int k, int k0, const u32* __
             const u32 slot = s_base[warp][lv] + (u32)__popc(s_mask[warp][lv] & lt);
             if (domagg_check(slot < n_partial, SITE_REDUCE)) acc = Op::F(acc, Op::from_part(partial[slot]));
         }
-        if (q && tmask) {
-            acc = Op::F(acc, Op::from_part(topv[p]));
-            if (carried) {
-                for (u32 top = bits0 & tmask; top; top &= top - 1) {
-                    const u32 lv = __ffs(top) - 1;
-                    acc = Op::F(acc, s_carry[(1u << (b0 - 1u - lv)) - 1u + (a >> (lv + 1u))]);
-                }
+        if (q && carried) {
+            for (u32 top = bits0 & tmask; top; top &= top - 1) {
+                const u32 lv = __ffs(top) - 1;
+                acc = Op::F(acc, s_carry[(1u << (b0 - 1u - lv)) - 1u + (a >> (lv + 1u))]);
             }
         }
         if (q) {
