@@ -351,9 +351,18 @@ domagg_status domagg_forward_noalloc(int m, const void* d_coords, int64_t nD, co
  *   "group_bits"     0 .. 13 (default 13): for m = 2, the rank levels below
  *                    gS <= group_bits (nodes of at most 2^gS ranks) are
  *                    formed, sorted and scanned per group of 2^gS ranks in
- *                    shared memory; 0 sends every level's records through
+ *                    shared memory; 0 sends those levels' records through
  *                    HBM;
- *   "ranges_per_cta" 1 .. 64 (default 4): radix-sort ranges per resident CTA;
+ *   "top_bits"       0 .. 12 (default 12): for m = 2, the rank levels from
+ *                    tS = max(gS, b0 - top_bits) up are formed, sorted and
+ *                    scanned per tile of points in the order of the last
+ *                    coordinate in shared memory, with each node's running
+ *                    F carried across tiles and ranges of tiles; 0 sends
+ *                    those levels' records through HBM;
+ *   "rank_windows"   0 .. 64 (default 0: about 48 MB of ranks each): windows
+ *                    of destination indices the rank scatter is split into;
+ *   "ranges_per_cta" 1 .. 64 (default 4): radix-sort ranges per resident CTA
+ *                    (and ranges of tiles of the top levels per SM);
  *   "blocks_per_sm"  1 .. 64 (default 16): flat-map / reduction blocks per SM.
  * The environment variable DOMAGG_TUNE="name=value,..." sets the defaults of
  * handles created afterwards.  Unknown names or values out of range return

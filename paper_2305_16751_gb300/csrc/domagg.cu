@@ -91,6 +91,8 @@ struct domagg_ctx {
     // each) per tile in shared memory (k_top); 0 = every level from gS up
     // through the records in HBM
     int top_bits = TOP_MAX_BITS;
+    // windows of the rank scatter (0: about 48 MB of ranks each)
+    int rank_windows = 0;
 
     size_t held() const { return pts.cap + recs.cap + st_multi.cap + st_seg.cap + stage.cap + st_wv.cap; }
 };
@@ -618,11 +620,20 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         L.start(KIND_SMALL, 0.0);
         k_tile_exscan<<<(unsigned)((k + 7) / 8), 256, 0, C.stream>>>(d_pt_tiles, k, C.tile_cnt);
         L.stop();
-        L.start(KIND_RANK, (double)N * 12);
-        k_rank_apply<SCAN_THREADS, SCAN_ITEMS><<<(unsigned)ntp, SCAN_THREADS, 0, C.stream>>>(
-            keys[cur], vals[cur], d_pt_offs, d_pt_tiles, k, C.tile_cnt, i == 0 ? r0 : (i == 1 ? r1 : r2), d_inst, i,
-            (i == 0 && use_groups) ? rstart : nullptr);
-        L.stop();
+        // the rank scatter in windows of destinations (each about 48 MB of
+        // ranks, so the L2 holds a window while its sectors fill)
+        const u64 nwin = h->rank_windows > 0 ? (u64)h->rank_windows
+                                             : std::max<u64>(1, (N * sizeof(u32) + (48ull << 20) - 1) / (48ull << 20));
+        const u64 span = (N + nwin - 1) / nwin;
+        for (u64 w = 0; w < nwin; ++w) {
+            const u64 lo = w * span, hi = std::min<u64>(N, lo + span);
+            if (lo >= hi && w > 0) break;
+            L.start(KIND_RANK, (double)N * 8 * (w == 0 ? 1 : 0) + (double)(hi - lo) * 4);
+            k_rank_apply<SCAN_THREADS, SCAN_ITEMS><<<(unsigned)ntp, SCAN_THREADS, 0, C.stream>>>(
+                keys[cur], vals[cur], d_pt_offs, d_pt_tiles, k, C.tile_cnt, i == 0 ? r0 : (i == 1 ? r1 : r2), d_inst,
+                i, (i == 0 && use_groups) ? rstart : nullptr, (u32)lo, (u32)hi);
+            L.stop();
+        }
     };
     auto last_dim = [&](const Chain& C) -> u32* {  // order of the last coordinate, queries first on ties (Sec. 5)
         L.stream = C.stream;
@@ -1247,6 +1258,9 @@ bool set_tuning(domagg_ctx* h, const std::string& name, int value) {
     } else if (name == "top_bits") {
         if (value < 0 || value > TOP_MAX_BITS) return false;
         h->top_bits = value;
+    } else if (name == "rank_windows") {
+        if (value < 0 || value > 64) return false;
+        h->rank_windows = value;
     } else if (name == "ranges_per_cta") {
         if (value < 1 || value > 64) return false;
         h->ranges_per_cta = value;

@@ -140,6 +140,7 @@ __global__ void k_encode(const Inst* __restrict__ inst, const u32* __restrict__ 
 template <int THREADS, int ITEMS>
 __device__ __forceinline__ void load_blocked_u32(const u32* __restrict__ src, u32 start, u32 end, u32* sbuf,
                                                  u32 (&out)[ITEMS], u32 fill) {
+#pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const u32 x = (u32)i * THREADS + threadIdx.x;
         sbuf[pidx(x)] = (start + x < end) ? src[start + x] : fill;
@@ -194,7 +195,10 @@ __device__ __forceinline__ void block_exscan(u32 (&v)[C], u32 (&tot)[C], u32* sc
 // the cost): (1) per tile, the number of keys that differ from their
 // predecessor; (2) per instance, the exclusive scan of those counts over its
 // tiles (one warp per instance); (3) k_rank_apply: flags again, a block scan
-// plus the tile's prefix, and the scatter by index.
+// plus the tile's prefix, and the scatter by index.  The scatter writes
+// 4 bytes at random; it runs in windows of destination indices [win_lo,
+// win_hi) small enough for the 129 MB L2 to hold while its sectors fill
+// (one launch per window; the first also writes rstart and U, b).
 template <int THREADS, int ITEMS>
 __global__ __launch_bounds__(THREADS) void k_rank_count(const u32* __restrict__ skeys, const u32* __restrict__ seg_off,
                                                         const u32* __restrict__ tile_off, int nseg,
@@ -264,7 +268,8 @@ __global__ __launch_bounds__(THREADS, 4) void k_rank_apply(const u32* __restrict
                                                         const u32* __restrict__ seg_off,
                                                         const u32* __restrict__ tile_off, int nseg,
                                                         const u32* __restrict__ tile_excl, u32* __restrict__ rank_out,
-                                                        Inst* inst, int dim, u32* __restrict__ rstart) {
+                                                        Inst* inst, int dim, u32* __restrict__ rstart, u32 win_lo,
+                                                        u32 win_hi) {
     constexpr int TILE = THREADS * ITEMS;
     __shared__ u32 sbuf[Padded<TILE>::value];
     __shared__ u32 scratch[THREADS / 32];
@@ -273,6 +278,7 @@ __global__ __launch_bounds__(THREADS, 4) void k_rank_apply(const u32* __restrict
     const TileLoc L = locate_tile<TILE>(t, seg_off, tile_off, nseg);
     const bool nonstrict = (inst[L.seg].flags >> dim) & 1u;
     const u32 nQ = inst[L.seg].nQ;
+    const bool first_window = win_lo == 0u;
     u32 key[ITEMS];
     load_blocked_u32<THREADS, ITEMS>(skeys, L.start, L.end, sbuf, key, 0u);
     const u32 x0 = L.start + threadIdx.x * ITEMS;
@@ -297,27 +303,34 @@ __global__ __launch_bounds__(THREADS, 4) void k_rank_apply(const u32* __restrict
     // rstart (first coordinate of m = 2): per instance, at seg_begin + seg,
     // the instance-local sorted position of every rank's first point, and
     // the instance's size at index U (the group sizes of k_group_plan)
-    u32* rs = rstart ? rstart + L.seg_begin + (u32)L.seg : nullptr;
+    u32* rs = (rstart && first_window) ? rstart + L.seg_begin + (u32)L.seg : nullptr;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const u32 x = x0 + i;
         run += (fmask >> i) & 1u;
         sbuf[pidx(lx0 + i)] = run - 1u;
         if (rs && ((fmask >> i) & 1u)) rs[run - 1u] = x - L.seg_begin;
-        if (x < L.end && x + 1 == L.seg_end) {
+        if (first_window && x < L.end && x + 1 == L.seg_end) {
             const u32 U = nonstrict ? 2u * run : run;
             inst[L.seg].U[dim] = U;
             inst[L.seg].b[dim] = U <= 1u ? 0u : 32u - __clz(U - 1u);
             if (rs) rs[run] = L.seg_end - L.seg_begin;
         }
     }
+    // the scatter's indices, all in flight before the barrier
+    u32 dsts[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const u32 x = L.start + (u32)i * THREADS + threadIdx.x;
+        dsts[i] = x < L.end ? sidx[x] : 0xffffffffu;
+    }
     __syncthreads();
     const u32 n_total = __ldg(seg_off + nseg);
-#pragma unroll 4
+#pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         const u32 x = (u32)i * THREADS + threadIdx.x;
-        if (L.start + x < L.end) {
-            const u32 dst = sidx[L.start + x];
+        const u32 dst = dsts[i];
+        if (L.start + x < L.end && dst - win_lo < win_hi - win_lo) {
             u32 r = sbuf[pidx(x)];
             if (nonstrict) r = 2u * r + ((dst - L.seg_begin) < nQ ? 1u : 0u);
             if (domagg_check(dst < n_total, SITE_RANK)) rank_out[dst] = r;
@@ -388,15 +401,32 @@ __global__ __launch_bounds__(256) void k_count_scan(
     // per lane (= level): the counts of every chunk of the warp
     u32 rc[CS_ROUNDS], qc[CS_ROUNDS];
     u32 run_all = 0, run_q = 0;
+    // eight rounds at a time: their permutation loads, then their gathers of
+    // the first rank, all in flight together
+    constexpr int BATCH = 8;
+    static_assert(CS_ROUNDS % BATCH == 0, "whole batches");
+    u32 jb[BATCH], ab[BATCH];
 #pragma unroll
     for (int i = 0; i < CS_ROUNDS; ++i) {
         const u32 x = wstart + (u32)i * 32u + (u32)lane;
         const bool valid = x < L.end;
-        u32 j = valid ? perm[rev ? L.seg_begin + (L.seg_end - 1u - x) : x] : L.seg_begin;
-        if (j >= n_total) j = L.seg_begin;  // never taken for a valid permutation
+        if (i % BATCH == 0) {
+#pragma unroll
+            for (int b = 0; b < BATCH; ++b) {
+                const u32 xb = wstart + (u32)(i + b) * 32u + (u32)lane;
+                u32 jj = xb < L.end ? perm[rev ? L.seg_begin + (L.seg_end - 1u - xb) : xb] : L.seg_begin;
+                if (jj >= n_total) jj = L.seg_begin;  // never taken for a valid permutation
+                jb[b] = jj;
+            }
+#pragma unroll
+            for (int b = 0; b < BATCH; ++b) {
+                const u32 xb = wstart + (u32)(i + b) * 32u + (u32)lane;
+                ab[b] = (M >= 2 && xb < L.end) ? r0[jb[b]] : 0u;
+            }
+        }
+        const u32 j = jb[i % BATCH];
         const bool q = valid && (j - L.seg_begin) < nQ;
-        u32 a = 0, c = 0, bits0 = 0, c1 = 1;
-        if (M >= 2 && valid) a = r0[j];
+        u32 a = ab[i % BATCH], c = 0, bits0 = 0, c1 = 1;
         if (M >= 3 && valid) c = r1[j];
         u32 e2 = 0;
         if (M >= 4 && valid) e2 = r2[j];

@@ -32,6 +32,7 @@ constexpr u32 TOP_STRIDE = 1u << TOP_MAX_BITS;       // per range: F of every to
 constexpr u32 TOP_NODES = TOP_STRIDE / 2;            // nodes of one level, at most
 constexpr int TOP_THREADS = GROUP_THREADS;
 constexpr u32 TOP_TILE = GROUP_CAP;                  // points per tile
+static_assert(TOP_TILE % TOP_THREADS == 0, "whole rounds of the tile load");
 
 // Shared memory of k_top: values (by the point's index in the tile),
 // handles (padded), node starts and zero counts, the range's F per node
@@ -93,6 +94,7 @@ __global__ __launch_bounds__(TOP_THREADS, 1) void k_top(const Inst* __restrict__
     Acc* ntot = reinterpret_cast<Acc*>(smem + SM::OFF_NTOT);
     __shared__ GScan<Acc> s_w[T / 32];
     __shared__ u32 s_slot;
+    __shared__ u32 s_qmask[T];  // per thread: which of its tile points are queries
     const int tid = threadIdx.x;
     const u32 total = __ldg(prange_off + k);
     for (;;) {
@@ -112,15 +114,45 @@ __global__ __launch_bounds__(TOP_THREADS, 1) void k_top(const Inst* __restrict__
             for (u32 a0 = R.start; a0 < R.end; a0 += TOP_TILE) {
                 const u32 n = min(R.end - a0, TOP_TILE);
                 __syncthreads();  // frun reset, or the previous tile's values written out
-                for (u32 i = tid; i < n; i += T) {
-                    const u32 v = pr0[a0 + i];
-                    const bool q = (v & QUERY_BIT) != 0u;
-                    xh[pidx(i)] = (((v & ~QUERY_BIT) >> tS) & lrmask) | ((q ? 1u : 0u) << nb) | (i << (nb + 1u));
-                    if (q) val[i] = grouped ? gacc[a0 + i] : Op::e();
-                    else if constexpr (Op::GATHER) val[i] = Op::from_w(pw[a0 + i]);
-                    else if constexpr (WT == 3) val[i] = Op::from_pay(0u);
-                    else val[i] = Op::from_pay((typename Op::Pay)pw[a0 + i]);
+                // thread t loads points t + k*T, half a tile's rounds at a time
+                // (their loads in flight together); s_qmask bit k: that point
+                // is a query
+                u32 qmask = 0;
+                constexpr int K = TOP_TILE / T, KH = K / 2;
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    u32 v[KH];
+#pragma unroll
+                    for (int kk = 0; kk < KH; ++kk) {
+                        const u32 i = (u32)tid + (u32)(half * KH + kk) * T;
+                        v[kk] = i < n ? pr0[a0 + i] : 0u;
+                    }
+                    Acc w[KH];
+#pragma unroll
+                    for (int kk = 0; kk < KH; ++kk) {
+                        const u32 i = (u32)tid + (u32)(half * KH + kk) * T;
+                        const bool q = (v[kk] & QUERY_BIT) != 0u;
+                        w[kk] = Op::e();
+                        if (i < n) {
+                            if (q) w[kk] = grouped ? gacc[a0 + i] : Op::e();
+                            else if constexpr (Op::GATHER) w[kk] = Op::from_w(pw[a0 + i]);
+                            else if constexpr (WT == 3) w[kk] = Op::from_pay(0u);
+                            else w[kk] = Op::from_pay((typename Op::Pay)pw[a0 + i]);
+                        }
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < KH; ++kk) {
+                        const u32 i = (u32)tid + (u32)(half * KH + kk) * T;
+                        if (i < n) {
+                            const bool q = (v[kk] & QUERY_BIT) != 0u;
+                            xh[pidx(i)] = (((v[kk] & ~QUERY_BIT) >> tS) & lrmask) | ((q ? 1u : 0u) << nb) |
+                                          (i << (nb + 1u));
+                            val[i] = w[kk];
+                            qmask |= (q ? 1u : 0u) << (half * KH + kk);
+                        }
+                    }
                 }
+                s_qmask[tid] = qmask;
                 const u32 itp = n <= 8u * T ? 8u : 12u;
                 const u32 npad = (n + itp - 1) / itp * itp;
                 // inert padding: data whose rank bits are all ones (see k_group)
@@ -129,8 +161,10 @@ __global__ __launch_bounds__(TOP_THREADS, 1) void k_top(const Inst* __restrict__
                 if (n <= 8u * T) group_levels<Op, 8, true>(npad, nb, tmask >> tS, val, xh, nstart, nzero, s_w, frun, ntot);
                 else group_levels<Op, 12, true>(npad, nb, tmask >> tS, val, xh, nstart, nzero, s_w, frun, ntot);
                 __syncthreads();
-                for (u32 i = tid; i < n; i += T)
-                    if (pr0[a0 + i] & QUERY_BIT) topv[a0 + i] = val[i];
+                const u32 qm = s_qmask[tid];
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk)
+                    if ((qm >> kk) & 1u) topv[a0 + (u32)tid + (u32)kk * T] = val[(u32)tid + (u32)kk * T];
             }
             __syncthreads();  // the last tile's node totals are in frun
             for (u32 h = tid; h < stride; h += T) agg[(u64)r * TOP_STRIDE + h] = frun[h];

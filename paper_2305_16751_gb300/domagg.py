@@ -198,7 +198,7 @@ def domagg_get_stats(h) -> dict:
 
 def domagg_set_tuning(h, name: str, value: int):
     """A tuning knob of the handle (see include/domagg.h): "group_bits",
-    "ranges_per_cta" or "blocks_per_sm"."""
+    "top_bits", "rank_windows", "ranges_per_cta" or "blocks_per_sm"."""
     _check(h, lib().domagg_set_tuning(h, name.encode(), int(value)))
 
 
