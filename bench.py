@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip fwd_bwd, m3, batch, e2e and the CPU baseline")
     ap.add_argument("--batch-k", type=int, default=4096, help="instances of the batch workload")
     ap.add_argument("--only-batch", action="store_true", help="print the batch line alone (e.g. --batch-k 4096)")
+    ap.add_argument("--only-m3", action="store_true", help="print the m = 3 line alone (e.g. --n3 524288)")
     ap.add_argument("--no-autotune", action="store_true", help="planned batch without the launch-shape autotuner")
     ap.add_argument("--variant", default="improved", choices=["improved", "wavelet"],
                     help="formulation of the timed m=2 step: the Sec. 5 record pipeline (default) or the "
@@ -325,6 +326,35 @@ def bench_variants(args, dev, stream, torch, domagg, workloads):
     return res
 
 
+def _pow2(n: int) -> str:
+    return f"2^{n.bit_length() - 1}" if n > 0 and n & (n - 1) == 0 else str(n)
+
+
+def bench_m3(args, dev, stream, torch, domagg, workloads):
+    """The m = 3 workload (Gaussian-mixture int32 coordinates, int64 sum):
+    forward steps, then one call with the library's per-kind timing; its
+    roofline is the records radix pass (64-bit and 32-bit key classes)."""
+    peak, peak_src = peaks()
+    h = domagg.handle(dev.index or 0)
+    p3 = workloads.gaussian_mixture_i32(n=args.n3)
+    D3, Q3, w3 = (torch.from_numpy(a).to(dev) for a in (p3.D, p3.Q, p3.w))
+    o3 = torch.empty(p3.Q.shape[0], dtype=torch.int64, device=dev)
+    t3 = timed_steps(lambda: domagg.forward(D3, Q3, w3, "sum", out=o3), max(3, args.steps // 2), 2, stream, torch)
+    m3_ms = statistics.mean(t3)
+    st3 = domagg.stats(dev.index or 0)
+    domagg.domagg_timing_enable(h, True)
+    domagg.domagg_timing_read(h)
+    domagg.forward(D3, Q3, w3, "sum", out=o3)
+    k3 = domagg.domagg_timing_read(h)
+    domagg.domagg_timing_enable(h, False)
+    return {"value": p3.Q.shape[0] / (m3_ms / 1e3), "unit": "queries/s", "ms_per_step": m3_ms,
+            "workload": f"m3_nD{_pow2(args.n3)}_nQ{_pow2(args.n3)}_gmm_i32coords_i64w_sum", "records": st3["n_records"],
+            "record_passes": st3["record_passes"], "phase_ms": {k: v["ms"] for k, v in k3.items()},
+            "roofline": kind_roofline(k3, "sort_records", peak, peak_src,
+                                      "k_onesweep (records radix pass, 64-bit and 32-bit key classes)"),
+            "step_model": step_model(2 * args.n3, st3["n_records"], args.n3, m3_ms, peak, m=3)}
+
+
 def bench_wavelet(args, D, Q, w, out, dev, stream, torch, domagg):
     """The level-wise formulation (variant "wavelet") on the headline
     workload: no flat-map records, two rank levels per pass over 16-byte
@@ -389,13 +419,16 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
-    if args.only_batch:
+    if args.only_batch or args.only_m3:
         import torch
         from paper_2305_16751_gb300 import domagg, workloads
         dev = torch.device("cuda", local)
         torch.cuda.set_device(dev)
-        line = bench_batch(args, dev, torch.cuda.current_stream(dev), torch, domagg, workloads)
-        print(json.dumps({"batch": line}), flush=True)
+        stream = torch.cuda.current_stream(dev)
+        if args.only_batch:
+            print(json.dumps({"batch": bench_batch(args, dev, stream, torch, domagg, workloads)}), flush=True)
+        else:
+            print(json.dumps({"m3": bench_m3(args, dev, stream, torch, domagg, workloads)}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -515,26 +548,7 @@ def main():
         line["fwd_bwd_wavelet"] = {"value": p.Q.shape[0] / (fbw_ms / 1e3), "unit": "queries/s",
                                    "ms_per_step": fbw_ms, "variant": "level-wise formulation"}
         del wg
-        # m = 3 workload
-        p3 = workloads.gaussian_mixture_i32(n=args.n3)
-        D3, Q3, w3 = (torch.from_numpy(a).to(dev) for a in (p3.D, p3.Q, p3.w))
-        o3 = torch.empty(p3.Q.shape[0], dtype=torch.int64, device=dev)
-        t3 = timed_steps(lambda: domagg.forward(D3, Q3, w3, "sum", out=o3), max(3, args.steps // 2), 2, stream,
-                         torch)
-        m3_ms = statistics.mean(t3)
-        st3 = domagg.stats(local)
-        # one more call with the library's per-kind timing
-        domagg.domagg_timing_enable(h, True)
-        domagg.forward(D3, Q3, w3, "sum", out=o3)
-        k3 = domagg.domagg_timing_read(h)
-        domagg.domagg_timing_enable(h, False)
-        line["m3"] = {"value": p3.Q.shape[0] / (m3_ms / 1e3), "unit": "queries/s", "ms_per_step": m3_ms,
-                      "workload": "m3_nD2^21_nQ2^21_gmm_i32coords_i64w_sum", "records": st3["n_records"],
-                      "record_passes": st3["record_passes"], "phase_ms": {k: v["ms"] for k, v in k3.items()},
-                      "roofline": kind_roofline(k3, "sort_records", peak, peak_src,
-                                                "k_onesweep (records radix pass, 64-bit and 32-bit key classes)"),
-                      "step_model": step_model(2 * args.n3, st3["n_records"], args.n3, m3_ms, peak, m=3)}
-        del D3, Q3, w3, o3
+        line["m3"] = bench_m3(args, dev, stream, torch, domagg, workloads)
         line["wavelet"] = bench_wavelet(args, D, Q, w, out, dev, stream, torch, domagg)
         line["variants"] = bench_variants(args, dev, stream, torch, domagg, workloads)
         line["batch"] = bench_batch(args, dev, stream, torch, domagg, workloads)

@@ -361,8 +361,7 @@ domagg_status domagg_forward_noalloc(int m, const void* d_coords, int64_t nD, co
  *                    those levels' records through HBM;
  *   "rank_windows"   0 .. 64 (default 0: about 48 MB of ranks each): windows
  *                    of destination indices the rank scatter is split into;
- *   "ranges_per_cta" 1 .. 64 (default 4): radix-sort ranges per resident CTA
- *                    (and ranges of tiles of the top levels per SM);
+ *   "ranges_per_cta" 1 .. 64 (default 4): radix-sort ranges per resident CTA;
  *   "blocks_per_sm"  1 .. 64 (default 16): flat-map / reduction blocks per SM.
  * The environment variable DOMAGG_TUNE="name=value,..." sets the defaults of
  * handles created afterwards.  Unknown names or values out of range return

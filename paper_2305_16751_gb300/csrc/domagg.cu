@@ -410,13 +410,15 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     // m = 2, the records path: the deep rank levels go through k_group
     const bool use_groups = M == 2 && h->group_bits > 0 && !(inst[0].flags & FLAG_WAVELET);
     // m = 2: the top rank levels per range of whole tiles (k_top): about
-    // ranges_per_cta ranges per SM over all points; prange_off[s] is instance
-    // s's first range; `multi` lists the instances of two or more ranges
+    // TOP_RANGES_PER_SM ranges per SM over all points (a function of the
+    // sizes alone: a planned run reuses the table its measuring run
+    // uploaded); prange_off[s] is instance s's first range; `multi` lists the
+    // instances of two or more ranges
     const bool use_top = M == 2 && h->top_bits > 0 && !(inst[0].flags & FLAG_WAVELET);
     u32 range_pts = TOP_TILE;
     std::vector<u32> prange_off(k + 1, 0), multi;
     if (use_top) {
-        const u64 want = (u64)std::max(1, h->ranges_per_cta) * (u64)std::max(h->sms, 1);
+        const u64 want = (u64)TOP_RANGES_PER_SM * (u64)std::max(h->sms, 1);
         const u64 tiles = (N + TOP_TILE - 1) / TOP_TILE;
         range_pts = (u32)std::min<u64>(TOP_TILE * std::max<u64>(1, (tiles + want - 1) / want), 1ull << 30);
         u64 nr = 0;
@@ -897,13 +899,13 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                               (double)NQ * sizeof(Acc) * (use_groups ? 2.0 : 1.0) +
                               (double)nranges * TOP_STRIDE * sizeof(Acc));
         k_top<Op, WT><<<(unsigned)h->sms, TOP_THREADS, tsm, stream>>>(d_inst, k, d_prange, d_pt_offs, range_pts, pr0,
-                                                                      (const W*)P[18], gacc, topv, top_agg, h->ctl,
-                                                                      li);
+                                                                      (const W*)P[18], gacc, topv, top_agg,
+                                                                      (u32)nranges, h->ctl, li);
         L.stop();
         if (!multi.empty()) {
             L.start(KIND_SMALL, 0.0);
-            k_top_carry<Op><<<dim3((unsigned)multi.size(), TOP_STRIDE / 32), 1024, 0, stream>>>(d_multi, d_prange,
-                                                                                               d_inst, top_agg);
+            k_top_carry<Op><<<dim3((unsigned)multi.size(), TOP_STRIDE / 32), 1024, 0, stream>>>(
+                d_multi, d_prange, d_inst, top_agg, (u32)nranges);
             L.stop();
         }
     }
@@ -1131,7 +1133,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             if (grid)
                 k_reduce_top<Op><<<grid, TOP_RED_THREADS, 0, stream>>>(
                     k, C.k0, d_prange, range_pts, d_chunk_off, d_pt_offs, pr0, pj, qchunk_base, d_pt_tiles,
-                    (const u32*)P[25], d_qsbase, d_inst, partial, (u32)C.Tq, gacc, topv, top_agg);
+                    (const u32*)P[25], d_qsbase, d_inst, partial, (u32)C.Tq, gacc, topv, top_agg, (u32)nranges);
             L.stop();
         } else if (qe > qb) {
             const unsigned grid = (unsigned)std::min<u64>((nchunk + 7) / 8, (u64)h->sms * L.blocks_per_sm);

@@ -30,6 +30,7 @@ namespace domagg {
 constexpr int TOP_MAX_BITS = 12;                     // top levels: at most 2^11 nodes each
 constexpr u32 TOP_STRIDE = 1u << TOP_MAX_BITS;       // per range: F of every top-level node (heap order)
 constexpr u32 TOP_NODES = TOP_STRIDE / 2;            // nodes of one level, at most
+constexpr int TOP_RANGES_PER_SM = 4;                  // ranges of tiles per SM over all points
 constexpr int TOP_THREADS = GROUP_THREADS;
 constexpr u32 TOP_TILE = GROUP_CAP;                  // points per tile
 static_assert(TOP_TILE % TOP_THREADS == 0, "whole rounds of the tile load");
@@ -72,7 +73,8 @@ __device__ __forceinline__ TopRange top_range(u32 r, const u32* prange_off, int 
 // query's F over the levels below gS).  Writes topv[x] (queries: F over
 // their partial results of the range's top levels and the levels below gS,
 // the unit if none) and agg[r][h] (F over the range's data of node h, heap
-// order).
+// order; rows r < nrows, the rows the caller reserved: a range outside them
+// is skipped).
 template <class Op, int WT>
 __global__ __launch_bounds__(TOP_THREADS, 1) void k_top(const Inst* __restrict__ inst, int k,
                                                         const u32* __restrict__ prange_off,
@@ -81,7 +83,8 @@ __global__ __launch_bounds__(TOP_THREADS, 1) void k_top(const Inst* __restrict__
                                                         const typename Op::W* __restrict__ pw,
                                                         const typename Op::Acc* __restrict__ gacc,
                                                         typename Op::Acc* __restrict__ topv,
-                                                        typename Op::Acc* __restrict__ agg, Ctl* ctl, int launch_idx) {
+                                                        typename Op::Acc* __restrict__ agg, u32 nrows, Ctl* ctl,
+                                                        int launch_idx) {
     typedef typename Op::Acc Acc;
     typedef TopSmem<Acc> SM;
     constexpr int T = TOP_THREADS;
@@ -102,6 +105,10 @@ __global__ __launch_bounds__(TOP_THREADS, 1) void k_top(const Inst* __restrict__
         __syncthreads();
         const u32 r = s_slot;
         if (r >= total) break;
+        if (!domagg_check(r < nrows, SITE_GROUP_OUT)) {  // never taken for a table of this call
+            __syncthreads();
+            continue;
+        }
         const TopRange R = top_range(r, prange_off, k, pt_offs, range_pts);
         const Inst& I = inst[R.s];
         const u32 tmask = I.topmask, tS = I.tS, b0 = I.b[0];
@@ -182,7 +189,8 @@ __global__ __launch_bounds__(TOP_THREADS, 1) void k_top(const Inst* __restrict__
 // fixed order, so float-float sums repeat exactly.
 template <class Op>
 __global__ __launch_bounds__(1024) void k_top_carry(const u32* __restrict__ multi, const u32* __restrict__ prange_off,
-                                                   const Inst* __restrict__ inst, typename Op::Acc* __restrict__ agg) {
+                                                   const Inst* __restrict__ inst, typename Op::Acc* __restrict__ agg,
+                                                   u32 nrows) {
     typedef typename Op::Acc Acc;
     __shared__ Acc s_sum[32][33];
     const int s = (int)__ldg(multi + blockIdx.x);
@@ -193,7 +201,9 @@ __global__ __launch_bounds__(1024) void k_top_carry(const u32* __restrict__ mult
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const u32 h = blockIdx.y * 32u + (u32)lane;
     const bool on = h < stride;
-    const u32 r0 = __ldg(prange_off + s), n = __ldg(prange_off + s + 1) - r0, per = (n + 31) / 32;
+    const u32 r0 = __ldg(prange_off + s), r1 = __ldg(prange_off + s + 1);
+    if (!domagg_check(r1 <= nrows && r0 <= r1, SITE_GROUP_OUT)) return;  // never taken for a table of this call
+    const u32 n = r1 - r0, per = (n + 31) / 32;
     const u32 a = r0 + min(n, (u32)warp * per), b = r0 + min(n, (u32)(warp + 1) * per);
     Acc sum = Op::e();
     for (u32 r = a; r < b; r += 8) {
@@ -238,7 +248,7 @@ __global__ __launch_bounds__(TOP_RED_THREADS) void k_reduce_top(int k, int k0, c
                                                     const typename Op::Part* __restrict__ partial, u32 n_partial,
                                                     const typename Op::Acc* __restrict__ gacc,
                                                     const typename Op::Acc* __restrict__ topv,
-                                                    const typename Op::Acc* __restrict__ carry) {
+                                                    const typename Op::Acc* __restrict__ carry, u32 nrows) {
     typedef typename Op::Acc Acc;
     __shared__ Acc s_carry[TOP_STRIDE];
     constexpr u32 WARPS = TOP_RED_THREADS / 32;
@@ -251,7 +261,7 @@ __global__ __launch_bounds__(TOP_RED_THREADS) void k_reduce_top(int k, int k0, c
     const int s = R.s;
     const Inst& I = inst[s];
     const u32 tmask = I.topmask, b0 = I.b[0];
-    const bool carried = tmask != 0u && R.rr > 0u;
+    const bool carried = tmask != 0u && R.rr > 0u && domagg_check(r < nrows, SITE_REDUCE);
     if (carried) {
         const u32 stride = 1u << (b0 - I.tS);
         for (u32 h = threadIdx.x; h < stride; h += blockDim.x) s_carry[h] = carry[(u64)r * TOP_STRIDE + h];

@@ -155,6 +155,28 @@ def test_plan_autotune_keeps_results():
         plan.close()
 
 
+def test_plan_autotune_with_ranges_of_top_levels():
+    """m = 2 instances large enough that the top levels run in hundreds of
+    ranges of tiles (8.5e6 points in 690 tiles): the range table, uploaded
+    by the plan's measuring run, does not depend on the launch shapes the
+    autotuner tries, and runs after it give the unplanned batch's integer
+    sums."""
+    rng = np.random.default_rng(905)
+    probs = [workloads.random_small(rng, 2, n, n, 1 << 22, "i32", "i64") for n in (2_500_000, 1_700_000, 40_000)]
+    dev = [(to_dev(D), to_dev(Q), to_dev(w)) for D, Q, w in probs]
+    want = domagg.batch(dev, "sum")
+    plan = domagg.BatchPlan(dev, "sum", headroom=0.2)
+    try:
+        plan.autotune()
+        for _ in range(2):
+            plan.run()
+            plan.status()
+            for o, wv in zip(plan.outs, want):
+                assert torch().equal(o, wv)
+    finally:
+        plan.close()
+
+
 def test_plan_with_both_key_classes_and_m4():
     """Planned runs with m = 3 instances large enough that some levels need
     64-bit node keys (the rest 32-bit), and m = 4 instances, replayed from a
