@@ -127,7 +127,7 @@ class ClockSampler:
 
 
 def profiled_traffic(bytes_per_launch: float, source: str = "k_radix.cuh",
-                     profile: str = "k_onesweep_points_m2_n2e22.md"):
+                     profile: str = "k_onesweep_points_m2_n2e24.md"):
     """DRAM bytes of one launch of the dominant HBM-bound kernel (a radix
     pass, or a level-wise pass): the committed ncu summary's measured DRAM
     bytes per algorithmic byte, times this run's algorithmic bytes per
