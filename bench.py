@@ -261,6 +261,21 @@ def bench_batch(args, dev, stream, torch, domagg, workloads):
     npts = sum(p.Q.shape[0] + p.D.shape[0] for p in probs)
     tb = timed_steps(lambda: domagg.batch(inst, "sum"), 2, 1, stream, torch)
     b_ms = statistics.mean(tb)
+    # one more call with the library's per-kind timing, and each half of the
+    # batch (the m = 2 and the m = 3 instances) on its own
+    h = domagg.handle(dev.index or 0)
+    domagg.domagg_timing_enable(h, True)
+    domagg.domagg_timing_read(h)
+    domagg.batch(inst, "sum")
+    kb = domagg.domagg_timing_read(h)
+    domagg.domagg_timing_enable(h, False)
+    by_m = {}
+    for m in (2, 3):
+        part = [t for t in inst if t[0].shape[1] == m]
+        if part:
+            by_m[f"m{m}_instances"] = {"instances": len(part), "points": sum(t[0].shape[0] + t[1].shape[0] for t in part),
+                                       "ms": statistics.mean(timed_steps(lambda: domagg.batch(part, "sum"), 2, 1,
+                                                                         stream, torch))}
 
     def loop():
         for D, Q, w in inst:
@@ -286,6 +301,7 @@ def bench_batch(args, dev, stream, torch, domagg, workloads):
             "points": npts, "queries": nq, "per_instance_loop": {"value": nq / (l_ms / 1e3), "ms_per_step": l_ms},
             "graph_replay": {"value": nq / (g_ms / 1e3), "ms_per_step": g_ms, "plan_workspace_gb": plan_gb,
                              "autotuned_ms": tuned_ms},
+            "phase_ms": {k: round(v["ms"], 3) for k, v in kb.items() if v["ms"] > 0}, "by_m": by_m,
             "workload": f"{len(probs)} instances, m in {{2,3}} 50/50, |D|=|Q| log-uniform [256, 2^18], "
                         "int32 coords U[0,2^31), f32 w, sum"}
 

@@ -286,29 +286,32 @@ __global__ __launch_bounds__(TOP_RED_THREADS) void k_reduce_top(int k, int k0, c
             }
         }
         if (__ballot_sync(0xffffffffu, q) == 0u) continue;
-        const u32 rec = bits0 & I.lvmask;
-        if ((u32)lane < b0)
-            s_base[warp][lane] = __ldg(qseg_base + (u64)(s - k0) * LMAX + lane) +
-                                 __ldg(qchunk_base + (u64)c * LMAX + lane) +
-                                 __ldg(tile_excl + (u64)(__ldg(pt_tiles + s) + (c - c0) / CS_CHUNKS) * CS_COUNTERS +
-                                       LMAX + lane);
-        s_mask[warp][lane] = warp_transpose32(rec, (u32)lane);  // lanes of level `lane`
-        __syncwarp();
         Acc acc = Op::e();
         if (q) acc = tmask ? topv[p] : (I.gS ? gacc[p] : Op::e());
-        u32 rem = rec;
+        if (I.lvmask) {  // levels whose records went through HBM: their partials
+            const u32 rec = bits0 & I.lvmask;
+            if ((u32)lane < b0)
+                s_base[warp][lane] =
+                    __ldg(qseg_base + (u64)(s - k0) * LMAX + lane) + __ldg(qchunk_base + (u64)c * LMAX + lane) +
+                    __ldg(tile_excl + (u64)(__ldg(pt_tiles + s) + (c - c0) / CS_CHUNKS) * CS_COUNTERS + LMAX + lane);
+            s_mask[warp][lane] = warp_transpose32(rec, (u32)lane);  // lanes of level `lane`
+            __syncwarp();
+            u32 rem = rec;
 #pragma unroll 4
-        while (rem) {
-            const u32 lv = __ffs(rem) - 1;
-            rem &= rem - 1;
-            const u32 slot = s_base[warp][lv] + (u32)__popc(s_mask[warp][lv] & lt);
-            if (domagg_check(slot < n_partial, SITE_REDUCE)) acc = Op::F(acc, Op::from_part(partial[slot]));
+            while (rem) {
+                const u32 lv = __ffs(rem) - 1;
+                rem &= rem - 1;
+                const u32 slot = s_base[warp][lv] + (u32)__popc(s_mask[warp][lv] & lt);
+                if (domagg_check(slot < n_partial, SITE_REDUCE)) acc = Op::F(acc, Op::from_part(partial[slot]));
+            }
         }
-        if (q && carried) {
+        if (q && carried) {  // the carries of its top-level nodes (a short sum: combined without renormalising)
+            Acc cs = Op::e();
             for (u32 top = bits0 & tmask; top; top &= top - 1) {
                 const u32 lv = __ffs(top) - 1;
-                acc = Op::F(acc, s_carry[(1u << (b0 - 1u - lv)) - 1u + (a >> (lv + 1u))]);
+                cs = Op::Fc(cs, s_carry[(1u << (b0 - 1u - lv)) - 1u + (a >> (lv + 1u))]);
             }
+            acc = Op::F(acc, cs);
         }
         if (q) {
             bool done = false;
