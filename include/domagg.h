@@ -154,6 +154,17 @@ domagg_status domagg_forward_shard(domagg_handle h, int shard, int nshards, int 
                                    const void* q_coords, int64_t nQ, domagg_dtype coord_dtype, const void* d_weights,
                                    domagg_dtype weight_dtype, domagg_op op, void* out, float* out_lo, void* stream);
 
+/* The two-sample distance of empirical CDFs (Sec. 1.2 names ECDFs as an
+ * application of dominance counting): *d_out = max over z < nz of
+ * |count_x[z] / nx - count_y[z] / ny|, with count_x, count_y (device int64
+ * [nz], e.g. the COUNT outputs of domagg_forward_ex with every coordinate
+ * non-strict and queries X u Y) the points of the samples (sizes nx, ny > 0)
+ * dominated by each z.  d_out: one device double, overwritten (0 when
+ * nz = 0).  Asynchronous on `stream`; DOMAGG_ERR_INVALID_ARG for null
+ * pointers or non-positive sample sizes. */
+domagg_status domagg_ecdf_distance(domagg_handle h, const int64_t* count_x, const int64_t* count_y, int64_t nz,
+                                   int64_t nx, int64_t ny, double* d_out, void* stream);
+
 /* out[q] = F over parts[s][q], s < nparts (1..64): joins the outputs of
  * domagg_forward_shard.  parts and parts_lo are HOST arrays of nparts device
  * pointers; parts_lo (float32 SUM, may be NULL) holds the low halves.  The

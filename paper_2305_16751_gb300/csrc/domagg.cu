@@ -1448,6 +1448,43 @@ domagg_status domagg_combine(domagg_handle h, domagg_op op, domagg_dtype weight_
     return e == cudaSuccess ? DOMAGG_OK : cuda_fail(h, e, "combine");
 }
 
+// max over z of |cx[z] * inv_x - cy[z] * inv_y|: a block-wide max, then an
+// atomic max on the bits of the (non-negative) double, which order as
+// integers.
+static __global__ __launch_bounds__(256) void k_ecdf_max(const long long* __restrict__ cx,
+                                                        const long long* __restrict__ cy, u64 nz, double inv_x,
+                                                        double inv_y, unsigned long long* out_bits) {
+    __shared__ double s_max[8];
+    double m = 0.0;
+    for (u64 z = (u64)blockIdx.x * blockDim.x + threadIdx.x; z < nz; z += (u64)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(__dsub_rn(__dmul_rn((double)cx[z], inv_x), __dmul_rn((double)cy[z], inv_y))));
+    for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_max[w]);
+        atomicMax(out_bits, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+domagg_status domagg_ecdf_distance(domagg_handle h, const int64_t* count_x, const int64_t* count_y, int64_t nz,
+                                   int64_t nx, int64_t ny, double* d_out, void* stream) {
+    if (!h) return DOMAGG_ERR_INVALID_ARG;
+    if (!d_out || nz < 0 || nx <= 0 || ny <= 0 || (nz > 0 && (!count_x || !count_y)))
+        return fail(h, DOMAGG_ERR_INVALID_ARG, "null pointer or non-positive sample size");
+    cudaSetDevice(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(d_out, 0, sizeof(double), s);
+    if (nz > 0) {
+        const unsigned grid = (unsigned)std::min<int64_t>((nz + 255) / 256, (int64_t)h->sms * 8);
+        k_ecdf_max<<<grid, 256, 0, s>>>(reinterpret_cast<const long long*>(count_x),
+                                        reinterpret_cast<const long long*>(count_y), (u64)nz, 1.0 / (double)nx,
+                                        1.0 / (double)ny, reinterpret_cast<unsigned long long*>(d_out));
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DOMAGG_OK : cuda_fail(h, e, "ecdf distance");
+}
+
 domagg_status domagg_forward_host(domagg_handle h, int m, const void* d_coords, int64_t nD, const void* q_coords,
                                   int64_t nQ, domagg_dtype coord_dtype, const void* d_weights,
                                   domagg_dtype weight_dtype, domagg_op op, void* out, void* stream) {

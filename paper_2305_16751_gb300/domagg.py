@@ -60,6 +60,7 @@ SIGNATURES = {
     "domagg_forward_shard": ([_vp, _int, _int, _int, _vp, _i64, _vp, _i64, _int, _vp, _int, _int, _vp, _vp, _vp],
                              _int),
     "domagg_combine": ([_vp, _int, _int, _int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i64, _vp, _vp], _int),
+    "domagg_ecdf_distance": ([_vp, _vp, _vp, _i64, _i64, _i64, _vp, _vp], _int),
     "domagg_backward": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _vp, _vp], _int),
     "domagg_backward_ex": ([_vp, _int, _vp, _i64, _vp, _i64, _int, _vp, _vp, ctypes.c_uint32, _int, _vp], _int),
     "domagg_batch": ([_vp, _int, ctypes.POINTER(domagg_instance), _int, _int, _int, _vp], _int),
@@ -338,13 +339,18 @@ def combine(parts, parts_lo, op: str, weight_dtype=None, out=None):
 def ks_statistic(X, Y) -> float:
     """Two-sample statistic max over z in X u Y of |F_X(z) - F_Y(z)|, with F
     the empirical CDF (the fraction of a sample <= z in every coordinate):
-    two dominance counts with every coordinate non-strict, on the GPU."""
+    two dominance counts with every coordinate non-strict and their largest
+    difference (domagg_ecdf_distance), on the GPU."""
     torch = _torch()
     Z = torch.cat([X, Y]).contiguous()
     full = (1 << X.shape[1]) - 1
-    fx = forward(X, Z, None, "count", nonstrict=full).double() / X.shape[0]
-    fy = forward(Y, Z, None, "count", nonstrict=full).double() / Y.shape[0]
-    return float((fx - fy).abs().max())
+    cx = forward(X, Z, None, "count", nonstrict=full)
+    cy = forward(Y, Z, None, "count", nonstrict=full)
+    out = torch.empty(1, dtype=torch.float64, device=Z.device)
+    h = handle(Z.device.index or 0)
+    _check(h, lib().domagg_ecdf_distance(h, _ptr(cx), _ptr(cy), Z.shape[0], X.shape[0], Y.shape[0], _ptr(out),
+                                         _stream(Z.device)))
+    return float(out.item())
 
 
 def forward_host(D, Q, w=None, op: str = "sum", device: int = 0):

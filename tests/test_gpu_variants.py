@@ -107,6 +107,23 @@ def test_ecdf_counts_and_two_sample_statistic():
     assert abs(ks - np.abs(fx - fy).max()) < 1e-12
 
 
+def test_ecdf_distance_entry_point():
+    """domagg_ecdf_distance on given counts: the largest |cx/nx - cy/ny|
+    (a hand case, then no points at all), and its argument checks."""
+    t = torch()
+    h = domagg.handle(0)
+    cx = t.tensor([0, 3, 5, 10], dtype=t.int64, device="cuda")
+    cy = t.tensor([1, 1, 4, 4], dtype=t.int64, device="cuda")
+    out = t.full((1,), -1.0, dtype=t.float64, device="cuda")
+    st = domagg.lib().domagg_ecdf_distance(h, domagg._ptr(cx), domagg._ptr(cy), 4, 10, 4, domagg._ptr(out), None)
+    assert st == 0
+    assert abs(out.item() - max(abs(a / 10 - b / 4) for a, b in zip([0, 3, 5, 10], [1, 1, 4, 4]))) < 1e-15
+    st = domagg.lib().domagg_ecdf_distance(h, None, None, 0, 10, 4, domagg._ptr(out), None)
+    assert st == 0 and out.item() == 0.0
+    assert domagg.lib().domagg_ecdf_distance(h, domagg._ptr(cx), domagg._ptr(cy), 4, 0, 4, domagg._ptr(out), None) == 1
+    assert domagg.lib().domagg_ecdf_distance(h, domagg._ptr(cx), None, 4, 10, 4, domagg._ptr(out), None) == 1
+
+
 def test_variant_arguments_are_checked():
     D = np.zeros((4, 4), np.int32)
     with pytest.raises(domagg.DomaggError) as e:
