@@ -620,7 +620,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                                                                                           d_pt_tiles, k, C.tile_cnt);
         L.stop();
         L.start(KIND_SMALL, 0.0);
-        k_tile_exscan<<<(unsigned)((k + 7) / 8), 256, 0, C.stream>>>(d_pt_tiles, k, C.tile_cnt);
+        k_tile_exscan<<<(unsigned)k, 1024, 0, C.stream>>>(d_pt_tiles, k, C.tile_cnt);
         L.stop();
         // the rank scatter in windows of destinations (each about 48 MB of
         // ranks, so the L2 holds a window while its sectors fill)
@@ -687,7 +687,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             qchunk_base, (u32*)P[25], use_groups ? gkey[0] : nullptr, use_groups ? gval[0] : nullptr);
         L.stop();
         L.start(KIND_SMALL, 0.0);
-        k_tile_exscan_counters<<<(unsigned)(((u64)k * CS_COUNTERS + 7) / 8), 256, 0, stream>>>(
+        k_tile_exscan_counters<<<dim3((unsigned)k, CS_COUNTERS / 32), 1024, 0, stream>>>(
             d_pt_tiles, k, (u32*)P[25], lvl_tot, qlvl_tot, h->ctl);
         L.stop();
     }

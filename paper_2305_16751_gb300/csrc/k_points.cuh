@@ -254,13 +254,21 @@ __device__ __forceinline__ u64 warp_exscan_column(u32* __restrict__ c, u64 strid
 }
 
 // Exclusive scan of per-tile counts within every segment (in place), one
-// warp per segment.
-static __global__ __launch_bounds__(256) void k_tile_exscan(const u32* __restrict__ tile_off, int nseg,
-                                                           u32* __restrict__ cnt) {
-    const int seg = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+// block per segment: its 32 warps scan 32 consecutive slices of the tiles,
+// then add the slices before them.
+static __global__ __launch_bounds__(1024) void k_tile_exscan(const u32* __restrict__ tile_off, int nseg,
+                                                            u32* __restrict__ cnt) {
+    __shared__ u64 s_sum[32];
+    const int seg = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (seg >= nseg) return;
-    const u32 a = __ldg(tile_off + seg), b = __ldg(tile_off + seg + 1);
-    warp_exscan_column(cnt + a, 1, b - a, lane);
+    const u32 t0 = __ldg(tile_off + seg), n = __ldg(tile_off + seg + 1) - t0, per = (n + 31) / 32;
+    const u32 a = min(n, (u32)warp * per), b = min(n, (u32)(warp + 1) * per);
+    const u64 tot = warp_exscan_column(cnt + t0 + a, 1, b - a, lane);
+    if (lane == 0) s_sum[warp] = tot;
+    __syncthreads();
+    u64 off = 0;
+    for (int w = 0; w < warp; ++w) off += s_sum[w];
+    for (u32 t = a + (u32)lane; t < b; t += 32) cnt[t0 + t] += (u32)off;
 }
 
 template <int THREADS, int ITEMS>
@@ -511,22 +519,46 @@ __global__ __launch_bounds__(256) void k_count_scan(
 }
 
 // Per instance and counter, the exclusive scan of the tiles' totals (in
-// place), and the instance's totals per level (lvl_tot, qlvl_tot).  One warp
-// per (instance, counter).  A total that does not fit 32 bits raises
-// ERR_OVERFLOW.
-static __global__ __launch_bounds__(256) void k_tile_exscan_counters(const u32* __restrict__ tile_off, int nseg,
-                                                                    u32* __restrict__ cnt, u32* __restrict__ lvl_tot,
-                                                                    u32* __restrict__ qlvl_tot, Ctl* ctl) {
-    const u64 gw = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gw >= (u64)nseg * CS_COUNTERS) return;
-    const int seg = (int)(gw / CS_COUNTERS), c = (int)(gw % CS_COUNTERS);
-    const u32 a = __ldg(tile_off + seg), b = __ldg(tile_off + seg + 1);
-    const u64 carry = warp_exscan_column(cnt + (u64)a * CS_COUNTERS + c, CS_COUNTERS, b - a, lane);
-    if (lane == 0) {
-        if (carry >> 32) atomicOr(&ctl->error, ERR_OVERFLOW);
-        if (c < LMAX) lvl_tot[(u64)seg * LMAX + c] = (u32)carry;
-        else qlvl_tot[(u64)seg * LMAX + (c - LMAX)] = (u32)carry;
+// place), and the instance's totals per level (lvl_tot, qlvl_tot).  Grid
+// (instance, CS_COUNTERS / 32): the 32 warps of a block split the instance's
+// tiles into 32 consecutive slices, lane = counter (so a warp's loads are a
+// tile's 32 consecutive counters): slice sums, their exclusive combination
+// in shared memory, then the running prefixes.  A total that does not fit 32
+// bits raises ERR_OVERFLOW.
+static __global__ __launch_bounds__(1024) void k_tile_exscan_counters(const u32* __restrict__ tile_off, int nseg,
+                                                                     u32* __restrict__ cnt, u32* __restrict__ lvl_tot,
+                                                                     u32* __restrict__ qlvl_tot, Ctl* ctl) {
+    __shared__ u64 s_sum[32][33];
+    const int seg = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = (int)blockIdx.y * 32 + lane;
+    const u32 t0 = __ldg(tile_off + seg), n = __ldg(tile_off + seg + 1) - t0, per = (n + 31) / 32;
+    const u32 a = t0 + min(n, (u32)warp * per), b = t0 + min(n, (u32)(warp + 1) * per);
+    u64 sum = 0;
+    for (u32 t = a; t < b; t += 16) {
+        u32 v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = t + i < b ? cnt[(u64)(t + i) * CS_COUNTERS + c] : 0u;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) sum += v[i];
+    }
+    s_sum[warp][lane] = sum;
+    __syncthreads();
+    u64 run = 0;
+    for (int w = 0; w < warp; ++w) run += s_sum[w][lane];
+    for (u32 t = a; t < b; t += 16) {
+        u32 v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = t + i < b ? cnt[(u64)(t + i) * CS_COUNTERS + c] : 0u;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if (t + i < b) cnt[(u64)(t + i) * CS_COUNTERS + c] = (u32)run;
+            run += v[i];
+        }
+    }
+    if (warp == 31) {  // the last slice ends at the instance's last tile: run is the total
+        if (run >> 32) atomicOr(&ctl->error, ERR_OVERFLOW);
+        if (c < LMAX) lvl_tot[(u64)seg * LMAX + c] = (u32)run;
+        else qlvl_tot[(u64)seg * LMAX + (c - LMAX)] = (u32)run;
     }
 }
 
