@@ -496,7 +496,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         P[55] = c.take<u32>(use_top ? std::max<size_t>(multi.size(), 1) : 0);
         // m = 2 groups: per query (by position in the order of the last
         // coordinate) F over the levels below gS
-        P[56] = c.take<typename Op::Acc>(grp ? N : 0);
+        P[56] = c.take<typename Op::Part>(grp ? N : 0);
     };
     void* P[57];
     {
@@ -520,7 +520,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     u32 *rstart = (u32*)P[45], *gkey[2] = {(u32*)P[46], (u32*)P[47]}, *gbits = (u32*)P[50], *gslot = (u32*)P[51];
     u64* gval[2] = {(u64*)P[48], (u64*)P[49]};
     typename Op::Acc* topv = (typename Op::Acc*)P[52];
-    typename Op::Acc* gacc = (typename Op::Acc*)P[56];
+    typename Op::Part* gacc = (typename Op::Part*)P[56];
     typename Op::Acc* top_agg = (typename Op::Acc*)P[53];
     u32 *d_prange = (u32*)P[54], *d_multi = (u32*)P[55];
 
@@ -883,7 +883,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         constexpr size_t gsm = group_smem_bytes<Acc>();
         if (!L.frozen) cudaFuncSetAttribute(k_group<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
         const int li = L.lookback_index();
-        L.start(KIND_GROUP, (double)N * 8.0 + (double)NQ * sizeof(typename Op::Acc));
+        L.start(KIND_GROUP, (double)N * 8.0 + (double)NQ * sizeof(Part));
         k_group<Op><<<(unsigned)h->sms, GROUP_THREADS, gsm, stream>>>(d_inst, k, gslot, rstart, gval[0], gval[1],
                                                                       (const W*)P[18], gacc, h->ctl, li);
         L.stop();
@@ -896,7 +896,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         if (!L.frozen) cudaFuncSetAttribute(k_top<Op, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
         const int li = L.lookback_index();
         L.start(KIND_TOP, (double)N * (4.0 + (WT == 3 ? 0.0 : sizeof(W))) +
-                              (double)NQ * sizeof(Acc) * (use_groups ? 2.0 : 1.0) +
+                              (double)NQ * (sizeof(Acc) + (use_groups ? sizeof(Part) : 0.0)) +
                               (double)nranges * TOP_STRIDE * sizeof(Acc));
         k_top<Op, WT><<<(unsigned)h->sms, TOP_THREADS, tsm, stream>>>(d_inst, k, d_prange, d_pt_offs, range_pts, pr0,
                                                                       (const W*)P[18], gacc, topv, top_agg,

@@ -370,15 +370,16 @@ __device__ __forceinline__ void group_levels(u32 n, u32 nb, u32 scan_mask, typen
 // passes): (rank | QUERY_BIT) << 32 | payload, the payload being a query's
 // position x in the order of the last coordinate, a datum's weight bits, or
 // (8-byte weights) the datum's position in pw.  Writes gacc[x] = F over the
-// query's partial results of the levels below gS (read in that order by
-// k_top and the per-query reduction).
+// query's partial results of the levels below gS, as a partial (rounded once,
+// like a level's partial; read in that order by k_top and the per-query
+// reduction).
 template <class Op>
 __global__ __launch_bounds__(GROUP_THREADS, 1) void k_group(const Inst* __restrict__ inst, int k,
                                                             const u32* __restrict__ gslot_off,
                                                             const u32* __restrict__ rstart, const u64* __restrict__ gv0,
                                                             const u64* __restrict__ gv1,
                                                             const typename Op::W* __restrict__ pw,
-                                                            typename Op::Acc* __restrict__ gacc, Ctl* ctl,
+                                                            typename Op::Part* __restrict__ gacc, Ctl* ctl,
                                                             int launch_idx) {
     typedef typename Op::Acc Acc;
     typedef GScan<Acc> E;
@@ -438,7 +439,7 @@ __global__ __launch_bounds__(GROUP_THREADS, 1) void k_group(const Inst* __restri
             const u64 v = gv[i];
             if ((u32)(v >> 32) & QUERY_BIT) {
                 const u32 x = (u32)v;
-                if (domagg_check(x - I.pt_off < I.nD + I.nQ, SITE_GROUP_OUT)) gacc[x] = val[i];
+                if (domagg_check(x - I.pt_off < I.nD + I.nQ, SITE_GROUP_OUT)) gacc[x] = Op::to_part(val[i]);
             }
         }
         __syncthreads();  // shared memory is free for the next group

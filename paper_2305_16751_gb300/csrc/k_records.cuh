@@ -676,9 +676,9 @@ __global__ __launch_bounds__(THREADS) void k_segscan_lb(const K* __restrict__ ke
 // a[0 .. n) = e: a shard's group parts start at the unit (k_group writes
 // only its own groups' queries).
 template <class Op>
-__global__ void k_fill_e(typename Op::Acc* __restrict__ a, u32 n) {
+__global__ void k_fill_e(typename Op::Part* __restrict__ a, u32 n) {
     const u32 g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < n) a[g] = Op::e();
+    if (g < n) a[g] = Op::to_part(Op::e());
 }
 
 // out[q] = F over the shards' partial outputs (float32 sums: the shards'
@@ -719,7 +719,7 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
                                                 const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/,
                                                 const Inst* __restrict__ inst,
                                                 const typename Op::Part* __restrict__ partial, u32 n_partial,
-                                                const typename Op::Acc* __restrict__ gacc) {
+                                                const typename Op::Part* __restrict__ gacc) {
     typedef typename Op::Part Part;
     __shared__ u32 s_mask[8][LMAX];  // per warp: query lanes holding a record of level lv
     __shared__ u32 s_base[8][LMAX];  // per warp: first partial slot of level lv in this chunk
@@ -765,7 +765,7 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
         __syncwarp();
         typename Op::Acc acc = Op::e();
         // m = 2 with groups: F over the levels below gS, by position
-        if (M == 2 && q && I.gS) acc = gacc[p];
+        if (M == 2 && q && I.gS) acc = Op::from_part(gacc[p]);
         if (M <= 2) {
             // one partial per query and level, at the level's base plus the
             // query lanes of that level before this one; each lane walks only

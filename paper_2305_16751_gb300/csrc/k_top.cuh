@@ -81,7 +81,7 @@ __global__ __launch_bounds__(TOP_THREADS, 1) void k_top(const Inst* __restrict__
                                                         const u32* __restrict__ pt_offs, u32 range_pts,
                                                         const u32* __restrict__ pr0,
                                                         const typename Op::W* __restrict__ pw,
-                                                        const typename Op::Acc* __restrict__ gacc,
+                                                        const typename Op::Part* __restrict__ gacc,
                                                         typename Op::Acc* __restrict__ topv,
                                                         typename Op::Acc* __restrict__ agg, u32 nrows, Ctl* ctl,
                                                         int launch_idx) {
@@ -141,7 +141,7 @@ __global__ __launch_bounds__(TOP_THREADS, 1) void k_top(const Inst* __restrict__
                         const bool q = (v[kk] & QUERY_BIT) != 0u;
                         w[kk] = Op::e();
                         if (i < n) {
-                            if (q) w[kk] = grouped ? gacc[a0 + i] : Op::e();
+                            if (q) w[kk] = grouped ? Op::from_part(gacc[a0 + i]) : Op::e();
                             else if constexpr (Op::GATHER) w[kk] = Op::from_w(pw[a0 + i]);
                             else if constexpr (WT == 3) w[kk] = Op::from_pay(0u);
                             else w[kk] = Op::from_pay((typename Op::Pay)pw[a0 + i]);
@@ -246,7 +246,7 @@ __global__ __launch_bounds__(TOP_RED_THREADS) void k_reduce_top(int k, int k0, c
                                                     const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/,
                                                     const Inst* __restrict__ inst,
                                                     const typename Op::Part* __restrict__ partial, u32 n_partial,
-                                                    const typename Op::Acc* __restrict__ gacc,
+                                                    const typename Op::Part* __restrict__ gacc,
                                                     const typename Op::Acc* __restrict__ topv,
                                                     const typename Op::Acc* __restrict__ carry, u32 nrows) {
     typedef typename Op::Acc Acc;
@@ -287,7 +287,7 @@ __global__ __launch_bounds__(TOP_RED_THREADS) void k_reduce_top(int k, int k0, c
         }
         if (__ballot_sync(0xffffffffu, q) == 0u) continue;
         Acc acc = Op::e();
-        if (q) acc = tmask ? topv[p] : (I.gS ? gacc[p] : Op::e());
+        if (q) acc = tmask ? topv[p] : (I.gS ? Op::from_part(gacc[p]) : Op::e());
         if (I.lvmask) {  // levels whose records went through HBM: their partials
             const u32 rec = bits0 & I.lvmask;
             if ((u32)lane < b0)
