@@ -13,9 +13,10 @@
 // down to 0, forms the level's records there, finishes their sort on the
 // remaining node-key bit and runs the segmented scan of F over them
 // (instruction 6m+3); each query keeps F over its partial results of these
-// levels (what instructions 6m+4, 6m+5 collect) and writes it to its output.
-// The levels lv >= gS go through the records in HBM as before and the
-// per-query reduction adds their partials to that output.
+// levels (what instructions 6m+4, 6m+5 collect) and writes it, as one
+// partial, at its position in the order of the last coordinate.  The levels
+// lv >= gS go to k_top (per tile of points, k_top.cuh) or through the
+// records in HBM, and the per-query reduction joins the parts.
 //
 // Shared-memory sort, level by level.  The group's points start in the
 // order of the last coordinate, which is the order of the level gS-1
