@@ -302,8 +302,9 @@ typedef struct {
     int32_t record_key_bits; /* bits of the node key sorted by the record sort */
     int32_t record_passes;   /* radix passes over the records */
     int64_t workspace_bytes; /* device workspace currently held by the handle */
-    int64_t n_records_shared; /* m = 2: records of the deep rank levels, formed, sorted and
-                                 scanned in shared memory (the rest of n_records go through HBM) */
+    int64_t n_records_shared; /* m = 2, 3: records formed, sorted and scanned in shared memory
+                                 (the groups' and the top-level tiles'); the rest of n_records go
+                                 through HBM (for a shard: also those left to the other shards) */
 } domagg_stats;
 
 domagg_status domagg_get_stats(domagg_handle h, domagg_stats* out);
@@ -359,11 +360,13 @@ domagg_status domagg_forward_noalloc(int m, const void* d_coords, int64_t nD, co
 
 /* Tuning knobs of a handle (the paper has no counterpart); every setting
  * computes the same results:
- *   "group_bits"     0 .. 13 (default 13): for m = 2, the rank levels below
- *                    gS <= group_bits (nodes of at most 2^gS ranks) are
- *                    formed, sorted and scanned per group of 2^gS ranks in
- *                    shared memory; 0 sends those levels' records through
- *                    HBM;
+ *   "group_bits"     0 .. 13 (default 13): for m = 2 and m = 3, the first
+ *                    rank's levels below gS <= group_bits (nodes of at most
+ *                    2^gS ranks) are formed, sorted and scanned per group of
+ *                    2^gS ranks in shared memory (a group too large for it,
+ *                    from heavy ties, sends its points' records of those
+ *                    levels through HBM); 0 sends every level's records
+ *                    through HBM;
  *   "top_bits"       0 .. 12 (default 12): for m = 2, the rank levels from
  *                    tS = max(gS, b0 - top_bits) up are formed, sorted and
  *                    scanned per tile of points in the order of the last

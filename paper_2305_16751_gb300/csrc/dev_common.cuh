@@ -54,9 +54,11 @@ struct Inst {
     u32 qrec_off, Tq;  // query records (partial slots) of this instance
     u32 key_bits;      // bits of the node key
     u32 flags;         // bit i (i < 3): coordinate i compared non-strictly; FLAG_VIRTUAL_LAST
-    // m = 2: rank levels below gS are aggregated per group of 2^gS ranks in
-    // shared memory (k_group); G groups.  gS = 0: every level goes through
-    // the records in HBM.
+    // m = 2, 3: rank levels below gS are aggregated per group of 2^gS ranks
+    // in shared memory (k_group, k_group3); G groups.  gS = 0: every level
+    // goes through the records in HBM.  A group with more points than shared
+    // memory holds (a heavy tie) sends its points' levels below gS through
+    // the records too (its flag in the groups' overflow array).
     u32 gS, G;
     // m = 2: rank levels tS .. b0-1 (at most TOP_MAX_BITS) are taken per tile
     // of points in the order of the last coordinate (k_top); topmask: those
@@ -76,6 +78,16 @@ constexpr u32 FLAG_VIRTUAL_LAST = 1u << 8;
 // Inst::flags: evaluate the levels of the first coordinate one by one on the
 // points (the level-wise formulation, m <= 2) instead of expanding records
 constexpr u32 FLAG_WAVELET = 1u << 9;
+
+// The first-rank levels whose records a point with (level) rank `rank` puts
+// through HBM in this call: the instance's (lvmask) and, if the point's
+// group overflowed shared memory (govf[pt_off + group], set by k_group_plan
+// for this call's groups), every level below gS as well.
+__device__ __forceinline__ u32 hbm_levels(const Inst& I, u32 rank, const unsigned char* __restrict__ govf) {
+    u32 m = I.lvmask;
+    if (I.gS && govf && govf[I.pt_off + (rank >> I.gS)]) m |= (1u << I.gS) - 1u;
+    return m;
+}
 
 // ---------------------------------------------------------------------
 // decoupled look-back status words: [63:34] epoch, [33:32] flag, [31:0] value

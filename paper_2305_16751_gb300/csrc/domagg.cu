@@ -21,6 +21,7 @@
 #include "k_points.cuh"
 #include "k_radix.cuh"
 #include "k_group.cuh"
+#include "k_group3.cuh"
 #include "k_records.cuh"
 #include "k_top.cuh"
 #include "k_wavelet.cuh"
@@ -407,8 +408,9 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     chunk_off[k] = (u32)NC;
     if (N >= (1ull << 31)) return fail(h, DOMAGG_ERR_UNSUPPORTED, "more than 2^31 points in one call");
     if (NQ == 0) return DOMAGG_OK;
-    // m = 2, the records path: the deep rank levels go through k_group
-    const bool use_groups = M == 2 && h->group_bits > 0 && !(inst[0].flags & FLAG_WAVELET);
+    // m = 2, 3, the records path: the deep rank levels go through k_group
+    // (m = 2) or k_group3 (m = 3)
+    const bool use_groups = (M == 2 || M == 3) && h->group_bits > 0 && !(inst[0].flags & FLAG_WAVELET);
     // m = 2: the top rank levels per range of whole tiles (k_top): about
     // TOP_RANGES_PER_SM ranges per SM over all points (a function of the
     // sizes alone: a planned run reuses the table its measuring run
@@ -477,9 +479,9 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             P[29 + (ch - 1) * 8 + 6] = c.take<u32>(used ? (size_t)sort_range_bound(pt_sizes) * RADIX : 0);
             P[29 + (ch - 1) * 8 + 7] = c.take<u32>(used ? (size_t)ntp : 0);             // rank tile counts
         }
-        // m = 2 groups: rank starts, the group sort's keys and values
+        // m = 2, 3 groups: rank starts, the group sort's keys and values
         // (ping-pong), per-instance group-id bits and group slots
-        const bool grp = M == 2 && use_groups;
+        const bool grp = use_groups;
         P[45] = c.take<u32>(grp ? N + k : 0);    // rank starts
         P[46] = c.take<u32>(grp ? N : 0);        // group keys
         P[47] = c.take<u32>(grp ? N : 0);
@@ -494,11 +496,16 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         P[53] = c.take<typename Op::Acc>(use_top ? (size_t)nranges * TOP_STRIDE : 0);
         P[54] = c.take<u32>(use_top ? k + 1 : 0);
         P[55] = c.take<u32>(use_top ? std::max<size_t>(multi.size(), 1) : 0);
-        // m = 2 groups: per query (by position in the order of the last
+        // groups: per query (by position in the order of the last
         // coordinate) F over the levels below gS
         P[56] = c.take<typename Op::Part>(grp ? N : 0);
+        // groups: this call's groups too large for shared memory (a flag per
+        // group, at the instance's point offset); per instance, every
+        // record of the flat map (a statistic)
+        P[57] = c.take<unsigned char>(grp ? N : 0);
+        P[58] = c.take<unsigned long long>(k);
     };
-    void* P[57];
+    void* P[59];
     {
         Carver c(nullptr);
         carve_points(c, P);
@@ -521,6 +528,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     u64* gval[2] = {(u64*)P[48], (u64*)P[49]};
     typename Op::Acc* topv = (typename Op::Acc*)P[52];
     typename Op::Part* gacc = (typename Op::Part*)P[56];
+    unsigned char* govf = use_groups ? (unsigned char*)P[57] : nullptr;
+    unsigned long long* rec_all = (unsigned long long*)P[58];
     typename Op::Acc* top_agg = (typename Op::Acc*)P[53];
     u32 *d_prange = (u32*)P[54], *d_multi = (u32*)P[55];
 
@@ -535,7 +544,8 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     // ---- upload the instance table and offsets
     const size_t up_bytes = sizeof(Inst) * k + 3 * sizeof(u32) * (k + 1) + (use_top ? sizeof(u32) * (2 * k + 2) : 0);
     const size_t lvl_pos = (up_bytes + 63) & ~(size_t)63;                          // level totals (read back)
-    const size_t ctl_pos = (lvl_pos + 2 * sizeof(u32) * k * LMAX + 63) & ~(size_t)63;  // control block (read back)
+    const size_t rec_pos = (lvl_pos + 2 * sizeof(u32) * k * LMAX + 63) & ~(size_t)63;  // records per instance (read back)
+    const size_t ctl_pos = (rec_pos + sizeof(unsigned long long) * k + 63) & ~(size_t)63;  // control block (read back)
     char* hp = nullptr;
     if (!planned) {
         domagg_status st = grow_pinned(h, ctl_pos + sizeof(Ctl) + 64);
@@ -675,7 +685,9 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
     // m = 2 the levels above the groups of ranks that k_group takes)
     L.start(KIND_SMALL, 0.0);
     k_group_plan<M><<<k, 1024, 0, stream>>>(d_inst, use_groups ? rstart : nullptr, use_groups ? gbits : nullptr,
-                                            GROUP_CAP, use_groups ? h->group_bits : 0, use_top ? h->top_bits : 0);
+                                            govf, M == 3 ? G3_CAP : GROUP_CAP, use_groups ? h->group_bits : 0,
+                                            use_top ? h->top_bits : 0);
+    cudaMemsetAsync(rec_all, 0, sizeof(unsigned long long) * k, stream);
     L.stop();
     // ---- count / offset scan of the flat map, per level
     {
@@ -684,7 +696,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
                                      (double)NC * 8 * LMAX);
         k_count_scan<M, W, WT><<<(unsigned)ntp, 256, 0, stream>>>(
             perm, d_pt_offs, d_pt_tiles, k, d_chunk_off, r0, r1, r2, d_inst, pr0, pr1, pr2, pj, (W*)P[18], chunk_base,
-            qchunk_base, (u32*)P[25], use_groups ? gkey[0] : nullptr, use_groups ? gval[0] : nullptr);
+            qchunk_base, (u32*)P[25], use_groups ? gkey[0] : nullptr, use_groups ? gval[0] : nullptr, govf, rec_all);
         L.stop();
         L.start(KIND_SMALL, 0.0);
         k_tile_exscan_counters<<<dim3((unsigned)k, CS_COUNTERS / 32), 1024, 0, stream>>>(
@@ -748,6 +760,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         cudaMemcpyAsync(h_inst, d_inst, sizeof(Inst) * k, cudaMemcpyDeviceToHost, stream);
         cudaMemcpyAsync(h_lvl, lvl_tot, sizeof(u32) * k * LMAX, cudaMemcpyDeviceToHost, stream);
         cudaMemcpyAsync(h_lvl + (size_t)k * LMAX, qlvl_tot, sizeof(u32) * k * LMAX, cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(hp + rec_pos, rec_all, sizeof(unsigned long long) * k, cudaMemcpyDeviceToHost, stream);
         cudaMemcpyAsync(h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, stream);
         L.stop();
         e = cudaStreamSynchronize(stream);
@@ -762,23 +775,21 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         // per instance: its levels, their record counts and sort-key bits
         lvl.assign(h_lvl, h_lvl + (size_t)k * LMAX);
         qlvl.assign(h_lvl + (size_t)k * LMAX, h_lvl + (size_t)2 * k * LMAX);
+        const unsigned long long* h_rec = (const unsigned long long*)(hp + rec_pos);
         for (int s = 0; s < k; ++s) {
             inst[s] = h_inst[s];
             nlev[s] = inst[s].nQ + inst[s].nD == 0 ? 0u : (M == 1 ? 1u : inst[s].b[0]);
+            // the counts hold the records this call puts through HBM: the
+            // levels of this shard that no group (k_group, k_group3: below
+            // gS, unless the point's group overflowed) or top-level tile
+            // (k_top: from tS up) takes in shared memory
             u64 T = 0, Tq = 0;
             for (u32 lv = 0; lv < nlev[s]; ++lv) {
-                T_flat += lvl[(size_t)s * LMAX + lv];
-                // levels below gS (k_group) and from tS up (k_top) are
-                // formed, sorted and scanned in shared memory, levels of
-                // other shards elsewhere: no records in HBM here
-                if (M == 2 && (lv < inst[s].gS || lv >= inst[s].tS)) T_shared += lvl[(size_t)s * LMAX + lv];
-                if (!((inst[s].lvmask >> lv) & 1u)) {
-                    lvl[(size_t)s * LMAX + lv] = 0;
-                    qlvl[(size_t)s * LMAX + lv] = 0;
-                }
                 T += lvl[(size_t)s * LMAX + lv];
                 Tq += qlvl[(size_t)s * LMAX + lv];
             }
+            T_flat += h_rec[s];
+            T_shared += h_rec[s] - std::min<u64>(h_rec[s], T);
             if (T >= (1ull << 32)) return fail(h, DOMAGG_ERR_UNSUPPORTED, "more than 2^32 flat-map records");
             // the node key (and the role bit above it) must fit 64 bits
             if (M >= 4 && nlev[s] > 0 && inst[s].b[0] - 1u + inst[s].b[1] + inst[s].b[2] > 63u)
@@ -852,9 +863,9 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         k_fill_e<Op><<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(gacc, (u32)N);
         L.stop();
     }
-    // ---- m = 2: the deep rank levels by groups, in shared memory (k_group):
-    // a stable sort of the points (in the order of the last coordinate) by
-    // their group of ranks, then one CTA per group
+    // ---- m = 2, 3: the deep rank levels by groups, in shared memory
+    // (k_group, k_group3): a stable sort of the points (in the order of the
+    // last coordinate) by their group of ranks, then one CTA per group
     if (use_groups) {
         std::vector<u32> gb_host;
         int gbits_max = 0;
@@ -880,13 +891,26 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         k_group_slots<<<1, 1024, 0, stream>>>(d_inst, k, gslot);
         L.stop();
         typedef typename Op::Acc Acc;
-        constexpr size_t gsm = group_smem_bytes<Acc>();
-        if (!L.frozen) cudaFuncSetAttribute(k_group<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
         const int li = L.lookback_index();
-        L.start(KIND_GROUP, (double)N * 8.0 + (double)NQ * sizeof(Part));
-        k_group<Op><<<(unsigned)h->sms, GROUP_THREADS, gsm, stream>>>(d_inst, k, gslot, rstart, gval[0], gval[1],
-                                                                      (const W*)P[18], gacc, h->ctl, li);
-        L.stop();
+        if constexpr (M == 2) {
+            constexpr size_t gsm = group_smem_bytes<Acc>();
+            if (!L.frozen) cudaFuncSetAttribute(k_group<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+            L.start(KIND_GROUP, (double)N * 8.0 + (double)NQ * sizeof(Part));
+            k_group<Op><<<(unsigned)h->sms, GROUP_THREADS, gsm, stream>>>(d_inst, k, gslot, rstart, gval[0], gval[1],
+                                                                          (const W*)P[18], gacc, h->ctl, li);
+            L.stop();
+        } else {
+            // m = 3: the group-sorted rank and position, the second rank and
+            // (data) the weight gathered by position, a partial per query
+            constexpr size_t gsm = G3Smem<Acc>::TOTAL;
+            if (!L.frozen) cudaFuncSetAttribute(k_group3<Op, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
+            L.start(KIND_GROUP, (double)N * (8.0 + 4.0) + (double)(N - NQ) * (WT == 3 ? 0.0 : sizeof(W)) +
+                                    (double)NQ * sizeof(Part));
+            k_group3<Op, WT><<<(unsigned)h->sms, G3_THREADS, gsm, stream>>>(d_inst, k, gslot, rstart, gval[0],
+                                                                            gval[1], pr1, (const W*)P[18], gacc,
+                                                                            h->ctl, li);
+            L.stop();
+        }
     }
     // ---- m = 2: the top levels per range of tiles in the order of the last
     // coordinate (k_top), then the nodes' carries across the ranges
@@ -1062,7 +1086,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             k_expand<M, K, Pay, W, WT><<<grid, 256, 0, stream>>>(
                 d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pr2, pj, (const W*)P[18], chunk_base, qchunk_base,
                 d_pt_tiles, (const u32*)P[25], d_inst, d_sbase, d_qsbase, M >= 3 ? d_nmask : nullptr, (u32)C.T0,
-                keys[0], pays[0], (u32)C.T1, keys1[0], pays1[0]);
+                keys[0], pays[0], (u32)C.T1, keys1[0], pays1[0], govf);
             L.stop();
         }
         // records sort (6m+2): stable, each level by the bits of its prefix; one
@@ -1133,14 +1157,15 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             if (grid)
                 k_reduce_top<Op><<<grid, TOP_RED_THREADS, 0, stream>>>(
                     k, C.k0, d_prange, range_pts, d_chunk_off, d_pt_offs, pr0, pj, qchunk_base, d_pt_tiles,
-                    (const u32*)P[25], d_qsbase, d_inst, partial, (u32)C.Tq, gacc, topv, top_agg, (u32)nranges);
+                    (const u32*)P[25], d_qsbase, d_inst, partial, (u32)C.Tq, gacc, topv, top_agg, (u32)nranges,
+                    govf);
             L.stop();
         } else if (qe > qb) {
             const unsigned grid = (unsigned)std::min<u64>((nchunk + 7) / 8, (u64)h->sms * L.blocks_per_sm);
             L.start(KIND_REDUCE, (double)C.Tq * sizeof(Part) + (double)(qe - qb) * (8 + sizeof(typename Op::Out)));
             k_reduce<Op, M><<<grid, 256, 0, stream>>>(d_chunk_off, k, C.k0, C.k1, d_pt_offs, pr0, pr1, pr2, pj,
                                                       qchunk_base, d_pt_tiles, (const u32*)P[25], d_qsbase, d_inst,
-                                                      partial, (u32)C.Tq, gacc);
+                                                      partial, (u32)C.Tq, gacc, govf);
             L.stop();
         }
         Tq_all += C.Tq;

@@ -48,9 +48,12 @@ __host__ __device__ constexpr size_t group_smem_bytes() {
 }
 
 // Per instance (one block each): the largest gS <= min(GROUP_MAX_BITS, b0)
-// whose groups of 2^gS ranks hold at most `cap` points each, and the number
-// of groups G; gS = 0 (no level in groups) if even groups of 2 ranks are too
-// large, or if the instance takes another path.  With top_bits > 0, the
+// whose groups of 2^gS ranks that hold more than `cap` points each (too
+// many for shared memory: heavy ties) hold at most a quarter of the points,
+// and the number of groups G (m = 2: k_group; m = 3: k_group3); gS = 0 (no
+// level in groups) if no width qualifies, or if the instance takes another
+// path.  govf[pt_off + g] = 1 marks this shard's groups that overflow: their
+// points' levels below gS go through the records in HBM.  With top_bits > 0, the
 // levels from tS = max(gS, b0 - top_bits) up go to k_top, and the levels
 // [gS, tS) through the records in HBM (lvmask); both masks hold this
 // shard's levels only.
@@ -61,8 +64,9 @@ __host__ __device__ constexpr size_t group_smem_bytes() {
 // the bits of the group id (b0 - gS) the group sort sorts.
 template <int M>
 __global__ __launch_bounds__(1024) void k_group_plan(Inst* inst, const u32* __restrict__ rstart,
-                                                    u32* __restrict__ gbits, u32 cap, int max_bits, int top_bits) {
-    __shared__ u32 s_max[32];
+                                                    u32* __restrict__ gbits, unsigned char* __restrict__ govf,
+                                                    u32 cap, int max_bits, int top_bits) {
+    __shared__ u32 s_ovf[32];
     __shared__ u32 s_done;
     const int s = blockIdx.x;
     Inst& I = inst[s];
@@ -72,22 +76,24 @@ __global__ __launch_bounds__(1024) void k_group_plan(Inst* inst, const u32* __re
     const u32 Uu = ns ? U / 2u : U;
     const u32* rs = rstart + I.pt_off + (u32)s;
     u32 chosen = 0, G = 0;
-    const bool eligible = M == 2 && rstart && n > 0 && b0 > 0 && !(I.flags & (FLAG_WAVELET | FLAG_VIRTUAL_LAST));
+    const bool eligible = (M == 2 || M == 3) && rstart && n > 0 && b0 > 0 &&
+                          !(I.flags & (FLAG_WAVELET | FLAG_VIRTUAL_LAST));
     for (int S = eligible ? min(min(max_bits, GROUP_MAX_BITS), (int)b0) : 0; S >= 1; --S) {
         const u32 us = (u32)S - ns;  // undoubled ranks per group: 2^us
         const u32 g_n = (Uu + (1u << us) - 1u) >> us;
-        u32 mx = 0;
+        u32 ov = 0;  // points in groups too large for shared memory
         for (u32 g = threadIdx.x; g < g_n; g += blockDim.x) {
             const u32 lo = g << us, hi = min((g + 1u) << us, Uu);
-            mx = max(mx, __ldg(rs + hi) - __ldg(rs + lo));
+            const u32 c = __ldg(rs + hi) - __ldg(rs + lo);
+            if (c > cap) ov += c;
         }
-        for (int o = 16; o >= 1; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+        for (int o = 16; o >= 1; o >>= 1) ov += __shfl_xor_sync(0xffffffffu, ov, o);
+        if ((threadIdx.x & 31) == 0) s_ovf[threadIdx.x >> 5] = ov;
         __syncthreads();
         if (threadIdx.x == 0) {
-            u32 m = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, s_max[w]);
-            s_done = m <= cap ? 1u : 0u;
+            u32 t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_ovf[w];
+            s_done = t <= n / 4u ? 1u : 0u;
         }
         __syncthreads();
         const bool ok = s_done != 0u;
@@ -96,6 +102,13 @@ __global__ __launch_bounds__(1024) void k_group_plan(Inst* inst, const u32* __re
             chosen = (u32)S;
             G = g_n;
             break;
+        }
+    }
+    if (chosen && govf) {  // this shard's groups that overflow
+        const u32 us = chosen - ns, nsh = max(I.nshards, 1u);
+        for (u32 g = threadIdx.x; g < G; g += blockDim.x) {
+            const u32 lo = g << us, hi = min((g + 1u) << us, Uu);
+            govf[I.pt_off + g] = (__ldg(rs + hi) - __ldg(rs + lo) > cap && g % nsh == I.shard) ? 1u : 0u;
         }
     }
     if (threadIdx.x == 0) {
@@ -365,6 +378,20 @@ __device__ __forceinline__ void group_levels(u32 n, u32 nb, u32 scan_mask, typen
     }
 }
 
+// A group too large for shared memory: its queries' group part is the unit
+// (their levels below gS go through the records in HBM).
+template <class Op>
+__device__ __forceinline__ void group_unit_parts(const u64* __restrict__ gv, u32 n, const Inst& I,
+                                                 typename Op::Part* __restrict__ gacc) {
+    for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
+        const u64 v = gv[i];
+        if ((u32)(v >> 32) & QUERY_BIT) {
+            const u32 x = (u32)v;
+            if (domagg_check(x - I.pt_off < I.nD + I.nQ, SITE_GROUP_OUT)) gacc[x] = Op::to_part(Op::e());
+        }
+    }
+}
+
 // The deep levels of every group (see the file comment).  Persistent CTAs
 // (one per SM) take groups from a counter.  Inputs: the group-sorted points
 // gv (per instance in buffer gv0 or gv1, by the parity of the group sort's
@@ -406,9 +433,14 @@ __global__ __launch_bounds__(GROUP_THREADS, 1) void k_group(const Inst* __restri
         const u32 us = gS - ns, Uu = ns ? I.U[0] / 2u : I.U[0];
         const u32* rs = rstart + I.pt_off + (u32)s;
         const u32 a = __ldg(rs + (g << us)), e = __ldg(rs + min((g + 1u) << us, Uu));
-        const u32 n = min(e - a, GROUP_CAP);  // k_group_plan guarantees e - a <= GROUP_CAP
         const bool odd = ((I.b[0] - gS + RADIX_BITS - 1) / RADIX_BITS) & 1u;
         const u64* __restrict__ gv = (odd ? gv1 : gv0) + I.pt_off + a;
+        if (e - a > GROUP_CAP) {  // too large for shared memory: its levels go through HBM
+            group_unit_parts<Op>(gv, e - a, I, gacc);
+            __syncthreads();
+            continue;
+        }
+        const u32 n = e - a;
         const u32 lrmask = (1u << gS) - 1u;
         // the group's points in the order of the last coordinate: handles
         // (rank bits below gS | query bit | original index) and values

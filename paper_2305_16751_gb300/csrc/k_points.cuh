@@ -378,7 +378,10 @@ __device__ __forceinline__ u32 levels_of(const Inst& I) {
 // of 32 points the exclusive count of both kinds
 // at the chunk's first point, for every level; per instance both totals of
 // every level.  The partial slots of a level are thereby a dense range in
-// which each query's records keep the order of the last coordinate.
+// which each query's records keep the order of the last coordinate.  The
+// counters hold the records this call puts through HBM (hbm_levels: the
+// levels of the call's shard that no group or top-level tile takes);
+// rec_all[instance] (if given) adds up every record of the flat map.
 constexpr int CS_ROUNDS = 16;
 constexpr int CS_COUNTERS = 2 * LMAX;             // per tile: records and query records of every level
 constexpr u32 CS_CHUNKS = 8 * CS_ROUNDS;          // 32-point chunks per tile
@@ -390,10 +393,12 @@ __global__ __launch_bounds__(256) void k_count_scan(
     const u32* __restrict__ r2, Inst* inst, u32* __restrict__ pr0, u32* __restrict__ pr1, u32* __restrict__ pr2,
     u32* __restrict__ pj, W* __restrict__ pw,
     u32* __restrict__ chunk_base, u32* __restrict__ qchunk_base, u32* __restrict__ tile_cnt,
-    u32* __restrict__ gkey, u64* __restrict__ gval) {
+    u32* __restrict__ gkey, u64* __restrict__ gval, const unsigned char* __restrict__ govf,
+    unsigned long long* __restrict__ rec_all) {
     constexpr int WARPS = 8, C = 2 * LMAX, TILE = WARPS * CS_ROUNDS * 32;
     static_assert(TILE == 4096, "point tiles");
     __shared__ u32 s_w[WARPS][C];
+    __shared__ unsigned long long s_all[WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const u32 t = blockIdx.x;
     if (t >= __ldg(tile_off + nseg)) return;
@@ -409,6 +414,7 @@ __global__ __launch_bounds__(256) void k_count_scan(
     // per lane (= level): the counts of every chunk of the warp
     u32 rc[CS_ROUNDS], qc[CS_ROUNDS];
     u32 run_all = 0, run_q = 0;
+    unsigned long long recs = 0;  // every record of the lane's points
     // eight rounds at a time: their permutation loads, then their gathers of
     // the first rank, all in flight together
     constexpr int BATCH = 8;
@@ -443,6 +449,11 @@ __global__ __launch_bounds__(256) void k_count_scan(
         if (M >= 4) c1 *= (u32)__popc((q ? e2 : ~e2) & m2);
         if (M == 1) bits0 = 1u;
         if (!valid) bits0 = 0;
+        recs += (unsigned long long)__popc(bits0) * c1;
+        // the levels whose records this call puts through HBM
+        u32 hb = bits0;
+        if (M >= 2 && valid) hb &= hbm_levels(I, a, govf);
+        if (M == 1) hb &= I.lvmask;
         if (valid) {
             if (M >= 2) pr0[x] = q ? (a | QUERY_BIT) : a;
             if (M >= 3) pr1[x] = c;
@@ -458,12 +469,12 @@ __global__ __launch_bounds__(256) void k_count_scan(
                     pw[x] = (W)wbits;
                 }
             }
-            // m = 2 with groups: the group sort's key (the group: rank >> gS)
-            // and value (rank | query bit, then a query's position in this
-            // order, a datum's weight bits or, for 8-byte weights, its
-            // position in pw)
-            if (M == 2 && gkey && I.gS) {
-                const u32 pv = (q || WT == 1) ? x : wbits;
+            // m = 2, 3 with groups: the group sort's key (the group: rank >>
+            // gS) and value (rank | query bit, then a query's position in
+            // this order, a datum's weight bits or, for 8-byte weights and
+            // for m = 3, its position x)
+            if ((M == 2 || M == 3) && gkey && I.gS) {
+                const u32 pv = (q || WT == 1 || M == 3) ? x : wbits;
                 gkey[x] = a >> I.gS;
                 gval[x] = ((u64)(q ? (a | QUERY_BIT) : a) << 32) | (u64)pv;
             }
@@ -471,11 +482,11 @@ __global__ __launch_bounds__(256) void k_count_scan(
         u32 mine = 0, mine_q = 0;
         if (M <= 2) {
             // one record per level: lane lv counts the lanes with bit lv set
-            mine = (u32)__popc(warp_transpose32(bits0, (u32)lane));
-            mine_q = (u32)__popc(warp_transpose32(q ? bits0 : 0u, (u32)lane));
+            mine = (u32)__popc(warp_transpose32(hb, (u32)lane));
+            mine_q = (u32)__popc(warp_transpose32(q ? hb : 0u, (u32)lane));
         } else {
             for (u32 lv = 0; lv < nlev; ++lv) {
-                const u32 w = ((bits0 >> lv) & 1u) ? c1 : 0u;
+                const u32 w = ((hb >> lv) & 1u) ? c1 : 0u;
                 const u32 sa = __reduce_add_sync(0xffffffffu, w);
                 const u32 sq = __reduce_add_sync(0xffffffffu, q ? w : 0u);
                 if ((u32)lane == lv) {
@@ -491,7 +502,14 @@ __global__ __launch_bounds__(256) void k_count_scan(
     }
     s_w[warp][lane] = run_all;
     s_w[warp][LMAX + lane] = run_q;
+    for (int o = 16; o >= 1; o >>= 1) recs += __shfl_xor_sync(0xffffffffu, recs, o);
+    if (lane == 0) s_all[warp] = recs;
     __syncthreads();
+    if (threadIdx.x == 0 && rec_all) {
+        unsigned long long t = 0;
+        for (int w = 0; w < WARPS; ++w) t += s_all[w];
+        if (t) atomicAdd(rec_all + L.seg, t);
+    }
     if (threadIdx.x < C) {  // exclusive over the warps; the tile's totals
         const int c = threadIdx.x;
         u32 sum = 0;
@@ -582,7 +600,7 @@ __global__ __launch_bounds__(256) void k_expand(
     const Inst* __restrict__ inst, const u32* __restrict__ seg_base /*[k1-k0][LMAX]*/,
     const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/, const u32* __restrict__ narrow_mask /*[k1-k0] or null*/,
     u32 n_rec, K* __restrict__ kout, Pay* __restrict__ pout, u32 n_rec1, u32* __restrict__ kout1,
-    Pay* __restrict__ pout1) {
+    Pay* __restrict__ pout1, const unsigned char* __restrict__ govf) {
     const int lane = threadIdx.x & 31;
     const u32 lt = lanemask_lt();
     const u32 c_begin = __ldg(chunk_off + k0), c_end = __ldg(chunk_off + k1);
@@ -631,7 +649,7 @@ __global__ __launch_bounds__(256) void k_expand(
                 X.q = (X.a & QUERY_BIT) != 0u;
                 X.a &= ~QUERY_BIT;
                 X.bits0 = (X.q ? X.a : ~X.a) & low_mask(I.b[0]);
-                X.bits0 &= I.lvmask;  // the levels this call takes through HBM (not k_group's, this shard's)
+                X.bits0 &= hbm_levels(I, X.a, govf);  // the levels this call takes through HBM
             } else {
                 X.q = pj[X.p] - X.ps < nQ;
                 X.bits0 = 1u & I.lvmask;  // the single level, unless another shard takes it

@@ -719,7 +719,8 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
                                                 const u32* __restrict__ qseg_base /*[k1-k0][LMAX]*/,
                                                 const Inst* __restrict__ inst,
                                                 const typename Op::Part* __restrict__ partial, u32 n_partial,
-                                                const typename Op::Part* __restrict__ gacc) {
+                                                const typename Op::Part* __restrict__ gacc,
+                                                const unsigned char* __restrict__ govf) {
     typedef typename Op::Part Part;
     __shared__ u32 s_mask[8][LMAX];  // per warp: query lanes holding a record of level lv
     __shared__ u32 s_base[8][LMAX];  // per warp: first partial slot of level lv in this chunk
@@ -744,7 +745,7 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
             q = local < nQ;
             if (q) {
                 if (M >= 2) bits0 = pr0[p] & low_mask(I.b[0]);
-                if (M >= 2) bits0 &= I.lvmask;  // this call's levels (k_group wrote out[q] for the others)
+                if (M >= 2) bits0 &= hbm_levels(I, pr0[p] & ~QUERY_BIT, govf);  // (the group kernels took the others)
                 if (M >= 3) {
                     bits1 = pr1[p] & low_mask(I.b[1]);
                     c1 = (u32)__popc(bits1);
@@ -764,8 +765,8 @@ __global__ __launch_bounds__(256) void k_reduce(const u32* __restrict__ chunk_of
         s_mask[warp][lane] = warp_transpose32(bits0, (u32)lane);  // lanes of level `lane`
         __syncwarp();
         typename Op::Acc acc = Op::e();
-        // m = 2 with groups: F over the levels below gS, by position
-        if (M == 2 && q && I.gS) acc = Op::from_part(gacc[p]);
+        // m = 2, 3 with groups: F over the levels below gS, by position
+        if ((M == 2 || M == 3) && q && I.gS) acc = Op::from_part(gacc[p]);
         if (M <= 2) {
             // one partial per query and level, at the level's base plus the
             // query lanes of that level before this one; each lane walks only

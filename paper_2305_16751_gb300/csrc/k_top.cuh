@@ -248,7 +248,8 @@ __global__ __launch_bounds__(TOP_RED_THREADS) void k_reduce_top(int k, int k0, c
                                                     const typename Op::Part* __restrict__ partial, u32 n_partial,
                                                     const typename Op::Part* __restrict__ gacc,
                                                     const typename Op::Acc* __restrict__ topv,
-                                                    const typename Op::Acc* __restrict__ carry, u32 nrows) {
+                                                    const typename Op::Acc* __restrict__ carry, u32 nrows,
+                                                    const unsigned char* __restrict__ govf) {
     typedef typename Op::Acc Acc;
     __shared__ Acc s_carry[TOP_STRIDE];
     constexpr u32 WARPS = TOP_RED_THREADS / 32;
@@ -288,8 +289,8 @@ __global__ __launch_bounds__(TOP_RED_THREADS) void k_reduce_top(int k, int k0, c
         if (__ballot_sync(0xffffffffu, q) == 0u) continue;
         Acc acc = Op::e();
         if (q) acc = tmask ? topv[p] : (I.gS ? Op::from_part(gacc[p]) : Op::e());
-        if (I.lvmask) {  // levels whose records went through HBM: their partials
-            const u32 rec = bits0 & I.lvmask;
+        const u32 rec = q ? bits0 & hbm_levels(I, a, govf) : 0u;
+        if (__ballot_sync(0xffffffffu, rec != 0u)) {  // levels whose records went through HBM: their partials
             if ((u32)lane < b0)
                 s_base[warp][lane] =
                     __ldg(qseg_base + (u64)(s - k0) * LMAX + lane) + __ldg(qchunk_base + (u64)c * LMAX + lane) +

@@ -79,15 +79,17 @@ def test_plan_graph_replay_with_new_data(op, wt):
 
 def test_plan_capacity_exceeded_is_reported_and_recoverable():
     """Planned on data whose every first coordinate ties (no records for
-    m >= 2), then run on spread-out data: the run reports DOMAGG_ERR_OOM and
-    writes nothing out of bounds; back on tied data it is correct again."""
+    m >= 2), then run on spread-out data (50000 points: at m = 3 the three
+    first-rank levels above the groups need records in HBM): the run reports
+    DOMAGG_ERR_OOM and writes nothing out of bounds; back on tied data it is
+    correct again."""
     t = torch()
     rng = np.random.default_rng(903)
     host = []
     for m in (2, 3):
-        D = np.full((3000, m), 7, dtype=np.int32)
-        Q = np.full((2000, m), 9, dtype=np.int32)
-        w = rng.integers(-50, 50, size=3000).astype(np.int64)
+        D = np.full((30000, m), 7, dtype=np.int32)
+        Q = np.full((20000, m), 9, dtype=np.int32)
+        w = rng.integers(-50, 50, size=30000).astype(np.int64)
         host.append((D, Q, w))
     dev = [(to_dev(D), to_dev(Q), to_dev(w)) for D, Q, w in host]
     plan = domagg.BatchPlan(dev, "sum", headroom=0.0)

@@ -65,10 +65,15 @@ def test_noalloc_rejects_inputs_beyond_its_scratch():
 
 def test_noalloc_refuses_an_oversized_flat_map_then_works():
     """Under the point limit but with a flat map too large for the scratch
-    (m = 3, 30000 points per side): refused after the point phase, with
-    `out` untouched; the next call on the same scratch is still correct."""
+    (m = 3, 30000 points per side, a third of them on one first coordinate:
+    the group holding them is too large for shared memory at every width,
+    so no level is taken in groups and all 16 levels' records would go
+    through the scratch): refused after the point phase, with `out`
+    untouched; the next call on the same scratch is still correct."""
     rng = np.random.default_rng(32)
     D, Q, w = workloads.random_small(rng, 3, 30000, 30000, 1 << 20, "i32", "i64")
+    D[:10000, 0] = 5
+    Q[:10000, 0] = 5
     Dd, Qd, wd = to_dev(D), to_dev(Q), to_dev(w)
     t = torch()
     sentinel = t.full((Q.shape[0],), 12345, dtype=t.int64, device=Dd.device)
@@ -84,3 +89,17 @@ def test_noalloc_refuses_an_oversized_flat_map_then_works():
     st, out = _noalloc(D2d, Q2d, w2d, op)
     assert st == 0
     assert np.array_equal(out.cpu().numpy(), domagg.forward(D2d, Q2d, w2d, op).cpu().numpy())
+
+
+def test_noalloc_m3_groups_fit_the_scratch():
+    """m = 3 with 30000 spread points per side: the first-rank levels below
+    the groups are formed in shared memory, the three above go through the
+    scratch; two calls in a row equal domagg_forward."""
+    rng = np.random.default_rng(33)
+    D, Q, w = workloads.random_small(rng, 3, 30000, 30000, 1 << 20, "i32", "i64")
+    Dd, Qd, wd = to_dev(D), to_dev(Q), to_dev(w)
+    ref = domagg.forward(Dd, Qd, wd, "sum").cpu().numpy()
+    for _ in range(2):
+        st, out = _noalloc(Dd, Qd, wd, "sum")
+        assert st == 0, domagg.STATUS.get(st)
+        assert np.array_equal(out.cpu().numpy(), ref)
