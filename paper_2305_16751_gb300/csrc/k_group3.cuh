@@ -272,15 +272,23 @@ __device__ __noinline__ void g3_walk(u32 n, u32 lv, u32 rmask, u32 qsh, bool spl
     }
 }
 
+// Points per thread of a walk over n points: G3_IT_SMALL up to
+// G3_IT_SMALL x 1024 points (fewer warps then hold them), else G3_ITEMS.
+#ifndef DOMAGG_G3_IT_SMALL
+#define DOMAGG_G3_IT_SMALL 5
+#endif
+constexpr u32 G3_IT_SMALL = DOMAGG_G3_IT_SMALL;
+__device__ __forceinline__ u32 g3_items(u32 n) { return n <= G3_IT_SMALL * G3_THREADS ? G3_IT_SMALL : (u32)G3_ITEMS; }
+
 template <class Op, bool SCAN, bool BMAP>
 __device__ __forceinline__ void g3_walk_any(u32 n, u32 lv, u32 rmask, u32 qsh, bool split, typename Op::Acc* val,
                                             u32* xh, unsigned short* hz, const u32* bmap, u32* s_pk,
                                             typename Op::Acc* s_acc) {
-    if (n <= 5u * G3_THREADS) g3_walk<Op, 5, SCAN, BMAP>(n, lv, rmask, qsh, split, val, xh, hz, bmap, s_pk, s_acc);
-    else g3_walk<Op, 10, SCAN, BMAP>(n, lv, rmask, qsh, split, val, xh, hz, bmap, s_pk, s_acc);
+    if (n <= G3_IT_SMALL * G3_THREADS)
+        g3_walk<Op, G3_IT_SMALL, SCAN, BMAP>(n, lv, rmask, qsh, split, val, xh, hz, bmap, s_pk, s_acc);
+    else
+        g3_walk<Op, G3_ITEMS, SCAN, BMAP>(n, lv, rmask, qsh, split, val, xh, hz, bmap, s_pk, s_acc);
 }
-
-__device__ __forceinline__ u32 g3_items(u32 n) { return n <= 5u * G3_THREADS ? 5u : 10u; }
 
 // The points level lv emits (data with rank bit lv = 0, queries with 1), in
 // the outer order (n points, padded to a multiple of IT): their inner
@@ -473,12 +481,12 @@ __global__ __launch_bounds__(G3_THREADS, 1) void k_group3(const Inst* __restrict
             __syncthreads();
             continue;
         }
-        const u32 rmax = n <= 5u * T ? g3_rerank<5>(n, npad, b1, ixh, hz, r1l, s_tmp)
-                                     : g3_rerank<10>(n, npad, b1, ixh, hz, r1l, s_tmp);
+        const u32 rmax = n <= G3_IT_SMALL * T ? g3_rerank<G3_IT_SMALL>(n, npad, b1, ixh, hz, r1l, s_tmp)
+                                              : g3_rerank<G3_ITEMS>(n, npad, b1, ixh, hz, r1l, s_tmp);
         const u32 nb1 = rmax ? 32u - (u32)__clz(rmax) : 0u;  // levels of the local second rank
         for (int lv = (int)gS - 1; lv >= 0; --lv) {
-            const u32 m = n <= 5u * T ? g3_compact<5>(npad, (u32)lv, gS, oxh, ixh, r1l, bmap, s_tmp)
-                                      : g3_compact<10>(npad, (u32)lv, gS, oxh, ixh, r1l, bmap, s_tmp);
+            const u32 m = n <= G3_IT_SMALL * T ? g3_compact<G3_IT_SMALL>(npad, (u32)lv, gS, oxh, ixh, r1l, bmap, s_tmp)
+                                               : g3_compact<G3_ITEMS>(npad, (u32)lv, gS, oxh, ixh, r1l, bmap, s_tmp);
             if (m > 0 && nb1 > 0) {
                 const u32 mpad = (m + g3_items(m) - 1u) / g3_items(m) * g3_items(m);
                 for (u32 x = m + (u32)tid; x < mpad; x += T) ixh[pidx(x)] = G3_LMASK;  // inert
