@@ -16,8 +16,11 @@ level lv's emitting points are compacted in that order into blocks (runs of
 one r0 >> (lv+1)), and the second rank's levels are walked over them with
 the points' dense ranks among the group's second ranks: per level j a
 segmented scan over the nodes (block, local rank >> (j+1)), then a stable
-split by bit j.  A group with more than `cap` points (heavy ties) sends its
-points' records of those levels through the HBM path instead.
+split by bit j.  At a level whose blocks hold at most `pair_max` points,
+each query the level emits takes F directly over the earlier data of its
+block (in that order) with a smaller second rank instead.  A group with
+more than `cap` points (heavy ties) sends its points' records of those
+levels through the HBM path instead.
 
 The sum over all levels equals the definition (brute force) on random
 inputs with heavy ties, for every gS and capacity, and for non-strict
@@ -65,7 +68,7 @@ def _split(order, node_of, bit_of):
     return new
 
 
-def _pipeline(D, Q, w, gS, cap, ns0=False, ns1=False):
+def _pipeline(D, Q, w, gS, cap, ns0=False, ns1=False, pair_max=0):
     nD = D.shape[0]
     P = np.concatenate([D, Q])
     n = P.shape[0]
@@ -113,6 +116,20 @@ def _pipeline(D, Q, w, gS, cap, ns0=False, ns1=False):
         order = list(pts)  # the order of level gS-1: the last coordinate
         for lv in range(gS - 1, -1, -1):
             blk = {i: r0[i] >> (lv + 1) for i in order}
+            sizes = {}
+            for i in order:
+                sizes[blk[i]] = sizes.get(blk[i], 0) + 1
+            if max(sizes.values()) <= pair_max:
+                for p, i in enumerate(order):  # by pairs, within the block
+                    if isq[i] and (r0[i] >> lv) & 1:
+                        for k in range(p - 1, -1, -1):
+                            d = order[k]
+                            if blk[d] != blk[i]:
+                                break
+                            if not isq[d] and not (r0[d] >> lv) & 1 and loc[d] < loc[i]:
+                                out[i] += wf[d]
+                order = _split(order, lambda i, lv=lv: r0[i] >> (lv + 1), lambda i, lv=lv: (r0[i] >> lv) & 1)
+                continue
             inner = [i for i in order if ((r0[i] >> lv) & 1) == int(isq[i])]
             for j in range(nb1 - 1, -1, -1):
                 node = lambda i, j=j: (blk[i], loc[i] >> (j + 1))
@@ -141,9 +158,9 @@ def test_group3_levels_equal_definition(ns0, ns1):
         w = rng.integers(-9, 10, size=nD).astype(np.int64)
         want = _brute(D, Q, w, ns0, ns1)
         for gS in range(0, 7):
-            for cap in (1000, 8):
-                got = _pipeline(D, Q, w, gS, cap, ns0, ns1)
-                assert np.array_equal(got, want), (gS, cap, nD, nQ, levels)
+            for cap, pair_max in ((1000, 0), (8, 0), (1000, 6), (1000, 1000)):
+                got = _pipeline(D, Q, w, gS, cap, ns0, ns1, pair_max)
+                assert np.array_equal(got, want), (gS, cap, pair_max, nD, nQ, levels)
 
 
 def test_group3_hand_case():
