@@ -363,11 +363,14 @@ def bench_m3(args, dev, stream, torch, domagg, workloads):
     domagg.forward(D3, Q3, w3, "sum", out=o3)
     k3 = domagg.domagg_timing_read(h)
     domagg.domagg_timing_enable(h, False)
+    roof = kind_roofline(k3, "sort_records", peak, peak_src,
+                         "k_onesweep (records radix pass, 64-bit and 32-bit key classes)")
+    if args.n3 == 2**21:  # the profile's workload: its DRAM bytes per algorithmic byte
+        roof["traffic"] = profiled_traffic(roof["bytes_per_launch"], "k_radix.cuh", "k_onesweep_records_m3_n2e21.md")
     return {"value": p3.Q.shape[0] / (m3_ms / 1e3), "unit": "queries/s", "ms_per_step": m3_ms,
             "workload": f"m3_nD{_pow2(args.n3)}_nQ{_pow2(args.n3)}_gmm_i32coords_i64w_sum", "records": st3["n_records"],
             "record_passes": st3["record_passes"], "phase_ms": {k: v["ms"] for k, v in k3.items()},
-            "roofline": kind_roofline(k3, "sort_records", peak, peak_src,
-                                      "k_onesweep (records radix pass, 64-bit and 32-bit key classes)"),
+            "roofline": roof,
             "step_model": step_model(2 * args.n3, st3["n_records"], args.n3, m3_ms, peak, m=3)}
 
 
