@@ -176,7 +176,10 @@ domagg_status domagg_combine(domagg_handle h, domagg_op op, domagg_dtype weight_
 
 /* Same as domagg_forward with HOST buffers (pageable or pinned): copies the
  * inputs to the handle's device staging area, runs the forward on `stream`,
- * copies `out` back and synchronises before returning. */
+ * copies `out` back and synchronises before returning.  The weights are
+ * copied on a stream of the handle beside the point phase (nothing reads
+ * them before the count scan); the call reads the host buffers only until
+ * it returns. */
 domagg_status domagg_forward_host(domagg_handle h, int m, const void* d_coords, int64_t nD,
                                   const void* q_coords, int64_t nQ, domagg_dtype coord_dtype,
                                   const void* d_weights, domagg_dtype weight_dtype, domagg_op op,

@@ -84,6 +84,12 @@ struct domagg_ctx {
     bool overlap = false;
     cudaStream_t aux[2] = {nullptr, nullptr};
     cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+    // domagg_forward_host: the weights' copy runs on its own stream beside
+    // the point phase (nothing reads them before the count scan); the
+    // pipeline's stream waits for ev_w there while w_pending
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_w = nullptr;
+    bool w_pending = false;
     int ranges_per_cta = 4, blocks_per_sm = 16;  // launch shapes (domagg_plan_autotune)
     // m = 2: the rank levels below gS <= group_bits are aggregated per group
     // in shared memory (k_group); 0 = every level through the records in HBM
@@ -677,6 +683,10 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         perm = last_dim(chain(0));
     }
     L.stream = stream;
+    if (h->w_pending) {  // the weights' host copy (domagg_forward_host), first read below
+        cudaStreamWaitEvent(stream, h->ev_w, 0);
+        h->w_pending = false;
+    }
     if (inst[0].flags & FLAG_WAVELET) {
         if constexpr (M <= 2) return run_wavelet<M, Op>(h, inst, d_inst, perm, r0, N, L, stream, hp, ctl_pos);
         else return fail(h, DOMAGG_ERR_UNSUPPORTED, "the level-wise formulation takes m <= 2");
@@ -1351,6 +1361,11 @@ domagg_status domagg_create(domagg_handle* out, int device, size_t max_workspace
                  cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
                  cudaEventCreateWithFlags(&h->ev_join[0], cudaEventDisableTiming) == cudaSuccess &&
                  cudaEventCreateWithFlags(&h->ev_join[1], cudaEventDisableTiming) == cudaSuccess;
+    if (cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_w, cudaEventDisableTiming) != cudaSuccess) {
+        h->copy_stream = nullptr;  // the weights then go on the call's stream
+        h->ev_w = nullptr;
+    }
     cudaGetLastError();
     if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&h->ctl, sizeof(Ctl)) != cudaSuccess) {
         cudaGetLastError();
@@ -1374,8 +1389,9 @@ domagg_status domagg_destroy(domagg_handle h) {
     for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
     for (cudaStream_t s : h->aux)
         if (s) cudaStreamDestroy(s);
-    for (cudaEvent_t e : {h->ev_fork, h->ev_join[0], h->ev_join[1]})
+    for (cudaEvent_t e : {h->ev_fork, h->ev_join[0], h->ev_join[1], h->ev_w})
         if (e) cudaEventDestroy(e);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     delete h;
     return DOMAGG_OK;
 }
@@ -1538,11 +1554,27 @@ domagg_status domagg_forward_host(domagg_handle h, int m, const void* d_coords, 
     L.start(KIND_H2D, (double)(bd + bq + bw));
     if (bd) cudaMemcpyAsync(dd, d_coords, bd, cudaMemcpyHostToDevice, s);
     if (bq) cudaMemcpyAsync(dq, q_coords, bq, cudaMemcpyHostToDevice, s);
-    if (bw) cudaMemcpyAsync(dw, d_weights, bw, cudaMemcpyHostToDevice, s);
+    // the weights beside the point phase: the pipeline waits for them before
+    // the count scan, their first reader (the staging buffer is idle: the
+    // previous call synchronised)
+    if (bw && h->copy_stream) {
+        cudaMemcpyAsync(dw, d_weights, bw, cudaMemcpyHostToDevice, h->copy_stream);
+        cudaEventRecord(h->ev_w, h->copy_stream);
+        h->w_pending = true;
+    } else if (bw) {
+        cudaMemcpyAsync(dw, d_weights, bw, cudaMemcpyHostToDevice, s);
+    }
     L.stop();
     std::vector<Inst> inst{make_inst(dd, nD, dq, nQ, bw ? dw : nullptr, dout)};
     st = dispatch(h, m, inst, coord_dtype, weight_dtype, op, false, s);
-    if (st) return st;
+    if (h->w_pending) {  // a path that read no weights (or failed before): join the copy anyway
+        cudaStreamWaitEvent(s, h->ev_w, 0);
+        h->w_pending = false;
+    }
+    if (st) {
+        cudaStreamSynchronize(h->copy_stream ? h->copy_stream : s);  // the copy reads the caller's buffer
+        return st;
+    }
     L.start(KIND_D2H, (double)bo);
     cudaMemcpyAsync(out, dout, bo, cudaMemcpyDeviceToHost, s);
     L.stop();
