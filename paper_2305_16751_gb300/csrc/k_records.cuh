@@ -41,7 +41,10 @@ __global__ __launch_bounds__(1024) void k_layout(const Inst* __restrict__ inst, 
         const Inst& I = inst[k0 + (int)srel];
         const u32 nlev = M == 1 ? 1u : I.b[0];
         na = nq = bits = 0;
-        if (lv < nlev && ((I.lvmask >> lv) & 1u)) {  // other levels: k_group's or another shard's
+        // the counts hold only the records this call puts through HBM
+        // (hbm_levels: this shard's levels outside the groups and the
+        // top-level tiles, and an overflowing group's levels below gS)
+        if (lv < nlev) {
             na = __ldg(lvl_tot + (u64)(k0 + (int)srel) * LMAX + lv);
             nq = __ldg(qlvl_tot + (u64)(k0 + (int)srel) * LMAX + lv);
             if (M >= 2) bits = I.b[0] - 1u - lv + (M >= 3 ? I.b[1] : 0u) + (M >= 4 ? I.b[2] : 0u);

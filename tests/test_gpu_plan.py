@@ -209,3 +209,28 @@ def test_plan_with_both_key_classes_and_m4():
             assert_matches_oracle(o.cpu().numpy(), D, Q, w, "sum", qidx=qi)
     finally:
         plan.close()
+
+
+def test_plan_with_overflowing_groups():
+    """Instances whose first coordinate piles 11000 points on one value: the
+    group holding them overflows shared memory, so only those points' deep
+    levels go through the planned record workspace (m = 2 and m = 3, beside
+    instances without such a tie); the planned run equals the oracle."""
+    rng = np.random.default_rng(904)
+    host = []
+    for m in (2, 3, 2, 3):
+        D, Q, w = workloads.random_small(rng, m, 40000, 31000, 1 << 20, "i32", "i64")
+        if len(host) < 2:
+            D[:6000, 0] = 0
+            Q[:5000, 0] = 0
+        host.append((D, Q, w))
+    dev = [(to_dev(D), to_dev(Q), to_dev(w)) for D, Q, w in host]
+    plan = domagg.BatchPlan(dev, "sum", headroom=0.1)
+    try:
+        for _ in range(2):
+            plan.run()
+            plan.status()
+            for (D, Q, w), o in zip(host, plan.outs):
+                assert_matches_oracle(o.cpu().numpy(), D, Q, w, "sum")
+    finally:
+        plan.close()
