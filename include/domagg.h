@@ -237,7 +237,8 @@ domagg_status domagg_batch(domagg_handle h, int k, const domagg_instance* inst,
  * each time) and returns when both runs have finished: the first run
  * measures every instance's record counts; the plan then reserves, in a
  * private workspace on `device`, room for (1 + headroom) times those counts
- * (plus 1024) per record chunk, and the second, planned run allocates that
+ * (plus 1024) per record chunk and key class (m >= 3: node keys of up to 31
+ * bits, and wider ones), and the second, planned run allocates that
  * workspace for good.  headroom >= 0.  The descriptors in `inst` are copied;
  * the buffers they point to must outlive the plan.
  *
@@ -245,7 +246,7 @@ domagg_status domagg_batch(domagg_handle h, int k, const domagg_instance* inst,
  * -- no synchronisation, no allocation, no host<->device copy -- so it can be
  * captured into a CUDA graph and replayed.  The record layout is computed on
  * the device from the current record counts.  If a run meets more records
- * (or query records) in a chunk than the plan reserved, the kernels of that
+ * of a key class (or query records) in a chunk than the plan reserved, the kernels of that
  * chunk write nothing outside the workspace, its outputs are undefined, and
  * DOMAGG_ERR_OOM is recorded for domagg_plan_status.  Device errors of a run
  * (NaN coordinates, a bounded wait that ran out, capacity) are only reported

@@ -90,6 +90,8 @@ struct domagg_ctx {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_w = nullptr;
     bool w_pending = false;
+    // the last unplanned run's records through HBM per (instance, level)
+    std::vector<u32> meas_lvl;
     int ranges_per_cta = 4, blocks_per_sm = 16;  // launch shapes (domagg_plan_autotune)
     // m = 2: the rank levels below gS <= group_bits are aggregated per group
     // in shared memory (k_group); 0 = every level through the records in HBM
@@ -254,7 +256,8 @@ void maybe_reset_epochs(domagg_ctx* h, cudaStream_t s) {
 // host, so a planned run never reads a count back.
 struct PlannedChunk {
     int k0 = 0, k1 = 0;
-    u64 T_cap = 0, Tq_cap = 0;  // reserved records (per key class) and query records (>= 1)
+    u64 T_cap = 0, Tq_cap = 0;  // reserved records of class 0 and query records (>= 1)
+    u64 T1_cap = 0;             // reserved records of class 1 (m >= 3)
     int nslot = 0;              // segment slots: every instance's largest possible level count
     int nslot0 = 0;             // slots of class 0 (listed first); the rest are class 1 (32-bit keys, m >= 3)
     int key_bits = 0, key_bits1 = 0;  // bounds on the node-key bits of the two classes
@@ -748,13 +751,13 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             Chunk c;
             c.k0 = pc.k0;
             c.k1 = pc.k1;
-            c.T = pc.T_cap;
+            c.T1 = pc.nslot > pc.nslot0 ? pc.T1_cap : 0;
+            c.T = pc.T_cap + c.T1;
             c.Tq = pc.Tq_cap;
             c.nseg = (u64)pc.nslot;
             c.nseg0 = (u64)pc.nslot0;
             c.nseg1 = (u64)(pc.nslot - pc.nslot0);
             c.T0 = pc.T_cap;
-            c.T1 = pc.nslot > pc.nslot0 ? pc.T_cap : 0;
             c.key_bits = pc.key_bits;
             c.key_bits1 = pc.key_bits1;
             c.slot_map = pc.d_slot_map;
@@ -807,6 +810,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
             inst[s].T = (u32)T;
             inst[s].Tq = (u32)Tq;
         }
+        h->meas_lvl = lvl;  // (a plan splits its capacities by key class from these)
 
         // chunks of instances whose records fit one record workspace: below
         // 2^32 records and ~60% of the free memory (plus the record workspace
@@ -1079,7 +1083,7 @@ domagg_status run(domagg_ctx* h, std::vector<Inst>& inst, bool negate, cudaStrea
         if (planned) {
             L.start(KIND_SMALL, 0.0);
             k_layout<M><<<1, 1024, 0, stream>>>(d_inst, C.k0, lvl_tot, qlvl_tot, C.slot_map, (int)nseg, (int)nseg0,
-                                                C.T0, C.Tq, d_so, d_sbits, d_sbase, d_qsbase, h->ctl);
+                                                C.T0, C.T1, C.Tq, d_so, d_sbits, d_sbase, d_qsbase, h->ctl);
             L.stop();
         }
         L.start(KIND_SMALL, 0.0);
@@ -1756,6 +1760,7 @@ domagg_status plan_group(domagg_plan p, int m, const std::vector<Inst>& part, do
     std::vector<u32> map0, map1, mask;
     auto close = [&]() {
         c.T_cap += 1024;  // never 0: the chunk's launches are the same whatever the data
+        c.T1_cap += 1024;
         c.Tq_cap += 1024;
         c.nslot0 = (int)map0.size();
         c.nslot = (int)(map0.size() + map1.size());
@@ -1767,16 +1772,30 @@ domagg_status plan_group(domagg_plan p, int m, const std::vector<Inst>& part, do
         map1.clear();
         mask.clear();
     };
+    // the measured records of every instance split by the key class the
+    // plan gives their level (from the level-count bound, as the slots below)
+    const std::vector<u32>& ml = G.ctx->meas_lvl;
+    auto class1_records = [&](int i) -> u64 {
+        if (m < 3 || ml.size() < (size_t)k * LMAX) return 0;
+        const u32 nb = level_bound(m, (u64)part[i].nD + part[i].nQ);
+        u64 t = 0;
+        for (u32 lv = 0; lv < nb && lv < (u32)LMAX; ++lv)
+            if ((int)(nb - 1 - lv) + (int)nb * (m - 2) <= 31) t += ml[(size_t)i * LMAX + lv];
+        return std::min<u64>(t, measured[i].T);
+    };
     for (int i = 0; i < k; ++i) {
-        const u64 Ti = scaled(measured[i].T), Tqi = scaled(measured[i].Tq);
-        if (Ti + 1024 > cap_limit) return plan_fail(p, DOMAGG_ERR_UNSUPPORTED, "one instance exceeds a record chunk");
-        if (c.k1 > c.k0 && c.T_cap + Ti + 1024 > cap_limit) {
+        const u64 T1m = class1_records(i);
+        const u64 Ti0 = scaled((u32)(measured[i].T - T1m)), Ti1 = scaled((u32)T1m), Tqi = scaled(measured[i].Tq);
+        const u64 Ti = Ti0 + Ti1;
+        if (Ti + 2048 > cap_limit) return plan_fail(p, DOMAGG_ERR_UNSUPPORTED, "one instance exceeds a record chunk");
+        if (c.k1 > c.k0 && c.T_cap + c.T1_cap + Ti + 2048 > cap_limit) {
             close();
             c = PlannedChunk();
             c.k0 = c.k1 = i;
         }
         c.k1 = i + 1;
-        c.T_cap += Ti;
+        c.T_cap += Ti0;
+        c.T1_cap += Ti1;
         c.Tq_cap += Tqi;
         const u32 nb = level_bound(m, (u64)part[i].nD + part[i].nQ);
         u32 msk = 0;

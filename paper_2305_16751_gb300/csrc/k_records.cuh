@@ -16,7 +16,8 @@ namespace domagg {
 // every instance reserving as many slots as its rank digits can be at most;
 // slots beyond an instance's actual levels are empty.  Writes the segment
 // offsets and key bits and the per-(instance, level) record and query-slot
-// bases.  If the records exceed the reserved capacity, every segment is made
+// bases.  If the records exceed a class's reserved capacity (T_cap for class
+// 0, T1_cap for class 1) or the query slots Tq_cap, every segment is made
 // empty and ERR_CAPACITY is raised: the kernels after it then write nothing
 // outside their buffers (the chunk's outputs are undefined).
 //
@@ -28,7 +29,7 @@ template <int M>
 __global__ __launch_bounds__(1024) void k_layout(const Inst* __restrict__ inst, int k0,
                                                  const u32* __restrict__ lvl_tot, const u32* __restrict__ qlvl_tot,
                                                  const u32* __restrict__ slot_map, int nslot, int nslot0, u64 T_cap,
-                                                 u64 Tq_cap, u32* __restrict__ so, u32* __restrict__ sbits,
+                                                 u64 T1_cap, u64 Tq_cap, u32* __restrict__ so, u32* __restrict__ sbits,
                                                  u32* __restrict__ sbase, u32* __restrict__ qsbase, Ctl* ctl) {
     __shared__ u64 w_a[32], w_q[32];
     __shared__ u64 carry_a, carry_q;
@@ -78,7 +79,7 @@ __global__ __launch_bounds__(1024) void k_layout(const Inst* __restrict__ inst, 
             B += w_b[w];
             Q += w_q[w];
         }
-        s_over = (A > T_cap || B > T_cap || Q > Tq_cap) ? 1 : 0;
+        s_over = (A > T_cap || B > T1_cap || Q > Tq_cap) ? 1 : 0;
         if (s_over) atomicOr(&ctl->error, ERR_CAPACITY);
         carry_a = carry_q = 0;
     }
