@@ -29,11 +29,16 @@
 //      or a block starts -- then a stable split by bit j.
 // Only comparisons of second ranks inside the group matter, so the walk
 // uses each point's dense rank among the group's second ranks (below 2^14:
-// fewer levels than the global rank, and 32-bit handles).  A query keeps F
-// over all its partial results of these levels and writes it, as one
-// partial, at its position in the order of the last coordinate; the levels
-// lv >= gS go through the records in HBM, and the per-query reduction joins
-// the parts.
+// fewer levels than the global rank, and 32-bit handles).  From the first
+// level whose blocks all hold at most G3_PAIR_MAX points down, step 3 is
+// replaced by its definition (g3_pairwise): each emitting query takes F over
+// the block's earlier emitting data of smaller local second rank.  A query
+// keeps F over all its partial results of these levels and writes it, as
+// one partial, at its position in the order of the last coordinate; the
+// levels lv >= gS go through the records in HBM, and the per-query
+// reduction joins the parts.  A group with more points than G3_CAP (heavy
+// ties) is not taken here: its queries' part is the unit and its points'
+// levels below gS go through HBM too (k_group_plan flags it).
 #pragma once
 #include "k_group.cuh"
 
